@@ -1,0 +1,182 @@
+"""Seeded synthetic inputs shaped like the workloads of CHERT (Darwis et al.).
+
+This module only *describes* media, grids, stencils and sources.  It holds none
+of the method's arithmetic: no Thomsen-to-moduli conversion, no Christoffel
+solve, no lookup and no relaxation.  Both the CUDA path (through the
+``chert`` binding) and the FP64 oracle under ``oracle/`` take what these
+generators return as plain arrays.
+
+Random numbers come from NumPy's PCG64 (``numpy.random.default_rng``) with the
+fixed seeds below, so every call returns the same model.
+
+Workloads (the recipes are restated with their citations in the design notes):
+
+* ``homogeneous_vti``  -- 2D homogeneous viscoelastic VTI, one class
+  (Vp0=3000 m/s, Vs0=1500 m/s, rho=2200, eps=0.2, delta=0.1, gamma=0.1,
+  Qp=60, Qs=30), 101x101 nodes at dx=10 m, one centre source.
+* ``layered_tti``      -- 2D layered viscoelastic TTI, 401x401 nodes at
+  dx=10 m, 8 flat layers of seeded Thomsen parameters and tilts, 64 surface
+  sources.
+* ``table2_layers``    -- the four visco-VTI layers that the paper prints in its
+  Table 2 (moduli in (km/s)^2 and per-component quality factors).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "ThomsenLayer", "TableLayer", "Model2D",
+    "homogeneous_vti", "layered_tti", "table2_layers",
+    "layered_class_map_2d", "stencil_2d", "stencil_3d", "surface_sources_2d",
+    "SEEDS",
+]
+
+# One seed per workload (PCG64).
+SEEDS = {"homogeneous_vti": 1001, "layered_tti": 1002}
+
+
+@dataclass(frozen=True)
+class ThomsenLayer:
+    """Thomsen-style description of one cache class (SI units, tilt in rad)."""
+    vp0: float
+    vs0: float
+    eps: float
+    delta: float
+    gamma: float
+    qp: float
+    qs: float
+    rho: float = 2200.0
+    tilt: float = 0.0
+    azim: float = 0.0
+
+
+@dataclass(frozen=True)
+class TableLayer:
+    """Density-normalised real moduli a11,a13,a33,a44,a66 in (m/s)^2 and the
+    per-component quality factors q11,q13,q33,q44,q66 (Table 2 form)."""
+    aR: tuple
+    q: tuple
+    rho: float = 2200.0
+    tilt: float = 0.0
+    azim: float = 0.0
+
+
+@dataclass
+class Model2D:
+    """A 2D model on an nx x nz node lattice (x fastest, z = depth rows)."""
+    name: str
+    nx: int
+    nz: int
+    dx: float
+    layers: list
+    class_of_node: np.ndarray            # uint8/uint16 [nz*nx], node = x + nx*z
+    sources: np.ndarray                  # int64 node indices
+    info: dict = field(default_factory=dict)
+
+
+# Table 2 of the paper: four layers of a 2D viscoelastic VTI model, moduli in
+# (km/s)^2 (converted to (m/s)^2 here) and quality factors per component.
+_TABLE2 = [
+    ((14.40, 4.50, 9.00, 2.25, 3.00), (30.0, 15.0, 20.0, 15.0, 12.0)),
+    ((21.60, 6.75, 13.50, 3.38, 4.50), (45.0, 22.5, 30.0, 22.5, 18.0)),
+    ((28.80, 9.00, 18.00, 4.50, 6.00), (60.0, 30.0, 40.0, 30.0, 24.0)),
+    ((36.00, 11.25, 22.50, 5.63, 7.50), (75.0, 37.5, 50.0, 37.5, 30.0)),
+]
+
+
+def table2_layers(tilt: float = 0.0) -> list:
+    """The paper's Table 2 layers as ``TableLayer`` records in SI units."""
+    return [TableLayer(aR=tuple(v * 1e6 for v in aR), q=tuple(q), tilt=tilt)
+            for aR, q in _TABLE2]
+
+
+def stencil_2d(radius: int) -> np.ndarray:
+    """Offsets (ox, oy=0, oz) with Chebyshev norm <= radius and gcd(|ox|,|oz|) = 1.
+
+    The gcd rule keeps one offset per lattice direction, so radius 5 gives 80
+    offsets.  Returned as int32 [n_off, 3], sorted by (oz, ox).
+    """
+    out = []
+    for oz in range(-radius, radius + 1):
+        for ox in range(-radius, radius + 1):
+            if (ox or oz) and math.gcd(abs(ox), abs(oz)) == 1:
+                out.append((ox, 0, oz))
+    return np.asarray(out, dtype=np.int32)
+
+
+def stencil_3d(radius: int) -> np.ndarray:
+    """3D analogue of ``stencil_2d``: radius 2 gives the 26 neighbours plus the
+    72 secondary directions (98 offsets).  int32 [n_off, 3], sorted by (oz, oy, ox)."""
+    out = []
+    for oz in range(-radius, radius + 1):
+        for oy in range(-radius, radius + 1):
+            for ox in range(-radius, radius + 1):
+                if (ox or oy or oz) and math.gcd(math.gcd(abs(ox), abs(oy)), abs(oz)) == 1:
+                    out.append((ox, oy, oz))
+    return np.asarray(out, dtype=np.int32)
+
+
+def layered_class_map_2d(nx: int, nz: int, n_layers: int) -> np.ndarray:
+    """Flat layers of equal thickness; a node on an interface joins the deeper layer.
+
+    Interfaces sit at depths i*(nz-1)/n_layers (in node units), i = 1..n_layers-1.
+    Returns uint8 [nz*nx] with node = x + nx*z.
+    """
+    z = np.arange(nz, dtype=np.float64)
+    bounds = np.arange(1, n_layers) * (nz - 1) / n_layers
+    layer_of_row = np.searchsorted(bounds, z, side="right").astype(np.uint8)
+    return np.repeat(layer_of_row, nx)
+
+
+def surface_sources_2d(nx: int, n: int) -> np.ndarray:
+    """n sources on the surface row z=0 at x = round(linspace(0, nx-1, n))."""
+    xs = np.round(np.linspace(0, nx - 1, n)).astype(np.int64)
+    return xs  # z = 0, so node index = x
+
+
+def homogeneous_vti(nx: int = 101, nz: int = 101) -> Model2D:
+    """2D homogeneous visco-VTI: one class, centre source, dx = 10 m."""
+    layer = ThomsenLayer(vp0=3000.0, vs0=1500.0, eps=0.2, delta=0.1, gamma=0.1,
+                         qp=60.0, qs=30.0, rho=2200.0)
+    cls = np.zeros(nx * nz, dtype=np.uint8)
+    src = np.array([(nx // 2) + nx * (nz // 2)], dtype=np.int64)
+    return Model2D("homogeneous_vti_%dx%d" % (nx, nz), nx, nz, 10.0, [layer], cls, src)
+
+
+def seeded_tti_layers(n_layers: int, seed: int) -> list:
+    """Seeded Thomsen layers: Vp0 ~ U(2000,4500) sorted with depth,
+    Vp0/Vs0 ~ U(1.7,2.0), eps ~ U(0.05,0.3), delta ~ U(-0.1,0.2),
+    gamma ~ U(0,0.2), tilt ~ U(0,45 deg), Qp,Qs ~ logU(20,200) with Qs <= Qp."""
+    rng = np.random.default_rng(seed)
+    vp0 = np.sort(rng.uniform(2000.0, 4500.0, n_layers))
+    ratio = rng.uniform(1.7, 2.0, n_layers)
+    eps = rng.uniform(0.05, 0.3, n_layers)
+    delta = rng.uniform(-0.1, 0.2, n_layers)
+    gamma = rng.uniform(0.0, 0.2, n_layers)
+    tilt = np.deg2rad(rng.uniform(0.0, 45.0, n_layers))
+    qa = np.exp(rng.uniform(math.log(20.0), math.log(200.0), n_layers))
+    qb = np.exp(rng.uniform(math.log(20.0), math.log(200.0), n_layers))
+    qp, qs = np.maximum(qa, qb), np.minimum(qa, qb)
+    return [ThomsenLayer(vp0=float(vp0[i]), vs0=float(vp0[i] / ratio[i]), eps=float(eps[i]),
+                         delta=float(delta[i]), gamma=float(gamma[i]), qp=float(qp[i]),
+                         qs=float(qs[i]), rho=2200.0, tilt=float(tilt[i]))
+            for i in range(n_layers)]
+
+
+def layered_tti(nx: int = 401, nz: int = 401, n_layers: int = 8, n_sources: int = 64,
+                seed: int = SEEDS["layered_tti"]) -> Model2D:
+    """2D layered visco-TTI, flat layers of equal thickness, surface sources."""
+    layers = seeded_tti_layers(n_layers, seed)
+    cls = layered_class_map_2d(nx, nz, n_layers)
+    src = surface_sources_2d(nx, n_sources)
+    return Model2D("layered_tti_%dx%d_%dL_%dsrc" % (nx, nz, n_layers, n_sources),
+                   nx, nz, 10.0, layers, cls, src)
+
+
+def random_class_map_2d(nx: int, nz: int, n_classes: int, seed: int) -> np.ndarray:
+    """Per-node random classes (a stress case for the lookup and the relaxation)."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, n_classes, nx * nz).astype(np.uint8)
