@@ -1,0 +1,332 @@
+"""Benchmark of the CHERT hot path on the layered visco-TTI workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl chert|reference]
+
+Workload: 2D layered viscoelastic TTI, 401 x 401 nodes at dx = 10 m, 8 flat
+layers of seeded Thomsen parameters, tilts and Q (PCG64 seed 1002), wave
+modes qP, qSV and qSH, 1 deg cache (M = 90 slowness angles per quadrant,
+MEV kernel, homogeneity scan step 0.001 deg over [-30, 30] deg), radius-5
+stencil (80 offsets), 64 surface sources.  One step runs the whole hot path:
+cache build (8,640 entries), direction lookup, propagation and attenuation
+relaxation of 192 (source, mode) fields with parents, and raypaths to 41
+surface receivers per field.  The cache is built with a float scan and a
+double root polish (float storage); lookup and relaxation run in float.
+
+`value` is traveltime fields per second (a field = one (source, mode) pair
+with both tau^R and tau^I and their parents); `e2e` is the same through the
+host-buffer call (inputs copied from pinned memory, both fields copied back).
+With torchrun, every rank runs the full workload on its own GPU (weak
+scaling, no collective on the data path).  `--impl reference` times the FP64
+CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2609_26108_b300 import inputs  # noqa: E402
+
+METRIC = "cache entries/s; traveltime fields/s, plain vs surrogate at ≤1e-4 rel error"
+MODES = ["qP", "qSV", "qSH"]
+M_PER_QUADRANT = 90
+SCAN_STEP = 0.001 * math.pi / 180
+SCAN_HALF = 30000
+RADIUS = 5
+N_RECEIVERS = 41
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+
+def workload():
+    model = inputs.layered_tti()
+    off = inputs.stencil_2d(RADIUS)
+    rcv = np.round(np.linspace(0, model.nx - 1, N_RECEIVERS)).astype(np.int64)   # surface row
+    return model, off, rcv
+
+
+def directed_edges(nx, nz, off):
+    return int(sum((nx - abs(int(o[0]))) * (nz - abs(int(o[2]))) for o in off
+                   if abs(int(o[0])) < nx and abs(int(o[2])) < nz))
+
+
+def config_dict(model, extra=None):
+    d = {"workload": "layered_visco_tti_2d_401x401_8layers_64src_3modes_1deg_R5",
+         "nx": model.nx, "nz": model.nz, "dx_m": model.dx, "n_layers": len(model.layers),
+         "n_sources": len(model.sources), "modes": MODES, "cache_deg": 90.0 / M_PER_QUADRANT,
+         "kernel": "MEV", "scan_step_deg": 0.001, "stencil_radius": RADIUS,
+         "n_offsets": int(len(inputs.stencil_2d(RADIUS))), "fields_per_step": len(model.sources) * 3,
+         "cache_entries_per_step": len(model.layers) * 3 * 4 * M_PER_QUADRANT,
+         "l2": "outputs (494 MB of fields) exceed L2; L2 also flushed (256 MB write) before each step"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------- CPU oracle
+def oracle_sample(model, off, n_solves=3, n_fields=2, seed=0):
+    """Time the FP64 oracle on a bounded sample of the workload (single thread).
+
+    Returns (fields_per_s, entries_per_s, description).  The cache part times
+    `n_solves` distinct (mode, class, angle) solves at the full scan grid and
+    scales to the 2,184 distinct solves of the 8,640-entry cache; the
+    relaxation part times `n_fields` (source, mode) fields, each tau^R and
+    tau^I by binary-heap Dijkstra with parents."""
+    from threadpoolctl import threadpool_limits
+    from oracle import cache_oracle as co
+    from oracle import graph_oracle as go
+    rng = np.random.default_rng(seed)
+    mods, tilts = [], []
+    for L in model.layers:
+        mods.append(co.moduli_from_thomsen(L.vp0, L.vs0, L.eps, L.delta, L.gamma, L.qp, L.qs))
+        tilts.append(L.tilt)
+    n_cls = len(model.layers)
+    with threadpool_limits(1):
+        t0 = time.perf_counter()
+        for _ in range(n_solves):
+            mi, k, j = rng.integers(0, 3), rng.integers(0, n_cls), rng.integers(0, M_PER_QUADRANT + 1)
+            co.solve_direction(co.stiffness_tensor(mods[k]), (math.pi / 2) * j / M_PER_QUADRANT,
+                               MODES[mi], "MEV", SCAN_STEP, SCAN_HALF)
+        t_solve = (time.perf_counter() - t0) / n_solves
+        # a cheap stand-in cache for the lookup (timed: lookup is per mode)
+        Vsel = rng.uniform(1500, 4500, (n_cls, len(off)))
+        Asel = rng.uniform(1e-6, 1e-4, (n_cls, len(off)))
+        cls = model.class_of_node.astype(np.int32)
+        go.build()
+        t0 = time.perf_counter()
+        for f in range(n_fields):
+            s = int(model.sources[rng.integers(0, len(model.sources))])
+            go.dijkstra((model.nx, 1, model.nz), model.dx, cls, off, Vsel, 0, s)
+            go.dijkstra((model.nx, 1, model.nz), model.dx, cls, off, Asel, 1, s)
+        t_field = (time.perf_counter() - t0) / n_fields
+    n_solves_total = n_cls * 3 * (M_PER_QUADRANT + 1)
+    n_fields_total = len(model.sources) * 3
+    t_step = n_solves_total * t_solve + n_fields_total * t_field
+    entries = n_cls * 3 * 4 * M_PER_QUADRANT
+    desc = ("%d cache solves at the full 0.001 deg scan (%.2f s each, scaled to %d solves) + %d fields "
+            "of tauR+tauI Dijkstra on 401x401 (%.2f s each, scaled to %d fields); 1 thread"
+            % (n_solves, t_solve, n_solves_total, n_fields, t_field, n_fields_total))
+    return n_fields_total / t_step, entries / (n_solves_total * t_solve), desc, t_step
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    model, off, _ = workload()
+    for _ in range(args.warmup):
+        oracle_sample(model, off, 1, 1)
+    vals, times = [], []
+    for s in range(args.steps):
+        fps, eps_, desc, t_step = oracle_sample(model, off, 1, 1, seed=s + 1)
+        vals.append(fps)
+        times.append(t_step)
+    value = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "fields/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_dict(model),
+           "cpu_baseline": {"value": value, "unit": "fields/s", "cores": 1, "kind": "oracle",
+                            "sample": "per step: " + desc},
+           "e2e": {"value": value, "unit": "fields/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+def run_chert(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2609_26108_b300 import build, chert
+    from paper_2609_26108_b300.pipeline import Tracer
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    model, off, rcv = workload()
+    classes = chert.classes_from_layers(model.layers)
+    d_classes = chert.classes_to_device(classes)
+    d_cls = torch.as_tensor(model.class_of_node.astype(np.int32), device="cuda")
+    tr = Tracer(len(classes), MODES, M_PER_QUADRANT, model.nx, model.nz, model.dx, off,
+                len(model.sources), rcv, scan_step=SCAN_STEP, scan_half=SCAN_HALF)
+    tr.set_inputs(d_classes, d_cls, model.sources)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        tr.run()
+    barrier()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)               # evict L2 between steps (not timed)
+            e = ev[k]
+            tr.run(events=e[:3])
+            e[3].record()
+        barrier()
+    clocks = clk.summary()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    cache_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    relax_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    nf = len(model.sources) * len(MODES)
+    entries = len(classes) * len(MODES) * 4 * M_PER_QUADRANT
+    value = world * nf * args.steps / (total_ms / 1e3)
+
+    # end to end: pinned host inputs in, both traveltime fields out, per step
+    h_classes = d_classes.cpu().pin_memory()
+    h_cls = d_cls.cpu().pin_memory()
+    h_tauR = torch.empty(tr.tau[0].shape, dtype=tr.tau[0].dtype).pin_memory()
+    h_tauI = torch.empty_like(h_tauR).pin_memory()
+    tr.run_host(h_classes, h_cls, model.sources, h_tauR, h_tauI)
+    barrier()
+    e2e_times = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tr.run_host(h_classes, h_cls, model.sources, h_tauR, h_tauI)
+        e2e_times.append(time.perf_counter() - t0)
+    t = torch.tensor([sum(e2e_times)], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * nf * args.steps / float(t.item())
+
+    # roofline of the dominant kernel (relaxation): algorithmic work = one
+    # relaxation (add + min: 2 FP32 ops) per directed edge per field component
+    relax_avg_s = statistics.mean(relax_ms) / 1e3
+    edges = directed_edges(model.nx, model.nz, off)
+    alg_ops = 2.0 * edges * nf * 2
+    sm_max = clocks.get("sm_max_mhz") or 2032.0
+    peak_tops = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    achieved = alg_ops / relax_avg_s / 1e12
+    roofline = {"bound": "alu", "kernel": "relax_kernel<float,true>", "achieved": achieved,
+                "peak": peak_tops, "unit": "TFLOP/s", "frac": achieved / peak_tops, "traffic": None,
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock (non-FMA op rate)",
+                "alg_ops_per_launch": alg_ops, "directed_edges_per_field": edges,
+                "launch_ms": 1e3 * relax_avg_s}
+    cache_avg_s = statistics.mean(cache_ms) / 1e3
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    out = {"metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": config_dict(model, {"cache_precision": "float scan, double polish, float storage",
+                                         "relax_precision": "fp32", "parallelism": "replicas" if world > 1 else "single"}),
+           "cache_entries_per_s": world * entries / cache_avg_s,
+           "cache_build_ms": 1e3 * cache_avg_s, "relax_ms": 1e3 * relax_avg_s,
+           "edge_relaxations_per_s": world * edges * nf * 2 / relax_avg_s,
+           "roofline": roofline, "clocks": clocks,
+           "e2e": {"value": e2e_value, "unit": "fields/s", "h2d_bytes_per_step": tr.h2d_bytes(),
+                   "d2h_bytes_per_step": tr.d2h_bytes()},
+           "gpu_launches": tr.launches_per_run * args.steps}
+    if world == 1 and not args.no_cpu_baseline:
+        fps, eps_, desc, _ = oracle_sample(model, off)
+        out["cpu_baseline"] = {"value": fps, "unit": "fields/s", "cores": 1, "kind": "oracle",
+                               "sample": desc, "cache_entries_per_s": eps_}
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="chert", choices=["chert", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_chert(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * chert.h -- C ABI of libchert.so, the sm_103a implementation of the hot path of
+ * CHERT (Darwis et al., "CHERT: Cached Hamiltonian-Enhanced Ray Tracing in
+ * Viscoelastic Anisotropic Media"): the directional cache build and the
+ * cache-lookup shortest-path traveltime relaxation.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a status code (CHERT_OK = 0 or a negative error)
+ *     and never aborts; chert_last_error() gives a message for the calling thread.
+ *   - "device" pointers are CUDA device memory of the current device; the caller
+ *     owns every buffer.  The library allocates no device memory: where it needs
+ *     scratch, the caller passes a workspace whose size a *_workspace_bytes()
+ *     query returns.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is only
+ *     enqueued unless a function says it synchronises.
+ *   - Units are SI: moduli in (m/s)^2 (density normalised), lengths in m,
+ *     traveltimes in s, angles in rad.
+ *   - Floating-point buffers are double for CHERT_FP64 and float for
+ *     CHERT_FP32 / CHERT_MIXED.
+ *   - 2D lattice: node = x + nx*z (z = depth).  3D: node = x + nx*(y + ny*z).
+ */
+#ifndef CHERT_H
+#define CHERT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define CHERT_OK        0
+#define CHERT_EINVAL   -1   /* bad argument (message in chert_last_error)      */
+#define CHERT_ENOMEM   -2   /* workspace smaller than *_workspace_bytes()      */
+#define CHERT_ECUDA    -3   /* a CUDA runtime call failed                       */
+#define CHERT_ETIMEOUT -4   /* relaxation hit its cycle cap before converging  */
+
+/* ---- wave modes, kernels, precisions ------------------------------------ */
+#define CHERT_QP  0
+#define CHERT_QSV 1
+#define CHERT_QSH 2
+
+#define CHERT_OEV 0         /* g-Hamiltonian, Eq. 12                           */
+#define CHERT_MEV 1         /* g*-Hamiltonian, Eq. 13-14                       */
+
+#define CHERT_FP64  0       /* every step in double                            */
+#define CHERT_FP32  1       /* every step in float                             */
+#define CHERT_MIXED 2       /* float scan, double root polish and ray
+                               quantities, float storage and relaxation        */
+
+/* One cache class k (a layer, facies, cell or tilt group).  Eq. 2:
+ * a = aR - i*aI per Voigt component (a11, a13, a33, a44, a66) of a VTI solid
+ * whose symmetry axis is tilted by (tilt, azim) = (theta_0, phi_0), Eq. 35. */
+typedef struct {
+    double aR[5];
+    double aI[5];
+    double rho;      /* stored only, Eq. 26 */
+    double tilt;     /* theta_0 */
+    double azim;     /* phi_0 (3D; 0 in 2D) */
+} chert_class;
+
+/* Thomsen (Vp0, Vs0, eps, delta, gamma) and quality factors to one class:
+ * a33 = Vp0^2, a44 = Vs0^2, a11 = a33(1+2 eps), a66 = a44(1+2 gamma),
+ * a13 = sqrt((a33-a44)(a33(1+2 delta)-a44)) - a44, and (Eq. 2 with the
+ * per-component reading of the paper's Table 2) aI = aR/Q with
+ * Q11 = Q13 = Q33 = qp, Q44 = Q66 = qs.  Host only.
+ * Errors: CHERT_EINVAL if out is NULL, a velocity or Q is not positive, or
+ * delta leaves no real a13. */
+int chert_thomsen_to_class(double vp0, double vs0, double eps, double delta,
+                           double gamma, double qp, double qs, double rho,
+                           double tilt, double azim, chert_class* out);
+
+/* ---- cache build (Eq. 4-14, 26, 35-36) ---------------------------------- */
+
+/* Output arrays of the directional cache C(m, k, theta), all device, each laid
+ * out [n_modes][n_classes][n_dir] with n_dir = 4*M (Eq. 26, Table 1).
+ * Directions d index the slowness angle theta_d = d*(pi/2)/M of the class's
+ * local symmetry-axis frame; the stored values are global:
+ *   V, A, Q     ray velocity (m/s), ray attenuation (s/m), ray quality (Eq. 11)
+ *   rx, rz      unit ray direction r in the global x-z plane (Eq. 36)
+ *   theta       global real slowness angle theta_d + tilt, from +z toward +x
+ *   vartheta    the imaginary slowness angle of the homogeneous solution, signed
+ *               as seen from direction d (Eq. 9)
+ *   flag        0 = valid, 1 = no acceptable (decaying) root; V, A, Q, rx, rz,
+ *               vartheta are NaN then and the lookup skips the entry.
+ * Any pointer except flag, V and rx/rz may be NULL to skip that output. */
+typedef struct {
+    void*    V;
+    void*    A;
+    void*    Q;
+    void*    rx;
+    void*    rz;
+    void*    theta;
+    void*    vartheta;
+    uint8_t* flag;
+} chert_cache_arrays;
+
+/* Homogeneity search settings.  The roots of the residual
+ * f(vartheta) = (v^R x v^I)_y / |v^R|^2 (Eq. 9) are the sign changes of f on
+ * the grid vartheta_k = k*scan_step, |k| <= scan_half, plus exact zeros on the
+ * grid; each is polished to a bracket below 1e-14 rad (FP64, MIXED) or to
+ * float resolution (FP32).  The chosen root is the decaying one (v_I <= 1e-9
+ * v_R, stored A clamped at 0) of least |vartheta|, the negative one on a tie.
+ * Defaults used by the paper's [-30, 30] deg bracket: scan_step = 0.001 deg,
+ * scan_half = 30000. */
+typedef struct {
+    int    M;            /* slowness angles per quadrant, >= 1 (1 deg: M = 90) */
+    double scan_step;    /* rad, > 0 */
+    int    scan_half;    /* >= 1 */
+    int    kernel;       /* CHERT_OEV or CHERT_MEV */
+    int    precision;    /* CHERT_FP64, CHERT_FP32 or CHERT_MIXED */
+} chert_cache_params;
+
+/* Build the cache for n_classes classes (device array d_classes) and n_modes
+ * wave modes (host array `modes`, values CHERT_QP/QSV/QSH, distinct, <= 3).
+ * One warp solves each distinct folded angle (0..90 deg) of each (mode,
+ * class) and writes the up to four mirrored entries.  Errors: CHERT_EINVAL
+ * (counts, params, NULL outputs), CHERT_ECUDA. */
+int chert_build_cache(const chert_class* d_classes, int n_classes,
+                      const int* modes, int n_modes,
+                      const chert_cache_params* params,
+                      const chert_cache_arrays* out, void* stream);
+
+/* ---- direction lookup (Eq. 27-28) --------------------------------------- */
+
+/* For every (mode, class, stencil offset o): the cache entry whose ray
+ * direction r has the largest dot product with d = o/|o| (both float64 for
+ * CHERT_FP64, float32 otherwise; products rounded separately, ties to the
+ * lower entry index, flagged entries skipped).  Writes device arrays
+ * [n_modes][n_classes][n_off]: idx (int32, -1 if a class has no valid
+ * entry), Vsel and Asel (the entry's V and A, NaN for idx = -1).
+ * offsets: host int32 [n_off][3] = (ox, oy, oz), 1 <= n_off <= 512, oy = 0
+ * in 2D.  Errors: CHERT_EINVAL, CHERT_ECUDA. */
+int chert_edge_table(const chert_cache_arrays* cache, int n_modes, int n_classes,
+                     int n_dir, int precision, const int32_t* offsets, int n_off,
+                     int32_t* d_idx, void* d_Vsel, void* d_Asel, void* stream);
+
+/* ---- traveltime relaxation (Eq. 22, 27-33) ------------------------------ */
+
+/* Scratch bytes chert_traveltime needs for this problem size. */
+size_t chert_traveltime_workspace_bytes(int n_modes, int n_classes, int n_off,
+                                        int precision, int n_sources);
+
+/* Propagation and attenuation traveltime fields for every (source, mode) of
+ * a cache, on a 2D lattice nx x nz (ny must be 1) with spacing dx.
+ *   d_class_of_node  device int32 [nz*nx], values in [0, n_classes)
+ *   offsets          host int32 [n_off][3], a set closed under negation
+ *   sources          host int64 [n_sources] node indices
+ * Each directed edge i -> j = i + o costs, with the selected (V, A) of the
+ * end classes (Eq. 28-30), wR = L/(0.5 (V_ki + V_kj)) and wI = L*0.5(A_ki + A_kj),
+ * L = dx|o|.  tauR and tauI are the fixed points of Eq. 31 from tau(source) = 0,
+ * solved separately; parR/parI (may be NULL) follow the rule
+ * par_j = argmin_i (tau_i + w_ij), ties to the smallest i, par(source) =
+ * source, par = -1 and tau = +inf where unreachable (Eq. 33).
+ * Outputs are device arrays [n_sources][n_modes][nz*nx].
+ * max_cycles caps the sweep cycles per field; a field that has not converged
+ * after it returns CHERT_ETIMEOUT (its values are valid upper bounds).
+ * Synchronises on `stream` once at the end to read the convergence status.
+ * Errors: CHERT_EINVAL, CHERT_ENOMEM (workspace too small), CHERT_ECUDA,
+ * CHERT_ETIMEOUT. */
+int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes,
+                     int n_dir, int nx, int ny, int nz, double dx,
+                     const int32_t* d_class_of_node, const int32_t* offsets,
+                     int n_off, const int64_t* sources, int n_sources,
+                     int precision, int max_cycles,
+                     void* d_tauR, void* d_tauI, int32_t* d_parR, int32_t* d_parI,
+                     void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* ---- raypaths (Eq. 33-34) ------------------------------------------------ */
+
+/* Backtrack parents from receivers to sources for a batch of fields.  Field
+ * f has parents d_par[f*n_nodes ...] (int32, as written by chert_traveltime)
+ * and source d_src[f]; for receiver r its path is written source-first to
+ * d_paths[(f*n_rcv + r)*cap ...] and its node count to d_len[f*n_rcv + r],
+ * 0 when the receiver is unreachable, a parent is out of range, or the walk
+ * exceeds cap nodes (a cycle cannot run forever).  All arrays are device
+ * memory: par int32 [n_fields][n_nodes], src int64 [n_fields], rcv int64
+ * [n_rcv], paths int64 [n_fields][n_rcv][cap], len int64 [n_fields][n_rcv].
+ * Errors: CHERT_EINVAL, CHERT_ECUDA. */
+int chert_raypath(const int32_t* d_par, int n_fields, int64_t n_nodes,
+                  const int64_t* d_src, const int64_t* d_rcv, int n_rcv, int64_t cap,
+                  int64_t* d_paths, int64_t* d_len, void* stream);
+
+/* Message describing the last error returned on the calling host thread. */
+const char* chert_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHERT_H */

@@ -10,7 +10,8 @@ against the equations, not for speed:
 * Eq. 4-7      Christoffel matrix of the complex slowness direction
                n = (sin(theta + i vartheta), 0, cos(theta + i vartheta)), built
                from the full 4th-order tensor and diagonalised with
-               numpy.linalg.eig (3x3, no closed form).
+               numpy.linalg.eig (no closed form); in this sagittal plane the
+               y-polarised block and the x-z block are solved separately.
 * Eq. 12       OEV: v_i = a_ijkl p_l g_j g_k with the bilinear norm g.g = 1.
 * Eq. 13-14    MEV, read literally: unsymmetrised Gbar_il = a_ijkl g*_j g_k with
                g^H g = 1, plus 1/2 g^H [Gamma(p) - I] dg/dp where dg/dp comes
@@ -97,6 +98,28 @@ def christoffel(A, x) -> np.ndarray:
     return np.einsum("ijkl,...i,...l->...jk", A, x, x)
 
 
+def eigenpairs(G):
+    """Eigenvalues w[..., 3] and eigenvectors V[..., :, 3] of Christoffel matrices.
+
+    With n_y = 0 (the sagittal plane of Eq. 7) the y row and column of Gamma
+    are exactly zero off the diagonal: the y-polarised mode (qSH) decouples from
+    the x-z block.  The two blocks are then diagonalised separately, so that
+    qSH stays y-polarised even where it is degenerate with qSV (on the
+    symmetry axis) and numpy.linalg.eig would mix the two."""
+    decoupled = not (np.any(G[..., 0, 1] != 0) or np.any(G[..., 1, 0] != 0)
+                     or np.any(G[..., 1, 2] != 0) or np.any(G[..., 2, 1] != 0))
+    if not decoupled:
+        return np.linalg.eig(G)
+    xz = G[..., [0, 2], :][..., :, [0, 2]]
+    w2, V2 = np.linalg.eig(xz)
+    w = np.concatenate([w2, G[..., 1, 1][..., None]], axis=-1)
+    V = np.zeros(G.shape, dtype=np.complex128)
+    V[..., 0, :2] = V2[..., 0, :]
+    V[..., 2, :2] = V2[..., 1, :]
+    V[..., 1, 2] = 1.0
+    return w, V
+
+
 def _mode_column(w, V, mode):
     """Index of the eigenpair of wave mode ``mode`` for each batch element.
 
@@ -117,7 +140,7 @@ def energy_velocity(A, n, mode, kernel) -> np.ndarray:
 
     OEV is Eq. 12; MEV is the literal form of Eq. 13-14 (module docstring)."""
     G = christoffel(A, n)
-    w, V = np.linalg.eig(G)
+    w, V = eigenpairs(G)
     col = _mode_column(w, V, mode)
     take = lambda arr: np.take_along_axis(arr, col[..., None], axis=-1)[..., 0]
     lam = take(w)                                     # eigenvalue c^2
@@ -145,7 +168,12 @@ def energy_velocity(A, n, mode, kernel) -> np.ndarray:
         t = np.einsum("...j,...jk,...k->...", gs, Gp_minus_I, h)   # g^H (Gamma-I) h
         with np.errstate(divide="ignore", invalid="ignore"):
             term = 0.5 * (t / ((1.0 - mu) * hTh))[..., None] * s
-        v = v + np.where(other[..., None], term, 0.0)
+        # (Gamma(p) - I) h = (mu - 1) h, so the term carries the factor g^H h:
+        # a mode orthogonal to g (qSH against the x-z modes in the sagittal
+        # plane) or one that dGamma does not couple to g adds exactly nothing,
+        # even where it is degenerate with g and the quotient reads 0/0
+        coupled = np.any(s != 0, axis=-1) & (np.sum(gs * h, axis=-1) != 0)
+        v = v + np.where((other & coupled)[..., None], term, 0.0)
     return v
 
 

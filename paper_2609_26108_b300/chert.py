@@ -1,0 +1,267 @@
+"""Python binding of libchert.so (argument marshalling only).
+
+Every step of the hot path runs in the library's CUDA kernels; this module only
+turns torch tensors into pointers and sizes and checks status codes.  Device
+memory comes from torch (caller-owned buffers and the relaxation workspace);
+the library itself allocates no device memory.  There is no CPU fallback: if
+the library is missing or a tensor is not on a CUDA device, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libchert.so")
+
+QP, QSV, QSH = 0, 1, 2
+MODE_IDS = {"qP": QP, "qSV": QSV, "qSH": QSH}
+OEV, MEV = 0, 1
+KERNEL_IDS = {"OEV": OEV, "MEV": MEV}
+FP64, FP32, MIXED = 0, 1, 2
+PRECISION_IDS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4
+
+
+class ChertError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libchert error %d: %s" % (code, msg))
+        self.code = code
+
+
+class chert_class(ctypes.Structure):
+    _fields_ = [("aR", ctypes.c_double * 5), ("aI", ctypes.c_double * 5), ("rho", ctypes.c_double),
+                ("tilt", ctypes.c_double), ("azim", ctypes.c_double)]
+
+
+class chert_cache_arrays(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_void_p), ("A", ctypes.c_void_p), ("Q", ctypes.c_void_p),
+                ("rx", ctypes.c_void_p), ("rz", ctypes.c_void_p), ("theta", ctypes.c_void_p),
+                ("vartheta", ctypes.c_void_p), ("flag", ctypes.c_void_p)]
+
+
+class chert_cache_params(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("scan_step", ctypes.c_double), ("scan_half", ctypes.c_int),
+                ("kernel", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libchert.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libchert.so not built: run python -m paper_2609_26108_b300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, I64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_size_t
+    L.chert_last_error.restype = ctypes.c_char_p
+    L.chert_thomsen_to_class.argtypes = [D] * 10 + [ctypes.POINTER(chert_class)]
+    L.chert_build_cache.argtypes = [P, I, P, I, ctypes.POINTER(chert_cache_params),
+                                    ctypes.POINTER(chert_cache_arrays), P]
+    L.chert_edge_table.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, P, I, P, P, P, P]
+    L.chert_traveltime_workspace_bytes.argtypes = [I, I, I, I, I]
+    L.chert_traveltime_workspace_bytes.restype = SZ
+    L.chert_traveltime.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P, I,
+                                   P, I, I, I, P, P, P, P, P, SZ, P]
+    L.chert_raypath.argtypes = [P, I, I64, P, P, I, I64, P, P, P]
+    for name in ("chert_thomsen_to_class", "chert_build_cache", "chert_edge_table",
+                 "chert_traveltime", "chert_raypath"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != OK:
+        raise ChertError(rc, lib().chert_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _fdtype(precision):
+    torch = _torch()
+    return torch.float64 if precision == FP64 else torch.float32
+
+
+# ------------------------------------------------------------------ classes
+def thomsen_to_class(vp0, vs0, eps, delta, gamma, qp, qs, rho=2200.0, tilt=0.0, azim=0.0):
+    out = chert_class()
+    _check(lib().chert_thomsen_to_class(vp0, vs0, eps, delta, gamma, qp, qs, rho, tilt, azim,
+                                        ctypes.byref(out)))
+    return out
+
+
+def table_class(aR, q, rho=2200.0, tilt=0.0, azim=0.0):
+    """A class from real moduli and per-component Q (Eq. 2: aI = aR/Q)."""
+    c = chert_class()
+    for i in range(5):
+        c.aR[i] = float(aR[i])
+        c.aI[i] = 0.0 if math.isinf(q[i]) else float(aR[i]) / float(q[i])
+    c.rho, c.tilt, c.azim = rho, tilt, azim
+    return c
+
+
+def classes_from_layers(layers):
+    """chert_class records for ThomsenLayer / TableLayer descriptions."""
+    out = []
+    for L in layers:
+        if hasattr(L, "vp0"):
+            out.append(thomsen_to_class(L.vp0, L.vs0, L.eps, L.delta, L.gamma, L.qp, L.qs,
+                                        L.rho, L.tilt, L.azim))
+        else:
+            out.append(table_class(L.aR, L.q, L.rho, L.tilt, L.azim))
+    return out
+
+
+def classes_to_device(classes, device="cuda"):
+    """Pack chert_class records into a device byte tensor (the ABI's array)."""
+    torch = _torch()
+    arr = (chert_class * len(classes))(*classes)
+    raw = np.frombuffer(bytes(arr), dtype=np.uint8).copy()
+    return torch.from_numpy(raw).to(device)
+
+
+# ------------------------------------------------------------------ cache
+class Cache:
+    """Device-resident directional cache (torch tensors [n_modes, n_classes, 4M])."""
+
+    def __init__(self, arrays, modes, n_classes, M, precision):
+        self.arrays, self.modes, self.n_classes, self.M, self.precision = arrays, modes, n_classes, M, precision
+
+    @property
+    def n_dir(self):
+        return 4 * self.M
+
+    def struct(self):
+        a = self.arrays
+        return chert_cache_arrays(*[None if a.get(k) is None else a[k].data_ptr()
+                                    for k in ("V", "A", "Q", "rx", "rz", "theta", "vartheta", "flag")])
+
+    def __getitem__(self, key):
+        return self.arrays[key]
+
+
+def build_cache(d_classes, n_classes, modes, M, scan_step=0.001 * math.pi / 180, scan_half=30000,
+                kernel="MEV", precision="fp32", stream=None, out=None):
+    """Enqueue chert_build_cache; returns a Cache of new (or given) torch tensors."""
+    torch = _torch()
+    prec = PRECISION_IDS[precision] if isinstance(precision, str) else precision
+    mode_ids = [MODE_IDS[m] if isinstance(m, str) else m for m in modes]
+    shape = (len(mode_ids), n_classes, 4 * M)
+    dev = d_classes.device
+    if out is None:
+        fd = _fdtype(prec)
+        out = {k: torch.empty(shape, dtype=fd, device=dev)
+               for k in ("V", "A", "Q", "rx", "rz", "theta", "vartheta")}
+        out["flag"] = torch.empty(shape, dtype=torch.uint8, device=dev)
+    cache = Cache(out, mode_ids, n_classes, M, prec)
+    params = chert_cache_params(M, scan_step, scan_half, KERNEL_IDS.get(kernel, kernel), prec)
+    modes_arr = (ctypes.c_int * len(mode_ids))(*mode_ids)
+    st = cache.struct()
+    _check(lib().chert_build_cache(_dev_ptr(d_classes), n_classes, modes_arr, len(mode_ids),
+                                   ctypes.byref(params), ctypes.byref(st), _stream_ptr(stream)))
+    return cache
+
+
+def _offsets_arr(offsets):
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1, 3))
+    return off, off.ctypes.data_as(ctypes.c_void_p)
+
+
+def edge_table(cache, offsets, stream=None):
+    """Enqueue chert_edge_table: (idx, Vsel, Asel) torch tensors [n_modes, n_classes, n_off]."""
+    torch = _torch()
+    off, off_p = _offsets_arr(offsets)
+    nm = len(cache.modes)
+    dev = cache["V"].device
+    idx = torch.empty((nm, cache.n_classes, len(off)), dtype=torch.int32, device=dev)
+    Vs = torch.empty(idx.shape, dtype=_fdtype(cache.precision), device=dev)
+    As = torch.empty_like(Vs)
+    st = cache.struct()
+    _check(lib().chert_edge_table(ctypes.byref(st), nm, cache.n_classes, cache.n_dir, cache.precision,
+                                  off_p, len(off), _dev_ptr(idx), _dev_ptr(Vs), _dev_ptr(As),
+                                  _stream_ptr(stream)))
+    return idx, Vs, As
+
+
+def workspace_bytes(n_modes, n_classes, n_off, precision, n_sources):
+    return int(lib().chert_traveltime_workspace_bytes(n_modes, n_classes, n_off, precision, n_sources))
+
+
+def traveltime(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64, parents=True,
+               stream=None, out=None, workspace=None):
+    """chert_traveltime for all (source, mode) fields of ``cache``.
+
+    Returns (tauR, tauI, parR, parI) torch tensors [n_sources, n_modes, nz*nx]."""
+    torch = _torch()
+    off, off_p = _offsets_arr(offsets)
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64).reshape(-1))
+    nm, ns = len(cache.modes), len(src)
+    dev = cache["V"].device
+    shape = (ns, nm, nx * nz)
+    if out is None:
+        fd = _fdtype(cache.precision)
+        out = (torch.empty(shape, dtype=fd, device=dev), torch.empty(shape, dtype=fd, device=dev),
+               torch.empty(shape, dtype=torch.int32, device=dev) if parents else None,
+               torch.empty(shape, dtype=torch.int32, device=dev) if parents else None)
+    wsb = workspace_bytes(nm, cache.n_classes, len(off), cache.precision, ns)
+    if workspace is None or workspace.numel() < wsb:
+        workspace = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    st = cache.struct()
+    _check(lib().chert_traveltime(ctypes.byref(st), nm, cache.n_classes, cache.n_dir, nx, 1, nz,
+                                  float(dx), _dev_ptr(d_cls), off_p, len(off),
+                                  src.ctypes.data_as(ctypes.c_void_p), ns, cache.precision,
+                                  max_cycles, _dev_ptr(out[0]), _dev_ptr(out[1]), _dev_ptr(out[2]),
+                                  _dev_ptr(out[3]), _dev_ptr(workspace), workspace.numel(),
+                                  _stream_ptr(stream)))
+    return out
+
+
+def raypath(par, sources, receivers, cap=4096, stream=None, out=None):
+    """chert_raypath for a batch of fields.
+
+    par: int32 [n_fields, n_nodes] (or [n_nodes] for one field); sources: one
+    source node per field; returns (paths int64 [n_fields, n_rcv, cap], lengths
+    int64 [n_fields, n_rcv]), paths source-first."""
+    torch = _torch()
+    dev = par.device
+    par2 = par.reshape(-1, par.shape[-1])
+    nf, nn = par2.shape
+    src = sources if torch.is_tensor(sources) else \
+        torch.as_tensor(np.asarray(sources, dtype=np.int64).reshape(-1), device=dev)
+    if src.numel() != nf:
+        raise ValueError("need one source per field")
+    rcv = receivers if torch.is_tensor(receivers) else \
+        torch.as_tensor(np.asarray(receivers, dtype=np.int64).reshape(-1), device=dev)
+    if out is None:
+        out = (torch.full((nf, len(rcv), cap), -1, dtype=torch.int64, device=dev),
+               torch.empty((nf, len(rcv)), dtype=torch.int64, device=dev))
+    _check(lib().chert_raypath(_dev_ptr(par2), nf, nn, _dev_ptr(src), _dev_ptr(rcv), len(rcv), cap,
+                               _dev_ptr(out[0]), _dev_ptr(out[1]), _stream_ptr(stream)))
+    return out

@@ -1,0 +1,44 @@
+// Host-only entry points of libchert: error text and the Thomsen conversion.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace chert {
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+}  // namespace chert
+
+extern "C" const char* chert_last_error(void) { return chert::g_err; }
+
+// Thomsen's (1986) parameters inverted for a VTI solid; quality factors per
+// Voigt component as in the paper's Table 2 (Eq. 2: aI = aR / Q).
+extern "C" int chert_thomsen_to_class(double vp0, double vs0, double eps, double delta,
+                                      double gamma, double qp, double qs, double rho,
+                                      double tilt, double azim, chert_class* out) {
+    CHERT_REQUIRE(out != nullptr, "chert_thomsen_to_class: out is NULL");
+    CHERT_REQUIRE(vp0 > 0 && vs0 > 0 && vp0 > vs0, "chert_thomsen_to_class: need vp0 > vs0 > 0");
+    CHERT_REQUIRE(qp > 0 && qs > 0, "chert_thomsen_to_class: quality factors must be positive");
+    const double a33 = vp0 * vp0, a44 = vs0 * vs0;
+    const double a11 = a33 * (1.0 + 2.0 * eps);
+    const double a66 = a44 * (1.0 + 2.0 * gamma);
+    const double rad = (a33 - a44) * (a33 * (1.0 + 2.0 * delta) - a44);
+    CHERT_REQUIRE(rad > 0.0, "chert_thomsen_to_class: delta=%g leaves no real a13", delta);
+    const double a13 = sqrt(rad) - a44;
+    const double aR[5] = {a11, a13, a33, a44, a66};
+    const double q[5] = {qp, qp, qp, qs, qs};
+    for (int i = 0; i < 5; i++) {
+        out->aR[i] = aR[i];
+        out->aI[i] = isinf(q[i]) ? 0.0 : aR[i] / q[i];
+    }
+    out->rho = rho;
+    out->tilt = tilt;
+    out->azim = azim;
+    return CHERT_OK;
+}

@@ -1,0 +1,496 @@
+// Direction lookup (Eq. 27-28), traveltime relaxation (Eq. 29-31), parents and
+// raypaths (Eq. 33-34) on a 2D node lattice.
+//
+// Relaxation.  The fixed point tau_j = min(tau_j, min_i tau_i + w_ij) of Eq. 31
+// is unique (all weights are >= 0), so any order of relaxations that runs to
+// convergence returns it exactly.  One CTA owns one (source, mode, component)
+// field and relaxes it in sweep order: a cycle pulls every node from its
+// in-neighbours on earlier lines of four sweeps -- rows top-down (offsets with
+// o_z > 0), columns left-to-right (o_x > 0), columns right-to-left (o_x < 0),
+// rows bottom-up (o_z < 0).  Every offset falls in at least one sweep, no node
+// is written by two threads, and a line only reads lines finished before it,
+// so no atomics are needed; the last R+1 lines of tau and class ids live in a
+// shared-memory ring.  A verification pass then pulls each node from all of its
+// in-neighbours: if nothing improves the field is the fixed point and the same
+// pass has produced the parents par_j = argmin_i (tau_i + w_ij) (ties to the
+// smallest i); otherwise another cycle runs.  Weights come from a per-CTA
+// table W[o][k_i][k_j] in shared memory built from the lookup.
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace chert {
+namespace {
+
+constexpr int kMaxOff = 512;
+
+struct Offsets {
+    int n;
+    short x[kMaxOff], y[kMaxOff], z[kMaxOff];
+};
+
+// ------------------------------------------------------------ lookup kernel
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+
+// One warp per (mode, class, offset): argmax of d.r over the class's entries.
+template <typename T>
+__global__ void edge_table_kernel(const T* __restrict__ rx, const T* __restrict__ rz,
+                                  const T* __restrict__ V, const T* __restrict__ A,
+                                  const uint8_t* __restrict__ flag, int n_modes, int n_classes,
+                                  int n_dir, Offsets off, int32_t* __restrict__ idx_out,
+                                  T* __restrict__ Vsel, T* __restrict__ Asel) {
+    const int lane = threadIdx.x & 31;
+    const long long w = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const long long total = static_cast<long long>(n_modes) * n_classes * off.n;
+    if (w >= total) return;
+    const int o = static_cast<int>(w % off.n);
+    const long long mk = w / off.n;                  // mode * n_classes + class
+    const double ox = off.x[o], oy = off.y[o], oz = off.z[o];
+    const T nrm = T(sqrt(ox * ox + oy * oy + oz * oz));
+    const T dx = div_rn(T(ox), nrm), dz = div_rn(T(oz), nrm);
+    const size_t base = static_cast<size_t>(mk) * n_dir;
+    T best = T(-INFINITY);
+    int bi = -1;
+    for (int e = lane; e < n_dir; e += 32) {
+        if (flag[base + e]) continue;
+        const T dot = add_rn(mul_rn(dx, rx[base + e]), mul_rn(dz, rz[base + e]));
+        if (dot > best) { best = dot; bi = e; }     // increasing e: first max kept
+    }
+    for (int s = 16; s > 0; s >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, s);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, s);
+        if (oi >= 0 && (bi < 0 || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+    }
+    if (lane == 0) {
+        const size_t out = static_cast<size_t>(mk) * off.n + o;
+        idx_out[out] = bi;
+        Vsel[out] = bi >= 0 ? V[base + bi] : T(NAN);
+        Asel[out] = bi >= 0 ? A[base + bi] : T(NAN);
+    }
+}
+
+// ------------------------------------------------------------ relaxation
+struct FieldArgs {
+    int nx, nz, n_classes, n_modes, n_sources, max_cycles, ring;
+    double dx;
+    const int32_t* cls;
+    const int64_t* src;
+    void *tauR, *tauI;
+    int32_t *parR, *parI;
+    const void *Vsel, *Asel;     // [n_modes][n_classes][n_off]
+    int* status;                 // [field*2 + component]: cycles used, -1 = cap hit
+};
+
+template <typename T>
+__device__ __forceinline__ T edge_w(int comp, T L, T a, T b) {
+    // Eq. 29-30 with the segment averages of Eq. 28
+    return comp == 0 ? div_rn(L, mul_rn(T(0.5), add_rn(a, b))) : mul_rn(L, mul_rn(T(0.5), add_rn(a, b)));
+}
+
+// Class ids index shared-memory tables, so every load is clamped into range;
+// check_classes_kernel reports out-of-range ids as an argument error.
+__device__ __forceinline__ int clamp_class(int k, int nk) { return min(max(k, 0), nk - 1); }
+
+__global__ void check_classes_kernel(const int32_t* __restrict__ cls, long long n, int nk, int* bad) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        if (cls[i] < 0 || cls[i] >= nk) { atomicOr(bad, 1); return; }
+}
+
+// Shared memory layout of relax_kernel.
+template <typename T>
+struct Smem {
+    T* W;          // [n_off][nk][nk] (table) or [nk][n_off] raw values
+    T* L;          // [n_off]
+    T* ring;       // [ring][line_max]
+    int32_t* cring;  // [ring][line_max]
+    short* lists;  // 4 x [n_off] offset indices per sweep
+    int* counts;   // 4
+};
+
+// One sweep: lines advance along `axis` (0: rows in z, 1: columns in x) in
+// direction `dir`; each node pulls from the offsets of its sweep list.
+template <typename T, bool TABLE>
+__device__ bool sweep(const Smem<T>& sm, const Offsets& off, int list, int axis, int dir, T* tau,
+                      const int32_t* __restrict__ cls, int nx, int nz, int nk, int comp, int ring) {
+    const int n_lines = axis == 0 ? nz : nx;
+    const int len = axis == 0 ? nx : nz;
+    const short* lst = sm.lists + list * off.n;
+    const int cnt = sm.counts[list];
+    bool changed = false;
+    for (int step = 0; step < n_lines; ++step) {
+        const int line = dir > 0 ? step : n_lines - 1 - step;
+        const int slot = line % ring;
+        for (int u = threadIdx.x; u < len; u += blockDim.x) {
+            const size_t j = axis == 0 ? (size_t)u + (size_t)nx * line : (size_t)line + (size_t)nx * u;
+            const T cur = tau[j];
+            const int kj = clamp_class(cls[j], nk);
+            sm.cring[slot * len + u] = kj;
+            T best = cur;
+            for (int q = 0; q < cnt; ++q) {
+                const int o = lst[q];
+                const int oa = axis == 0 ? off.z[o] : off.x[o];   // across-line component
+                const int ol = axis == 0 ? off.x[o] : off.z[o];   // along-line component
+                const int il = line - oa;
+                const int iu = u - ol;
+                if (il < 0 || il >= n_lines || iu < 0 || iu >= len) continue;
+                const int s = (il % ring) * len + iu;
+                const int ki = sm.cring[s];
+                T w;
+                if (TABLE) w = sm.W[(o * nk + ki) * nk + kj];
+                else w = edge_w<T>(comp, sm.L[o], sm.W[ki * off.n + o], sm.W[kj * off.n + o]);
+                best = fmin(best, sm.ring[s] + w);
+            }
+            sm.ring[slot * len + u] = best;
+            if (best < cur) {
+                tau[j] = best;
+                changed = true;
+            }
+        }
+        __syncthreads();
+    }
+    return __syncthreads_or(changed);
+}
+
+// Pull every node from all in-neighbours; lower tau where possible (returns
+// true if anything changed) and record the argmin parent.
+template <typename T, bool TABLE>
+__device__ bool verify(const Smem<T>& sm, const Offsets& off, T* tau, const int32_t* __restrict__ cls,
+                       int nx, int nz, int nk, int comp, int64_t src, int32_t* par) {
+    bool changed = false;
+    const int n = nx * nz;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int xj = j % nx, zj = j / nx;
+        const int kj = clamp_class(cls[j], nk);
+        const T cur = tau[j];
+        T best = T(INFINITY);
+        int bi = -1;
+        for (int o = 0; o < off.n; ++o) {
+            const int xi = xj - off.x[o], zi = zj - off.z[o];
+            if (xi < 0 || xi >= nx || zi < 0 || zi >= nz) continue;
+            const int i = xi + nx * zi;
+            const T ti = tau[i];
+            const int ki = clamp_class(cls[i], nk);
+            T w;
+            if (TABLE) w = sm.W[(o * nk + ki) * nk + kj];
+            else w = edge_w<T>(comp, sm.L[o], sm.W[ki * off.n + o], sm.W[kj * off.n + o]);
+            const T c = ti + w;
+            if (c < best || (c == best && i < bi)) { best = c; bi = i; }
+        }
+        if (best < cur) {
+            tau[j] = best;
+            changed = true;
+        } else if (par) {
+            par[j] = (j == src) ? static_cast<int32_t>(src) : (isinf(cur) ? -1 : bi);
+        }
+    }
+    return __syncthreads_or(changed);
+}
+
+template <typename T, bool TABLE>
+__global__ void __launch_bounds__(512) relax_kernel(FieldArgs a, Offsets off) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nk = a.n_classes;
+    const int field = blockIdx.x >> 1;          // source * n_modes + mode
+    const int comp = blockIdx.x & 1;            // 0: propagation, 1: attenuation
+    const int mode = field % a.n_modes;
+    const int s = field / a.n_modes;
+    const int line_max = max(a.nx, a.nz);
+    const size_t n = static_cast<size_t>(a.nx) * a.nz;
+
+    Smem<T> sm;
+    unsigned char* p = smem_raw;
+    const size_t wcount = TABLE ? static_cast<size_t>(off.n) * nk * nk : static_cast<size_t>(nk) * off.n;
+    sm.W = reinterpret_cast<T*>(p); p += wcount * sizeof(T);
+    sm.L = reinterpret_cast<T*>(p); p += off.n * sizeof(T);
+    sm.ring = reinterpret_cast<T*>(p); p += static_cast<size_t>(a.ring) * line_max * sizeof(T);
+    sm.cring = reinterpret_cast<int32_t*>(p); p += static_cast<size_t>(a.ring) * line_max * 4;
+    sm.lists = reinterpret_cast<short*>(p); p += 4 * off.n * sizeof(short);
+    sm.counts = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
+
+    // weights of this (mode, component)
+    const T* sel = static_cast<const T*>(comp == 0 ? a.Vsel : a.Asel) +
+                   static_cast<size_t>(mode) * nk * off.n;
+    for (int o = threadIdx.x; o < off.n; o += blockDim.x) {
+        const double ox = off.x[o], oz = off.z[o];
+        sm.L[o] = T(a.dx * sqrt(ox * ox + oz * oz));
+    }
+    __syncthreads();
+    if (TABLE) {
+        for (int t = threadIdx.x; t < off.n * nk * nk; t += blockDim.x) {
+            const int kj = t % nk, ki = (t / nk) % nk, o = t / (nk * nk);
+            sm.W[t] = edge_w<T>(comp, sm.L[o], sel[ki * off.n + o], sel[kj * off.n + o]);
+        }
+    } else {
+        for (int t = threadIdx.x; t < nk * off.n; t += blockDim.x) sm.W[t] = sel[t];
+    }
+    if (threadIdx.x == 0) {
+        int c[4] = {0, 0, 0, 0};
+        for (int o = 0; o < off.n; ++o) {
+            if (off.z[o] > 0) sm.lists[0 * off.n + c[0]++] = (short)o;   // rows, top-down
+            if (off.x[o] > 0) sm.lists[1 * off.n + c[1]++] = (short)o;   // columns, left-right
+            if (off.x[o] < 0) sm.lists[2 * off.n + c[2]++] = (short)o;   // columns, right-left
+            if (off.z[o] < 0) sm.lists[3 * off.n + c[3]++] = (short)o;   // rows, bottom-up
+        }
+        for (int i = 0; i < 4; ++i) sm.counts[i] = c[i];
+    }
+
+    T* tau = static_cast<T*>(comp == 0 ? a.tauR : a.tauI) + static_cast<size_t>(field) * n;
+    int32_t* par = comp == 0 ? a.parR : a.parI;
+    if (par) par += static_cast<size_t>(field) * n;
+    const int64_t src = a.src[s];
+    for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
+    __syncthreads();
+
+    int used = -1;
+    for (int cycle = 0; cycle < a.max_cycles; ++cycle) {
+        sweep<T, TABLE>(sm, off, 0, 0, +1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
+        sweep<T, TABLE>(sm, off, 1, 1, +1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
+        sweep<T, TABLE>(sm, off, 2, 1, -1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
+        sweep<T, TABLE>(sm, off, 3, 0, -1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
+        if (!verify<T, TABLE>(sm, off, tau, a.cls, a.nx, a.nz, nk, comp, src, par)) {
+            used = cycle + 1;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) a.status[blockIdx.x] = used;
+}
+
+// ------------------------------------------------------------ raypaths
+// One thread per (field, receiver): walk the parents once to count the path
+// (bounded by cap), then again to write it source-first.
+__global__ void raypath_kernel(const int32_t* __restrict__ par, int n_fields, int64_t n_nodes,
+                               const int64_t* __restrict__ src, const int64_t* __restrict__ rcv,
+                               int n_rcv, int64_t cap, int64_t* __restrict__ paths,
+                               int64_t* __restrict__ len) {
+    const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= static_cast<long long>(n_fields) * n_rcv) return;
+    const int f = static_cast<int>(t / n_rcv);
+    const int32_t* p = par + static_cast<size_t>(f) * n_nodes;
+    const int64_t s = src[f];
+    int64_t node = rcv[t % n_rcv];
+    int64_t count = 0;
+    bool ok = node >= 0 && node < n_nodes;
+    while (ok) {
+        ++count;
+        if (node == s) break;
+        if (count >= cap) { ok = false; break; }
+        const int64_t nxt = p[node];
+        if (nxt < 0 || nxt >= n_nodes) { ok = false; break; }
+        node = nxt;
+    }
+    if (!ok) { len[t] = 0; return; }
+    len[t] = count;
+    node = rcv[t % n_rcv];
+    int64_t* out = paths + static_cast<size_t>(t) * cap;
+    for (int64_t q = count - 1; q >= 0; --q) {
+        out[q] = node;
+        if (q > 0) node = p[node];
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct WsLayout {
+    size_t sel, idx, src, status, total;
+};
+
+WsLayout ws_layout(int n_modes, int n_classes, int n_off, int precision, int n_sources) {
+    const size_t es = precision == CHERT_FP64 ? 8 : 4;
+    const size_t m = static_cast<size_t>(n_modes) * n_classes * n_off;
+    WsLayout w;
+    w.sel = 0;
+    w.idx = align256(2 * m * es);
+    w.src = w.idx + align256(m * 4);
+    w.status = w.src + align256(static_cast<size_t>(n_sources) * 8);
+    w.total = w.status + align256((static_cast<size_t>(n_sources) * n_modes * 2 + 1) * 4);
+    return w;
+}
+
+int fill_offsets(Offsets& o, const int32_t* offsets, int n_off, const char* who) {
+    CHERT_REQUIRE(offsets != nullptr, "%s: offsets is NULL", who);
+    CHERT_REQUIRE(n_off >= 1 && n_off <= kMaxOff, "%s: n_off=%d (1..%d)", who, n_off, kMaxOff);
+    o.n = n_off;
+    for (int i = 0; i < n_off; i++) {
+        const int32_t x = offsets[3 * i], y = offsets[3 * i + 1], z = offsets[3 * i + 2];
+        CHERT_REQUIRE(x || y || z, "%s: zero offset", who);
+        CHERT_REQUIRE(abs(x) < 32768 && abs(y) < 32768 && abs(z) < 32768, "%s: offset too large", who);
+        o.x[i] = (short)x; o.y[i] = (short)y; o.z[i] = (short)z;
+    }
+    return CHERT_OK;
+}
+
+}  // namespace
+}  // namespace chert
+
+using namespace chert;
+
+extern "C" int chert_edge_table(const chert_cache_arrays* cache, int n_modes, int n_classes,
+                                int n_dir, int precision, const int32_t* offsets, int n_off,
+                                int32_t* d_idx, void* d_Vsel, void* d_Asel, void* stream) {
+    CHERT_REQUIRE(cache && cache->V && cache->A && cache->rx && cache->rz && cache->flag,
+                  "chert_edge_table: cache arrays V, A, rx, rz, flag are required");
+    CHERT_REQUIRE(d_idx && d_Vsel && d_Asel, "chert_edge_table: NULL output");
+    CHERT_REQUIRE(n_modes >= 1 && n_classes >= 1 && n_dir >= 1, "chert_edge_table: bad counts");
+    Offsets off;
+    int rc = fill_offsets(off, offsets, n_off, "chert_edge_table");
+    if (rc) return rc;
+    const long long warps = static_cast<long long>(n_modes) * n_classes * n_off;
+    const unsigned blocks = static_cast<unsigned>((warps * 32 + 255) / 256);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == CHERT_FP64) {
+        edge_table_kernel<double><<<blocks, 256, 0, s>>>(
+            (const double*)cache->rx, (const double*)cache->rz, (const double*)cache->V,
+            (const double*)cache->A, cache->flag, n_modes, n_classes, n_dir, off, d_idx,
+            (double*)d_Vsel, (double*)d_Asel);
+    } else {
+        CHERT_REQUIRE(precision == CHERT_FP32 || precision == CHERT_MIXED,
+                      "chert_edge_table: precision=%d", precision);
+        edge_table_kernel<float><<<blocks, 256, 0, s>>>(
+            (const float*)cache->rx, (const float*)cache->rz, (const float*)cache->V,
+            (const float*)cache->A, cache->flag, n_modes, n_classes, n_dir, off, d_idx,
+            (float*)d_Vsel, (float*)d_Asel);
+    }
+    return launch_check("chert_edge_table");
+}
+
+extern "C" size_t chert_traveltime_workspace_bytes(int n_modes, int n_classes, int n_off,
+                                                   int precision, int n_sources) {
+    if (n_modes < 1 || n_classes < 1 || n_off < 1 || n_sources < 1) return 0;
+    return ws_layout(n_modes, n_classes, n_off, precision, n_sources).total;
+}
+
+template <typename T, bool TABLE>
+static int launch_relax(const FieldArgs& a, const Offsets& off, size_t smem, int blocks,
+                        cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(relax_kernel<T, TABLE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
+    relax_kernel<T, TABLE><<<blocks, 512, smem, s>>>(a, off);
+    return launch_check("chert_traveltime: relax");
+}
+
+extern "C" int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes,
+                                int n_dir, int nx, int ny, int nz, double dx,
+                                const int32_t* d_class_of_node, const int32_t* offsets, int n_off,
+                                const int64_t* sources, int n_sources, int precision,
+                                int max_cycles, void* d_tauR, void* d_tauI, int32_t* d_parR,
+                                int32_t* d_parI, void* d_workspace, size_t workspace_bytes,
+                                void* stream) {
+    CHERT_REQUIRE(ny == 1, "chert_traveltime: only 2D lattices (ny = 1) are supported");
+    CHERT_REQUIRE(nx >= 1 && nz >= 1 && (long long)nx * nz < (1LL << 31),
+                  "chert_traveltime: bad lattice %d x %d", nx, nz);
+    CHERT_REQUIRE(dx > 0, "chert_traveltime: dx must be positive");
+    CHERT_REQUIRE(d_class_of_node && sources && d_tauR && d_tauI && d_workspace,
+                  "chert_traveltime: NULL argument");
+    CHERT_REQUIRE(n_sources >= 1 && n_modes >= 1 && n_modes <= 3 && n_classes >= 1,
+                  "chert_traveltime: bad counts");
+    CHERT_REQUIRE(max_cycles >= 1, "chert_traveltime: max_cycles must be >= 1");
+    CHERT_REQUIRE(precision == CHERT_FP64 || precision == CHERT_FP32 || precision == CHERT_MIXED,
+                  "chert_traveltime: precision=%d", precision);
+    for (int i = 0; i < n_sources; i++)
+        CHERT_REQUIRE(sources[i] >= 0 && sources[i] < (int64_t)nx * nz,
+                      "chert_traveltime: source %d out of range", i);
+    Offsets off;
+    int rc = fill_offsets(off, offsets, n_off, "chert_traveltime");
+    if (rc) return rc;
+    int R = 0;
+    for (int i = 0; i < n_off; i++) {
+        CHERT_REQUIRE(off.y[i] == 0, "chert_traveltime: 2D offsets need oy = 0");
+        R = std::max(R, std::max(abs((int)off.x[i]), abs((int)off.z[i])));
+        bool has_neg = false;
+        for (int j = 0; j < n_off; j++)
+            if (off.x[j] == -off.x[i] && off.z[j] == -off.z[i]) has_neg = true;
+        CHERT_REQUIRE(has_neg, "chert_traveltime: offset set must be closed under negation");
+    }
+    const WsLayout ws = ws_layout(n_modes, n_classes, n_off, precision, n_sources);
+    if (workspace_bytes < ws.total) {
+        set_error("chert_traveltime: workspace %zu < %zu bytes", workspace_bytes, ws.total);
+        return CHERT_ENOMEM;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* w = static_cast<unsigned char*>(d_workspace);
+    const size_t es = precision == CHERT_FP64 ? 8 : 4;
+    const size_t m = static_cast<size_t>(n_modes) * n_classes * n_off;
+    void* Vsel = w + ws.sel;
+    void* Asel = w + ws.sel + m * es;
+    rc = chert_edge_table(cache, n_modes, n_classes, n_dir, precision, offsets, n_off,
+                          reinterpret_cast<int32_t*>(w + ws.idx), Vsel, Asel, stream);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(w + ws.src, sources, sizeof(int64_t) * n_sources,
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: sources copy");
+
+    int* bad_class = reinterpret_cast<int*>(w + ws.status) + (size_t)n_sources * n_modes * 2;
+    e = cudaMemsetAsync(bad_class, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: memset");
+    check_classes_kernel<<<296, 256, 0, s>>>(d_class_of_node, (long long)nx * nz, n_classes, bad_class);
+    rc = launch_check("chert_traveltime: class check");
+    if (rc) return rc;
+
+    FieldArgs a;
+    a.nx = nx; a.nz = nz; a.n_classes = n_classes; a.n_modes = n_modes;
+    a.n_sources = n_sources; a.max_cycles = max_cycles; a.ring = R + 2; a.dx = dx;
+    a.cls = d_class_of_node; a.src = reinterpret_cast<const int64_t*>(w + ws.src);
+    a.tauR = d_tauR; a.tauI = d_tauI; a.parR = d_parR; a.parI = d_parI;
+    a.Vsel = Vsel; a.Asel = Asel; a.status = reinterpret_cast<int*>(w + ws.status);
+    const int line_max = std::max(nx, nz);
+    const size_t common = n_off * es + (size_t)a.ring * line_max * (es + 4) + 4 * n_off * 2 + 32;
+    const size_t smem_table = (size_t)n_off * n_classes * n_classes * es + common;
+    const size_t smem_raw = (size_t)n_classes * n_off * es + common;
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const bool table = smem_table <= (size_t)std::min(smem_max, 120 * 1024);
+    CHERT_REQUIRE(table || smem_raw <= (size_t)smem_max,
+                  "chert_traveltime: %d classes x %d offsets do not fit in shared memory",
+                  n_classes, n_off);
+    const int blocks = n_sources * n_modes * 2;
+    if (precision == CHERT_FP64)
+        rc = table ? launch_relax<double, true>(a, off, smem_table, blocks, s)
+                   : launch_relax<double, false>(a, off, smem_raw, blocks, s);
+    else
+        rc = table ? launch_relax<float, true>(a, off, smem_table, blocks, s)
+                   : launch_relax<float, false>(a, off, smem_raw, blocks, s);
+    if (rc) return rc;
+    // convergence status: one int per CTA
+    int* host_status = static_cast<int*>(malloc(sizeof(int) * (blocks + 1)));
+    if (!host_status) { set_error("chert_traveltime: host malloc"); return CHERT_ENOMEM; }
+    e = cudaMemcpyAsync(host_status, a.status, sizeof(int) * (blocks + 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { free(host_status); return cuda_fail(e, "chert_traveltime: status"); }
+    int bad = -1;
+    for (int b = 0; b < blocks; b++) if (host_status[b] < 0) { bad = b; break; }
+    const int bad_cls = host_status[blocks];
+    free(host_status);
+    if (bad_cls) {
+        set_error("chert_traveltime: class map holds ids outside [0, %d)", n_classes);
+        return CHERT_EINVAL;
+    }
+    if (bad >= 0) {
+        set_error("chert_traveltime: field %d component %d did not converge in %d cycles",
+                  bad / 2, bad % 2, max_cycles);
+        return CHERT_ETIMEOUT;
+    }
+    return CHERT_OK;
+}
+
+extern "C" int chert_raypath(const int32_t* d_par, int n_fields, int64_t n_nodes,
+                             const int64_t* d_src, const int64_t* d_rcv, int n_rcv, int64_t cap,
+                             int64_t* d_paths, int64_t* d_len, void* stream) {
+    CHERT_REQUIRE(d_par && d_src && d_rcv && d_paths && d_len, "chert_raypath: NULL argument");
+    CHERT_REQUIRE(n_fields >= 1 && n_nodes >= 1 && n_rcv >= 1 && cap >= 1,
+                  "chert_raypath: bad counts");
+    const long long n = static_cast<long long>(n_fields) * n_rcv;
+    raypath_kernel<<<(unsigned)((n + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        d_par, n_fields, n_nodes, d_src, d_rcv, n_rcv, cap, d_paths, d_len);
+    return launch_check("chert_raypath");
+}

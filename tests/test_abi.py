@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+that include/chert.h declares; host-only entry points behave as documented."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from paper_2609_26108_b300 import build, chert
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "chert.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(chert_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return chert.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["chert_build_cache", "chert_traveltime", "chert_raypath", "chert_edge_table",
+                     "chert_thomsen_to_class", "chert_last_error", "chert_traveltime_workspace_bytes"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_thomsen_to_class_host_only(lib):
+    c = chert.thomsen_to_class(3000.0, 1500.0, 0.2, 0.1, 0.1, 60.0, 30.0, tilt=0.3)
+    assert list(c.aR)[2] == 9.0e6 and list(c.aR)[3] == 2.25e6
+    assert c.aI[0] == pytest.approx(c.aR[0] / 60.0) and c.aI[4] == pytest.approx(c.aR[4] / 30.0)
+    assert c.tilt == 0.3
+    # Thomsen's delta recovered from the stored moduli
+    a11, a13, a33, a44, a66 = list(c.aR)
+    d = ((a13 + a44) ** 2 - (a33 - a44) ** 2) / (2 * a33 * (a33 - a44))
+    assert d == pytest.approx(0.1, abs=1e-12)
+
+
+def test_thomsen_to_class_rejects_bad_input(lib):
+    with pytest.raises(chert.ChertError) as e:
+        chert.thomsen_to_class(1000.0, 1500.0, 0.2, 0.1, 0.1, 60.0, 30.0)
+    assert e.value.code == chert.EINVAL
+    with pytest.raises(chert.ChertError):
+        chert.thomsen_to_class(3000.0, 1500.0, 0.2, -0.9, 0.1, 60.0, 30.0)
+    assert "delta" in lib.chert_last_error().decode()
+
+
+def test_workspace_query(lib):
+    a = chert.workspace_bytes(3, 8, 80, chert.FP32, 64)
+    b = chert.workspace_bytes(3, 8, 80, chert.FP64, 64)
+    assert 0 < a < b and a % 256 == 0
+    assert chert.workspace_bytes(0, 8, 80, chert.FP32, 64) == 0
+
+
+def test_null_arguments_are_rejected_without_gpu(lib):
+    assert lib.chert_build_cache(None, 1, None, 1, None, None, None) == chert.EINVAL
+    assert lib.chert_raypath(None, 1, 10, None, None, 1, 4, None, None, None) == chert.EINVAL

@@ -1,0 +1,241 @@
+"""Parity of the CUDA lookup, relaxation, parents and raypaths with the oracle.
+
+Both sides read the same cache (the oracle's, cast to the path's precision),
+so every discrete decision -- the looked-up entry of each (mode, class, offset)
+-- is taken in the same precision on both sides and must agree exactly.
+Tolerances: FP64 traveltimes equal the oracle's to 1e-12 relative (the fixed
+point is unique; both sides add the same double increments) and parents are
+identical; FP32 traveltimes to 1e-5 relative, parents valid to that tolerance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cache_oracle as co
+from oracle import graph_oracle as go
+from paper_2609_26108_b300 import chert, inputs
+
+from helpers import DEG, cache_to_torch, mixed_layers, oracle_moduli
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    from paper_2609_26108_b300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+_small = {}
+
+
+def small_oracle_cache():
+    """Oracle cache of five classes, qP and qSV, 6 slowness angles per quadrant."""
+    if "c" not in _small:
+        mods, tilts = oracle_moduli(mixed_layers())
+        _small["c"] = co.build_cache(mods, tilts, ["qP", "qSV"], 6, "MEV", 0.02 * DEG, 1500)
+    return _small["c"]
+
+
+def as_cache(torch, cnp, precision):
+    prec = chert.PRECISION_IDS[precision]
+    dt = torch.float64 if prec == chert.FP64 else torch.float32
+    arr = cache_to_torch(cnp, dt, "cuda")
+    nm, nk, nd = cnp["V"].shape
+    return chert.Cache(arr, list(range(nm)), nk, nd // 4, prec)
+
+
+def oracle_fields(cnp, precision, shape, dx, cls, off, sources):
+    """tau and parents of the oracle, with the lookup taken in the path's precision."""
+    dt = np.float64 if precision == "fp64" else np.float32
+    cast = {k: (cnp[k].astype(dt).astype(np.float64) if k != "flag" else cnp[k]) for k in cnp}
+    nm = cnp["V"].shape[0]
+    out = {}
+    for m in range(nm):
+        idx, Vs, As = go.lookup_tables(cast, m, off, dtype=dt)
+        for s in sources:
+            out[(s, m, 0)] = go.dijkstra(shape, dx, cls, off, Vs, 0, s)
+            out[(s, m, 1)] = go.dijkstra(shape, dx, cls, off, As, 1, s)
+    return out
+
+
+def run_gpu(torch, cache, nx, nz, dx, cls, off, sources, max_cycles=64):
+    d_cls = torch.as_tensor(np.asarray(cls, dtype=np.int32), device="cuda")
+    tR, tI, pR, pI = chert.traveltime(cache, nx, nz, dx, d_cls, off, sources, max_cycles)
+    torch.cuda.synchronize()
+    return tR.cpu().numpy(), tI.cpu().numpy(), pR.cpu().numpy(), pI.cpu().numpy()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_edge_table_matches_oracle(torch_dev, precision):
+    cnp = small_oracle_cache()
+    cache = as_cache(torch_dev, cnp, precision)
+    off = inputs.stencil_2d(5)
+    idx, Vs, As = chert.edge_table(cache, off)
+    idx = idx.cpu().numpy()
+    dt = np.float64 if precision == "fp64" else np.float32
+    cast = {k: (cnp[k].astype(dt) if k != "flag" else cnp[k]) for k in cnp}
+    for m in range(2):
+        ref, rV, rA = go.lookup_tables(cast, m, off, dtype=dt)
+        assert np.array_equal(idx[m], ref)
+        assert np.array_equal(Vs[m].cpu().numpy(), rV.astype(dt))
+
+
+def _check_fields(g, ref, sources, nm, precision, shape, dx, cls, off, cnp):
+    tR, tI, pR, pI = g
+    for si, s in enumerate(sources):
+        for m in range(nm):
+            for comp, (t, p) in enumerate([(tR, pR), (tI, pI)]):
+                rt, rp = ref[(s, m, comp)]
+                gt, gp = t[si, m], p[si, m]
+                fin = np.isfinite(rt)
+                assert np.array_equal(np.isfinite(gt), fin)
+                assert np.array_equal(gp[~fin], rp[~fin])
+                if precision == "fp64":
+                    assert np.allclose(gt[fin], rt[fin], rtol=1e-12, atol=0)
+                    assert np.array_equal(gp, rp)
+                else:
+                    scale = np.max(rt[fin])
+                    err = np.abs(gt[fin] - rt[fin]) / np.maximum(rt[fin], 1e-3 * scale)
+                    assert np.max(err) < 1e-5, (s, m, comp, np.max(err))
+                    assert gp[s] == s
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_relaxation_layered_matches_oracle(torch_dev, precision):
+    nx, nz, dx = 61, 47, 10.0            # ragged, several sweep lines of each kind
+    cls = inputs.layered_class_map_2d(nx, nz, 5).astype(np.int32)
+    off = inputs.stencil_2d(5)
+    sources = [0, 30, nx * nz - 1, 23 + nx * 20]
+    cnp = small_oracle_cache()
+    cache = as_cache(torch_dev, cnp, precision)
+    g = run_gpu(torch_dev, cache, nx, nz, dx, cls, off, sources)
+    ref = oracle_fields(cnp, precision, (nx, 1, nz), dx, cls, off, sources)
+    _check_fields(g, ref, sources, 2, precision, (nx, 1, nz), dx, cls, off, cnp)
+
+
+def test_relaxation_random_classes_fp64(torch_dev):
+    nx, nz, dx = 37, 53, 7.5
+    cls = inputs.random_class_map_2d(nx, nz, 5, seed=9).astype(np.int32)
+    off = inputs.stencil_2d(3)
+    sources = [5, 1000]
+    cnp = small_oracle_cache()
+    g = run_gpu(torch_dev, as_cache(torch_dev, cnp, "fp64"), nx, nz, dx, cls, off, sources)
+    ref = oracle_fields(cnp, "fp64", (nx, 1, nz), dx, cls, off, sources)
+    _check_fields(g, ref, sources, 2, "fp64", (nx, 1, nz), dx, cls, off, cnp)
+
+
+def _synthetic_cache(Vk, Ak, M=8):
+    """Isotropic classes with given V and A (a lookup-only cache)."""
+    nd = 4 * M
+    th = (math.pi / 2) * np.arange(nd) / M
+    nk = len(Vk)
+    c = {"V": np.repeat(np.asarray(Vk, float)[None, :, None], nd, 2),
+         "A": np.repeat(np.asarray(Ak, float)[None, :, None], nd, 2),
+         "rx": np.tile(np.sin(th), (1, nk, 1)), "rz": np.tile(np.cos(th), (1, nk, 1)),
+         "theta": np.tile(th, (1, nk, 1)), "vartheta": np.zeros((1, nk, nd)),
+         "flag": np.zeros((1, nk, nd), np.uint8)}
+    c["Q"] = np.full_like(c["V"], np.inf)
+    return c
+
+
+def test_serpentine_channel_needs_several_cycles(torch_dev):
+    """A fast channel that winds down and up forces several sweep cycles; a cap
+    of one cycle must report CHERT_ETIMEOUT, a larger cap the oracle's field."""
+    nx, nz = 45, 30
+    cls = np.zeros((nz, nx), np.int32)
+    for c in range(5):
+        x0 = 2 + 9 * c
+        cls[1:nz - 1, x0:x0 + 3] = 1
+        row = nz - 3 if c % 2 == 0 else 1
+        if c < 4:
+            cls[row:row + 2, x0:x0 + 12] = 1
+    cls = cls.reshape(-1)
+    cnp = _synthetic_cache([150.0, 6000.0], [1e-3, 1e-5])
+    off = inputs.stencil_2d(2)
+    src = [2 + nx * 1]
+    cache = as_cache(torch_dev, cnp, "fp64")
+    d_cls = torch_dev.as_tensor(cls, device="cuda")
+    with pytest.raises(chert.ChertError) as e:
+        chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=1)
+    assert e.value.code == chert.ETIMEOUT
+    g = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, src)
+    ref = oracle_fields(cnp, "fp64", (nx, 1, nz), 10.0, cls, off, src)
+    _check_fields(g, ref, src, 1, "fp64", (nx, 1, nz), 10.0, cls, off, cnp)
+
+
+def test_unreachable_nodes_and_raypaths(torch_dev):
+    nx, nz = 20, 9
+    off = np.array([(2, 0, 0), (-2, 0, 0), (0, 0, 1), (0, 0, -1)], np.int32)
+    cls = np.zeros(nx * nz, np.int32)
+    cnp = _synthetic_cache([3000.0], [2e-5])
+    g = run_gpu(torch_dev, as_cache(torch_dev, cnp, "fp64"), nx, nz, 10.0, cls, off, [4])
+    tR, _, pR, _ = g
+    odd = (np.arange(nx * nz) % nx) % 2 == 1
+    assert np.all(np.isinf(tR[0, 0, odd])) and np.all(pR[0, 0, odd] == -1)
+    assert np.all(np.isfinite(tR[0, 0, ~odd]))
+    rcv = [4, 6 + nx * 8, 7, 18 + nx * 3]
+    paths, lens = chert.raypath(torch_dev.as_tensor(pR[0, 0], device="cuda"), [4], rcv, cap=64)
+    paths, lens = paths[0].cpu().numpy(), lens[0].cpu().numpy()
+    ref_tau, ref_par = go.dijkstra((nx, 1, nz), 10.0, cls, off, np.full((1, 4), 3000.0), 0, 4)
+    for r, node in enumerate(rcv):
+        want = go.raypath(ref_par, 4, node)
+        assert lens[r] == len(want)
+        assert list(paths[r, :lens[r]]) == want
+
+
+def test_pipeline_gpu_cache_to_traveltime_fp64(torch_dev):
+    """End to end on the GPU (cache build -> lookup -> relaxation -> raypaths)
+    against the oracle's own cache, lookup and Dijkstra."""
+    layers = mixed_layers()
+    mods, tilts = oracle_moduli(layers)
+    modes = ["qP", "qSH"]
+    cnp = co.build_cache(mods, tilts, modes, 9, "MEV", 0.02 * DEG, 1500)
+    d_cls = chert.classes_to_device(chert.classes_from_layers(layers))
+    cache = chert.build_cache(d_cls, len(layers), modes, 9, 0.02 * DEG, 1500, "MEV", "fp64")
+    nx, nz = 50, 41
+    cls = inputs.layered_class_map_2d(nx, nz, 5).astype(np.int32)
+    off = inputs.stencil_2d(5)
+    sources = [0, 25]
+    tR, tI, pR, pI = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, sources)
+    ref = oracle_fields(cnp, "fp64", (nx, 1, nz), 10.0, cls, off, sources)
+    for si, s in enumerate(sources):
+        for m in range(2):
+            for comp, t in enumerate([tR, tI]):
+                rt, _ = ref[(s, m, comp)]
+                assert np.allclose(t[si, m], rt, rtol=1e-9, atol=0)
+    rcv = [nx * nz - 1, nx * 20 + 3]
+    paths, lens = chert.raypath(torch_dev.as_tensor(pR.reshape(4, -1), device="cuda"),
+                                [0, 0, 25, 25], rcv, cap=256)
+    for f, (s, m) in enumerate([(0, 0), (0, 1), (25, 0), (25, 1)]):
+        _, rp = ref[(s, m, 0)]
+        for r, node in enumerate(rcv):
+            assert list(paths[f, r, :lens[f, r]].cpu().numpy()) == go.raypath(rp, s, node)
+
+
+def test_layered_tti_full_size_sampled_fields(torch_dev):
+    """The 401x401, 8-layer, 64-source, 3-mode launch that the benchmark
+    times, in FP32: sampled fields against the oracle (cache from the oracle
+    at a 0.1 deg scan step, the same cache on both sides)."""
+    model = inputs.layered_tti()
+    mods, tilts = oracle_moduli(model.layers)
+    cnp = co.build_cache(mods, tilts, ["qP", "qSV", "qSH"], 90, "MEV", 0.1 * DEG, 300)
+    off = inputs.stencil_2d(5)
+    cache = as_cache(torch_dev, cnp, "fp32")
+    cls = model.class_of_node.astype(np.int32)
+    g = run_gpu(torch_dev, cache, model.nx, model.nz, model.dx, cls, off, model.sources)
+    pick = [0, 31, 63]
+    ref = oracle_fields(cnp, "fp32", (model.nx, 1, model.nz), model.dx, cls, off,
+                        [int(model.sources[i]) for i in pick])
+    sub = tuple(x[pick] for x in g)
+    _check_fields(sub, ref, [int(model.sources[i]) for i in pick], 3, "fp32",
+                  (model.nx, 1, model.nz), model.dx, cls, off, cnp)
+    # reciprocity-free sanity that holds for every field: tau >= 0, source at 0
+    tR = g[0]
+    assert np.all(tR >= 0)
+    for si, s in enumerate(model.sources):
+        assert np.all(tR[si, :, s] == 0)

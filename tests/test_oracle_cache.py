@@ -83,11 +83,7 @@ def test_isotropic_viscoelastic_closed_form(kernel, mode):
     for th in [0.0, 0.2, 0.7, 1.1, math.pi / 2]:
         s = co.solve_direction(A, th, mode, kernel, H, K)
         assert s["flag"] == 0
-        # qSV and qSH are degenerate in an isotropic solid, where the eigenvector
-        # derivative of Eq. 14 is 0/0; the literal MEV form then carries
-        # rounding noise of that size into the residual.
-        tol = 1e-8 if (kernel == "MEV" and mode != "qP") else 1e-10
-        assert abs(s["vartheta"]) < tol
+        assert abs(s["vartheta"]) < 1e-10
         assert s["V"] == pytest.approx(1.0 / (1.0 / c).real, rel=1e-12)
         assert s["A"] == pytest.approx((1.0 / c).imag, rel=1e-9)
         assert np.allclose(s["r"], [math.sin(th), 0.0, math.cos(th)], atol=1e-12)
