@@ -49,8 +49,8 @@ SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 
 
-def workload():
-    model = inputs.layered_tti()
+def workload(n_sources=64):
+    model = inputs.layered_tti(n_sources=n_sources)
     off = inputs.stencil_2d(RADIUS)
     rcv = np.round(np.linspace(0, model.nx - 1, N_RECEIVERS)).astype(np.int64)   # surface row
     return model, off, rcv
@@ -62,7 +62,7 @@ def directed_edges(nx, nz, off):
 
 
 def config_dict(model, extra=None):
-    d = {"workload": "layered_visco_tti_2d_401x401_8layers_64src_3modes_1deg_R5",
+    d = {"workload": "layered_visco_tti_2d_401x401_8layers_%dsrc_3modes_1deg_R5" % len(model.sources),
          "nx": model.nx, "nz": model.nz, "dx_m": model.dx, "n_layers": len(model.layers),
          "n_sources": len(model.sources), "modes": MODES, "cache_deg": 90.0 / M_PER_QUADRANT,
          "kernel": "MEV", "scan_step_deg": 0.001, "stencil_radius": RADIUS,
@@ -141,7 +141,11 @@ def oracle_sample(model, off, n_solves=3, n_fields=2, seed=0):
     scales to the 2,184 distinct solves of the 8,640-entry cache; the
     relaxation part times `n_fields` (source, mode) fields, each tau^R and
     tau^I by binary-heap Dijkstra with parents."""
-    from threadpoolctl import threadpool_limits
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:                    # the oracle's numpy calls are 2x2 solves
+        import contextlib
+        threadpool_limits = lambda n: contextlib.nullcontext()   # noqa: E731
     from oracle import cache_oracle as co
     from oracle import graph_oracle as go
     rng = np.random.default_rng(seed)
@@ -217,7 +221,7 @@ def run_chert(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
-    model, off, rcv = workload()
+    model, off, rcv = workload(args.sources)
     classes = chert.classes_from_layers(model.layers)
     d_classes = chert.classes_to_device(classes)
     d_cls = torch.as_tensor(model.class_of_node.astype(np.int32), device="cuda")
@@ -322,6 +326,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="chert", choices=["chert", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sources", type=int, default=64,
+                    help="surface sources (64 = the benchmark workload; fewer only for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

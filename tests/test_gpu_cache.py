@@ -95,7 +95,8 @@ def test_cache_isotropic_closed_form(torch_dev):
     a11, a44 = M_ * (1 - 1j / 60), mu * (1 - 1j / 30)
     a13 = a11 - 2 * a44
     aR = [a11.real, a13.real, a11.real, a44.real, a44.real]
-    q = [60.0, a13.real / -a13.imag, 60.0, 30.0, 30.0]
+    q13 = math.inf if a13.imag == 0 else a13.real / -a13.imag
+    q = [60.0, q13, 60.0, 30.0, 30.0]
     layer = TableLayer(aR=tuple(aR), q=tuple(q))
     g = gpu_cache(torch_dev, "OEV", "fp64", [layer], ["qP", "qSH"], 9, H, K)
     for mi, a in enumerate([a11, a44]):
