@@ -378,62 +378,63 @@ static int launch_relax(const FieldArgs& a, const Offsets& off, size_t smem, int
     return launch_check("chert_traveltime: relax");
 }
 
-extern "C" int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes,
-                                int n_dir, int nx, int ny, int nz, double dx,
-                                const int32_t* d_class_of_node, const int32_t* offsets, int n_off,
-                                const int64_t* sources, int n_sources, int precision,
-                                int max_cycles, void* d_tauR, void* d_tauI, int32_t* d_parR,
-                                int32_t* d_parI, void* d_workspace, size_t workspace_bytes,
-                                void* stream) {
-    CHERT_REQUIRE(ny == 1, "chert_traveltime: only 2D lattices (ny = 1) are supported");
+// Validates the arguments and enqueues lookup, class check and relaxation on
+// `s`, using `w` (bytes long) as scratch.  On success *blocks_out is the number
+// of relaxation CTAs and *status_out points at their status words (followed by
+// the class-check flag), which the caller reads back.
+static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, int n_modes,
+                              int n_classes, int n_dir, int nx, int ny, int nz, double dx,
+                              const int32_t* d_class_of_node, const int32_t* offsets, int n_off,
+                              const int64_t* sources, int n_sources, int precision, int max_cycles,
+                              void* d_tauR, void* d_tauI, int32_t* d_parR, int32_t* d_parI,
+                              unsigned char* w, size_t bytes, cudaStream_t s, int* blocks_out,
+                              int** status_out) {
+    CHERT_REQUIRE(ny == 1, "%s: only 2D lattices (ny = 1) are supported", who);
     CHERT_REQUIRE(nx >= 1 && nz >= 1 && (long long)nx * nz < (1LL << 31),
-                  "chert_traveltime: bad lattice %d x %d", nx, nz);
-    CHERT_REQUIRE(dx > 0, "chert_traveltime: dx must be positive");
-    CHERT_REQUIRE(d_class_of_node && sources && d_tauR && d_tauI && d_workspace,
-                  "chert_traveltime: NULL argument");
+                  "%s: bad lattice %d x %d", who, nx, nz);
+    CHERT_REQUIRE(dx > 0, "%s: dx must be positive", who);
+    CHERT_REQUIRE(d_class_of_node && sources && d_tauR && d_tauI && w, "%s: NULL argument", who);
     CHERT_REQUIRE(n_sources >= 1 && n_modes >= 1 && n_modes <= 3 && n_classes >= 1,
-                  "chert_traveltime: bad counts");
-    CHERT_REQUIRE(max_cycles >= 1, "chert_traveltime: max_cycles must be >= 1");
+                  "%s: bad counts", who);
+    CHERT_REQUIRE(max_cycles >= 1, "%s: max_cycles must be >= 1", who);
     CHERT_REQUIRE(precision == CHERT_FP64 || precision == CHERT_FP32 || precision == CHERT_MIXED,
-                  "chert_traveltime: precision=%d", precision);
+                  "%s: precision=%d", who, precision);
     for (int i = 0; i < n_sources; i++)
         CHERT_REQUIRE(sources[i] >= 0 && sources[i] < (int64_t)nx * nz,
-                      "chert_traveltime: source %d out of range", i);
+                      "%s: source %d out of range", who, i);
     Offsets off;
-    int rc = fill_offsets(off, offsets, n_off, "chert_traveltime");
+    int rc = fill_offsets(off, offsets, n_off, who);
     if (rc) return rc;
     int R = 0;
     for (int i = 0; i < n_off; i++) {
-        CHERT_REQUIRE(off.y[i] == 0, "chert_traveltime: 2D offsets need oy = 0");
+        CHERT_REQUIRE(off.y[i] == 0, "%s: 2D offsets need oy = 0", who);
         R = std::max(R, std::max(abs((int)off.x[i]), abs((int)off.z[i])));
         bool has_neg = false;
         for (int j = 0; j < n_off; j++)
             if (off.x[j] == -off.x[i] && off.z[j] == -off.z[i]) has_neg = true;
-        CHERT_REQUIRE(has_neg, "chert_traveltime: offset set must be closed under negation");
+        CHERT_REQUIRE(has_neg, "%s: offset set must be closed under negation", who);
     }
     const WsLayout ws = ws_layout(n_modes, n_classes, n_off, precision, n_sources);
-    if (workspace_bytes < ws.total) {
-        set_error("chert_traveltime: workspace %zu < %zu bytes", workspace_bytes, ws.total);
+    if (bytes < ws.total) {
+        set_error("%s: workspace %zu < %zu bytes", who, bytes, ws.total);
         return CHERT_ENOMEM;
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    unsigned char* w = static_cast<unsigned char*>(d_workspace);
     const size_t es = precision == CHERT_FP64 ? 8 : 4;
     const size_t m = static_cast<size_t>(n_modes) * n_classes * n_off;
     void* Vsel = w + ws.sel;
     void* Asel = w + ws.sel + m * es;
     rc = chert_edge_table(cache, n_modes, n_classes, n_dir, precision, offsets, n_off,
-                          reinterpret_cast<int32_t*>(w + ws.idx), Vsel, Asel, stream);
+                          reinterpret_cast<int32_t*>(w + ws.idx), Vsel, Asel, s);
     if (rc) return rc;
     cudaError_t e = cudaMemcpyAsync(w + ws.src, sources, sizeof(int64_t) * n_sources,
                                     cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: sources copy");
+    if (e != cudaSuccess) return cuda_fail(e, "sources copy");
 
     int* bad_class = reinterpret_cast<int*>(w + ws.status) + (size_t)n_sources * n_modes * 2;
     e = cudaMemsetAsync(bad_class, 0, sizeof(int), s);
-    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: memset");
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
     check_classes_kernel<<<296, 256, 0, s>>>(d_class_of_node, (long long)nx * nz, n_classes, bad_class);
-    rc = launch_check("chert_traveltime: class check");
+    rc = launch_check("class check");
     if (rc) return rc;
 
     FieldArgs a;
@@ -451,8 +452,7 @@ extern "C" int chert_traveltime(const chert_cache_arrays* cache, int n_modes, in
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const bool table = smem_table <= (size_t)std::min(smem_max, 120 * 1024);
     CHERT_REQUIRE(table || smem_raw <= (size_t)smem_max,
-                  "chert_traveltime: %d classes x %d offsets do not fit in shared memory",
-                  n_classes, n_off);
+                  "%s: %d classes x %d offsets do not fit in shared memory", who, n_classes, n_off);
     const int blocks = n_sources * n_modes * 2;
     if (precision == CHERT_FP64)
         rc = table ? launch_relax<double, true>(a, off, smem_table, blocks, s)
@@ -461,26 +461,53 @@ extern "C" int chert_traveltime(const chert_cache_arrays* cache, int n_modes, in
         rc = table ? launch_relax<float, true>(a, off, smem_table, blocks, s)
                    : launch_relax<float, false>(a, off, smem_raw, blocks, s);
     if (rc) return rc;
-    // convergence status: one int per CTA
+    *blocks_out = blocks;
+    *status_out = a.status;
+    return CHERT_OK;
+}
+
+static int status_to_code(const char* who, int first_bad_block, int bad_class, int n_classes,
+                          int max_cycles) {
+    if (bad_class) {
+        set_error("%s: class map holds ids outside [0, %d)", who, n_classes);
+        return CHERT_EINVAL;
+    }
+    if (first_bad_block >= 0) {
+        set_error("%s: field %d component %d did not converge in %d cycles", who,
+                  first_bad_block / 2, first_bad_block % 2, max_cycles);
+        return CHERT_ETIMEOUT;
+    }
+    return CHERT_OK;
+}
+
+extern "C" int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes,
+                                int n_dir, int nx, int ny, int nz, double dx,
+                                const int32_t* d_class_of_node, const int32_t* offsets, int n_off,
+                                const int64_t* sources, int n_sources, int precision,
+                                int max_cycles, void* d_tauR, void* d_tauI, int32_t* d_parR,
+                                int32_t* d_parI, void* d_workspace, size_t workspace_bytes,
+                                void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int blocks = 0;
+    int* status = nullptr;
+    int rc = enqueue_traveltime("chert_traveltime", cache, n_modes, n_classes, n_dir, nx, ny, nz,
+                                dx, d_class_of_node, offsets, n_off, sources, n_sources, precision,
+                                max_cycles, d_tauR, d_tauI, d_parR, d_parI,
+                                static_cast<unsigned char*>(d_workspace), workspace_bytes, s,
+                                &blocks, &status);
+    if (rc) return rc;
+    // convergence status: one int per CTA, then the class-check flag
     int* host_status = static_cast<int*>(malloc(sizeof(int) * (blocks + 1)));
     if (!host_status) { set_error("chert_traveltime: host malloc"); return CHERT_ENOMEM; }
-    e = cudaMemcpyAsync(host_status, a.status, sizeof(int) * (blocks + 1), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaMemcpyAsync(host_status, status, sizeof(int) * (blocks + 1),
+                                    cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { free(host_status); return cuda_fail(e, "chert_traveltime: status"); }
     int bad = -1;
     for (int b = 0; b < blocks; b++) if (host_status[b] < 0) { bad = b; break; }
     const int bad_cls = host_status[blocks];
     free(host_status);
-    if (bad_cls) {
-        set_error("chert_traveltime: class map holds ids outside [0, %d)", n_classes);
-        return CHERT_EINVAL;
-    }
-    if (bad >= 0) {
-        set_error("chert_traveltime: field %d component %d did not converge in %d cycles",
-                  bad / 2, bad % 2, max_cycles);
-        return CHERT_ETIMEOUT;
-    }
-    return CHERT_OK;
+    return status_to_code("chert_traveltime", bad, bad_cls, n_classes, max_cycles);
 }
 
 extern "C" int chert_raypath(const int32_t* d_par, int n_fields, int64_t n_nodes,
