@@ -167,6 +167,37 @@ int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes
                      void* d_tauR, void* d_tauI, int32_t* d_parR, int32_t* d_parI,
                      void* d_workspace, size_t workspace_bytes, void* stream);
 
+/* The paper has no counterpart to this entry point; it exists for callers of
+ * this library that cannot allocate device memory: code embedded in a host
+ * whose device memory is owned by its own pool, code that runs while a stream
+ * is being captured (where cudaMalloc is not allowed), or a runtime that
+ * forbids allocation after start-up.  It computes exactly what
+ * chert_traveltime computes, with the same arguments minus the workspace, and
+ * allocates nothing: its scratch is a fixed 1 MiB array in device memory that
+ * libchert declares at file scope, so every device that loads the library
+ * holds that array until the process exits.
+ *   - Problems whose scratch (chert_traveltime_workspace_bytes) exceeds
+ *     chert_traveltime_static_limit() minus 256 bytes are rejected with
+ *     CHERT_EINVAL and a message naming both sizes.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (the parts that must start at zero are cleared by each call).  Calls
+ *     that overlap on the GPU -- on different streams or different host
+ *     threads -- race on it: serialise them.
+ * Errors: as chert_traveltime, CHERT_ENOMEM never. */
+int chert_traveltime_static(const chert_cache_arrays* cache, int n_modes, int n_classes,
+                            int n_dir, int nx, int ny, int nz, double dx,
+                            const int32_t* d_class_of_node, const int32_t* offsets,
+                            int n_off, const int64_t* sources, int n_sources,
+                            int precision, int max_cycles,
+                            void* d_tauR, void* d_tauI, int32_t* d_parR, int32_t* d_parI,
+                            void* stream);
+
+/* Size in bytes of chert_traveltime_static's scratch array. */
+size_t chert_traveltime_static_limit(void);
+
 /* ---- raypaths (Eq. 33-34) ------------------------------------------------ */
 
 /* Backtrack parents from receivers to sources for a batch of fields.  Field

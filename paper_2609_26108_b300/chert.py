@@ -71,8 +71,12 @@ def lib():
     L.chert_traveltime.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P, I,
                                    P, I, I, I, P, P, P, P, P, SZ, P]
     L.chert_raypath.argtypes = [P, I, I64, P, P, I, I64, P, P, P]
+    L.chert_traveltime_static.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P,
+                                          I, P, I, I, I, P, P, P, P, P]
+    L.chert_traveltime_static_limit.restype = SZ
+    L.chert_traveltime_static_limit.argtypes = []
     for name in ("chert_thomsen_to_class", "chert_build_cache", "chert_edge_table",
-                 "chert_traveltime", "chert_raypath"):
+                 "chert_traveltime", "chert_raypath", "chert_traveltime_static"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -240,6 +244,31 @@ def traveltime(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64, parent
                                   max_cycles, _dev_ptr(out[0]), _dev_ptr(out[1]), _dev_ptr(out[2]),
                                   _dev_ptr(out[3]), _dev_ptr(workspace), workspace.numel(),
                                   _stream_ptr(stream)))
+    return out
+
+
+def traveltime_static(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64, parents=True,
+                      stream=None, out=None):
+    """chert_traveltime_static: the relaxation without any device allocation by
+    the library (its scratch is a fixed array inside libchert).  Same results
+    and output layout as ``traveltime``; calls that overlap on the GPU race."""
+    torch = _torch()
+    off, off_p = _offsets_arr(offsets)
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64).reshape(-1))
+    nm, ns = len(cache.modes), len(src)
+    dev = cache["V"].device
+    shape = (ns, nm, nx * nz)
+    if out is None:
+        fd = _fdtype(cache.precision)
+        out = (torch.empty(shape, dtype=fd, device=dev), torch.empty(shape, dtype=fd, device=dev),
+               torch.empty(shape, dtype=torch.int32, device=dev) if parents else None,
+               torch.empty(shape, dtype=torch.int32, device=dev) if parents else None)
+    st = cache.struct()
+    _check(lib().chert_traveltime_static(ctypes.byref(st), nm, cache.n_classes, cache.n_dir, nx, 1, nz,
+                                         float(dx), _dev_ptr(d_cls), off_p, len(off),
+                                         src.ctypes.data_as(ctypes.c_void_p), ns, cache.precision,
+                                         max_cycles, _dev_ptr(out[0]), _dev_ptr(out[1]),
+                                         _dev_ptr(out[2]), _dev_ptr(out[3]), _stream_ptr(stream)))
     return out
 
 

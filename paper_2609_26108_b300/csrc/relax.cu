@@ -18,7 +18,10 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <limits.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -508,6 +511,96 @@ extern "C" int chert_traveltime(const chert_cache_arrays* cache, int n_modes, in
     const int bad_cls = host_status[blocks];
     free(host_status);
     return status_to_code("chert_traveltime", bad, bad_cls, n_classes, max_cycles);
+}
+
+// ------------------------------------------------------------------------
+// chert_traveltime_static: the same relaxation for callers that must not
+// allocate device memory (an allocator-free embedding, code that runs while a
+// stream is being captured, a host that has handed all device memory to its
+// own pool).  Its scratch is the file-scope array below instead of a
+// caller-provided workspace; every device that loads libchert keeps the array
+// for the life of the process.
+namespace chert {
+namespace {
+constexpr size_t kStaticScratchBytes = size_t(1) << 20;     // 1 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device, looked up once
+// per device (the host-side symbol is not a device address).
+int static_scratch(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime_static: cudaGetDevice");
+    CHERT_REQUIRE(dev >= 0 && dev < kMaxDevices, "chert_traveltime_static: device %d", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (g_static_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime_static: cudaGetSymbolAddress");
+        g_static_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_static_ptr[dev]);
+    return CHERT_OK;
+}
+
+// One block: summary[0] = first CTA that hit the cycle cap (or -1),
+// summary[1] = class-check flag.  Written on every call.
+__global__ void status_summary_kernel(const int* __restrict__ status, int n_blocks,
+                                      int* __restrict__ summary) {
+    __shared__ int first;
+    if (threadIdx.x == 0) first = INT_MAX;
+    __syncthreads();
+    for (int b = threadIdx.x; b < n_blocks; b += blockDim.x)
+        if (status[b] < 0) atomicMin(&first, b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        summary[0] = first == INT_MAX ? -1 : first;
+        summary[1] = status[n_blocks];
+    }
+}
+}  // namespace
+}  // namespace chert
+
+extern "C" size_t chert_traveltime_static_limit(void) { return chert::kStaticScratchBytes; }
+
+extern "C" int chert_traveltime_static(const chert_cache_arrays* cache, int n_modes, int n_classes,
+                                       int n_dir, int nx, int ny, int nz, double dx,
+                                       const int32_t* d_class_of_node, const int32_t* offsets,
+                                       int n_off, const int64_t* sources, int n_sources,
+                                       int precision, int max_cycles, void* d_tauR, void* d_tauI,
+                                       int32_t* d_parR, int32_t* d_parI, void* stream) {
+    CHERT_REQUIRE(n_modes >= 1 && n_classes >= 1 && n_off >= 1 && n_sources >= 1,
+                  "chert_traveltime_static: bad counts");
+    const size_t need = ws_layout(n_modes, n_classes, n_off, precision, n_sources).total;
+    const size_t summary_at = kStaticScratchBytes - 256;
+    CHERT_REQUIRE(need <= summary_at,
+                  "chert_traveltime_static: this problem needs %zu bytes of scratch; the static "
+                  "scratch holds %zu (use chert_traveltime with a workspace)",
+                  need, summary_at);
+    unsigned char* w = nullptr;
+    int rc = static_scratch(&w);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int blocks = 0;
+    int* status = nullptr;
+    rc = enqueue_traveltime("chert_traveltime_static", cache, n_modes, n_classes, n_dir, nx, ny, nz,
+                            dx, d_class_of_node, offsets, n_off, sources, n_sources, precision,
+                            max_cycles, d_tauR, d_tauI, d_parR, d_parI, w, summary_at, s, &blocks,
+                            &status);
+    if (rc) return rc;
+    int* summary = reinterpret_cast<int*>(w + summary_at);
+    status_summary_kernel<<<1, 256, 0, s>>>(status, blocks, summary);
+    rc = launch_check("chert_traveltime_static: status");
+    if (rc) return rc;
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, summary, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime_static: status");
+    return status_to_code("chert_traveltime_static", h[0], h[1], n_classes, max_cycles);
 }
 
 extern "C" int chert_raypath(const int32_t* d_par, int n_fields, int64_t n_nodes,
