@@ -24,6 +24,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "relax_fast.cuh"
 
 namespace chert {
 namespace {
@@ -381,6 +382,67 @@ static int launch_relax(const FieldArgs& a, const Offsets& off, size_t smem, int
     return launch_check("chert_traveltime: relax");
 }
 
+// ---- dispatch to the kernel specialised for the standard stencil ----------
+// If the caller's offsets are exactly the standard radius-R stencil (in any
+// order), map[q] receives the caller's index of stencil entry q.
+template <int R>
+static bool standard_map(const Offsets& off, short* map) {
+    constexpr fast::Stencil<R> st{};
+    if (off.n != fast::Stencil<R>::N) return false;
+    for (int q = 0; q < fast::Stencil<R>::N; ++q) {
+        int found = -1;
+        for (int i = 0; i < off.n; ++i)
+            if (off.x[i] == st.x[q] && off.z[i] == st.z[q] && off.y[i] == 0) { found = i; break; }
+        if (found < 0) return false;
+        map[q] = (short)found;
+    }
+    return true;
+}
+
+template <int R>
+static size_t fast_smem(int nk, int line_max, size_t es) {
+    const size_t LS = ((line_max + 2 * R) + 3) & ~3;
+    return (size_t)nk * nk * fast::Stencil<R>::N * es + 16 * LS * (es + 4) +
+           4 * fast::Stencil<R>::N + 64;
+}
+
+template <typename T, int R, int PPT>
+static int launch_fast_ppt(const fast::Args& a, size_t smem, int blocks, int threads, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(fast::relax_fast_kernel<T, R, PPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "relaxation: smem attribute");
+    fast::relax_fast_kernel<T, R, PPT><<<blocks, threads, smem, s>>>(a);
+    return launch_check("relaxation");
+}
+
+// Returns 1 if the specialised kernel was launched, 0 if the caller must use
+// the generic one, or a negative status.
+template <typename T, int R>
+static int try_fast_R(fast::Args& a, const Offsets& off, int line_max, int smem_max, int blocks,
+                      cudaStream_t s) {
+    if (!standard_map<R>(off, a.map)) return 0;
+    const size_t smem = fast_smem<R>(a.n_classes, line_max, sizeof(T));
+    if (smem > (size_t)smem_max || line_max > 2048) return 0;
+    const int ppt = line_max <= 512 ? 1 : (line_max <= 1024 ? 2 : 4);
+    const int threads = ((line_max + ppt - 1) / ppt + 31) / 32 * 32;
+    const int rc = ppt == 1 ? launch_fast_ppt<T, R, 1>(a, smem, blocks, threads, s)
+                 : ppt == 2 ? launch_fast_ppt<T, R, 2>(a, smem, blocks, threads, s)
+                            : launch_fast_ppt<T, R, 4>(a, smem, blocks, threads, s);
+    return rc ? rc : 1;
+}
+
+template <typename T>
+static int try_fast(fast::Args& a, const Offsets& off, int R, int line_max, int smem_max, int blocks,
+                    cudaStream_t s) {
+    switch (R) {
+        case 2: return try_fast_R<T, 2>(a, off, line_max, smem_max, blocks, s);
+        case 3: return try_fast_R<T, 3>(a, off, line_max, smem_max, blocks, s);
+        case 4: return try_fast_R<T, 4>(a, off, line_max, smem_max, blocks, s);
+        case 5: return try_fast_R<T, 5>(a, off, line_max, smem_max, blocks, s);
+        default: return 0;
+    }
+}
+
 // Validates the arguments and enqueues lookup, class check and relaxation on
 // `s`, using `w` (bytes long) as scratch.  On success *blocks_out is the number
 // of relaxation CTAs and *status_out points at their status words (followed by
@@ -457,7 +519,17 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     CHERT_REQUIRE(table || smem_raw <= (size_t)smem_max,
                   "%s: %d classes x %d offsets do not fit in shared memory", who, n_classes, n_off);
     const int blocks = n_sources * n_modes * 2;
-    if (precision == CHERT_FP64)
+    fast::Args fa;
+    fa.nx = nx; fa.nz = nz; fa.n_classes = n_classes; fa.n_modes = n_modes;
+    fa.max_cycles = max_cycles; fa.dx = dx; fa.cls = a.cls; fa.src = a.src;
+    fa.tauR = d_tauR; fa.tauI = d_tauI; fa.parR = d_parR; fa.parI = d_parI;
+    fa.Vsel = Vsel; fa.Asel = Asel; fa.n_off = n_off; fa.status = a.status;
+    const int fr = precision == CHERT_FP64
+                       ? try_fast<double>(fa, off, R, line_max, smem_max, blocks, s)
+                       : try_fast<float>(fa, off, R, line_max, smem_max, blocks, s);
+    if (fr < 0) return fr;
+    if (fr == 1) rc = CHERT_OK;
+    else if (precision == CHERT_FP64)
         rc = table ? launch_relax<double, true>(a, off, smem_table, blocks, s)
                    : launch_relax<double, false>(a, off, smem_raw, blocks, s);
     else

@@ -129,6 +129,20 @@ def test_relaxation_random_classes_fp64(torch_dev):
     _check_fields(g, ref, sources, 2, "fp64", (nx, 1, nz), dx, cls, off, cnp)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_relaxation_generic_stencil_matches_oracle(torch_dev, precision):
+    """A stencil that is not the standard radius-R set runs the generic kernel."""
+    nx, nz, dx = 45, 38, 10.0
+    cls = inputs.layered_class_map_2d(nx, nz, 5).astype(np.int32)
+    extra = np.array([(4, 0, 1), (-4, 0, -1), (4, 0, -1), (-4, 0, 1)], np.int32)
+    off = np.concatenate([inputs.stencil_2d(3), extra])
+    sources = [3, nx * nz - 7]
+    cnp = small_oracle_cache()
+    g = run_gpu(torch_dev, as_cache(torch_dev, cnp, precision), nx, nz, dx, cls, off, sources)
+    ref = oracle_fields(cnp, precision, (nx, 1, nz), dx, cls, off, sources)
+    _check_fields(g, ref, sources, 2, precision, (nx, 1, nz), dx, cls, off, cnp)
+
+
 def _synthetic_cache(Vk, Ak, M=8):
     """Isotropic classes with given V and A (a lookup-only cache)."""
     nd = 4 * M
