@@ -1,9 +1,11 @@
-// Directional cache build: one warp per (mode, class, folded slowness angle).
+// Directional cache build: one warp per (mode, class, folded slowness angle),
+// and a second launch that gives the few solves with a far (or no) root a
+// whole CTA.
 //
 // For the folded real slowness angle theta in [0, pi/2] (the 0-90 deg TI range
 // of the cache, Eq. 26) the warp searches the imaginary angle vartheta that makes
 // the complex energy velocity homogeneous (Eq. 9): it walks the grid
-// vartheta_k = k*h outward from 0, 16 points per side per step (one per lane),
+// vartheta_k = k*h outward from 0, 64 points per side per step (4 per lane),
 // finds sign changes of the residual with a ballot, polishes each candidate by
 // 33-way subdivision (one point per lane per round) and keeps the first
 // decaying root in order of |vartheta|.  Walking outward and stopping at the
@@ -111,7 +113,7 @@ __device__ __forceinline__ T residual(const Medium<T>& m, T s, T c, T vt, int mo
 
 template <typename T>
 struct RayQ {
-    T V, A, Q, rx, rz;
+    T V, A, Q, rx, rz, vr, vi;
     bool ok;
 };
 
@@ -131,20 +133,25 @@ __device__ __forceinline__ RayQ<T> ray_quantities(const Medium<T>& m, T s, T c, 
     q.A = fmax(-vi / mag2, T(0));
     q.Q = vi == T(0) ? T(INFINITY) : -(vr * vr - vi * vi) / (T(2) * vr * vi);
     q.ok = vi <= T(kAcceptTol) * vr;
+    q.vr = vr;
+    q.vi = vi;
     return q;
 }
 
-// 33-way subdivision of the bracket [lo, hi] (f(lo) has sign flo): every
-// round each lane evaluates one interior point and the warp keeps the first
-// sub-interval with a sign change.  All lanes return the same root.
+// 33-way subdivision of the bracket [lo, hi] (residuals flo, fhi at its ends):
+// every round each lane evaluates one interior point and the warp keeps the
+// first sub-interval with a sign change, until the bracket is narrower than
+// `stop` or than the precision allows; a final secant step inside the last
+// bracket then places the root (its error is of the order of the squared
+// bracket width).  All lanes return the same root.
 template <typename T>
-__device__ T polish(const Medium<T>& m, T s, T c, int mode, int kernel, T lo, T hi, T flo,
-                    int lane) {
+__device__ T polish(const Medium<T>& m, T s, T c, int mode, int kernel, T lo, T hi, T flo, T fhi,
+                    int lane, T stop) {
+    const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(2.3e-16);
     for (int round = 0; round < 12; ++round) {
         const T width = hi - lo;
-        if (!(width > T(kPolishTol))) break;
-        if (width <= T(2) * (sizeof(T) == 4 ? T(1.2e-7) : T(2.3e-16)) * fmax(fabs(lo), fabs(hi)))
-            break;
+        if (!(width > stop) || !(width > T(kPolishTol))) break;
+        if (width <= T(2) * eps * fmax(fabs(lo), fabs(hi))) break;
         const T x = lo + width * T(lane + 1) / T(33);
         const T fx = residual(m, s, c, x, mode, kernel);
         const bool chg = (fx == T(0)) || (signbit(fx) != signbit(flo));
@@ -165,8 +172,44 @@ __device__ T polish(const Medium<T>& m, T s, T c, int mode, int kernel, T lo, T 
             flo = fp;
         }
         hi = xi;
+        fhi = fi;
+    }
+    if (flo != fhi && isfinite(flo) && isfinite(fhi)) {
+        const T r = lo - flo * (hi - lo) / (fhi - flo);
+        if (r >= lo && r <= hi) return r;
     }
     return T(0.5) * (lo + hi);
+}
+
+// Double refinement of a float root r32 that lies in the grid bracket
+// [glo, ghi]: one 33-point round on [r32 - d, r32 + d] in double (lanes 0 and
+// 32's neighbour evaluate the ends), then a secant step.  If the ends do not
+// bracket a sign change in double, fall back to polishing the grid bracket.
+__device__ double refine_double(const Medium<double>& m, double s, double c, int mode, int kernel,
+                                double r32, double glo, double ghi, int lane) {
+    const double d = 1e-8 + 16.0 * 1.2e-7 * fabs(r32);
+    const double a = fmax(glo, r32 - d), b = fmin(ghi, r32 + d);
+    const double x = a + (b - a) * double(lane) / 31.0;          // lane 0: a, lane 31: b
+    const double fx = residual(m, s, c, x, mode, kernel);
+    const double fa = __shfl_sync(0xffffffffu, fx, 0), fb = __shfl_sync(0xffffffffu, fx, 31);
+    if (fa == 0.0) return a;
+    if (fb == 0.0) return b;
+    if (signbit(fa) == signbit(fb)) {
+        const double flo = residual(m, s, c, glo, mode, kernel);
+        const double fhi = residual(m, s, c, ghi, mode, kernel);
+        if (flo == 0.0) return glo;
+        if (fhi == 0.0) return ghi;
+        if (signbit(flo) == signbit(fhi)) return r32;        // no double sign change: keep float root
+        return polish(m, s, c, mode, kernel, glo, ghi, flo, fhi, lane, 1e-9);
+    }
+    const bool chg = (fx == 0.0) || (signbit(fx) != signbit(fa));
+    const unsigned mask = __ballot_sync(0xffffffffu, chg) & ~1u;
+    const int i = __ffs(mask) - 1;                             // first lane past a sign change
+    const double xi = __shfl_sync(0xffffffffu, x, i), fi = __shfl_sync(0xffffffffu, fx, i);
+    const double xp = __shfl_sync(0xffffffffu, x, i - 1), fp = __shfl_sync(0xffffffffu, fx, i - 1);
+    if (fi == 0.0) return xi;
+    const double r = xp - fp * (xi - xp) / (fi - fp);
+    return (r >= xp && r <= xi) ? r : 0.5 * (xp + xi);
 }
 
 struct Outs {
@@ -184,6 +227,180 @@ __device__ __forceinline__ void put(void* p, size_t i, double v) {
     if (p) reinterpret_cast<TO*>(p)[i] = TO(v);
 }
 
+constexpr int kPending = 2;          // flag value between the two launches
+constexpr int kPhase1Reach = 2048;   // grid points per side scanned by the first launch
+
+// One solve: (mode, class, folded angle index j), its medium and angle.
+template <typename TS, typename TP>
+struct Solve {
+    int mi, k, j, mode;
+    chert_class cls;
+    Medium<TS> ms;
+    Medium<TP> mp;
+    double sd, cd;
+    TS ss, cs;
+    TP sp, cp;
+};
+
+template <typename TS, typename TP>
+__device__ __forceinline__ Solve<TS, TP> make_solve(const chert_class* classes, int n_classes,
+                                                     const ModeList& modes, int M, long long idx) {
+    Solve<TS, TP> v;
+    const int per = M + 1;
+    v.j = static_cast<int>(idx % per);
+    v.k = static_cast<int>((idx / per) % n_classes);
+    v.mi = static_cast<int>(idx / (static_cast<long long>(per) * n_classes));
+    v.mode = modes.m[v.mi];
+    v.cls = classes[v.k];
+    v.ms = load_medium<TS>(v.cls);
+    v.mp = load_medium<TP>(v.cls);
+    const double theta = (M_PI / 2 * v.j) / M;
+    sincos(theta, &v.sd, &v.cd);
+    v.ss = TS(v.sd); v.cs = TS(v.cd);
+    v.sp = TP(v.sd); v.cp = TP(v.cd);
+    return v;
+}
+
+// Outward scan of the grid distances kk in [k_begin, k_end] on both sides by
+// one warp.  fb_pos / fb_neg are the residuals at +-(k_begin-1)h.  Candidates
+// are taken in order of |vartheta| (brackets at inner distance kk-1 before the
+// exact zeros at kk; on one key the smaller polished |vartheta|, the negative
+// root on a tie); returns true with the first decaying root.
+template <typename TS, typename TP>
+__device__ bool scan_window(const Solve<TS, TP>& v, int kernel, double h, int k_begin, int k_end,
+                            TS fb_pos, TS fb_neg, int lane, TP& root, RayQ<TP>& fq) {
+    constexpr bool mixed = sizeof(TS) != sizeof(TP);
+    constexpr int P = 4;     // consecutive grid points per lane per step
+    const int mode = v.mode;
+    TS prev_pos = fb_pos, prev_neg = fb_neg;
+    for (int base = k_begin - 1; base < k_end; base += 16 * P) {
+        const bool neg = lane >= 16;
+        const int l16 = lane & 15;
+        TS fv[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int kk = base + 1 + l16 * P + p;
+            const double xk = (neg ? -static_cast<double>(kk) : static_cast<double>(kk)) * h;
+            fv[p] = kk <= k_end ? residual(v.ms, v.ss, v.cs, TS(xk), mode, kernel) : TS(NAN);
+        }
+        TS before = __shfl_up_sync(0xffffffffu, fv[P - 1], 1);    // point just inside
+        if (l16 == 0) before = neg ? prev_neg : prev_pos;
+        unsigned bm[P], zm[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const TS fprev = p == 0 ? before : fv[p - 1];
+            bm[p] = __ballot_sync(0xffffffffu, fprev * fv[p] < TS(0));
+            zm[p] = __ballot_sync(0xffffffffu, fv[p] == TS(0));
+        }
+        prev_pos = __shfl_sync(0xffffffffu, fv[P - 1], 15);
+        prev_neg = __shfl_sync(0xffffffffu, fv[P - 1], 31);
+        unsigned anyb = 0, anyz = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) { anyb |= bm[p]; anyz |= zm[p]; }
+        unsigned lanes = (anyb | anyz);
+        lanes = (lanes | (lanes >> 16)) & 0xffffu;
+        while (lanes) {
+            const int l = __ffs(lanes) - 1;
+            lanes &= lanes - 1;
+            for (int p = 0; p < P; ++p) {
+                const double kkl = static_cast<double>(base + 1 + l * P + p);
+                TP cand[2];
+                bool cok[2] = {false, false};
+                RayQ<TP> cq[2];
+                for (int side = 0; side < 2; ++side) {      // 0: negative, 1: positive
+                    const int ln = side ? l : 16 + l;
+                    if (!((bm[p] >> ln) & 1u)) continue;
+                    const TS fcur = __shfl_sync(0xffffffffu, fv[p], ln);
+                    const TS fin = __shfl_sync(0xffffffffu, p == 0 ? before : fv[p > 0 ? p - 1 : 0], ln);
+                    const TS fl = side ? fin : fcur, fh = side ? fcur : fin;
+                    const double glo = side ? (kkl - 1.0) * h : -kkl * h;
+                    const double ghi = side ? kkl * h : -(kkl - 1.0) * h;
+                    // polish in the scan precision (float for FP32 and MIXED)
+                    const TS rs = polish(v.ms, v.ss, v.cs, mode, kernel, TS(glo), TS(ghi), fl, fh, lane,
+                                         sizeof(TS) == 8 ? TS(1e-9) : TS(0));
+                    TP r = TP(rs);
+                    if constexpr (mixed) {
+                        // drop clearly growing roots in float; decide the rest in double
+                        const RayQ<TS> q32 = ray_quantities(v.ms, v.ss, v.cs, rs, mode, kernel);
+                        if (!(q32.vi <= TS(1e-4) * q32.vr)) continue;
+                        r = refine_double(v.mp, v.sd, v.cd, mode, kernel, double(rs), glo, ghi, lane);
+                    }
+                    cq[side] = ray_quantities(v.mp, v.sp, v.cp, r, mode, kernel);
+                    cand[side] = r;
+                    cok[side] = cq[side].ok;
+                }
+                if (cok[0] || cok[1]) {
+                    const int pick = (cok[0] && cok[1]) ? (fabs(cand[1]) < fabs(cand[0]) ? 1 : 0)
+                                                        : (cok[0] ? 0 : 1);
+                    root = cand[pick];
+                    fq = cq[pick];
+                    return true;
+                }
+                for (int side = 0; side < 2; ++side) {   // negative first
+                    const int ln = side ? l : 16 + l;
+                    if (!((zm[p] >> ln) & 1u)) continue;
+                    const TP r = side ? TP(kkl * h) : TP(-kkl * h);
+                    const RayQ<TP> q = ray_quantities(v.mp, v.sp, v.cp, r, mode, kernel);
+                    if (q.ok) { root = r; fq = q; return true; }
+                }
+            }
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ size_t entry_index(int mi, int k, int n_classes, int M, int d) {
+    return (static_cast<size_t>(mi) * n_classes + k) * (4 * M) + d;
+}
+
+// Write the up to four mirrored entries of a folded solve (lanes 0..3), the
+// ray direction reflected into the quadrant of theta_d, then rotated by the
+// tilt (Eq. 36).
+template <typename TS, typename TP, typename TO>
+__device__ void write_entries(const Outs& out, const Solve<TS, TP>& v, int n_classes, int M,
+                              bool found, TP root, const RayQ<TP>& q, int lane) {
+    const int j = v.j;
+    int d, sx, sz, cnt;
+    if (j == 0) {
+        cnt = 2;
+        d = lane == 0 ? 0 : 2 * M; sx = lane == 0 ? 1 : -1; sz = sx;
+    } else if (j == M) {
+        cnt = 2;
+        d = lane == 0 ? M : 3 * M; sx = lane == 0 ? 1 : -1; sz = -sx;
+    } else {
+        cnt = 4;
+        d = lane == 0 ? j : lane == 1 ? 2 * M - j : lane == 2 ? 2 * M + j : 4 * M - j;
+        sx = lane < 2 ? 1 : -1;
+        sz = (lane == 0 || lane == 3) ? 1 : -1;
+    }
+    if (lane >= cnt) return;
+    const size_t e = entry_index(v.mi, v.k, n_classes, M, d);
+    double ct, st;
+    sincos(v.cls.tilt, &st, &ct);
+    put<TO>(out.theta, e, (M_PI / 2 * d) / M + v.cls.tilt);
+    if (found) {
+        const double lx = sx * double(q.rx), lz = sz * double(q.rz);
+        put<TO>(out.rx, e, lx * ct + lz * st);
+        put<TO>(out.rz, e, -lx * st + lz * ct);
+        put<TO>(out.V, e, double(q.V));
+        put<TO>(out.A, e, double(q.A));
+        put<TO>(out.Q, e, double(q.Q));
+        put<TO>(out.vartheta, e, double(root) * sx * sz);
+        out.flag[e] = 0;
+    } else {
+        put<TO>(out.rx, e, NAN);
+        put<TO>(out.rz, e, NAN);
+        put<TO>(out.V, e, NAN);
+        put<TO>(out.A, e, NAN);
+        put<TO>(out.Q, e, NAN);
+        put<TO>(out.vartheta, e, NAN);
+        out.flag[e] = 1;
+    }
+}
+
+// First launch: one warp per solve scans the first kPhase1Reach grid points per
+// side (the bulk of the roots lie there); solves that need a longer scan are
+// left marked kPending for the second launch.
 // TS: scan precision, TP: polish + ray-quantity precision, TO: storage.
 template <typename TS, typename TP, typename TO>
 __global__ void __launch_bounds__(256) cache_build_kernel(const chert_class* __restrict__ classes,
@@ -191,146 +408,74 @@ __global__ void __launch_bounds__(256) cache_build_kernel(const chert_class* __r
                                                           double h, int K, int kernel, Outs out) {
     const int lane = threadIdx.x & 31;
     const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int per = M + 1;
-    const long long total = static_cast<long long>(modes.n) * n_classes * per;
+    const long long total = static_cast<long long>(modes.n) * n_classes * (M + 1);
     if (warp >= total) return;
-    const int j = static_cast<int>(warp % per);
-    const int k = static_cast<int>((warp / per) % n_classes);
-    const int mi = static_cast<int>(warp / (static_cast<long long>(per) * n_classes));
-    const int mode = modes.m[mi];
-    const chert_class cls = classes[k];
-    const Medium<TS> ms = load_medium<TS>(cls);
-    const Medium<TP> mp = load_medium<TP>(cls);
-    const double theta = (M_PI / 2 * j) / M;
-    double sd, cd;
-    sincos(theta, &sd, &cd);
-    const TS ss = TS(sd), cs = TS(cd);
-    const TP sp = TP(sd), cp = TP(cd);
-    const bool mixed = sizeof(TS) != sizeof(TP);
-
-    // ---- walk the grid outward from vartheta = 0 ----
+    const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, M, warp);
     bool found = false;
     TP root = TP(0);
-    const TS f0 = residual(ms, ss, cs, TS(0), mode, kernel);
+    RayQ<TP> fq{};
+    const TS f0 = residual(v.ms, v.ss, v.cs, TS(0), v.mode, kernel);
     if (f0 == TS(0)) {
-        const RayQ<TP> q = ray_quantities(mp, sp, cp, TP(0), mode, kernel);
-        if (q.ok) found = true;
+        const RayQ<TP> q = ray_quantities(v.mp, v.sp, v.cp, TP(0), v.mode, kernel);
+        if (q.ok) { found = true; fq = q; }
     }
-    TS prev_pos = f0, prev_neg = f0;
-    for (int base = 0; !found && base < K; base += 16) {
-        const int kk = base + 1 + (lane & 15);
-        const bool neg = lane >= 16;
-        const bool valid = kk <= K;
-        const double xk = (neg ? -static_cast<double>(kk) : static_cast<double>(kk)) * h;
-        const TS f = valid ? residual(ms, ss, cs, TS(xk), mode, kernel) : TS(NAN);
-        TS fprev = __shfl_up_sync(0xffffffffu, f, 1);
-        if ((lane & 15) == 0) fprev = neg ? prev_neg : prev_pos;
-        const bool br = valid && (fprev * f < TS(0));
-        const bool zr = valid && (f == TS(0));
-        unsigned bmask = __ballot_sync(0xffffffffu, br);
-        unsigned zmask = __ballot_sync(0xffffffffu, zr);
-        prev_pos = __shfl_sync(0xffffffffu, f, 15);
-        prev_neg = __shfl_sync(0xffffffffu, f, 31);
-        while (!found && (bmask | zmask)) {
-            const unsigned any = (bmask | zmask);
-            const int l = __ffs((any | (any >> 16)) & 0xffffu) - 1;
-            const double kkl = static_cast<double>(base + 1 + l);
-            // brackets at inner distance kk-1 (key 2kk-1), then zeros at kk (key 2kk)
-            TP cand[2];
-            bool cok[2] = {false, false};
-            for (int side = 0; side < 2; ++side) {      // 0: negative, 1: positive
-                const int ln = side ? l : 16 + l;
-                if (!((bmask >> ln) & 1u)) continue;
-                const TS fl = __shfl_sync(0xffffffffu, side ? fprev : f, ln);
-                TP lo = side ? TP((kkl - 1.0) * h) : TP(-kkl * h);
-                TP hi = side ? TP(kkl * h) : TP(-(kkl - 1.0) * h);
-                TP flo = TP(fl);
-                bool usable = true;
-                if (mixed) {
-                    // re-take the bracket signs in the polish precision; if the
-                    // root sits within float noise of a grid point, step one cell
-                    const TP h2 = TP(h);
-                    TP xs = lo - h2 + TP(lane & 3) * h2;     // lo-h, lo, hi, hi+h
-                    if (lane >= 4) xs = lo;
-                    const TP fx = residual(mp, sp, cp, xs, mode, kernel);
-                    const TP fa = __shfl_sync(0xffffffffu, fx, 0), fb = __shfl_sync(0xffffffffu, fx, 1);
-                    const TP fc = __shfl_sync(0xffffffffu, fx, 2), fd = __shfl_sync(0xffffffffu, fx, 3);
-                    if (fb * fc < TP(0)) {
-                        flo = fb;
-                    } else if (fb == TP(0) || fc == TP(0)) {
-                        lo = hi = (fb == TP(0)) ? lo : hi;
-                    } else if (fa * fb < TP(0)) {
-                        hi = lo; lo = lo - h2; flo = fa;
-                    } else if (fc * fd < TP(0)) {
-                        lo = hi; hi = hi + h2; flo = fc;
-                    } else {
-                        usable = false;
-                    }
-                }
-                if (!usable) continue;
-                const TP r = (lo == hi) ? lo : polish(mp, sp, cp, mode, kernel, lo, hi, flo, lane);
-                const RayQ<TP> q = ray_quantities(mp, sp, cp, r, mode, kernel);
-                cand[side] = r;
-                cok[side] = q.ok;
-            }
-            if (cok[0] || cok[1]) {
-                found = true;
-                if (cok[0] && cok[1]) root = (fabs(cand[1]) < fabs(cand[0])) ? cand[1] : cand[0];
-                else root = cok[0] ? cand[0] : cand[1];
-                break;
-            }
-            for (int side = 0; side < 2 && !found; ++side) {   // negative first
-                const int ln = side ? l : 16 + l;
-                if (!((zmask >> ln) & 1u)) continue;
-                const TP r = side ? TP(kkl * h) : TP(-kkl * h);
-                const RayQ<TP> q = ray_quantities(mp, sp, cp, r, mode, kernel);
-                if (q.ok) { found = true; root = r; }
-            }
-            bmask &= ~((1u << l) | (1u << (16 + l)));
-            zmask &= ~((1u << l) | (1u << (16 + l)));
-        }
+    const int reach = min(K, kPhase1Reach);
+    if (!found) found = scan_window(v, kernel, h, 1, reach, f0, f0, lane, root, fq);
+    if (!found && K > reach) {
+        if (lane == 0) out.flag[entry_index(v.mi, v.k, n_classes, M, v.j)] = kPending;
+        return;
     }
+    write_entries<TS, TP, TO>(out, v, n_classes, M, found, root, fq, lane);
+}
 
-    // ---- write the mirrored entries ----
-    RayQ<TP> q{};
-    if (found) q = ray_quantities(mp, sp, cp, root, mode, kernel);
-    const int nd = 4 * M;
-    int d[4], sxv[4], szv[4], cnt;
-    if (j == 0) {
-        cnt = 2; d[0] = 0; sxv[0] = 1; szv[0] = 1; d[1] = 2 * M; sxv[1] = -1; szv[1] = -1;
-    } else if (j == M) {
-        cnt = 2; d[0] = M; sxv[0] = 1; szv[0] = -1; d[1] = 3 * M; sxv[1] = -1; szv[1] = 1;
-    } else {
-        cnt = 4;
-        d[0] = j;         sxv[0] = 1;  szv[0] = 1;
-        d[1] = 2 * M - j; sxv[1] = 1;  szv[1] = -1;
-        d[2] = 2 * M + j; sxv[2] = -1; szv[2] = -1;
-        d[3] = 4 * M - j; sxv[3] = -1; szv[3] = 1;
+// Second launch: one 1024-thread CTA per pending solve.  Each round its 32
+// warps scan consecutive 64-point slices of grid distance (2048 per side per
+// round); the nearest slice with a decaying root wins.
+template <typename TS, typename TP, typename TO>
+__global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* __restrict__ classes,
+                                                            int n_classes, ModeList modes, int M,
+                                                            double h, int K, int kernel, Outs out) {
+    const long long idx = blockIdx.x;
+    const int per = M + 1;
+    {
+        const int j = static_cast<int>(idx % per);
+        const int k = static_cast<int>((idx / per) % n_classes);
+        const int mi = static_cast<int>(idx / (static_cast<long long>(per) * n_classes));
+        if (out.flag[entry_index(mi, k, n_classes, M, j)] != kPending) return;
     }
-    if (lane < cnt) {
-        const size_t e = (static_cast<size_t>(mi) * n_classes + k) * nd + d[lane];
-        double ct, st;
-        sincos(cls.tilt, &st, &ct);
-        const double sx = sxv[lane], sz = szv[lane];
-        put<TO>(out.theta, e, (M_PI / 2 * d[lane]) / M + cls.tilt);
-        if (found) {
-            const double lx = sx * double(q.rx), lz = sz * double(q.rz);
-            put<TO>(out.rx, e, lx * ct + lz * st);
-            put<TO>(out.rz, e, -lx * st + lz * ct);
-            put<TO>(out.V, e, double(q.V));
-            put<TO>(out.A, e, double(q.A));
-            put<TO>(out.Q, e, double(q.Q));
-            put<TO>(out.vartheta, e, double(root) * sx * sz);
-            out.flag[e] = 0;
-        } else {
-            put<TO>(out.rx, e, NAN);
-            put<TO>(out.rz, e, NAN);
-            put<TO>(out.V, e, NAN);
-            put<TO>(out.A, e, NAN);
-            put<TO>(out.Q, e, NAN);
-            put<TO>(out.vartheta, e, NAN);
-            out.flag[e] = 1;
+    __shared__ int s_found[32];
+    __shared__ double s_root[32];
+    __shared__ RayQ<TP> s_q[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, M, idx);
+    constexpr int slice = 64;
+    int winner = -1;
+    for (int r0 = kPhase1Reach; r0 < K && winner < 0; r0 += 32 * slice) {
+        const int kb = r0 + w * slice + 1, ke = min(K, r0 + (w + 1) * slice);
+        bool found = false;
+        TP root = TP(0);
+        RayQ<TP> q{};
+        if (kb <= ke) {
+            const double xb = (kb - 1) * h;
+            const TS fp = residual(v.ms, v.ss, v.cs, TS(xb), v.mode, kernel);
+            const TS fn = residual(v.ms, v.ss, v.cs, TS(-xb), v.mode, kernel);
+            found = scan_window(v, kernel, h, kb, ke, fp, fn, lane, root, q);
         }
+        if (lane == 0) {
+            s_found[w] = found;
+            s_root[w] = double(root);
+            s_q[w] = q;
+        }
+        __syncthreads();
+        for (int i = 0; i < 32; ++i)
+            if (s_found[i]) { winner = i; break; }
+        __syncthreads();
+    }
+    if (w == 0) {
+        const bool found = winner >= 0;
+        const TP root = found ? TP(s_root[winner]) : TP(0);
+        const RayQ<TP> q = found ? s_q[winner] : RayQ<TP>{};
+        write_entries<TS, TP, TO>(out, v, n_classes, M, found, root, q, lane);
     }
 }
 
@@ -368,18 +513,28 @@ extern "C" int chert_build_cache(const chert_class* d_classes, int n_classes, co
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double h = params->scan_step;
     const int K = params->scan_half;
+    const unsigned solves = (unsigned)warps;
     switch (params->precision) {
         case CHERT_FP64:
             cache_build_kernel<double, double, double><<<(unsigned)blocks, threads, 0, s>>>(
                 d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
+            if (K > kPhase1Reach)
+                cache_finish_kernel<double, double, double><<<solves, 1024, 0, s>>>(
+                    d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
             break;
         case CHERT_FP32:
             cache_build_kernel<float, float, float><<<(unsigned)blocks, threads, 0, s>>>(
                 d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
+            if (K > kPhase1Reach)
+                cache_finish_kernel<float, float, float><<<solves, 1024, 0, s>>>(
+                    d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
             break;
         case CHERT_MIXED:
             cache_build_kernel<float, double, float><<<(unsigned)blocks, threads, 0, s>>>(
                 d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
+            if (K > kPhase1Reach)
+                cache_finish_kernel<float, double, float><<<solves, 1024, 0, s>>>(
+                    d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
             break;
         default:
             CHERT_REQUIRE(false, "chert_build_cache: precision=%d", params->precision);

@@ -402,7 +402,7 @@ static bool standard_map(const Offsets& off, short* map) {
 template <int R>
 static size_t fast_smem(int nk, int line_max, size_t es) {
     const size_t LS = ((line_max + 2 * R) + 3) & ~3;
-    return (size_t)nk * nk * fast::Stencil<R>::N * es + 16 * LS * (es + 4) +
+    return (size_t)nk * nk * fast::Stencil<R>::N * es + 16 * LS * (2 * es) +
            4 * fast::Stencil<R>::N + 64;
 }
 

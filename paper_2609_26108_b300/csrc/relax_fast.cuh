@@ -90,11 +90,18 @@ struct Args {
     short map[128];            // stencil index -> caller offset index
 };
 
+// One ring element: the node's tau and its class id pre-multiplied by nk*N,
+// read by a single 8-byte (float) or 16-byte (double) shared load.
+template <typename T>
+struct alignas(2 * sizeof(T)) Cell {
+    T tau;
+    int ck;
+};
+
 template <typename T>
 struct Ctx {
     T* W;            // [nk][nk][N]: W[(ki*nk + kj)*N + q]
-    T* rt;           // tau ring   [16][LS]
-    int* rc;         // class ring [16][LS], ids pre-multiplied by nk*N
+    Cell<T>* ring;   // [16][LS]
     short* sx;       // stencil offsets (for decoding the winning parent)
     short* sz;
     int LS, nx, nz, nk;
@@ -113,7 +120,7 @@ __device__ void sweep(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __res
     const int len = AXIS == 0 ? c.nx : c.nz;
     const int nx = c.nx;
     const int tid = threadIdx.x, bd = blockDim.x;
-    for (int i = tid; i < 8 * c.LS; i += bd) { c.rt[i] = T(INFINITY); c.rc[i] = 0; }
+    for (int i = tid; i < 8 * c.LS; i += bd) c.ring[i] = Cell<T>{T(INFINITY), 0};
     __syncthreads();
     T cur[PPT];
     int kr[PPT];
@@ -134,14 +141,9 @@ __device__ void sweep(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __res
         T nxt[PPT];
         int nkr[PPT];
         if (step + 1 < n_lines) load(DIR > 0 ? line + 1 : line - 1, nxt, nkr);
-        const T* pt[R + 1];
-        const int* pc[R + 1];
+        const Cell<T>* pt[R + 1];
 #pragma unroll
-        for (int lag = 1; lag <= R; ++lag) {
-            const int slot = ((line - DIR * lag) & 7) * c.LS + R;
-            pt[lag] = c.rt + slot;
-            pc[lag] = c.rc + slot;
-        }
+        for (int lag = 1; lag <= R; ++lag) pt[lag] = c.ring + ((line - DIR * lag) & 7) * c.LS + R;
         const int own = (line & 7) * c.LS + R;
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
@@ -155,13 +157,11 @@ __device__ void sweep(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __res
                     constexpr int ol = AXIS == 0 ? Table<R>::v.x[q] : Table<R>::v.z[q];
                     if constexpr (oa * DIR > 0) {
                         constexpr int lag = oa * DIR;
-                        const T ti = pt[lag][u - ol];
-                        const int ci = pc[lag][u - ol];
-                        best = fmin_(best, ti + Wj[ci + q]);
+                        const Cell<T> ci = pt[lag][u - ol];
+                        best = fmin_(best, ci.tau + Wj[ci.ck + q]);
                     }
                 });
-                c.rt[own + u] = best;
-                c.rc[own + u] = kr[p] * c.nk * N;
+                c.ring[own + u] = Cell<T>{best, kr[p] * c.nk * N};
                 if (best < cur[p]) {
                     const size_t j = AXIS == 0 ? (size_t)u + (size_t)nx * line : (size_t)line + (size_t)nx * u;
                     tau[j] = best;
@@ -183,7 +183,7 @@ __device__ bool verify(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __re
     constexpr int N = Stencil<R>::N;
     const int nx = c.nx, nz = c.nz;
     const int tid = threadIdx.x, bd = blockDim.x;
-    for (int i = tid; i < 16 * c.LS; i += bd) { c.rt[i] = T(INFINITY); c.rc[i] = 0; }
+    for (int i = tid; i < 16 * c.LS; i += bd) c.ring[i] = Cell<T>{T(INFINITY), 0};
     __syncthreads();
     auto store_row = [&](int row) {          // global row -> ring (inf beyond the lattice)
         const int base = (row & 15) * c.LS + R;
@@ -193,11 +193,9 @@ __device__ bool verify(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __re
             if (x < nx) {
                 if (row < nz) {
                     const size_t j = (size_t)x + (size_t)nx * row;
-                    c.rt[base + x] = tau[j];
-                    c.rc[base + x] = min(max(cls[j], 0), c.nk - 1) * c.nk * N;
+                    c.ring[base + x] = Cell<T>{tau[j], min(max(cls[j], 0), c.nk - 1) * c.nk * N};
                 } else {
-                    c.rt[base + x] = T(INFINITY);
-                    c.rc[base + x] = 0;
+                    c.ring[base + x] = Cell<T>{T(INFINITY), 0};
                 }
             }
         }
@@ -207,28 +205,25 @@ __device__ bool verify(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __re
     for (int z = 0; z < nz; ++z) {
         store_row(z + R);
         __syncthreads();
-        const T* pt[2 * R + 1];
-        const int* pc[2 * R + 1];
+        const Cell<T>* pt[2 * R + 1];
 #pragma unroll
-        for (int d = -R; d <= R; ++d) {        // row z - d
-            const int slot = ((z - d) & 15) * c.LS + R;
-            pt[d + R] = c.rt + slot;
-            pc[d + R] = c.rc + slot;
-        }
+        for (int d = -R; d <= R; ++d) pt[d + R] = c.ring + ((z - d) & 15) * c.LS + R;   // row z - d
         const int own = (z & 15) * c.LS + R;
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
             const int x = tid + p * bd;
             if (x < nx) {
-                const T cur = c.rt[own + x];
-                const int kj = c.rc[own + x] / (c.nk * N);
+                const Cell<T> me = c.ring[own + x];
+                const T cur = me.tau;
+                const int kj = me.ck / (c.nk * N);
                 const T* Wj = c.W + kj * N;
                 T best = T(INFINITY);
                 int bq = -1;
                 static_for<N>([&](auto qc) {
                     constexpr int q = decltype(qc)::value;
                     constexpr int oz = Table<R>::v.z[q], ox = Table<R>::v.x[q];
-                    const T cand = pt[oz + R][x - ox] + Wj[pc[oz + R][x - ox] + q];
+                    const Cell<T> ci = pt[oz + R][x - ox];
+                    const T cand = ci.tau + Wj[ci.ck + q];
                     if (cand < best) { best = cand; bq = q; }
                 });
                 const size_t j = (size_t)x + (size_t)nx * z;
@@ -263,8 +258,7 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
     c.LS = ((line_max + 2 * R) + 3) & ~3;
     unsigned char* p = smem_raw;
     c.W = reinterpret_cast<T*>(p); p += (size_t)nk * nk * N * sizeof(T);
-    c.rt = reinterpret_cast<T*>(p); p += (size_t)16 * c.LS * sizeof(T);
-    c.rc = reinterpret_cast<int*>(p); p += (size_t)16 * c.LS * sizeof(int);
+    c.ring = reinterpret_cast<Cell<T>*>(p); p += (size_t)16 * c.LS * sizeof(Cell<T>);
     c.sx = reinterpret_cast<short*>(p); p += N * sizeof(short);
     c.sz = reinterpret_cast<short*>(p);
 
