@@ -211,7 +211,7 @@ def run_reference(args):
 def run_chert(args):
     import torch
     import torch.distributed as dist
-    from paper_2609_26108_b300 import build, chert
+    from paper_2609_26108_b300 import build, chert, replicas
     from paper_2609_26108_b300.pipeline import Tracer
 
     rank = int(os.environ.get("RANK", "0"))
@@ -251,14 +251,10 @@ def run_chert(args):
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     cache_ms = [e[0].elapsed_time(e[1]) for e in ev]
     relax_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
     nf = len(model.sources) * len(MODES)
     entries = len(classes) * len(MODES) * 4 * M_PER_QUADRANT
-    value = world * nf * args.steps / (total_ms / 1e3)
+    value, slowest_s = replicas.job_throughput(sum(step_ms) / 1e3, nf * args.steps, device="cuda")
+    total_ms = 1e3 * slowest_s
 
     # end to end: pinned host inputs in, both traveltime fields out, per step
     h_classes = d_classes.cpu().pin_memory()
@@ -274,10 +270,7 @@ def run_chert(args):
         t0 = time.perf_counter()
         tr.run_host(h_classes, h_cls, model.sources, h_tauR, h_tauI)
         e2e_times.append(time.perf_counter() - t0)
-    t = torch.tensor([sum(e2e_times)], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * nf * args.steps / float(t.item())
+    e2e_value, _ = replicas.job_throughput(sum(e2e_times), nf * args.steps, device="cuda")
 
     # roofline of the dominant kernel (relaxation): algorithmic work = one
     # relaxation (add + min: 2 FP32 ops) per directed edge per field component
