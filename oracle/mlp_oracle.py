@@ -1,0 +1,161 @@
+"""FP64 oracle of the cache surrogate -- TEST INFRASTRUCTURE ONLY.
+
+Only tests, the smoke check and the benchmark's CPU-baseline leg may call this.
+
+The surrogate replaces the homogeneity solve of one cache entry (the paper's
+Eq. 9-11 at a folded slowness angle) by a small network: per wave mode an MLP
+7 -> 256 -> 256 -> 256 -> 256 -> 5 with SiLU hidden activations predicts a
+correction to the exact *elastic* ray quantities of the same medium.  This
+module restates, in plain numpy double precision:
+
+* ``elastic_baseline``  the elastic phase velocity of the real moduli (the
+  eigenvalue of the 2x2 x-z Christoffel block, or a66 sin^2 + a44 cos^2 for
+  qSH), its angular derivative by a complex step, and from them the group
+  velocity Vg = sqrt(V^2 + V'^2) and ray angle psi = theta + atan2(V', V).
+* ``features`` / ``encode_targets`` / ``decode``  the fixed input scaling and
+  the output parametrisation (V/Vg - 1, A*Vg, psi - psi_el, validity logit,
+  vartheta).
+* ``forward`` / ``backward`` / ``adam``  the network, the gradient of the
+  masked mean-square + logistic loss, and Adam with bias correction.
+
+Parity status: forward and backward are pinned by finite differences and by
+explicit loops; the baseline is pinned by the oracle's own exact cache in the
+elastic limit.  The learned weights have no pin: they are an approximation
+whose error the tests measure against the exact cache.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+N_IN, N_HID, N_LAYERS, N_OUT = 7, 256, 4, 5
+# fixed input ranges (the training range of the seeded TTI media)
+IN_LO = np.array([0.0, 0.49, 0.04, -0.11, 0.0, 0.004, 0.004])
+IN_HI = np.array([math.pi / 2, 0.6, 0.31, 0.21, 0.21, 0.051, 0.051])
+
+
+def elastic_baseline(aR, theta, mode):
+    """Elastic group velocity and ray angle (x from +z toward +x) for real
+    moduli aR = (a11, a13, a33, a44, a66) at slowness angles theta."""
+    a11, a13, a33, a44, a66 = [float(v) for v in aR]
+    h = 1e-30
+
+    def phase(t):
+        s2, c2 = np.sin(t) ** 2, np.cos(t) ** 2
+        if mode == "qSH":
+            lam = a66 * s2 + a44 * c2
+        else:
+            g11 = a11 * s2 + a44 * c2
+            g33 = a44 * s2 + a33 * c2
+            g13 = (a13 + a44) * np.sin(t) * np.cos(t)
+            root = np.sqrt((g11 - g33) ** 2 + 4 * g13 * g13)
+            lam = 0.5 * (g11 + g33 + (root if mode == "qP" else -root))
+        return np.sqrt(lam)
+
+    z = np.asarray(theta, dtype=np.float64) + 1j * h
+    Vc = phase(z)
+    V, dV = Vc.real, Vc.imag / h
+    return np.sqrt(V * V + dV * dV), np.asarray(theta) + np.arctan2(dV, V)
+
+
+def features(theta_fold, rs, eps, delta, gamma, inv_qp, inv_qs):
+    """Inputs scaled to [-1, 1] over the training range; also returns the
+    mask of samples outside that range."""
+    x = np.stack([theta_fold, rs, eps, delta, gamma, inv_qp, inv_qs], axis=-1).astype(np.float64)
+    u = 2.0 * (x - IN_LO) / (IN_HI - IN_LO) - 1.0
+    outside = np.any(np.abs(u) > 1.0, axis=-1)
+    return u, outside
+
+
+def encode_targets(V, A, psi, flag, vartheta, Vg, psi_el):
+    """Network targets: (V/Vg - 1, A*Vg, psi - psi_el, valid, vartheta)."""
+    valid = (np.asarray(flag) == 0)
+    t = np.zeros(np.shape(V) + (N_OUT,))
+    t[..., 0] = np.where(valid, V / Vg - 1.0, 0.0)
+    t[..., 1] = np.where(valid, A * Vg, 0.0)
+    t[..., 2] = np.where(valid, np.angle(np.exp(1j * (psi - psi_el))), 0.0)
+    t[..., 3] = valid.astype(np.float64)
+    t[..., 4] = np.where(valid, vartheta, 0.0)
+    return t
+
+
+def init_params(seed):
+    """He-style initialisation; W[l] is [out, in], b[l] is [out]."""
+    rng = np.random.default_rng(seed)
+    sizes = [N_IN] + [N_HID] * N_LAYERS + [N_OUT]
+    W, b = [], []
+    for fan_in, fan_out in zip(sizes[:-1], sizes[1:]):
+        W.append(rng.normal(0.0, math.sqrt(2.0 / fan_in), (fan_out, fan_in)))
+        b.append(np.zeros(fan_out))
+    return W, b
+
+
+def silu(x):
+    return x / (1.0 + np.exp(-x))
+
+
+def dsilu(x):
+    s = 1.0 / (1.0 + np.exp(-x))
+    return s * (1.0 + x * (1.0 - s))
+
+
+def forward(W, b, x):
+    """Returns the output and the pre-activations of every layer."""
+    pre, h = [], x
+    for l in range(len(W)):
+        z = h @ W[l].T + b[l]
+        pre.append(z)
+        h = silu(z) if l < len(W) - 1 else z
+    return h, pre
+
+
+def loss_and_grad(W, b, x, target, out_mean, out_std):
+    """Mean over the batch of: sum over outputs 0,1,2,4 of ((y - t')^2)/2 on
+    valid samples (t' = standardised target) + logistic loss of output 3.
+    Returns (loss, dW, db)."""
+    y, pre = forward(W, b, x)
+    n = x.shape[0]
+    valid = target[:, 3] > 0.5
+    tstd = (target - out_mean) / out_std
+    g = np.zeros_like(y)
+    loss = 0.0
+    for k in (0, 1, 2, 4):
+        d = np.where(valid, y[:, k] - tstd[:, k], 0.0)
+        loss += 0.5 * np.sum(d * d)
+        g[:, k] = d
+    p = 1.0 / (1.0 + np.exp(-y[:, 3]))
+    loss += np.sum(np.logaddexp(0.0, y[:, 3]) - target[:, 3] * y[:, 3])
+    g[:, 3] = p - target[:, 3]
+    loss /= n
+    g /= n
+    dW, db = [None] * len(W), [None] * len(W)
+    for l in reversed(range(len(W))):
+        h_in = x if l == 0 else silu(pre[l - 1])
+        dW[l] = g.T @ h_in
+        db[l] = g.sum(axis=0)
+        if l > 0:
+            g = (g @ W[l]) * dsilu(pre[l - 1])
+    return loss, dW, db
+
+
+def adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update with bias correction (in place); step counts from 1."""
+    for p, g, mm, vv in zip(params, grads, m, v):
+        mm *= beta1
+        mm += (1 - beta1) * g
+        vv *= beta2
+        vv += (1 - beta2) * g * g
+        mhat = mm / (1 - beta1 ** step)
+        vhat = vv / (1 - beta2 ** step)
+        p -= lr * mhat / (np.sqrt(vhat) + eps)
+
+
+def decode(y, out_mean, out_std, Vg, psi_el):
+    """Network output -> (V, A, psi, p_valid, vartheta)."""
+    t = y * out_std + out_mean
+    V = Vg * (1.0 + t[..., 0])
+    A = t[..., 1] / Vg
+    psi = psi_el + t[..., 2]
+    p_valid = 1.0 / (1.0 + np.exp(-y[..., 3]))
+    return V, A, psi, p_valid, t[..., 4]
