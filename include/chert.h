@@ -167,6 +167,62 @@ int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes
                      void* d_tauR, void* d_tauI, int32_t* d_parR, int32_t* d_parI,
                      void* d_workspace, size_t workspace_bytes, void* stream);
 
+/* ---- cache surrogate (spec pattern 4; no counterpart in the paper) -
+ * One MLP per wave mode, 7 -> 256 -> 256 -> 256 -> 256 -> 5 with SiLU hidden
+ * activations, BF16 operands, FP32 accumulation and FP32 master weights.  It
+ * predicts the correction of a cache entry (the homogeneity solve of Eq. 9-11
+ * at a folded slowness angle theta in [0, pi/2]) to the exact elastic ray
+ * quantities of the same medium:
+ *   inputs  x = (theta, Vs0/Vp0, eps, delta, gamma, 1/Qp, 1/Qs), each scaled to
+ *           [-1, 1] over the training range (theta in [0, pi/2], Vs0/Vp0 in
+ *           [0.49, 0.6], eps in [0.04, 0.31], delta in [-0.11, 0.21], gamma in
+ *           [0, 0.21], 1/Q in [0.004, 0.051]); rows are padded to 8 floats;
+ *   outputs (V/Vg - 1, A*Vg, psi - psi_el, validity logit, vartheta), stored
+ *           standardised (y = (raw - out_mean) / out_std; out_mean[3] = 0,
+ *           out_std[3] = 1), with Vg, psi_el the elastic group velocity and ray
+ *           angle of the real moduli.
+ * Parameter vector (float, chert_mlp_param_count() values): W0 [256 x 7], b0,
+ * W1..W3 [256 x 256], b1..b3, W4 [5 x 256], b4, out_mean [5], out_std [5]
+ * (W as [out][in]). */
+size_t chert_mlp_param_count(void);
+size_t chert_mlp_workspace_bytes(int64_t n, int training);
+
+/* y [n][5] (standardised outputs) for x [n][8]; all device.  Errors:
+ * CHERT_EINVAL, CHERT_ENOMEM (workspace), CHERT_ECUDA. */
+int chert_mlp_forward(const float* d_params, const float* d_x, int64_t n, float* d_y,
+                      void* d_ws, size_t ws_bytes, void* stream);
+
+/* One training step on a batch: loss = mean over samples of the halved
+ * squared error of outputs 0, 1, 2, 4 against the standardised targets (valid
+ * samples only) plus the logistic loss of output 3 against the validity in
+ * t[:, 3]; t [n][5] holds raw targets.  Writes the gradient to d_grad_out
+ * (may be NULL) and, if lr > 0, applies Adam (beta 0.9/0.999, eps 1e-8, bias
+ * correction with step >= 1) to the trained part of d_params with moments
+ * d_m, d_v.  d_loss (device float, may be NULL) receives the batch loss. */
+int chert_mlp_train_step(float* d_params, float* d_m, float* d_v, int step, float lr,
+                         const float* d_x, const float* d_t, int64_t n, float* d_loss,
+                         float* d_grad_out, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Training pairs from an exact cache built by chert_build_cache with the same
+ * classes and M: for every (class, folded angle j = 0..M) of cache mode slot
+ * `mode_slot` (wave mode `mode`), features x [n][8] and raw targets t [n][5]
+ * (n = n_classes*(M+1)); flagged entries get t[:, 3] = 0.  d_scratch holds
+ * at least 9*n bytes.  precision: storage type of the exact cache. */
+int chert_surrogate_dataset(const chert_class* d_classes, int n_classes, int M, int mode,
+                            int mode_slot, const chert_cache_arrays* exact, int precision,
+                            float* d_x, float* d_t, void* d_scratch, size_t scratch_bytes,
+                            void* stream);
+
+/* A cache of the same layout and meaning as chert_build_cache's, filled by
+ * the networks (d_params_per_mode: host array of n_modes device pointers).
+ * flag = 0 valid, 1 no acceptable root (network), 2 medium outside the
+ * training range (the caller recomputes those classes with the exact solver). */
+size_t chert_surrogate_cache_workspace_bytes(int n_classes, int M);
+int chert_surrogate_cache(const float* const* d_params_per_mode, const chert_class* d_classes,
+                          int n_classes, const int* modes, int n_modes, int M, int precision,
+                          const chert_cache_arrays* out, void* d_ws, size_t ws_bytes,
+                          void* stream);
+
 /* The paper has no counterpart to this entry point; it exists for callers of
  * this library that cannot allocate device memory: code embedded in a host
  * whose device memory is owned by its own pool, code that runs while a stream

@@ -91,6 +91,14 @@ def init_params(seed):
     return W, b
 
 
+def bf16(a):
+    """Round to bfloat16 (round to nearest even), via float32, returned as float64."""
+    a32 = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = a32.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def silu(x):
     return x / (1.0 + np.exp(-x))
 
@@ -100,21 +108,27 @@ def dsilu(x):
     return s * (1.0 + x * (1.0 - s))
 
 
-def forward(W, b, x):
-    """Returns the output and the pre-activations of every layer."""
-    pre, h = [], x
+def forward(W, b, x, quantize=False):
+    """Returns the output and the pre-activations of every layer.  With
+    quantize=True the inputs of every product (activations, weights) are
+    rounded to bfloat16 first, as a BF16-operand network computes."""
+    q = bf16 if quantize else (lambda a: a)
+    pre, h = [], q(x)
     for l in range(len(W)):
-        z = h @ W[l].T + b[l]
+        z = h @ q(W[l]).T + b[l]
         pre.append(z)
-        h = silu(z) if l < len(W) - 1 else z
+        h = q(silu(z)) if l < len(W) - 1 else z
     return h, pre
 
 
-def loss_and_grad(W, b, x, target, out_mean, out_std):
+def loss_and_grad(W, b, x, target, out_mean, out_std, quantize=False):
     """Mean over the batch of: sum over outputs 0,1,2,4 of ((y - t')^2)/2 on
     valid samples (t' = standardised target) + logistic loss of output 3.
-    Returns (loss, dW, db)."""
-    y, pre = forward(W, b, x)
+    Returns (loss, dW, db).  With quantize=True every product operand
+    (activations, weights and back-propagated gradients) is rounded to
+    bfloat16 first, as BF16-operand training computes."""
+    q = bf16 if quantize else (lambda a: a)
+    y, pre = forward(W, b, x, quantize)
     n = x.shape[0]
     valid = target[:, 3] > 0.5
     tstd = (target - out_mean) / out_std
@@ -131,11 +145,11 @@ def loss_and_grad(W, b, x, target, out_mean, out_std):
     g /= n
     dW, db = [None] * len(W), [None] * len(W)
     for l in reversed(range(len(W))):
-        h_in = x if l == 0 else silu(pre[l - 1])
-        dW[l] = g.T @ h_in
+        h_in = q(x) if l == 0 else q(silu(pre[l - 1]))
+        dW[l] = q(g).T @ h_in
         db[l] = g.sum(axis=0)
         if l > 0:
-            g = (g @ W[l]) * dsilu(pre[l - 1])
+            g = (q(g) @ q(W[l])) * dsilu(pre[l - 1])
     return loss, dW, db
 
 

@@ -75,8 +75,20 @@ def lib():
                                           I, P, I, I, I, P, P, P, P, P]
     L.chert_traveltime_static_limit.restype = SZ
     L.chert_traveltime_static_limit.argtypes = []
+    L.chert_mlp_param_count.restype = SZ
+    L.chert_mlp_param_count.argtypes = []
+    L.chert_mlp_workspace_bytes.restype = SZ
+    L.chert_mlp_workspace_bytes.argtypes = [I64, I]
+    L.chert_mlp_forward.argtypes = [P, P, I64, P, P, SZ, P]
+    L.chert_mlp_train_step.argtypes = [P, P, P, I, ctypes.c_float, P, P, I64, P, P, P, SZ, P]
+    L.chert_surrogate_dataset.argtypes = [P, I, I, I, I, ctypes.POINTER(chert_cache_arrays), I, P, P,
+                                          P, SZ, P]
+    L.chert_surrogate_cache_workspace_bytes.restype = SZ
+    L.chert_surrogate_cache_workspace_bytes.argtypes = [I, I]
+    L.chert_surrogate_cache.argtypes = [P, P, I, P, I, I, I, ctypes.POINTER(chert_cache_arrays), P, SZ, P]
     for name in ("chert_thomsen_to_class", "chert_build_cache", "chert_edge_table",
-                 "chert_traveltime", "chert_raypath", "chert_traveltime_static"):
+                 "chert_traveltime", "chert_raypath", "chert_traveltime_static", "chert_mlp_forward",
+                 "chert_mlp_train_step", "chert_surrogate_dataset", "chert_surrogate_cache"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -294,3 +306,76 @@ def raypath(par, sources, receivers, cap=4096, stream=None, out=None):
     _check(lib().chert_raypath(_dev_ptr(par2), nf, nn, _dev_ptr(src), _dev_ptr(rcv), len(rcv), cap,
                                _dev_ptr(out[0]), _dev_ptr(out[1]), _stream_ptr(stream)))
     return out
+
+
+# ------------------------------------------------------------------ surrogate
+def mlp_param_count():
+    return int(lib().chert_mlp_param_count())
+
+
+def mlp_forward(params, x, stream=None, workspace=None):
+    """Standardised network outputs y [n, 5] for features x [n, 8] (device)."""
+    torch = _torch()
+    n = x.shape[0]
+    y = torch.empty((n, 5), dtype=torch.float32, device=x.device)
+    wsb = int(lib().chert_mlp_workspace_bytes(n, 0))
+    if workspace is None or workspace.numel() < wsb:
+        workspace = torch.empty(wsb, dtype=torch.uint8, device=x.device)
+    _check(lib().chert_mlp_forward(_dev_ptr(params), _dev_ptr(x), n, _dev_ptr(y), _dev_ptr(workspace),
+                                   workspace.numel(), _stream_ptr(stream)))
+    return y
+
+
+def mlp_train_step(params, m, v, step, lr, x, t, stream=None, workspace=None, want_grad=False, loss=None):
+    """One Adam step (lr > 0) or a gradient evaluation (lr = 0); returns (loss tensor, grad or None)."""
+    torch = _torch()
+    n = x.shape[0]
+    wsb = int(lib().chert_mlp_workspace_bytes(n, 1))
+    if workspace is None or workspace.numel() < wsb:
+        workspace = torch.empty(wsb, dtype=torch.uint8, device=x.device)
+    grad = torch.empty_like(params) if want_grad else None
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+    _check(lib().chert_mlp_train_step(_dev_ptr(params), _dev_ptr(m), _dev_ptr(v), int(step), float(lr),
+                                      _dev_ptr(x), _dev_ptr(t), n, _dev_ptr(loss), _dev_ptr(grad),
+                                      _dev_ptr(workspace), workspace.numel(), _stream_ptr(stream)))
+    return loss, grad
+
+
+def surrogate_dataset(d_classes, n_classes, M, mode, mode_slot, exact_cache, stream=None):
+    """(x [n, 8], t [n, 5]) training pairs from an exact cache (device tensors)."""
+    torch = _torch()
+    n = n_classes * (M + 1)
+    dev = d_classes.device
+    x = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    t = torch.empty((n, 5), dtype=torch.float32, device=dev)
+    scratch = torch.empty(9 * n + 256, dtype=torch.uint8, device=dev)
+    st = exact_cache.struct()
+    mid = MODE_IDS[mode] if isinstance(mode, str) else mode
+    _check(lib().chert_surrogate_dataset(_dev_ptr(d_classes), n_classes, M, mid, mode_slot, ctypes.byref(st),
+                                         exact_cache.precision, _dev_ptr(x), _dev_ptr(t), _dev_ptr(scratch),
+                                         scratch.numel(), _stream_ptr(stream)))
+    return x, t
+
+
+def surrogate_cache(params_per_mode, d_classes, n_classes, modes, M, precision="fp32", stream=None, out=None):
+    """Cache arrays (same layout as build_cache) filled by the networks."""
+    torch = _torch()
+    prec = PRECISION_IDS[precision] if isinstance(precision, str) else precision
+    mode_ids = [MODE_IDS[m] if isinstance(m, str) else m for m in modes]
+    dev = d_classes.device
+    shape = (len(mode_ids), n_classes, 4 * M)
+    if out is None:
+        fd = _fdtype(prec)
+        out = {k: torch.empty(shape, dtype=fd, device=dev)
+               for k in ("V", "A", "Q", "rx", "rz", "theta", "vartheta")}
+        out["flag"] = torch.empty(shape, dtype=torch.uint8, device=dev)
+    cache = Cache(out, mode_ids, n_classes, M, prec)
+    wsb = int(lib().chert_surrogate_cache_workspace_bytes(n_classes, M))
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    ptrs = (ctypes.c_void_p * len(mode_ids))(*[p.data_ptr() for p in params_per_mode])
+    modes_arr = (ctypes.c_int * len(mode_ids))(*mode_ids)
+    st = cache.struct()
+    _check(lib().chert_surrogate_cache(ptrs, _dev_ptr(d_classes), n_classes, modes_arr, len(mode_ids), M, prec,
+                                       ctypes.byref(st), _dev_ptr(ws), ws.numel(), _stream_ptr(stream)))
+    return cache

@@ -180,3 +180,30 @@ def random_class_map_2d(nx: int, nz: int, n_classes: int, seed: int) -> np.ndarr
     """Per-node random classes (a stress case for the lookup and the relaxation)."""
     rng = np.random.default_rng(seed)
     return rng.integers(0, n_classes, nx * nz).astype(np.uint8)
+
+
+def random_tti_classes(n: int, seed: int, q_lo: float = 20.0, q_hi: float = 200.0) -> list:
+    """n independent seeded TTI media over the surrogate's training range
+    (Vp0 ~ U(2000, 4500), Vp0/Vs0 ~ U(1.7, 2.0), eps ~ U(0.05, 0.3),
+    delta ~ U(-0.1, 0.2), gamma ~ U(0, 0.2), tilt ~ U(0, 45 deg),
+    Qp, Qs ~ logU(q_lo, q_hi) with Qs <= Qp)."""
+    rng = np.random.default_rng(seed)
+    vp0 = rng.uniform(2000.0, 4500.0, n)
+    ratio = rng.uniform(1.7, 2.0, n)
+    eps = rng.uniform(0.05, 0.3, n)
+    delta = rng.uniform(-0.1, 0.2, n)
+    gamma = rng.uniform(0.0, 0.2, n)
+    tilt = np.deg2rad(rng.uniform(0.0, 45.0, n))
+    qa = np.exp(rng.uniform(math.log(q_lo), math.log(q_hi), n))
+    qb = np.exp(rng.uniform(math.log(q_lo), math.log(q_hi), n))
+    qp, qs = np.maximum(qa, qb), np.minimum(qa, qb)
+    return [ThomsenLayer(vp0=float(vp0[i]), vs0=float(vp0[i] / ratio[i]), eps=float(eps[i]),
+                         delta=float(delta[i]), gamma=float(gamma[i]), qp=float(qp[i]), qs=float(qs[i]),
+                         rho=2200.0, tilt=float(tilt[i])) for i in range(n)]
+
+
+def mlp_init(seed: int, n_in: int = 7, n_hid: int = 256, n_layers: int = 4, n_out: int = 5) -> list:
+    """Seeded He-normal initial weights [(W [out, in], b [out]), ...] (float64)."""
+    rng = np.random.default_rng(seed)
+    sizes = [n_in] + [n_hid] * n_layers + [n_out]
+    return [(rng.normal(0.0, math.sqrt(2.0 / a), (b_, a)), np.zeros(b_)) for a, b_ in zip(sizes[:-1], sizes[1:])]

@@ -1,0 +1,152 @@
+"""The cache surrogate on the GPU: BF16 forward and gradient against the FP64
+oracle network with the same BF16 rounding points, the training pairs against
+the oracle's own exact cache, and what a trained network gains.
+
+Tolerances: with the operands rounded to bfloat16 at the same points on both
+sides, the remaining difference is FP32 against FP64 accumulation, plus an
+occasional activation that rounds to the neighbouring bfloat16 value (2^-8
+relative) because the two accumulations straddle a rounding boundary; one
+such flip moves an output by about 2^-8 * |w| * |h| / sqrt(256).  Outputs and
+gradients are compared to 1e-2 of their scale and must agree to 1e-3 in the
+median."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cache_oracle as co
+from oracle import mlp_oracle as mo
+from paper_2609_26108_b300 import chert, inputs, surrogate
+
+from helpers import DEG, cache_to_torch, oracle_moduli
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    from paper_2609_26108_b300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def _net(seed):
+    layers = inputs.mlp_init(seed)
+    rng = np.random.default_rng(seed + 1)
+    layers = [(W, rng.normal(0, 0.05, b.shape)) for W, b in layers]
+    mean = rng.normal(0, 0.1, 5)
+    std = rng.uniform(0.5, 2.0, 5)
+    mean[3], std[3] = 0.0, 1.0
+    return layers, mean, std
+
+
+def _x(n, seed):
+    x = np.random.default_rng(seed).uniform(-1, 1, (n, 8))
+    x[:, 7] = 0.0
+    return x
+
+
+def test_forward_matches_oracle_bf16(torch_dev):
+    layers, mean, std = _net(3)
+    params = torch_dev.as_tensor(surrogate.pack_params(layers, mean, std), device="cuda")
+    x = _x(1000, 4)
+    y = chert.mlp_forward(params, torch_dev.as_tensor(x, dtype=torch_dev.float32, device="cuda"))
+    torch_dev.cuda.synchronize()
+    W = [l[0].astype(np.float32).astype(np.float64) for l in layers]
+    b = [l[1].astype(np.float32).astype(np.float64) for l in layers]
+    ref, _ = mo.forward(W, b, x[:, :7].astype(np.float32).astype(np.float64), quantize=True)
+    err = np.abs(y.cpu().numpy() - ref)
+    scale = np.abs(ref).mean(0)
+    assert np.all(err <= 1e-2 * scale + 1e-4)
+    assert np.median(err / scale) < 1e-3
+
+
+def test_gradient_matches_oracle_bf16(torch_dev):
+    layers, mean, std = _net(5)
+    params = torch_dev.as_tensor(surrogate.pack_params(layers, mean, std), device="cuda")
+    n = 512
+    x = _x(n, 6)
+    rng = np.random.default_rng(7)
+    t = rng.normal(0, 1, (n, 5)) * std + mean
+    t[:, 3] = (rng.uniform(size=n) > 0.2).astype(float)
+    zeros = torch_dev.zeros_like(params)
+    loss, grad = chert.mlp_train_step(params, zeros.clone(), zeros.clone(), 1, 0.0,
+                                      torch_dev.as_tensor(x, dtype=torch_dev.float32, device="cuda"),
+                                      torch_dev.as_tensor(t, dtype=torch_dev.float32, device="cuda"),
+                                      want_grad=True)
+    torch_dev.cuda.synchronize()
+    W = [l[0].astype(np.float32).astype(np.float64) for l in layers]
+    b = [l[1].astype(np.float32).astype(np.float64) for l in layers]
+    rl, dW, db = mo.loss_and_grad(W, b, x[:, :7].astype(np.float32).astype(np.float64),
+                                  t.astype(np.float32).astype(np.float64),
+                                  mean.astype(np.float32), std.astype(np.float32), quantize=True)
+    assert float(loss.item()) == pytest.approx(rl, rel=1e-3)
+    g_layers, _, _ = surrogate.unpack_params(grad.cpu().numpy())
+    for l in range(5):
+        for got, ref in [(g_layers[l][0], dW[l]), (g_layers[l][1], db[l])]:
+            scale = np.abs(ref).mean() + 1e-12
+            err = np.abs(got - ref)
+            assert np.all(err <= 1e-2 * scale + 1e-2 * np.abs(ref)), (l, err.max() / scale)
+            assert np.median(err / scale) < 1e-3
+
+
+@pytest.mark.parametrize("mode", ["qP", "qSV", "qSH"])
+def test_training_pairs_match_oracle(torch_dev, mode):
+    """Features, elastic baseline and targets from the oracle's exact cache."""
+    classes = inputs.random_tti_classes(4, seed=11)
+    M = 6
+    mods, tilts = oracle_moduli(classes)
+    cnp = co.build_cache(mods, tilts, [mode], M, "MEV", 0.02 * DEG, 1500)
+    cache = chert.Cache(cache_to_torch(cnp, torch_dev.float64, "cuda"), [0], 4, M, chert.FP64)
+    d_cls = chert.classes_to_device(chert.classes_from_layers(classes))
+    x, t = chert.surrogate_dataset(d_cls, 4, M, mode, 0, cache)
+    torch_dev.cuda.synchronize()
+    x, t = x.cpu().numpy(), t.cpu().numpy()
+    for k, L in enumerate(classes):
+        aR = mods[k].real
+        A = co.stiffness_tensor(mods[k])
+        th = (math.pi / 2) * np.arange(M + 1) / M
+        u, out = mo.features(th, np.full(M + 1, L.vs0 / L.vp0), np.full(M + 1, L.eps),
+                             np.full(M + 1, L.delta), np.full(M + 1, L.gamma), np.full(M + 1, 1 / L.qp),
+                             np.full(M + 1, 1 / L.qs))
+        rows = slice(k * (M + 1), (k + 1) * (M + 1))
+        assert np.allclose(x[rows, :7], u, atol=2e-6)
+        Vg, psi_el = mo.elastic_baseline(aR, th, mode)
+        for j in range(M + 1):
+            s = co.solve_direction(A, th[j], mode, "MEV", 0.02 * DEG, 1500)
+            ref = mo.encode_targets(s["V"], s["A"], math.atan2(s["r"][0], s["r"][2]), s["flag"],
+                                    s["vartheta"], Vg[j], psi_el[j])
+            assert np.allclose(t[k * (M + 1) + j], ref, atol=3e-6, rtol=1e-5), (k, j)
+
+
+def test_trained_surrogate_beats_elastic_baseline(torch_dev):
+    """Trained on exact entries of 512 seeded media, evaluated on 48 others:
+    the surrogate's ray velocity and attenuation errors against the exact
+    cache, and the same errors of the elastic baseline alone (the network
+    predicting no correction)."""
+    modes = ["qP", "qSV", "qSH"]
+    M = 30
+    train_sets = surrogate.exact_training_set(inputs.random_tti_classes(512, seed=21), modes, M)
+    test_cls = inputs.random_tti_classes(48, seed=99)
+    d_test = chert.classes_to_device(chert.classes_from_layers(test_cls))
+    exact = chert.build_cache(d_test, 48, modes, M, kernel="MEV", precision="mixed")
+    params = []
+    for m in modes:
+        x, t = train_sets[m]
+        p, hist = surrogate.train(x, t, steps=1500, batch=2048, lr=2e-3, seed=1, log_every=500)
+        params.append(p)
+    surr = chert.surrogate_cache(params, d_test, 48, modes, M)
+    torch_dev.cuda.synchronize()
+    ex = {k: v.cpu().numpy() for k, v in exact.arrays.items()}
+    su = {k: v.cpu().numpy() for k, v in surr.arrays.items()}
+    both = (ex["flag"] == 0) & (su["flag"] == 0)
+    agree = np.mean((ex["flag"] == 0) == (su["flag"] == 0))
+    assert agree > 0.97
+    for mi, m in enumerate(modes):
+        ok = both[mi]
+        dv = np.abs(su["V"][mi][ok] / ex["V"][mi][ok] - 1)
+        da = np.abs(su["A"][mi][ok] - ex["A"][mi][ok]) / np.abs(ex["A"][mi][ok])
+        assert np.median(dv) < 2e-3, (m, np.median(dv))
+        assert np.median(da) < 5e-2, (m, np.median(da))
