@@ -424,7 +424,8 @@ extern "C" int chert_mlp_forward(const float* d_params, const float* d_x, int64_
     if (rc) return rc;
     cudaError_t e = cudaMemcpyAsync(d_y, w.y, sizeof(float) * n * kOut, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "chert_mlp_forward");
-    return launch_check("chert_mlp_forward");
+    rc = launch_check("chert_mlp_forward");
+    return rc ? rc : gemm::tc::check_and_clear(s, "chert_mlp_forward");
 }
 
 extern "C" int chert_mlp_train_step(float* d_params, float* d_m, float* d_v, int step, float lr,
@@ -495,7 +496,8 @@ extern "C" int chert_mlp_train_step(float* d_params, float* d_m, float* d_v, int
         e = cudaMemcpyAsync(d_loss, w.loss, 4, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return cuda_fail(e, "chert_mlp_train_step");
     }
-    return launch_check("chert_mlp_train_step");
+    rc = launch_check("chert_mlp_train_step");
+    return rc ? rc : gemm::tc::check_and_clear(s, "chert_mlp_train_step");
 }
 
 extern "C" int chert_surrogate_dataset(const chert_class* d_classes, int n_classes, int M, int mode,

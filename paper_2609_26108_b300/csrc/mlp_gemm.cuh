@@ -1,6 +1,7 @@
 // GEMM C[M x N] = A[M x K] * B[N x K]^T of the surrogate (BF16 operands, FP32
-// accumulation) with the fused epilogues the MLP needs.  This is the plain
-// CUDA-core kernel: shared-memory tiles of 64 x 64 outputs, 4 x 4 per thread.
+// accumulation) with the fused epilogues the MLP needs.  The tcgen05 kernel
+// (mlp_tc.cuh) takes the large shapes; the plain CUDA-core kernel here
+// (shared-memory tiles of 64 x 64 outputs, 4 x 4 per thread) takes the rest.
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -81,9 +82,23 @@ __global__ void __launch_bounds__(256) nt_simt_kernel(const __nv_bfloat16* __res
         for (int j = 0; j < 4; ++j) epilogue_store(e, M, N, m0 + ty * 4 + i, n0 + tx * 4 + j, acc[i][j]);
 }
 
+}  // namespace gemm
+}  // namespace chert
+
+#include "mlp_tc.cuh"
+
+namespace chert {
+namespace gemm {
+
+// tcgen05 kernel when the shapes allow it (M >= 128, N a multiple of 128,
+// K >= 16, 16-byte aligned rows), the CUDA-core kernel otherwise.
 inline int nt(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
-              const Epilogue& e, cudaStream_t s) {
+              const Epilogue& e, cudaStream_t s, bool allow_tc = true) {
     if (M <= 0 || N <= 0 || K <= 0) return CHERT_OK;
+    if (allow_tc) {
+        const int r = tc::try_nt(A, lda, B, ldb, M, N, K, e, s);
+        if (r != 0) return r < 0 ? r : CHERT_OK;
+    }
     const dim3 grid((N + 63) / 64, (M + 63) / 64);
     if (grid.y > 65535u) {
         set_error("surrogate GEMM: M=%d too large for one launch", M);
