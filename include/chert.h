@@ -187,6 +187,12 @@ int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes
 size_t chert_mlp_param_count(void);
 size_t chert_mlp_workspace_bytes(int64_t n, int training);
 
+/* GEMMs with M >= 128 rows and N a multiple of 128 run on the tcgen05 tensor
+ * cores (TMA-fed, accumulator in tensor memory), the others on a CUDA-core
+ * kernel.  enable = 0 sends every GEMM to the CUDA-core kernel (process-wide;
+ * used to compare the two).  Returns the previous setting. */
+int chert_mlp_set_tensor_cores(int enable);
+
 /* y [n][5] (standardised outputs) for x [n][8]; all device.  Errors:
  * CHERT_EINVAL, CHERT_ENOMEM (workspace), CHERT_ECUDA. */
 int chert_mlp_forward(const float* d_params, const float* d_x, int64_t n, float* d_y,

@@ -80,6 +80,8 @@ def lib():
     L.chert_mlp_workspace_bytes.restype = SZ
     L.chert_mlp_workspace_bytes.argtypes = [I64, I]
     L.chert_mlp_forward.argtypes = [P, P, I64, P, P, SZ, P]
+    L.chert_mlp_set_tensor_cores.argtypes = [I]
+    L.chert_mlp_set_tensor_cores.restype = I
     L.chert_mlp_train_step.argtypes = [P, P, P, I, ctypes.c_float, P, P, I64, P, P, P, SZ, P]
     L.chert_surrogate_dataset.argtypes = [P, I, I, I, I, ctypes.POINTER(chert_cache_arrays), I, P, P,
                                           P, SZ, P]

@@ -405,6 +405,12 @@ using namespace chert::mlp;
 
 extern "C" size_t chert_mlp_param_count(void) { return layout().total; }
 
+extern "C" int chert_mlp_set_tensor_cores(int enable) {
+    const int before = gemm::tc::tensor_cores_enabled() ? 1 : 0;
+    gemm::tc::tensor_cores_enabled() = enable != 0;
+    return before;
+}
+
 extern "C" size_t chert_mlp_workspace_bytes(int64_t n, int training) {
     if (n < 1) return 0;
     return ws_carve(nullptr, n, training != 0).bytes;

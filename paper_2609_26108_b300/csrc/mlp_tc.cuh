@@ -1,7 +1,7 @@
 // tcgen05 GEMM of the surrogate: C[M x N] = A[M x K] * B[N x K]^T, BF16
 // operands, FP32 accumulation in tensor memory, fused epilogue.
 //
-// One CTA of 4 warps computes a 128 x NT tile (NT = 128 or 256):
+// One CTA of 8 warps computes a 128 x NT tile (NT = 128 or 256):
 //   * TMA (cp.async.bulk.tensor.2d, 128-byte swizzle) brings 64-wide K chunks
 //     of A (128 x 64) and B (NT x 64) into a ring of kStages shared-memory
 //     stages; an mbarrier per stage counts the arriving bytes.
@@ -9,8 +9,9 @@
 //     K = 16 per instruction, four per chunk) into an FP32 accumulator of NT
 //     tensor-memory columns, and tcgen05.commit releases each stage back to
 //     the loader once the tensor cores have read it.
-//   * After the last chunk the four warps read their 32 accumulator lanes with
-//     tcgen05.ld.32x32b and apply the epilogue.
+//   * After the last chunk the eight warps read the accumulator with
+//     tcgen05.ld.32x32b (warp w: lanes 32*(w%4).., column half w/4) and apply
+//     the epilogue through a shared-memory transpose (coalesced stores).
 // Every mbarrier wait is bounded: on timeout the kernel records an error in
 // g_tc_error, stops issuing work, waits (bounded) for the tensor cores, frees
 // its tensor memory and returns.
@@ -147,7 +148,7 @@ struct Smem {
 };
 
 template <int NT>
-__global__ void __launch_bounds__(128, 1) nt_tc_kernel(const __grid_constant__ CUtensorMap ta,
+__global__ void __launch_bounds__(256, 1) nt_tc_kernel(const __grid_constant__ CUtensorMap ta,
                                                        const __grid_constant__ CUtensorMap tb, int M, int N,
                                                        int K, Epilogue e) {
     extern __shared__ __align__(1024) unsigned char raw[];
@@ -209,15 +210,25 @@ __global__ void __launch_bounds__(128, 1) nt_tc_kernel(const __grid_constant__ C
     if (!done && tid == 0) atomicExch(&g_tc_error, 2);
     fence_after_sync();
     if (done && !s_fail) {
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t lane_base = tmem + (uint32_t(warp * 32) << 16);
-        for (int c0 = 0; c0 < NT; c0 += 32) {
+        // Eight warps: warp w reads accumulator lanes 32*(w%4).. (its rows) and
+        // the column half w/4.  A 32 x 32 block is read from tensor memory
+        // (one row per thread), transposed through a padded shared-memory tile
+        // (the operand stages are free once the MMAs are done), and the
+        // epilogue runs with the lanes along the row, so every global access
+        // is a coalesced row segment.
+        const int quarter = warp & 3, half = warp >> 2;
+        float* stg = reinterpret_cast<float*>(s.a[0]) + warp * 32 * 33;
+        const uint32_t lane_base = tmem + (uint32_t(quarter * 32) << 16);
+        const int row0 = m0 + quarter * 32;
+        for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += 32) {
             float v[32];
             tmem_ld32(lane_base + c0, v);
-            if (row < M) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) epilogue_store(e, M, N, row, n0 + c0 + i, v[i]);
-            }
+            for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = v[i];
+            __syncwarp();
+            for (int r = 0; r < 32; ++r)
+                if (row0 + r < M) epilogue_store(e, M, N, row0 + r, n0 + c0 + lane, stg[r * 33 + lane]);
+            __syncwarp();
         }
     }
     fence_before_sync();
@@ -229,31 +240,48 @@ using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, voi
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-inline EncodeFn encoder() {
+inline EncodeFn encoder(const char** why) {
     static EncodeFn fn = nullptr;
+    static char msg[160] = "";
     if (!fn) {
         void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeFn>(p);
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        const cudaError_t e =
+            cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e == cudaSuccess && q == cudaDriverEntryPointSuccess && p) fn = reinterpret_cast<EncodeFn>(p);
+        else snprintf(msg, sizeof(msg), "cuTensorMapEncodeTiled not available (%s, query %d)",
+                      cudaGetErrorString(e), (int)q);
     }
+    if (why) *why = msg;
     return fn;
 }
 
 // 2D map over a row-major bf16 matrix [rows x cols] with row pitch ld; boxes
 // of 64 columns x box_rows rows, 128-byte swizzle, zero fill outside.
-inline bool make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int cols, int ld, int box_rows) {
-    EncodeFn fn = encoder();
-    if (!fn) return false;
+inline int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int cols, int ld, int box_rows) {
+    const char* why = nullptr;
+    EncodeFn fn = encoder(&why);
+    if (!fn) {
+        set_error("surrogate GEMM: %s", why);
+        return CHERT_ECUDA;
+    }
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
     const cuuint32_t box[2] = {(cuuint32_t)kKChunk, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("surrogate GEMM: cuTensorMapEncodeTiled failed (%d) for %d x %d, ld %d", (int)r, rows, cols, ld);
+        return CHERT_ECUDA;
+    }
+    return CHERT_OK;
+}
+
+inline bool& tensor_cores_enabled() {
+    static bool on = true;
+    return on;
 }
 
 // Reads and clears the error flag of the tensor-core kernel (synchronises s).
@@ -276,28 +304,34 @@ inline int check_and_clear(cudaStream_t s, const char* who) {
 // 0 when the caller should use the CUDA-core kernel, or a negative status.
 inline int try_nt(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                   const Epilogue& e, cudaStream_t s) {
+    if (!tensor_cores_enabled()) return 0;
     if (M < 128 || K < 16 || (N % 128) != 0) return 0;
     if ((lda % 8) || (ldb % 8) || (reinterpret_cast<uintptr_t>(A) % 16) || (reinterpret_cast<uintptr_t>(B) % 16))
         return 0;
     const int nt = (N % 256 == 0 && (long long)((M + 127) / 128) * (N / 256) >= 148) ? 256 : 128;
     CUtensorMap ta, tb;
-    if (!make_map(&ta, A, M, K, lda, 128) || !make_map(&tb, B, N, K, ldb, nt)) return 0;
+    int rc = make_map(&ta, A, M, K, lda, 128);
+    if (!rc) rc = make_map(&tb, B, N, K, ldb, nt);
+    if (rc) return rc;
     const dim3 grid(N / nt, (M + 127) / 128);
-    if (grid.y > 65535u) return 0;
+    if (grid.y > 65535u) {
+        set_error("surrogate GEMM: M=%d exceeds one launch; split the batch", M);
+        return CHERT_EINVAL;
+    }
     if (nt == 256) {
         const size_t smem = sizeof(Smem<256>) + 1024;
         cudaError_t err = cudaFuncSetAttribute(nt_tc_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
         if (err != cudaSuccess) return cuda_fail(err, "surrogate GEMM (tcgen05)");
-        nt_tc_kernel<256><<<grid, 128, smem, s>>>(ta, tb, M, N, K, e);
+        nt_tc_kernel<256><<<grid, 256, smem, s>>>(ta, tb, M, N, K, e);
     } else {
         const size_t smem = sizeof(Smem<128>) + 1024;
         cudaError_t err = cudaFuncSetAttribute(nt_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);
         if (err != cudaSuccess) return cuda_fail(err, "surrogate GEMM (tcgen05)");
-        nt_tc_kernel<128><<<grid, 128, smem, s>>>(ta, tb, M, N, K, e);
+        nt_tc_kernel<128><<<grid, 256, smem, s>>>(ta, tb, M, N, K, e);
     }
-    const int rc = launch_check("surrogate GEMM (tcgen05)");
+    rc = launch_check("surrogate GEMM (tcgen05)");
     return rc ? rc : 1;
 }
 

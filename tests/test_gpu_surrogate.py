@@ -92,6 +92,35 @@ def test_gradient_matches_oracle_bf16(torch_dev):
             assert np.median(err / scale) < 1e-3
 
 
+def test_tensor_core_gemm_matches_cuda_core_gemm(torch_dev):
+    """The tcgen05 GEMMs (256-wide layers) against the CUDA-core kernel on the
+    same bf16 operands: forward outputs and gradients, to accumulation order."""
+    layers, mean, std = _net(8)
+    params = torch_dev.as_tensor(surrogate.pack_params(layers, mean, std), device="cuda")
+    n = 3000                                   # ragged: 23 full 128-row tiles and a tail
+    x = torch_dev.as_tensor(_x(n, 9), dtype=torch_dev.float32, device="cuda")
+    rng = np.random.default_rng(10)
+    t = rng.normal(0, 1, (n, 5)) * std + mean
+    t[:, 3] = (rng.uniform(size=n) > 0.2).astype(float)
+    t = torch_dev.as_tensor(t, dtype=torch_dev.float32, device="cuda")
+    out = {}
+    lib = chert.lib()
+    try:
+        for tc in (1, 0):
+            lib.chert_mlp_set_tensor_cores(tc)
+            y = chert.mlp_forward(params, x)
+            z = torch_dev.zeros_like(params)
+            _, g = chert.mlp_train_step(params, z.clone(), z.clone(), 1, 0.0, x, t, want_grad=True)
+            torch_dev.cuda.synchronize()
+            out[tc] = (y.cpu().numpy(), g.cpu().numpy())
+    finally:
+        lib.chert_mlp_set_tensor_cores(1)
+    for a, b in zip(out[1], out[0]):
+        scale = np.abs(b).mean()
+        assert np.all(np.abs(a - b) <= 1e-2 * scale + 1e-2 * np.abs(b))
+        assert np.median(np.abs(a - b)) < 1e-4 * scale
+
+
 @pytest.mark.parametrize("mode", ["qP", "qSV", "qSH"])
 def test_training_pairs_match_oracle(torch_dev, mode):
     """Features, elastic baseline and targets from the oracle's exact cache."""
