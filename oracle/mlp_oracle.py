@@ -12,15 +12,21 @@ module restates, in plain numpy double precision:
   eigenvalue of the 2x2 x-z Christoffel block, or a66 sin^2 + a44 cos^2 for
   qSH), its angular derivative by a complex step, and from them the group
   velocity Vg = sqrt(V^2 + V'^2) and ray angle psi = theta + atan2(V', V).
+* ``attenuation_baseline``  the attenuation A0 of the homogeneous plane wave
+  whose slowness points along theta: Im(1/c) for the complex phase velocity
+  c = sqrt(lambda) of the complex Christoffel block, projected on the elastic
+  ray direction, cos(psi_el - theta) Im(1/c).
 * ``features`` / ``encode_targets`` / ``decode``  the fixed input scaling and
-  the output parametrisation (V/Vg - 1, A*Vg, psi - psi_el, validity logit,
-  vartheta).
+  the output parametrisation (V/Vg - 1, log(A/A0), psi - psi_el, validity
+  logit, vartheta).
 * ``forward`` / ``backward`` / ``adam``  the network, the gradient of the
   masked mean-square + logistic loss, and Adam with bias correction.
 
 Parity status: forward and backward are pinned by finite differences and by
-explicit loops; the baseline is pinned by the oracle's own exact cache in the
-elastic limit.  The learned weights have no pin: they are an approximation
+explicit loops; the elastic baseline is pinned by the oracle's own exact cache
+in the elastic limit, the attenuation baseline by the exact cache where the
+exact wave is homogeneous (isotropic media, and the symmetry axis of a VTI
+medium).  The learned weights have no pin: they are an approximation
 whose error the tests measure against the exact cache.
 """
 from __future__ import annotations
@@ -59,6 +65,28 @@ def elastic_baseline(aR, theta, mode):
     return np.sqrt(V * V + dV * dV), np.asarray(theta) + np.arctan2(dV, V)
 
 
+def attenuation_baseline(a, theta, mode, psi_el):
+    """Homogeneous-wave attenuation for complex moduli a = (a11, a13, a33,
+    a44, a66) (a = aR - i aI) at slowness angles theta, projected on the ray
+    direction psi_el."""
+    a11, a13, a33, a44, a66 = [complex(v) for v in a]
+    t = np.asarray(theta, dtype=np.float64)
+    out = np.zeros(t.shape)
+    for idx in np.ndindex(t.shape):
+        s, c = math.sin(t[idx]), math.cos(t[idx])
+        if mode == "qSH":
+            lam = a66 * s * s + a44 * c * c
+        else:
+            G = np.array([[a11 * s * s + a44 * c * c, (a13 + a44) * s * c],
+                          [(a13 + a44) * s * c, a44 * s * s + a33 * c * c]])
+            ev = np.linalg.eigvals(G)
+            ev = ev[np.argsort(ev.real)]
+            lam = ev[1] if mode == "qP" else ev[0]
+        slowness = 1.0 / np.sqrt(lam)
+        out[idx] = slowness.imag * math.cos(float(np.asarray(psi_el)[idx]) - t[idx])
+    return out
+
+
 def features(theta_fold, rs, eps, delta, gamma, inv_qp, inv_qs):
     """Inputs scaled to [-1, 1] over the training range; also returns the
     mask of samples outside that range."""
@@ -68,15 +96,22 @@ def features(theta_fold, rs, eps, delta, gamma, inv_qp, inv_qs):
     return u, outside
 
 
-def encode_targets(V, A, psi, flag, vartheta, Vg, psi_el):
-    """Network targets: (V/Vg - 1, A*Vg, psi - psi_el, valid, vartheta)."""
+def encode_targets(V, A, psi, flag, vartheta, Vg, psi_el, A0, vt_max=None):
+    """Network targets: (V/Vg - 1, log(A/A0), psi - psi_el, valid, vartheta).
+    A and A0 share their unit; either one under 1e-30 of it counts as 1e-30.
+    With vt_max, samples with |vartheta| > vt_max get NaN for outputs 0-2
+    (left out of the fit of those outputs)."""
     valid = (np.asarray(flag) == 0)
     t = np.zeros(np.shape(V) + (N_OUT,))
     t[..., 0] = np.where(valid, V / Vg - 1.0, 0.0)
-    t[..., 1] = np.where(valid, A * Vg, 0.0)
+    ratio = np.maximum(np.where(valid, A, 1.0), 1e-30) / np.maximum(A0, 1e-30)
+    t[..., 1] = np.where(valid, np.log(ratio), 0.0)
     t[..., 2] = np.where(valid, np.angle(np.exp(1j * (psi - psi_el))), 0.0)
     t[..., 3] = valid.astype(np.float64)
     t[..., 4] = np.where(valid, vartheta, 0.0)
+    if vt_max is not None:
+        far = valid & (np.abs(vartheta) > vt_max)
+        t[far, 0:3] = np.nan
     return t
 
 
@@ -123,7 +158,8 @@ def forward(W, b, x, quantize=False):
 
 def loss_and_grad(W, b, x, target, out_mean, out_std, quantize=False):
     """Mean over the batch of: sum over outputs 0,1,2,4 of ((y - t')^2)/2 on
-    valid samples (t' = standardised target) + logistic loss of output 3.
+    valid samples whose target is not NaN (t' = standardised target) +
+    logistic loss of output 3.
     Returns (loss, dW, db).  With quantize=True every product operand
     (activations, weights and back-propagated gradients) is rounded to
     bfloat16 first, as BF16-operand training computes."""
@@ -135,7 +171,8 @@ def loss_and_grad(W, b, x, target, out_mean, out_std, quantize=False):
     g = np.zeros_like(y)
     loss = 0.0
     for k in (0, 1, 2, 4):
-        d = np.where(valid, y[:, k] - tstd[:, k], 0.0)
+        use = valid & ~np.isnan(tstd[:, k])
+        d = np.where(use, y[:, k] - np.where(use, tstd[:, k], 0.0), 0.0)
         loss += 0.5 * np.sum(d * d)
         g[:, k] = d
     p = 1.0 / (1.0 + np.exp(-y[:, 3]))
@@ -165,11 +202,11 @@ def adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         p -= lr * mhat / (np.sqrt(vhat) + eps)
 
 
-def decode(y, out_mean, out_std, Vg, psi_el):
+def decode(y, out_mean, out_std, Vg, psi_el, A0):
     """Network output -> (V, A, psi, p_valid, vartheta)."""
     t = y * out_std + out_mean
     V = Vg * (1.0 + t[..., 0])
-    A = t[..., 1] / Vg
+    A = A0 * np.exp(t[..., 1])
     psi = psi_el + t[..., 2]
     p_valid = 1.0 / (1.0 + np.exp(-y[..., 3]))
     return V, A, psi, p_valid, t[..., 4]
