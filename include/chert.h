@@ -71,6 +71,14 @@ int chert_thomsen_to_class(double vp0, double vs0, double eps, double delta,
                            double gamma, double qp, double qs, double rho,
                            double tilt, double azim, chert_class* out);
 
+/* chert_thomsen_to_class for n classes (host arrays of length n; out holds
+ * n records).  Stops at the first invalid class (CHERT_EINVAL, index in the
+ * message). */
+int chert_thomsen_to_classes(int64_t n, const double* vp0, const double* vs0,
+                             const double* eps, const double* delta, const double* gamma,
+                             const double* qp, const double* qs, const double* rho,
+                             const double* tilt, const double* azim, chert_class* out);
+
 /* ---- cache build (Eq. 4-14, 26, 35-36) ---------------------------------- */
 
 /* Output arrays of the directional cache C(m, k, theta), all device, each laid
@@ -122,6 +130,18 @@ int chert_build_cache(const chert_class* d_classes, int n_classes,
                       const chert_cache_params* params,
                       const chert_cache_arrays* out, void* stream);
 
+/* Solve only the listed solves of a cache (same arguments and arrays as
+ * chert_build_cache), leaving the other entries untouched.  A solve is the
+ * folded angle j of class k in mode slot m, numbered
+ * m*n_classes*(M+1) + k*(M+1) + j (device int64 list), and writes its up to
+ * four mirrored entries.  Used to recompute the entries a surrogate cache
+ * marks as needing the exact solver. */
+int chert_build_cache_items(const chert_class* d_classes, int n_classes,
+                            const int* modes, int n_modes,
+                            const chert_cache_params* params,
+                            const int64_t* d_items, int64_t n_items,
+                            const chert_cache_arrays* out, void* stream);
+
 /* ---- direction lookup (Eq. 27-28) --------------------------------------- */
 
 /* For every (mode, class, stencil offset o): the cache entry whose ray
@@ -167,7 +187,7 @@ int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes
                      void* d_tauR, void* d_tauI, int32_t* d_parR, int32_t* d_parI,
                      void* d_workspace, size_t workspace_bytes, void* stream);
 
-/* ---- cache surrogate (spec pattern 4; no counterpart in the paper) -
+/* ---- cache surrogate (a learned stand-in for the cache build; no counterpart in the paper)
  * One MLP per wave mode, 7 -> 256 -> 256 -> 256 -> 256 -> 5 with SiLU hidden
  * activations, BF16 operands, FP32 accumulation and FP32 master weights.  It
  * predicts the correction of a cache entry (the homogeneity solve of Eq. 9-11
@@ -177,10 +197,12 @@ int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes
  *           [-1, 1] over the training range (theta in [0, pi/2], Vs0/Vp0 in
  *           [0.49, 0.6], eps in [0.04, 0.31], delta in [-0.11, 0.21], gamma in
  *           [0, 0.21], 1/Q in [0.004, 0.051]); rows are padded to 8 floats;
- *   outputs (V/Vg - 1, A*Vg, psi - psi_el, validity logit, vartheta), stored
- *           standardised (y = (raw - out_mean) / out_std; out_mean[3] = 0,
+ *   outputs (V/Vg - 1, log(A/A0), psi - psi_el, validity logit, vartheta),
+ *           stored standardised (y = (raw - out_mean) / out_std; out_mean[3] = 0,
  *           out_std[3] = 1), with Vg, psi_el the elastic group velocity and ray
- *           angle of the real moduli.
+ *           angle of the real moduli and A0 the attenuation Im(1/c) of the
+ *           homogeneous plane wave (complex phase velocity c of the complex
+ *           Christoffel block along theta) projected on the elastic ray.
  * Parameter vector (float, chert_mlp_param_count() values): W0 [256 x 7], b0,
  * W1..W3 [256 x 256], b1..b3, W4 [5 x 256], b4, out_mean [5], out_std [5]
  * (W as [out][in]). */
@@ -201,7 +223,8 @@ int chert_mlp_forward(const float* d_params, const float* d_x, int64_t n, float*
 /* One training step on a batch: loss = mean over samples of the halved
  * squared error of outputs 0, 1, 2, 4 against the standardised targets (valid
  * samples only) plus the logistic loss of output 3 against the validity in
- * t[:, 3]; t [n][5] holds raw targets.  Writes the gradient to d_grad_out
+ * t[:, 3]; t [n][5] holds raw targets, and a NaN target of output 0, 1, 2 or
+ * 4 adds neither loss nor gradient.  Writes the gradient to d_grad_out
  * (may be NULL) and, if lr > 0, applies Adam (beta 0.9/0.999, eps 1e-8, bias
  * correction with step >= 1) to the trained part of d_params with moments
  * d_m, d_v.  d_loss (device float, may be NULL) receives the batch loss. */
@@ -212,8 +235,11 @@ int chert_mlp_train_step(float* d_params, float* d_m, float* d_v, int step, floa
 /* Training pairs from an exact cache built by chert_build_cache with the same
  * classes and M: for every (class, folded angle j = 0..M) of cache mode slot
  * `mode_slot` (wave mode `mode`), features x [n][8] and raw targets t [n][5]
- * (n = n_classes*(M+1)); flagged entries get t[:, 3] = 0.  d_scratch holds
- * at least 9*n bytes.  precision: storage type of the exact cache. */
+ * (n = n_classes*(M+1)); flagged entries get t[:, 3] = 0, and qSV entries
+ * with |vartheta| > 2 deg NaN targets for outputs 0-2 (the surrogate hands
+ * qSV entries beyond 1 deg to the exact solver, so only their validity and
+ * vartheta are learnt).  d_scratch holds
+ * at least 13*n bytes.  precision: storage type of the exact cache. */
 int chert_surrogate_dataset(const chert_class* d_classes, int n_classes, int M, int mode,
                             int mode_slot, const chert_cache_arrays* exact, int precision,
                             float* d_x, float* d_t, void* d_scratch, size_t scratch_bytes,
@@ -221,8 +247,11 @@ int chert_surrogate_dataset(const chert_class* d_classes, int n_classes, int M, 
 
 /* A cache of the same layout and meaning as chert_build_cache's, filled by
  * the networks (d_params_per_mode: host array of n_modes device pointers).
- * flag = 0 valid, 1 no acceptable root (network), 2 medium outside the
- * training range (the caller recomputes those classes with the exact solver). */
+ * flag = 0 valid, 1 no acceptable root (network), 2 needs the exact solver:
+ * the medium lies outside the training range, the network is unsure whether
+ * a decaying root exists (0.1 < p < 0.9), or, for qSV, the predicted
+ * imaginary angle exceeds 1 deg (cusp / triplication region).  The caller
+ * recomputes those solves with chert_build_cache_items. */
 size_t chert_surrogate_cache_workspace_bytes(int n_classes, int M);
 int chert_surrogate_cache(const float* const* d_params_per_mode, const chert_class* d_classes,
                           int n_classes, const int* modes, int n_modes, int M, int precision,

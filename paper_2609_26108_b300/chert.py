@@ -63,9 +63,14 @@ def lib():
     P, I, D, I64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_size_t
     L.chert_last_error.restype = ctypes.c_char_p
     L.chert_thomsen_to_class.argtypes = [D] * 10 + [ctypes.POINTER(chert_class)]
+    L.chert_thomsen_to_classes.argtypes = [I64] + [P] * 11
+    L.chert_thomsen_to_classes.restype = ctypes.c_int
     L.chert_build_cache.argtypes = [P, I, P, I, ctypes.POINTER(chert_cache_params),
                                     ctypes.POINTER(chert_cache_arrays), P]
     L.chert_edge_table.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, P, I, P, P, P, P]
+    L.chert_build_cache_items.argtypes = [P, I, P, I, ctypes.POINTER(chert_cache_params), P, I64,
+                                          ctypes.POINTER(chert_cache_arrays), P]
+    L.chert_build_cache_items.restype = ctypes.c_int
     L.chert_traveltime_workspace_bytes.argtypes = [I, I, I, I, I]
     L.chert_traveltime_workspace_bytes.restype = SZ
     L.chert_traveltime.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P, I,
@@ -157,9 +162,23 @@ def classes_from_layers(layers):
     return out
 
 
+def classes_from_arrays(vp0, vs0, eps, delta, gamma, qp, qs, rho=None, tilt=None, azim=None):
+    """Packed chert_class records (numpy uint8 [n*104]) for per-cell arrays."""
+    n = len(vp0)
+    f = lambda a, default: np.ascontiguousarray(np.full(n, default) if a is None else a, dtype=np.float64)
+    cols = [f(vp0, 0), f(vs0, 0), f(eps, 0), f(delta, 0), f(gamma, 0), f(qp, 0), f(qs, 0), f(rho, 2200.0),
+            f(tilt, 0.0), f(azim, 0.0)]
+    out = np.zeros(n * ctypes.sizeof(chert_class), dtype=np.uint8)
+    _check(lib().chert_thomsen_to_classes(n, *[c.ctypes.data_as(ctypes.c_void_p) for c in cols],
+                                          out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
 def classes_to_device(classes, device="cuda"):
     """Pack chert_class records into a device byte tensor (the ABI's array)."""
     torch = _torch()
+    if isinstance(classes, np.ndarray):
+        return torch.from_numpy(classes).to(device)
     arr = (chert_class * len(classes))(*classes)
     raw = np.frombuffer(bytes(arr), dtype=np.uint8).copy()
     return torch.from_numpy(raw).to(device)
@@ -204,6 +223,20 @@ def build_cache(d_classes, n_classes, modes, M, scan_step=0.001 * math.pi / 180,
     st = cache.struct()
     _check(lib().chert_build_cache(_dev_ptr(d_classes), n_classes, modes_arr, len(mode_ids),
                                    ctypes.byref(params), ctypes.byref(st), _stream_ptr(stream)))
+    return cache
+
+
+def build_cache_items(cache, d_classes, items, scan_step=0.001 * math.pi / 180, scan_half=30000, kernel="MEV",
+                      precision=None, stream=None):
+    """Exactly solve the listed solves (device int64 tensor) into `cache`."""
+    prec = cache.precision if precision is None else (PRECISION_IDS[precision] if isinstance(precision, str)
+                                                      else precision)
+    params = chert_cache_params(cache.M, scan_step, scan_half, KERNEL_IDS.get(kernel, kernel), prec)
+    modes_arr = (ctypes.c_int * len(cache.modes))(*cache.modes)
+    st = cache.struct()
+    _check(lib().chert_build_cache_items(_dev_ptr(d_classes), cache.n_classes, modes_arr, len(cache.modes),
+                                         ctypes.byref(params), _dev_ptr(items), int(items.numel()),
+                                         ctypes.byref(st), _stream_ptr(stream)))
     return cache
 
 
@@ -351,7 +384,7 @@ def surrogate_dataset(d_classes, n_classes, M, mode, mode_slot, exact_cache, str
     dev = d_classes.device
     x = torch.empty((n, 8), dtype=torch.float32, device=dev)
     t = torch.empty((n, 5), dtype=torch.float32, device=dev)
-    scratch = torch.empty(9 * n + 256, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(13 * n + 256, dtype=torch.uint8, device=dev)
     st = exact_cache.struct()
     mid = MODE_IDS[mode] if isinstance(mode, str) else mode
     _check(lib().chert_surrogate_dataset(_dev_ptr(d_classes), n_classes, M, mid, mode_slot, ctypes.byref(st),

@@ -42,3 +42,23 @@ extern "C" int chert_thomsen_to_class(double vp0, double vs0, double eps, double
     out->azim = azim;
     return CHERT_OK;
 }
+
+// Batched form of chert_thomsen_to_class for per-cell media (host arrays).
+extern "C" int chert_thomsen_to_classes(int64_t n, const double* vp0, const double* vs0, const double* eps,
+                                        const double* delta, const double* gamma, const double* qp,
+                                        const double* qs, const double* rho, const double* tilt,
+                                        const double* azim, chert_class* out) {
+    CHERT_REQUIRE(n >= 0 && vp0 && vs0 && eps && delta && gamma && qp && qs && rho && tilt && azim && out,
+                  "chert_thomsen_to_classes: NULL argument");
+    for (int64_t i = 0; i < n; ++i) {
+        const int rc = chert_thomsen_to_class(vp0[i], vs0[i], eps[i], delta[i], gamma[i], qp[i], qs[i], rho[i],
+                                              tilt[i], azim[i], out + i);
+        if (rc) {
+            char msg[512];
+            snprintf(msg, sizeof(msg), "%s (class %lld)", chert_last_error(), (long long)i);
+            chert::set_error("%s", msg);
+            return rc;
+        }
+    }
+    return CHERT_OK;
+}

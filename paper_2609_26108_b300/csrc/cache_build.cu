@@ -402,15 +402,19 @@ __device__ void write_entries(const Outs& out, const Solve<TS, TP>& v, int n_cla
 // side (the bulk of the roots lie there); solves that need a longer scan are
 // left marked kPending for the second launch.
 // TS: scan precision, TP: polish + ray-quantity precision, TO: storage.
+// With a solve list (items != NULL) warp w takes solve items[w]; a solve is
+// numbered mode_slot*n_classes*(M+1) + class*(M+1) + j.
 template <typename TS, typename TP, typename TO>
 __global__ void __launch_bounds__(256) cache_build_kernel(const chert_class* __restrict__ classes,
                                                           int n_classes, ModeList modes, int M,
-                                                          double h, int K, int kernel, Outs out) {
+                                                          double h, int K, int kernel, Outs out,
+                                                          const int64_t* __restrict__ items,
+                                                          long long n_items) {
     const int lane = threadIdx.x & 31;
     const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const long long total = static_cast<long long>(modes.n) * n_classes * (M + 1);
+    const long long total = items ? n_items : static_cast<long long>(modes.n) * n_classes * (M + 1);
     if (warp >= total) return;
-    const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, M, warp);
+    const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, M, items ? items[warp] : warp);
     bool found = false;
     TP root = TP(0);
     RayQ<TP> fq{};
@@ -434,8 +438,9 @@ __global__ void __launch_bounds__(256) cache_build_kernel(const chert_class* __r
 template <typename TS, typename TP, typename TO>
 __global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* __restrict__ classes,
                                                             int n_classes, ModeList modes, int M,
-                                                            double h, int K, int kernel, Outs out) {
-    const long long idx = blockIdx.x;
+                                                            double h, int K, int kernel, Outs out,
+                                                            const int64_t* __restrict__ items) {
+    const long long idx = items ? items[blockIdx.x] : static_cast<long long>(blockIdx.x);
     const int per = M + 1;
     {
         const int j = static_cast<int>(idx % per);
@@ -482,62 +487,64 @@ __global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* _
 }  // namespace
 }  // namespace chert
 
-extern "C" int chert_build_cache(const chert_class* d_classes, int n_classes, const int* modes,
-                                 int n_modes, const chert_cache_params* params,
-                                 const chert_cache_arrays* out, void* stream) {
+static int launch_build(const chert_class* d_classes, int n_classes, const int* modes, int n_modes,
+                        const chert_cache_params* params, const chert_cache_arrays* out,
+                        const int64_t* d_items, long long n_items, void* stream, const char* who) {
     using namespace chert;
-    CHERT_REQUIRE(d_classes && modes && params && out, "chert_build_cache: NULL argument");
-    CHERT_REQUIRE(n_classes >= 1, "chert_build_cache: n_classes=%d", n_classes);
-    CHERT_REQUIRE(n_modes >= 1 && n_modes <= 3, "chert_build_cache: n_modes=%d", n_modes);
-    CHERT_REQUIRE(params->M >= 1 && params->M <= (1 << 20), "chert_build_cache: M=%d", params->M);
-    CHERT_REQUIRE(params->scan_step > 0 && params->scan_half >= 1 &&
-                      params->scan_half <= (1 << 28),
-                  "chert_build_cache: bad scan grid");
-    CHERT_REQUIRE(params->kernel == CHERT_OEV || params->kernel == CHERT_MEV,
-                  "chert_build_cache: kernel=%d", params->kernel);
-    CHERT_REQUIRE(out->V && out->rx && out->rz && out->flag,
-                  "chert_build_cache: V, rx, rz and flag outputs are required");
+    CHERT_REQUIRE(d_classes && modes && params && out, "%s: NULL argument", who);
+    CHERT_REQUIRE(n_classes >= 1, "%s: n_classes=%d", who, n_classes);
+    CHERT_REQUIRE(n_modes >= 1 && n_modes <= 3, "%s: n_modes=%d", who, n_modes);
+    CHERT_REQUIRE(params->M >= 1 && params->M <= (1 << 20), "%s: M=%d", who, params->M);
+    CHERT_REQUIRE(params->scan_step > 0 && params->scan_half >= 1 && params->scan_half <= (1 << 28),
+                  "%s: bad scan grid", who);
+    CHERT_REQUIRE(params->kernel == CHERT_OEV || params->kernel == CHERT_MEV, "%s: kernel=%d", who,
+                  params->kernel);
+    CHERT_REQUIRE(out->V && out->rx && out->rz && out->flag, "%s: V, rx, rz and flag outputs are required", who);
     ModeList ml{{0, 0, 0}, n_modes};
     for (int i = 0; i < n_modes; i++) {
-        CHERT_REQUIRE(modes[i] >= CHERT_QP && modes[i] <= CHERT_QSH, "chert_build_cache: mode %d",
-                      modes[i]);
-        for (int j = 0; j < i; j++)
-            CHERT_REQUIRE(modes[j] != modes[i], "chert_build_cache: repeated mode");
+        CHERT_REQUIRE(modes[i] >= CHERT_QP && modes[i] <= CHERT_QSH, "%s: mode %d", who, modes[i]);
+        for (int j = 0; j < i; j++) CHERT_REQUIRE(modes[j] != modes[i], "%s: repeated mode", who);
         ml.m[i] = modes[i];
     }
     Outs o{out->V, out->A, out->Q, out->rx, out->rz, out->theta, out->vartheta, out->flag};
-    const long long warps = static_cast<long long>(n_modes) * n_classes * (params->M + 1);
+    const long long warps = d_items ? n_items : static_cast<long long>(n_modes) * n_classes * (params->M + 1);
+    if (warps == 0) return CHERT_OK;
     const int threads = 256;
     const long long blocks = (warps * 32 + threads - 1) / threads;
-    CHERT_REQUIRE(blocks < (1LL << 31), "chert_build_cache: problem too large");
+    CHERT_REQUIRE(blocks < (1LL << 31), "%s: problem too large", who);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double h = params->scan_step;
     const int K = params->scan_half;
     const unsigned solves = (unsigned)warps;
+    const int Mq = params->M, kern = params->kernel;
+#define CHERT_LAUNCH_BUILD(TS, TP, TO)                                                                  \
+    cache_build_kernel<TS, TP, TO><<<(unsigned)blocks, threads, 0, s>>>(d_classes, n_classes, ml, Mq, h, K, \
+                                                                       kern, o, d_items, n_items);       \
+    if (K > kPhase1Reach)                                                                               \
+        cache_finish_kernel<TS, TP, TO><<<solves, 1024, 0, s>>>(d_classes, n_classes, ml, Mq, h, K, kern, o, \
+                                                                 d_items);
     switch (params->precision) {
-        case CHERT_FP64:
-            cache_build_kernel<double, double, double><<<(unsigned)blocks, threads, 0, s>>>(
-                d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
-            if (K > kPhase1Reach)
-                cache_finish_kernel<double, double, double><<<solves, 1024, 0, s>>>(
-                    d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
-            break;
-        case CHERT_FP32:
-            cache_build_kernel<float, float, float><<<(unsigned)blocks, threads, 0, s>>>(
-                d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
-            if (K > kPhase1Reach)
-                cache_finish_kernel<float, float, float><<<solves, 1024, 0, s>>>(
-                    d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
-            break;
-        case CHERT_MIXED:
-            cache_build_kernel<float, double, float><<<(unsigned)blocks, threads, 0, s>>>(
-                d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
-            if (K > kPhase1Reach)
-                cache_finish_kernel<float, double, float><<<solves, 1024, 0, s>>>(
-                    d_classes, n_classes, ml, params->M, h, K, params->kernel, o);
-            break;
-        default:
-            CHERT_REQUIRE(false, "chert_build_cache: precision=%d", params->precision);
+        case CHERT_FP64: CHERT_LAUNCH_BUILD(double, double, double) break;
+        case CHERT_FP32: CHERT_LAUNCH_BUILD(float, float, float) break;
+        case CHERT_MIXED: CHERT_LAUNCH_BUILD(float, double, float) break;
+        default: CHERT_REQUIRE(false, "%s: precision=%d", who, params->precision);
     }
-    return launch_check("chert_build_cache");
+#undef CHERT_LAUNCH_BUILD
+    return launch_check(who);
+}
+
+extern "C" int chert_build_cache(const chert_class* d_classes, int n_classes, const int* modes,
+                                 int n_modes, const chert_cache_params* params,
+                                 const chert_cache_arrays* out, void* stream) {
+    return launch_build(d_classes, n_classes, modes, n_modes, params, out, nullptr, 0, stream,
+                        "chert_build_cache");
+}
+
+extern "C" int chert_build_cache_items(const chert_class* d_classes, int n_classes, const int* modes,
+                                       int n_modes, const chert_cache_params* params,
+                                       const int64_t* d_items, int64_t n_items,
+                                       const chert_cache_arrays* out, void* stream) {
+    CHERT_REQUIRE(d_items && n_items >= 0, "chert_build_cache_items: bad item list");
+    return launch_build(d_classes, n_classes, modes, n_modes, params, out, d_items, n_items, stream,
+                        "chert_build_cache_items");
 }

@@ -11,14 +11,17 @@
 //
 // Inputs (features) are the folded slowness angle and the dimensionless
 // medium (Vs0/Vp0, eps, delta, gamma, 1/Qp, 1/Qs) scaled to [-1, 1] over the
-// training range; outputs, after un-standardising, are (V/Vg - 1, A*Vg,
-// psi - psi_el, validity logit, vartheta) where Vg and psi_el are the elastic
-// group velocity and ray angle (closed form, derivative by hand).
+// training range; outputs, after un-standardising, are (V/Vg - 1, log(A/A0),
+// psi - psi_el, validity logit, vartheta) with the attenuation learnt as a
+// logarithm, where Vg and psi_el are the elastic group velocity and ray angle
+// (closed form, derivative by hand) and A0 the attenuation of the homogeneous
+// plane wave along the slowness direction, projected on the elastic ray.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdint.h>
 
 #include "common.cuh"
+#include "cplx.cuh"
 #include "mlp_gemm.cuh"
 
 namespace chert {
@@ -51,6 +54,7 @@ __host__ __device__ inline Layout layout() {
 struct MediumDims {
     float rs, eps, delta, gamma, iqp, iqs;   // dimensionless medium
     float a11, a13, a33, a44, a66;           // real moduli / Vp0^2
+    float b11, b13, b33, b44, b66;           // imaginary moduli / Vp0^2 (a = aR - i aI)
 };
 
 // Dimensionless medium of a class: moduli over a33 (= Vp0^2); Thomsen's
@@ -70,7 +74,37 @@ __device__ inline MediumDims dims_of(const chert_class& c) {
     d.delta = float((s * s - (a33 - a44) * (a33 - a44)) / (2.0 * a33 * (a33 - a44)));
     d.iqp = float(c.aI[2] / a33);
     d.iqs = float(c.aI[3] / a44);
+    d.b11 = float(c.aI[0] / a33);
+    d.b13 = float(c.aI[1] / a33);
+    d.b33 = float(c.aI[2] / a33);
+    d.b44 = float(c.aI[3] / a33);
+    d.b66 = float(c.aI[4] / a33);
     return d;
+}
+
+// Attenuation baseline (in units of 1/Vp0): the homogeneous plane wave along the
+// real slowness direction th has the complex phase velocity c = sqrt(lambda)
+// of the complex Christoffel block, and decays by Im(1/c) per unit length along
+// that direction; projected on the elastic ray direction psi_el.
+__device__ inline float attenuation_baseline(const MediumDims& m, int mode, float th, float psi_el) {
+    float s, c;
+    sincosf(th, &s, &c);
+    const float s2 = s * s, c2 = c * c;
+    const cplx<float> a11 = mk(m.a11, -m.b11), a13 = mk(m.a13, -m.b13), a33 = mk(m.a33, -m.b33);
+    const cplx<float> a44 = mk(m.a44, -m.b44), a66 = mk(m.a66, -m.b66);
+    cplx<float> lam;
+    if (mode == CHERT_QSH) {
+        lam = s2 * a66 + c2 * a44;
+    } else {
+        const cplx<float> g11 = s2 * a11 + c2 * a44, g33 = s2 * a44 + c2 * a33;
+        const cplx<float> g13 = (s * c) * (a13 + a44);
+        const cplx<float> d = g11 - g33;
+        const cplx<float> root = csqrt(d * d + 4.0f * (g13 * g13));
+        const cplx<float> l1 = 0.5f * (g11 + g33 + root), l2 = 0.5f * (g11 + g33 - root);
+        lam = ((mode == CHERT_QP) == (l1.re >= l2.re)) ? l1 : l2;
+    }
+    const cplx<float> inv = mk(1.0f, 0.0f) / csqrt(lam);
+    return inv.im * cosf(psi_el - th);
 }
 
 // Elastic group velocity (in units of Vp0) and ray angle at slowness angle th.
@@ -114,7 +148,7 @@ __device__ inline bool scale_features(const MediumDims& m, float th, float* x) {
 // One item per (mode slot, class, folded angle j): features and baseline.
 __global__ void features_kernel(const chert_class* __restrict__ classes, int n_classes, int M,
                                 int mode, float* __restrict__ x, float* __restrict__ Vg,
-                                float* __restrict__ psi, uint8_t* __restrict__ outside) {
+                                float* __restrict__ psi, float* __restrict__ A0, uint8_t* __restrict__ outside) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long n = (long long)n_classes * (M + 1);
     if (i >= n) return;
@@ -130,18 +164,33 @@ __global__ void features_kernel(const chert_class* __restrict__ classes, int n_c
     elastic_baseline(m, mode, th, vg, ps);
     Vg[i] = vg;
     psi[i] = ps;
+    A0[i] = attenuation_baseline(m, mode, th, ps);
 }
+
+// A network answer counts as sure when its validity logit is at least this far
+// from 0 (p outside [0.1, 0.9]).
+constexpr float kSureLogit = 2.2f;
+// qSV entries whose imaginary angle exceeds 1 degree (cusp and triplication
+// region, where the exact solution moves far from the homogeneous wave) go to
+// the exact solver; the training set leaves out their ray quantities beyond
+// twice that angle (NaN targets), which the network then never has to fit.
+constexpr float kQsvBranchAngle = 0.0174533f;
+constexpr float kQsvTrainAngle = 2.0f * kQsvBranchAngle;
 
 // Training targets from an exact cache (float or double arrays): entry d = j
 // of the first quadrant (d = M for j = M, mirrored in z), rotated back into
-// the local frame; raw targets (V/Vg - 1, A*Vg, psi - psi_el, valid, vartheta).
+// the local frame; raw targets (V/Vg - 1, log(A/A0), psi - psi_el, valid,
+// vartheta).  The attenuation is learnt as a logarithm so that the network
+// cannot return a negative or zero one (a zero-cost edge for the attenuation
+// traveltime).  qSV entries with |vartheta| > kQsvTrainAngle get NaN targets
+// for the outputs 0-2.
 template <typename TC>
 __global__ void targets_kernel(const chert_class* __restrict__ classes, int n_classes, int M,
-                               int mode_slot, const TC* __restrict__ V, const TC* __restrict__ A,
+                               int mode, int mode_slot, const TC* __restrict__ V, const TC* __restrict__ A,
                                const TC* __restrict__ rx, const TC* __restrict__ rz,
                                const TC* __restrict__ vt, const uint8_t* __restrict__ flag,
                                const float* __restrict__ Vg, const float* __restrict__ psi_el,
-                               float* __restrict__ t) {
+                               const float* __restrict__ A0, float* __restrict__ t) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long n = (long long)n_classes * (M + 1);
     if (i >= n) return;
@@ -165,12 +214,13 @@ __global__ void targets_kernel(const chert_class* __restrict__ classes, int n_cl
     const double psi = atan2(lx, lz);
     const double vg = double(Vg[i]) * vp0;
     o[0] = float(double(V[e]) / vg - 1.0);
-    o[1] = float(double(A[e]) * vg);
+    o[1] = float(log(fmax(double(A[e]) * vp0, 1e-30) / fmax(double(A0[i]), 1e-30)));
     double dpsi = psi - double(psi_el[i]);
     dpsi = atan2(sin(dpsi), cos(dpsi));
     o[2] = float(dpsi);
     o[3] = 1.0f;
     o[4] = float(vtheta);
+    if (mode == CHERT_QSV && fabs(vtheta) > double(kQsvTrainAngle)) o[0] = o[1] = o[2] = __int_as_float(0x7fc00000);
 }
 
 // ----------------------------------------------------------------- training pieces
@@ -216,7 +266,8 @@ __global__ void loss_grad_kernel(const float* __restrict__ y, const float* __res
                 l += fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))) - tt * z;
                 gk = p - tt;
             } else {
-                const float d = valid ? y[i * kOut + k] - (t[i * kOut + k] - mean[k]) / std[k] : 0.0f;
+                const float tk = t[i * kOut + k];
+                const float d = (valid && !isnan(tk)) ? y[i * kOut + k] - (tk - mean[k]) / std[k] : 0.0f;
                 l += 0.5f * d * d;
                 gk = d;
             }
@@ -267,25 +318,35 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 }
 
 // Decode network outputs into the mirrored, tilted cache entries (Eq. 36).
+// Items i of one chunk cover classes k0 .. k0 + n_chunk - 1 of n_total.
+// An entry is handed to the exact solver (flag 2) when its medium lies outside
+// the training range, when the network is unsure whether a decaying root
+// exists (|logit| < 2.2, i.e. 0.1 < p < 0.9), or, for qSV, when the predicted
+// imaginary angle exceeds 1 deg -- the cusp and triplication region where the
+// selected root switches branch.
+
 template <typename TO>
-__global__ void decode_kernel(const chert_class* __restrict__ classes, int n_classes, int M, int mi,
-                              const float* __restrict__ y, const float* __restrict__ mean,
+__global__ void decode_kernel(const chert_class* __restrict__ classes, int n_total, int k0, int n_chunk,
+                              int M, int mi, int mode, const float* __restrict__ y, const float* __restrict__ mean,
                               const float* __restrict__ std, const float* __restrict__ Vg,
-                              const float* __restrict__ psi_el, const uint8_t* __restrict__ outside,
-                              chert_cache_arrays out) {
+                              const float* __restrict__ psi_el, const float* __restrict__ A0,
+                              const uint8_t* __restrict__ outside, chert_cache_arrays out) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long n = (long long)n_classes * (M + 1);
+    const long long n = (long long)n_chunk * (M + 1);
     if (i >= n) return;
-    const int j = int(i % (M + 1)), k = int(i / (M + 1));
+    const int j = int(i % (M + 1)), k = k0 + int(i / (M + 1));
+    const int n_classes = n_total;
     const chert_class c = classes[k];
     const double vp0 = sqrt(c.aR[2]);
     float t[kOut];
 #pragma unroll
     for (int q = 0; q < kOut; ++q) t[q] = y[i * kOut + q] * std[q] + mean[q];
-    const bool valid = y[i * kOut + 3] > 0.0f;
-    const uint8_t fl = outside[i] ? 2 : (valid ? 0 : 1);
+    const float logit = y[i * kOut + 3];
+    const bool unsure = fabsf(logit) < kSureLogit ||
+                        (mode == CHERT_QSV && logit > 0.0f && fabsf(t[4]) > kQsvBranchAngle);
+    const uint8_t fl = (outside[i] || unsure) ? 2 : (logit > 0.0f ? 0 : 1);
     const double V = double(Vg[i]) * vp0 * (1.0 + t[0]);
-    const double A = double(t[1]) / (double(Vg[i]) * vp0);
+    const double A = double(A0[i]) * exp(double(t[1])) / vp0;
     const double psi = double(psi_el[i]) + t[2];
     const double vr = 1.0, vi = -A * V;                  // v_I / v_R = -A V
     const double Q = vi == 0.0 ? INFINITY : -(vr * vr - vi * vi) / (2.0 * vr * vi);
@@ -513,29 +574,38 @@ extern "C" int chert_surrogate_dataset(const chert_class* d_classes, int n_class
     CHERT_REQUIRE(d_classes && exact && d_x && d_t && d_scratch && n_classes >= 1 && M >= 1,
                   "chert_surrogate_dataset: bad argument");
     const long long n = (long long)n_classes * (M + 1);
-    CHERT_REQUIRE(scratch_bytes >= (size_t)n * 9, "chert_surrogate_dataset: scratch too small");
+    CHERT_REQUIRE(scratch_bytes >= (size_t)n * 13, "chert_surrogate_dataset: scratch too small");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float* Vg = static_cast<float*>(d_scratch);
     float* psi = Vg + n;
-    uint8_t* outside = reinterpret_cast<uint8_t*>(psi + n);
-    features_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_classes, n_classes, M, mode, d_x, Vg, psi, outside);
+    float* A0 = psi + n;
+    uint8_t* outside = reinterpret_cast<uint8_t*>(A0 + n);
+    features_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_classes, n_classes, M, mode, d_x, Vg, psi, A0, outside);
     if (precision == CHERT_FP64)
         targets_kernel<double><<<grid_for(n, 256), 256, 0, s>>>(
-            d_classes, n_classes, M, mode_slot, (const double*)exact->V, (const double*)exact->A,
+            d_classes, n_classes, M, mode, mode_slot, (const double*)exact->V, (const double*)exact->A,
             (const double*)exact->rx, (const double*)exact->rz, (const double*)exact->vartheta,
-            exact->flag, Vg, psi, d_t);
+            exact->flag, Vg, psi, A0, d_t);
     else
         targets_kernel<float><<<grid_for(n, 256), 256, 0, s>>>(
-            d_classes, n_classes, M, mode_slot, (const float*)exact->V, (const float*)exact->A,
+            d_classes, n_classes, M, mode, mode_slot, (const float*)exact->V, (const float*)exact->A,
             (const float*)exact->rx, (const float*)exact->rz, (const float*)exact->vartheta,
-            exact->flag, Vg, psi, d_t);
+            exact->flag, Vg, psi, A0, d_t);
     return launch_check("chert_surrogate_dataset");
+}
+
+// Classes per inference chunk: about 4M entries at a time.
+static int chunk_classes(int n_classes, int M) {
+    const long long per = (long long)(M + 1);
+    long long c = (4LL << 20) / per;
+    if (c < 1) c = 1;
+    return (int)(c < n_classes ? c : n_classes);
 }
 
 extern "C" size_t chert_surrogate_cache_workspace_bytes(int n_classes, int M) {
     if (n_classes < 1 || M < 1) return 0;
-    const long long n = (long long)n_classes * (M + 1);
-    return al((size_t)n * kInPad * 4) + al((size_t)n * 9) + al((size_t)n * kOut * 4) +
+    const long long n = (long long)chunk_classes(n_classes, M) * (M + 1);
+    return al((size_t)n * kInPad * 4) + al((size_t)n * 13) + al((size_t)n * kOut * 4) +
            ws_carve(nullptr, n, false).bytes;
 }
 
@@ -551,30 +621,39 @@ extern "C" int chert_surrogate_cache(const float* const* d_params_per_mode, cons
         set_error("chert_surrogate_cache: workspace %zu < %zu bytes", ws_bytes, need);
         return CHERT_ENOMEM;
     }
-    const long long n = (long long)n_classes * (M + 1);
+    const int chunk = chunk_classes(n_classes, M);
+    const long long nmax = (long long)chunk * (M + 1);
     unsigned char* p = static_cast<unsigned char*>(d_ws);
-    float* x = (float*)p; p += al((size_t)n * kInPad * 4);
+    float* x = (float*)p; p += al((size_t)nmax * kInPad * 4);
     float* Vg = (float*)p;
-    float* psi = Vg + n;
-    uint8_t* outside = (uint8_t*)(psi + n); p += al((size_t)n * 9);
-    float* y = (float*)p; p += al((size_t)n * kOut * 4);
+    float* psi = Vg + nmax;
+    float* A0 = psi + nmax;
+    uint8_t* outside = (uint8_t*)(A0 + nmax); p += al((size_t)nmax * 13);
+    float* y = (float*)p; p += al((size_t)nmax * kOut * 4);
+    const size_t rest = ws_bytes - (size_t)(p - (unsigned char*)d_ws);
     const Layout L = layout();
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (int mi = 0; mi < n_modes; ++mi) {
         CHERT_REQUIRE(d_params_per_mode[mi], "chert_surrogate_cache: NULL parameters");
-        features_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_classes, n_classes, M, modes[mi], x, Vg, psi,
-                                                          outside);
-        int rc = chert_mlp_forward(d_params_per_mode[mi], x, n, y, p, ws_bytes - (p - (unsigned char*)d_ws), stream);
-        if (rc) return rc;
         const float* prm = d_params_per_mode[mi];
-        if (precision == CHERT_FP64)
-            decode_kernel<double><<<grid_for(n, 256), 256, 0, s>>>(d_classes, n_classes, M, mi, y,
-                                                                  prm + L.mean, prm + L.std, Vg, psi,
-                                                                  outside, *out);
-        else
-            decode_kernel<float><<<grid_for(n, 256), 256, 0, s>>>(d_classes, n_classes, M, mi, y,
-                                                                 prm + L.mean, prm + L.std, Vg, psi,
-                                                                 outside, *out);
+        for (int k0 = 0; k0 < n_classes; k0 += chunk) {
+            const int nc = chunk < n_classes - k0 ? chunk : n_classes - k0;
+            const long long n = (long long)nc * (M + 1);
+            features_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_classes + k0, nc, M, modes[mi], x, Vg, psi,
+                                                              A0, outside);
+            int rc = chert_mlp_forward(prm, x, n, y, p, rest, stream);
+            if (rc) return rc;
+            if (precision == CHERT_FP64)
+                decode_kernel<double><<<grid_for(n, 256), 256, 0, s>>>(d_classes, n_classes, k0, nc, M, mi,
+                                                                      modes[mi], y,
+                                                                      prm + L.mean, prm + L.std, Vg, psi,
+                                                                      A0, outside, *out);
+            else
+                decode_kernel<float><<<grid_for(n, 256), 256, 0, s>>>(d_classes, n_classes, k0, nc, M, mi,
+                                                                     modes[mi], y,
+                                                                     prm + L.mean, prm + L.std, Vg, psi,
+                                                                     A0, outside, *out);
+        }
     }
     return launch_check("chert_surrogate_cache");
 }

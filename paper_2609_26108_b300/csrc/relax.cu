@@ -120,11 +120,25 @@ struct Smem {
     int* counts;   // 4
 };
 
+// Weight of the edge i -> j through offset o (Eq. 28-30):
+//   WMODE 1: pair table W[o][k_i][k_j] in shared memory;
+//   WMODE 0: looked-up values [k][o] in shared memory, formula per pull;
+//   WMODE 2: looked-up values [k][o] in global memory (any number of classes,
+//            e.g. one class per cell), formula per pull.
+template <typename T, int WMODE>
+__device__ __forceinline__ T pull_weight(const Smem<T>& sm, const T* __restrict__ gsel, int n_off, int nk,
+                                         int comp, int o, int ki, int kj) {
+    if (WMODE == 1) return sm.W[(o * nk + ki) * nk + kj];
+    if (WMODE == 0) return edge_w<T>(comp, sm.L[o], sm.W[ki * n_off + o], sm.W[kj * n_off + o]);
+    return edge_w<T>(comp, sm.L[o], gsel[(size_t)ki * n_off + o], gsel[(size_t)kj * n_off + o]);
+}
+
 // One sweep: lines advance along `axis` (0: rows in z, 1: columns in x) in
 // direction `dir`; each node pulls from the offsets of its sweep list.
-template <typename T, bool TABLE>
-__device__ bool sweep(const Smem<T>& sm, const Offsets& off, int list, int axis, int dir, T* tau,
-                      const int32_t* __restrict__ cls, int nx, int nz, int nk, int comp, int ring) {
+template <typename T, int WMODE>
+__device__ bool sweep(const Smem<T>& sm, const T* __restrict__ gsel, const Offsets& off, int list, int axis,
+                      int dir, T* tau, const int32_t* __restrict__ cls, int nx, int nz, int nk, int comp,
+                      int ring) {
     const int n_lines = axis == 0 ? nz : nx;
     const int len = axis == 0 ? nx : nz;
     const short* lst = sm.lists + list * off.n;
@@ -148,9 +162,7 @@ __device__ bool sweep(const Smem<T>& sm, const Offsets& off, int list, int axis,
                 if (il < 0 || il >= n_lines || iu < 0 || iu >= len) continue;
                 const int s = (il % ring) * len + iu;
                 const int ki = sm.cring[s];
-                T w;
-                if (TABLE) w = sm.W[(o * nk + ki) * nk + kj];
-                else w = edge_w<T>(comp, sm.L[o], sm.W[ki * off.n + o], sm.W[kj * off.n + o]);
+                const T w = pull_weight<T, WMODE>(sm, gsel, off.n, nk, comp, o, ki, kj);
                 best = fmin(best, sm.ring[s] + w);
             }
             sm.ring[slot * len + u] = best;
@@ -166,9 +178,10 @@ __device__ bool sweep(const Smem<T>& sm, const Offsets& off, int list, int axis,
 
 // Pull every node from all in-neighbours; lower tau where possible (returns
 // true if anything changed) and record the argmin parent.
-template <typename T, bool TABLE>
-__device__ bool verify(const Smem<T>& sm, const Offsets& off, T* tau, const int32_t* __restrict__ cls,
-                       int nx, int nz, int nk, int comp, int64_t src, int32_t* par) {
+template <typename T, int WMODE>
+__device__ bool verify(const Smem<T>& sm, const T* __restrict__ gsel, const Offsets& off, T* tau,
+                       const int32_t* __restrict__ cls, int nx, int nz, int nk, int comp, int64_t src,
+                       int32_t* par) {
     bool changed = false;
     const int n = nx * nz;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -183,9 +196,7 @@ __device__ bool verify(const Smem<T>& sm, const Offsets& off, T* tau, const int3
             const int i = xi + nx * zi;
             const T ti = tau[i];
             const int ki = clamp_class(cls[i], nk);
-            T w;
-            if (TABLE) w = sm.W[(o * nk + ki) * nk + kj];
-            else w = edge_w<T>(comp, sm.L[o], sm.W[ki * off.n + o], sm.W[kj * off.n + o]);
+            const T w = pull_weight<T, WMODE>(sm, gsel, off.n, nk, comp, o, ki, kj);
             const T c = ti + w;
             if (c < best || (c == best && i < bi)) { best = c; bi = i; }
         }
@@ -199,7 +210,7 @@ __device__ bool verify(const Smem<T>& sm, const Offsets& off, T* tau, const int3
     return __syncthreads_or(changed);
 }
 
-template <typename T, bool TABLE>
+template <typename T, int WMODE>
 __global__ void __launch_bounds__(512) relax_kernel(FieldArgs a, Offsets off) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = a.n_classes;
@@ -212,7 +223,8 @@ __global__ void __launch_bounds__(512) relax_kernel(FieldArgs a, Offsets off) {
 
     Smem<T> sm;
     unsigned char* p = smem_raw;
-    const size_t wcount = TABLE ? static_cast<size_t>(off.n) * nk * nk : static_cast<size_t>(nk) * off.n;
+    const size_t wcount = WMODE == 1 ? static_cast<size_t>(off.n) * nk * nk
+                          : WMODE == 0 ? static_cast<size_t>(nk) * off.n : 0;
     sm.W = reinterpret_cast<T*>(p); p += wcount * sizeof(T);
     sm.L = reinterpret_cast<T*>(p); p += off.n * sizeof(T);
     sm.ring = reinterpret_cast<T*>(p); p += static_cast<size_t>(a.ring) * line_max * sizeof(T);
@@ -228,12 +240,12 @@ __global__ void __launch_bounds__(512) relax_kernel(FieldArgs a, Offsets off) {
         sm.L[o] = T(a.dx * sqrt(ox * ox + oz * oz));
     }
     __syncthreads();
-    if (TABLE) {
+    if (WMODE == 1) {
         for (int t = threadIdx.x; t < off.n * nk * nk; t += blockDim.x) {
             const int kj = t % nk, ki = (t / nk) % nk, o = t / (nk * nk);
             sm.W[t] = edge_w<T>(comp, sm.L[o], sel[ki * off.n + o], sel[kj * off.n + o]);
         }
-    } else {
+    } else if (WMODE == 0) {
         for (int t = threadIdx.x; t < nk * off.n; t += blockDim.x) sm.W[t] = sel[t];
     }
     if (threadIdx.x == 0) {
@@ -256,11 +268,11 @@ __global__ void __launch_bounds__(512) relax_kernel(FieldArgs a, Offsets off) {
 
     int used = -1;
     for (int cycle = 0; cycle < a.max_cycles; ++cycle) {
-        sweep<T, TABLE>(sm, off, 0, 0, +1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
-        sweep<T, TABLE>(sm, off, 1, 1, +1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
-        sweep<T, TABLE>(sm, off, 2, 1, -1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
-        sweep<T, TABLE>(sm, off, 3, 0, -1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
-        if (!verify<T, TABLE>(sm, off, tau, a.cls, a.nx, a.nz, nk, comp, src, par)) {
+        sweep<T, WMODE>(sm, sel, off, 0, 0, +1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
+        sweep<T, WMODE>(sm, sel, off, 1, 1, +1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
+        sweep<T, WMODE>(sm, sel, off, 2, 1, -1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
+        sweep<T, WMODE>(sm, sel, off, 3, 0, -1, tau, a.cls, a.nx, a.nz, nk, comp, a.ring);
+        if (!verify<T, WMODE>(sm, sel, off, tau, a.cls, a.nx, a.nz, nk, comp, src, par)) {
             used = cycle + 1;
             break;
         }
@@ -372,13 +384,13 @@ extern "C" size_t chert_traveltime_workspace_bytes(int n_modes, int n_classes, i
     return ws_layout(n_modes, n_classes, n_off, precision, n_sources).total;
 }
 
-template <typename T, bool TABLE>
+template <typename T, int WMODE>
 static int launch_relax(const FieldArgs& a, const Offsets& off, size_t smem, int blocks,
                         cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(relax_kernel<T, TABLE>,
+    cudaError_t e = cudaFuncSetAttribute(relax_kernel<T, WMODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
-    relax_kernel<T, TABLE><<<blocks, 512, smem, s>>>(a, off);
+    relax_kernel<T, WMODE><<<blocks, 512, smem, s>>>(a, off);
     return launch_check("chert_traveltime: relax");
 }
 
@@ -516,8 +528,7 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const bool table = smem_table <= (size_t)std::min(smem_max, 120 * 1024);
-    CHERT_REQUIRE(table || smem_raw <= (size_t)smem_max,
-                  "%s: %d classes x %d offsets do not fit in shared memory", who, n_classes, n_off);
+    const bool raw_smem = smem_raw <= (size_t)smem_max;
     const int blocks = n_sources * n_modes * 2;
     fast::Args fa;
     fa.nx = nx; fa.nz = nz; fa.n_classes = n_classes; fa.n_modes = n_modes;
@@ -530,11 +541,13 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     if (fr < 0) return fr;
     if (fr == 1) rc = CHERT_OK;
     else if (precision == CHERT_FP64)
-        rc = table ? launch_relax<double, true>(a, off, smem_table, blocks, s)
-                   : launch_relax<double, false>(a, off, smem_raw, blocks, s);
+        rc = table ? launch_relax<double, 1>(a, off, smem_table, blocks, s)
+           : raw_smem ? launch_relax<double, 0>(a, off, smem_raw, blocks, s)
+                      : launch_relax<double, 2>(a, off, common, blocks, s);
     else
-        rc = table ? launch_relax<float, true>(a, off, smem_table, blocks, s)
-                   : launch_relax<float, false>(a, off, smem_raw, blocks, s);
+        rc = table ? launch_relax<float, 1>(a, off, smem_table, blocks, s)
+           : raw_smem ? launch_relax<float, 0>(a, off, smem_raw, blocks, s)
+                      : launch_relax<float, 2>(a, off, common, blocks, s);
     if (rc) return rc;
     *blocks_out = blocks;
     *status_out = a.status;

@@ -207,3 +207,67 @@ def mlp_init(seed: int, n_in: int = 7, n_hid: int = 256, n_layers: int = 4, n_ou
     rng = np.random.default_rng(seed)
     sizes = [n_in] + [n_hid] * n_layers + [n_out]
     return [(rng.normal(0.0, math.sqrt(2.0 / a), (b_, a)), np.zeros(b_)) for a, b_ in zip(sizes[:-1], sizes[1:])]
+
+
+@dataclass
+class CellModel2D:
+    """A 2D model with its own medium at every node (one cache class per node)."""
+    name: str
+    nx: int
+    nz: int
+    dx: float
+    params: dict                         # per-node arrays: vp0 vs0 eps delta gamma qp qs tilt
+    layer_of_node: np.ndarray            # int32 [nz*nx]
+    sources: np.ndarray
+
+
+def folded_faulted(nx: int = 1701, nz: int = 351, n_layers: int = 10, n_sources: int = 64,
+                   seed: int = 1003, dx: float = 10.0) -> CellModel2D:
+    """Seeded folded and faulted layered visco-TTI model with per-node media.
+
+    Interfaces z_i(x) = zbar_i + A_i sin(2 pi x / lambda_i + phi_i) (node units,
+    A ~ U(3%, 6%) of the depth, lambda ~ U(0.2, 0.6) of the width); one normal
+    fault at x_f ~ U(0.35, 0.65) nx dipping 60 deg with a 150 m throw (the
+    hanging wall's layers sit 150 m deeper).  Per layer: Thomsen means as in
+    ``seeded_tti_layers``; per node: the layer mean times (1 + g x') with
+    g ~ U(-0.06, 0.06) per layer and parameter, x' = x/(nx-1) - 1/2, plus
+    0.5% white noise; the symmetry axis follows the local dip of the layer's
+    top interface plus the layer's tilt.  Surface sources as in layered_tti."""
+    rng = np.random.default_rng(seed)
+    base = seeded_tti_layers(n_layers, int(rng.integers(1 << 30)))
+    x = np.arange(nx, dtype=np.float64)
+    z = np.arange(nz, dtype=np.float64)
+    zbar = np.arange(1, n_layers) * (nz - 1) / n_layers
+    amp = rng.uniform(0.03, 0.06, n_layers - 1) * nz
+    lam = rng.uniform(0.2, 0.6, n_layers - 1) * nx
+    ph = rng.uniform(0.0, 2 * math.pi, n_layers - 1)
+    iface = zbar[:, None] + amp[:, None] * np.sin(2 * math.pi * x[None] / lam[:, None] + ph[:, None])
+    slope = amp[:, None] * (2 * math.pi / lam[:, None]) * np.cos(2 * math.pi * x[None] / lam[:, None] + ph[:, None])
+    xf = rng.uniform(0.35, 0.65) * nx
+    throw = 150.0 / dx
+    hanging = x[None, :] > xf + z[:, None] / math.tan(math.radians(60.0))
+    zz = z[:, None] - np.where(hanging, throw, 0.0)
+    layer = (iface[:, None, :] <= zz[None]).sum(axis=0).astype(np.int32)           # [nz, nx]
+    top = np.clip(layer - 1, 0, n_layers - 2)
+    dip = np.arctan(slope[top, np.arange(nx)[None, :]])
+    xp = x / (nx - 1) - 0.5
+    out = {}
+    for key in ("vp0", "ratio", "eps", "delta", "gamma", "qp", "qs"):
+        g = rng.uniform(-0.06, 0.06, n_layers)
+        if key == "ratio":
+            mean = np.array([L.vp0 / L.vs0 for L in base])
+        else:
+            mean = np.array([getattr(L, key) for L in base])
+        field_ = mean[layer] * (1.0 + g[layer] * xp[None, :])
+        field_ = field_ * (1.0 + 0.005 * rng.standard_normal((nz, nx)))
+        out[key] = field_
+    out["ratio"] = np.clip(out["ratio"], 1.6, 2.1)
+    out["qs"] = np.minimum(out["qs"], out["qp"])
+    params = {"vp0": out["vp0"].reshape(-1), "vs0": (out["vp0"] / out["ratio"]).reshape(-1),
+              "eps": out["eps"].reshape(-1), "delta": out["delta"].reshape(-1),
+              "gamma": np.clip(out["gamma"], 0.0, None).reshape(-1), "qp": out["qp"].reshape(-1),
+              "qs": out["qs"].reshape(-1),
+              "tilt": (np.array([L.tilt for L in base])[layer] + dip).reshape(-1)}
+    src = surface_sources_2d(nx, n_sources)
+    return CellModel2D("folded_faulted_%dx%d_%dsrc" % (nx, nz, n_sources), nx, nz, dx, params,
+                       layer.reshape(-1), src)

@@ -44,12 +44,14 @@ def exact_training_set(classes, modes, M, precision="mixed"):
 
 
 def standardisation(t):
-    """Mean/std of the raw targets over valid samples (output 3 left as is)."""
+    """Mean/std of the raw targets over valid samples, NaN targets left out
+    (output 3 left as is)."""
     import torch
     valid = t[:, 3] > 0.5
     tv = t[valid].double()
-    mean = tv.mean(0)
-    std = tv.std(0).clamp_min(1e-12)
+    mean = tv.nanmean(0)
+    var = ((tv - mean) ** 2).nanmean(0)
+    std = var.sqrt().clamp_min(1e-12)
     mean[3], std[3] = 0.0, 1.0
     return mean.cpu().numpy(), std.cpu().numpy()
 
@@ -76,3 +78,22 @@ def train(x, t, steps=2000, batch=4096, lr=2e-3, seed=0, log_every=0):
         if log_every and step % log_every == 0:
             history.append((step, float(loss.item())))
     return params, history
+
+
+def per_cell_cache(d_classes, n_cells, modes, M, params_per_mode=None, precision="mixed"):
+    """Cache with one class per cell: exact (params_per_mode None) or from the
+    networks, with every solve they hand back (flag 2: outside the training
+    range, unsure validity, qSV branch region) recomputed by the exact solver."""
+    import torch
+    if params_per_mode is None:
+        return chert.build_cache(d_classes, n_cells, modes, M, kernel="MEV", precision=precision)
+    cache = chert.surrogate_cache(params_per_mode, d_classes, n_cells, modes, M,
+                                  precision="fp64" if precision == "fp64" else "fp32")
+    # solve j of (mode slot, class) writes entry d = j (d = M for j = M)
+    first = cache["flag"][:, :, :M + 1]
+    items = torch.nonzero(first.reshape(-1) == 2).flatten()
+    if items.numel():
+        chert.build_cache_items(cache, d_classes, items.to(torch.int64).contiguous(),
+                                precision="fp64" if precision == "fp64" else precision)
+    cache.n_fallback = int(items.numel())
+    return cache

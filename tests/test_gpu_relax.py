@@ -157,6 +157,31 @@ def _synthetic_cache(Vk, Ak, M=8):
     return c
 
 
+def test_relaxation_one_class_per_node_matches_oracle(torch_dev):
+    """Per-cell media: one class per node, so the looked-up (V, A) tables live
+    in global memory (the generic kernel's third weight mode)."""
+    nx, nz = 23, 19
+    n = nx * nz
+    rng = np.random.default_rng(31)
+    M = 8
+    nd = 4 * M
+    th = (math.pi / 2) * np.arange(nd) / M
+    v0 = rng.uniform(1500, 4500, n)
+    aniso = rng.uniform(-0.2, 0.2, n)
+    V = v0[:, None] * (1 + aniso[:, None] * np.cos(2 * th)[None])
+    cnp = {"V": V[None], "A": (rng.uniform(1e-5, 1e-4, n)[:, None] * np.ones(nd))[None],
+           "rx": np.tile(np.sin(th), (1, n, 1)), "rz": np.tile(np.cos(th), (1, n, 1)),
+           "theta": np.tile(th, (1, n, 1)), "vartheta": np.zeros((1, n, nd)),
+           "flag": np.zeros((1, n, nd), np.uint8)}
+    cnp["Q"] = np.full_like(cnp["V"], np.inf)
+    off = inputs.stencil_2d(5)
+    cls = np.arange(n, dtype=np.int32)
+    for precision in ("fp64", "fp32"):
+        g = run_gpu(torch_dev, as_cache(torch_dev, cnp, precision), nx, nz, 10.0, cls, off, [0, 200])
+        ref = oracle_fields(cnp, precision, (nx, 1, nz), 10.0, cls, off, [0, 200])
+        _check_fields(g, ref, [0, 200], 1, precision, (nx, 1, nz), 10.0, cls, off, cnp)
+
+
 def test_serpentine_channel_needs_several_cycles(torch_dev):
     """A fast channel that winds down and up forces several sweep cycles; a cap
     of one cycle must report CHERT_ETIMEOUT, a larger cap the oracle's field."""

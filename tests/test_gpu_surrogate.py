@@ -71,6 +71,8 @@ def test_gradient_matches_oracle_bf16(torch_dev):
     rng = np.random.default_rng(7)
     t = rng.normal(0, 1, (n, 5)) * std + mean
     t[:, 3] = (rng.uniform(size=n) > 0.2).astype(float)
+    t[::7, 1] = np.nan                        # left out of the fit of output 1
+    t[3::11, 0:3] = np.nan
     zeros = torch_dev.zeros_like(params)
     loss, grad = chert.mlp_train_step(params, zeros.clone(), zeros.clone(), 1, 0.0,
                                       torch_dev.as_tensor(x, dtype=torch_dev.float32, device="cuda"),
@@ -143,11 +145,15 @@ def test_training_pairs_match_oracle(torch_dev, mode):
         rows = slice(k * (M + 1), (k + 1) * (M + 1))
         assert np.allclose(x[rows, :7], u, atol=2e-6)
         Vg, psi_el = mo.elastic_baseline(aR, th, mode)
+        A0 = mo.attenuation_baseline(mods[k], th, mode, psi_el)
         for j in range(M + 1):
             s = co.solve_direction(A, th[j], mode, "MEV", 0.02 * DEG, 1500)
             ref = mo.encode_targets(s["V"], s["A"], math.atan2(s["r"][0], s["r"][2]), s["flag"],
-                                    s["vartheta"], Vg[j], psi_el[j])
-            assert np.allclose(t[k * (M + 1) + j], ref, atol=3e-6, rtol=1e-5), (k, j)
+                                    s["vartheta"], Vg[j], psi_el[j], A0[j],
+                                    vt_max=2 * DEG if mode == "qSV" else None)
+            # A0 is evaluated in float on the device: log(A/A0) to 1e-5
+            assert np.allclose(t[k * (M + 1) + j], ref, atol=[3e-6, 1e-5, 3e-6, 0, 3e-6], rtol=1e-5,
+                               equal_nan=True), (k, j)
 
 
 def test_trained_surrogate_beats_elastic_baseline(torch_dev):
@@ -170,9 +176,11 @@ def test_trained_surrogate_beats_elastic_baseline(torch_dev):
     torch_dev.cuda.synchronize()
     ex = {k: v.cpu().numpy() for k, v in exact.arrays.items()}
     su = {k: v.cpu().numpy() for k, v in surr.arrays.items()}
+    decided = su["flag"] != 2                 # 2: handed to the exact solver
     both = (ex["flag"] == 0) & (su["flag"] == 0)
-    agree = np.mean((ex["flag"] == 0) == (su["flag"] == 0))
-    assert agree > 0.97
+    agree = np.mean(((ex["flag"] == 0) == (su["flag"] == 0))[decided])
+    assert agree > 0.99
+    assert np.mean(decided[0]) > 0.9 and np.mean(decided[2]) > 0.9        # qP, qSH mostly decided
     for mi, m in enumerate(modes):
         ok = both[mi]
         dv = np.abs(su["V"][mi][ok] / ex["V"][mi][ok] - 1)
