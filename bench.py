@@ -207,6 +207,125 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------- surrogate
+SURR_TRAIN_CLASSES = 110_000       # x 31 angles x 3 modes = 10.2M exact training entries
+SURR_TRAIN_M = 30
+SURR_TRAIN_STEPS = 3000
+SURR_BATCH = 4096
+SURR_MAX_CYCLES = 512              # attenuation paths through the folds turn often
+
+
+def surrogate_section(n_sources, flush, log=None):
+    """Plain vs surrogate form on the per-cell folded and faulted model.
+
+    1701 x 351 nodes (597,051 cells, each its own medium), 10 folded layers and
+    a normal fault (PCG64 seed 1003), modes qP/qSV/qSH, 1 deg cache, radius-5
+    stencil, `n_sources` surface sources.  Plain: the exact solver for every
+    (cell, mode, angle) solve.  Surrogate: the networks for every solve, the
+    exact solver for those they hand back (flag 2).  The networks are trained
+    once beforehand (reported, not part of the timed step) on exact entries of
+    independently seeded media.  Each form is timed once (cache build, then
+    the relaxation of all fields with parents), with L2 flushed before each
+    part; the error is the surrogate form's traveltime against the plain
+    form's, over all nodes with tau > 0."""
+    import torch
+    from paper_2609_26108_b300 import chert, surrogate
+
+    model = inputs.folded_faulted(n_sources=n_sources)
+    n = model.nx * model.nz
+    p = model.params
+    keys = ["vp0", "vs0", "eps", "delta", "gamma", "qp", "qs", "tilt"]
+    d_cells = chert.classes_to_device(chert.classes_from_arrays(**{k: p[k] for k in keys}))
+    d_cls = torch.arange(n, dtype=torch.int32, device="cuda")
+    off = inputs.stencil_2d(RADIUS)
+    src = [int(v) for v in model.sources]
+    M = M_PER_QUADRANT
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    train = surrogate.exact_training_set(inputs.random_tti_classes(SURR_TRAIN_CLASSES, seed=2003), MODES,
+                                         SURR_TRAIN_M)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    params = [surrogate.train(*train[m], steps=SURR_TRAIN_STEPS, batch=SURR_BATCH, lr=2e-3, seed=1)[0]
+              for m in MODES]
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del train
+    if log:
+        log("training set %.1f s, training %.1f s" % (t_data, t_train))
+
+    shape = (len(MODES), n, 4 * M)
+    bufs = []
+    for _ in range(2):
+        b = {k: torch.empty(shape, dtype=torch.float32, device="cuda")
+             for k in ("V", "A", "Q", "rx", "rz", "theta", "vartheta")}
+        b["flag"] = torch.empty(shape, dtype=torch.uint8, device="cuda")
+        bufs.append(b)
+    fshape = (len(src), len(MODES), n)
+    taus = [tuple(torch.empty(fshape, dtype=dt, device="cuda")
+                  for dt in (torch.float32, torch.float32, torch.int32, torch.int32)) for _ in range(2)]
+    ws = torch.empty(chert.workspace_bytes(len(MODES), n, len(off), chert.FP32, len(src), model.nx, model.nz),
+                     dtype=torch.uint8,
+                     device="cuda")
+    # load every kernel once on a small slice before timing
+    small = surrogate.per_cell_cache(d_cells[: 104 * 64], 64, MODES, M)
+    surrogate.per_cell_cache(d_cells[: 104 * 64], 64, MODES, M, params)
+    chert.traveltime(small, 8, 8, model.dx, d_cls[:64], off, [0], workspace=ws)
+
+    def timed(fn):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b) / 1e3
+
+    res = {}
+    for form, prm, buf, tau in (("plain", None, bufs[0], taus[0]), ("surrogate", params, bufs[1], taus[1])):
+        cache, t_cache = timed(lambda: surrogate.per_cell_cache(d_cells, n, MODES, M, prm, out=buf))
+        if log:
+            log("%s cache %.3f s" % (form, t_cache))
+        _, t_relax = timed(lambda: chert.traveltime(cache, model.nx, model.nz, model.dx, d_cls, off, src,
+                                                    max_cycles=SURR_MAX_CYCLES, out=tau, workspace=ws))
+        if log:
+            log("%s relax %.3f s" % (form, t_relax))
+        nf = len(src) * len(MODES)
+        res[form] = {"cache_s": t_cache, "relax_s": t_relax,
+                     "cache_entries_per_s": n * len(MODES) * 4 * M / t_cache,
+                     "fields_per_s": nf / (t_cache + t_relax)}
+        if form == "surrogate":
+            res[form]["solves_recomputed_exactly"] = int(cache.n_fallback)
+            res[form]["solves_total"] = n * len(MODES) * (M + 1)
+    errs = {}
+    worst = 0.0
+    for comp, name in ((0, "tauR"), (1, "tauI")):
+        for mi, m in enumerate(MODES):
+            r = taus[0][comp][:, mi].double()
+            g = taus[1][comp][:, mi].double()
+            ok = torch.isfinite(r) & (r > 0)
+            rel = ((g - r).abs() / r)[ok]
+            q = torch.quantile(rel[torch.randperm(rel.numel(), device="cuda")[:1 << 24]],
+                               torch.tensor([0.5, 0.99], dtype=torch.float64, device="cuda"))
+            errs["%s_%s" % (name, m)] = {"median": float(q[0]), "p99": float(q[1]), "max": float(rel.max()),
+                                         "frac_le_1e-4": float((rel <= 1e-4).double().mean())}
+            if comp == 0:
+                worst = max(worst, float(q[0]))
+    return {"workload": "folded_faulted_visco_tti_2d_1701x351_per_cell_%dsrc_3modes_1deg_R5" % len(src),
+            "cells": n, "fields": len(src) * len(MODES),
+            "training": {"exact_entries": SURR_TRAIN_CLASSES * (SURR_TRAIN_M + 1) * len(MODES),
+                         "steps_per_mode": SURR_TRAIN_STEPS, "batch": SURR_BATCH,
+                         "dataset_s": t_data, "train_s": t_train, "one_off": True},
+            "plain": res["plain"], "surrogate": res["surrogate"],
+            "speedup_fields_per_s": res["surrogate"]["fields_per_s"] / res["plain"]["fields_per_s"],
+            "speedup_cache": res["plain"]["cache_s"] / res["surrogate"]["cache_s"],
+            "traveltime_rel_error_vs_plain": errs,
+            "tauR_median_rel_error_worst_mode": worst}
+
+
 # --------------------------------------------------------------- GPU arm
 def run_chert(args):
     import torch
@@ -280,7 +399,7 @@ def run_chert(args):
     sm_max = clocks.get("sm_max_mhz") or 2032.0
     peak_tops = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     achieved = alg_ops / relax_avg_s / 1e12
-    roofline = {"bound": "alu", "kernel": "relax_kernel<float,true>", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": "relax_fast_kernel<float,5,1,false>", "achieved": achieved,
                 "peak": peak_tops, "unit": "TFLOP/s", "frac": achieved / peak_tops, "traffic": None,
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock (non-FMA op rate)",
                 "alg_ops_per_launch": alg_ops, "directed_edges_per_field": edges,
@@ -302,6 +421,8 @@ def run_chert(args):
            "e2e": {"value": e2e_value, "unit": "fields/s", "h2d_bytes_per_step": tr.h2d_bytes(),
                    "d2h_bytes_per_step": tr.d2h_bytes()},
            "gpu_launches": tr.launches_per_run * args.steps}
+    if world == 1 and args.surrogate_sources > 0:
+        out["surrogate"] = surrogate_section(args.surrogate_sources, flush)
     if world == 1 and not args.no_cpu_baseline:
         fps, eps_, desc, _ = oracle_sample(model, off)
         out["cpu_baseline"] = {"value": fps, "unit": "fields/s", "cores": 1, "kind": "oracle",
@@ -321,6 +442,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sources", type=int, default=64,
                     help="surface sources (64 = the benchmark workload; fewer only for profiling)")
+    ap.add_argument("--surrogate-sources", type=int, default=16,
+                    help="sources of the per-cell plain-vs-surrogate comparison (0: leave it out)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -158,9 +158,21 @@ int chert_edge_table(const chert_cache_arrays* cache, int n_modes, int n_classes
 
 /* ---- traveltime relaxation (Eq. 22, 27-33) ------------------------------ */
 
-/* Scratch bytes chert_traveltime needs for this problem size. */
+/* Scratch bytes chert_traveltime needs for this problem size (the class
+ * tables only; enough for every lattice). */
 size_t chert_traveltime_workspace_bytes(int n_modes, int n_classes, int n_off,
                                         int precision, int n_sources);
+
+/* Scratch bytes for this problem on an nx x ny x nz lattice (ny = 1), including
+ * the per-node weight area: with the standard secondary-node stencil and too
+ * many classes for the class-pair table in shared memory (e.g. one class per
+ * node), chert_traveltime precomputes each node's directed edge weights in row-
+ * and column-major layouts, n_modes x 2 x n_off x nodes values each, when the
+ * workspace it is given holds them, and otherwise relaxes with weights read
+ * through the class map (same results, slower).  Returns 0 for invalid
+ * counts. */
+size_t chert_traveltime_workspace_bytes_grid(int n_modes, int n_classes, int n_off, int precision,
+                                             int n_sources, int nx, int ny, int nz);
 
 /* Propagation and attenuation traveltime fields for every (source, mode) of
  * a cache, on a 2D lattice nx x nz (ny must be 1) with spacing dx.

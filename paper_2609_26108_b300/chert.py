@@ -73,6 +73,8 @@ def lib():
     L.chert_build_cache_items.restype = ctypes.c_int
     L.chert_traveltime_workspace_bytes.argtypes = [I, I, I, I, I]
     L.chert_traveltime_workspace_bytes.restype = SZ
+    L.chert_traveltime_workspace_bytes_grid.argtypes = [I, I, I, I, I, I, I, I]
+    L.chert_traveltime_workspace_bytes_grid.restype = SZ
     L.chert_traveltime.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P, I,
                                    P, I, I, I, P, P, P, P, P, SZ, P]
     L.chert_raypath.argtypes = [P, I, I64, P, P, I, I64, P, P, P]
@@ -261,8 +263,13 @@ def edge_table(cache, offsets, stream=None):
     return idx, Vs, As
 
 
-def workspace_bytes(n_modes, n_classes, n_off, precision, n_sources):
-    return int(lib().chert_traveltime_workspace_bytes(n_modes, n_classes, n_off, precision, n_sources))
+def workspace_bytes(n_modes, n_classes, n_off, precision, n_sources, nx=None, nz=None):
+    """Relaxation scratch; with the lattice size it includes the per-node
+    weight area that the specialised kernel uses for many classes."""
+    if nx is None:
+        return int(lib().chert_traveltime_workspace_bytes(n_modes, n_classes, n_off, precision, n_sources))
+    return int(lib().chert_traveltime_workspace_bytes_grid(n_modes, n_classes, n_off, precision, n_sources,
+                                                           nx, 1, nz))
 
 
 def traveltime(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64, parents=True,
@@ -281,8 +288,8 @@ def traveltime(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64, parent
         out = (torch.empty(shape, dtype=fd, device=dev), torch.empty(shape, dtype=fd, device=dev),
                torch.empty(shape, dtype=torch.int32, device=dev) if parents else None,
                torch.empty(shape, dtype=torch.int32, device=dev) if parents else None)
-    wsb = workspace_bytes(nm, cache.n_classes, len(off), cache.precision, ns)
-    if workspace is None or workspace.numel() < wsb:
+    if workspace is None:
+        wsb = workspace_bytes(nm, cache.n_classes, len(off), cache.precision, ns, nx, nz)
         workspace = torch.empty(wsb, dtype=torch.uint8, device=dev)
     st = cache.struct()
     _check(lib().chert_traveltime(ctypes.byref(st), nm, cache.n_classes, cache.n_dir, nx, 1, nz,

@@ -378,11 +378,6 @@ extern "C" int chert_edge_table(const chert_cache_arrays* cache, int n_modes, in
     return launch_check("chert_edge_table");
 }
 
-extern "C" size_t chert_traveltime_workspace_bytes(int n_modes, int n_classes, int n_off,
-                                                   int precision, int n_sources) {
-    if (n_modes < 1 || n_classes < 1 || n_off < 1 || n_sources < 1) return 0;
-    return ws_layout(n_modes, n_classes, n_off, precision, n_sources).total;
-}
 
 template <typename T, int WMODE>
 static int launch_relax(const FieldArgs& a, const Offsets& off, size_t smem, int blocks,
@@ -412,47 +407,230 @@ static bool standard_map(const Offsets& off, short* map) {
 }
 
 template <int R>
-static size_t fast_smem(int nk, int line_max, size_t es) {
+static size_t fast_smem(int nk, int nx, int nz, size_t es, bool pn) {
+    const int line_max = std::max(nx, nz);
     const size_t LS = ((line_max + 2 * R) + 3) & ~3;
-    return (size_t)nk * nk * fast::Stencil<R>::N * es + 16 * LS * (2 * es) +
+    const size_t tiles = (size_t)((nx + fast::kTile - 1) / fast::kTile) * ((nz + fast::kTile - 1) / fast::kTile);
+    return (pn ? 0 : (size_t)nk * nk * fast::Stencil<R>::N * es) + 16 * LS * (2 * es) + 4 * tiles +
            4 * fast::Stencil<R>::N + 64;
 }
 
-template <typename T, int R, int PPT>
+template <typename T, int R, int PPT, bool PN>
 static int launch_fast_ppt(const fast::Args& a, size_t smem, int blocks, int threads, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(fast::relax_fast_kernel<T, R, PPT>,
+    cudaError_t e = cudaFuncSetAttribute(fast::relax_fast_kernel<T, R, PPT, PN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "relaxation: smem attribute");
-    fast::relax_fast_kernel<T, R, PPT><<<blocks, threads, smem, s>>>(a);
+    fast::relax_fast_kernel<T, R, PPT, PN><<<blocks, threads, smem, s>>>(a);
     return launch_check("relaxation");
 }
 
+// ---- per-node weights -----------------------------------------------------
+// Edge-table values [2][n_modes][nk][n_off] (V block, then A block) transposed
+// to [2][n_modes][n_off][nk], so that the weight build below reads them along
+// the lattice rows when neighbouring nodes have neighbouring classes.
+template <typename T>
+__global__ void transpose_sel_kernel(const T* __restrict__ in, int nk, int n_off, T* __restrict__ out) {
+    __shared__ T tile[32][33];
+    const size_t mb = blockIdx.z;                    // block index in [2][n_modes]
+    const int k0 = blockIdx.x * 32, o0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int k = k0 + r, o = o0 + threadIdx.x;
+        if (k < nk && o < n_off) tile[r][threadIdx.x] = in[(mb * nk + k) * n_off + o];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int o = o0 + r, k = k0 + threadIdx.x;
+        if (k < nk && o < n_off) out[(mb * n_off + o) * nk + k] = tile[threadIdx.x][r];
+    }
+}
+
+struct StencilArg {
+    short x[128], z[128], map[128];
+};
+
+// Directed weight of the edge j - o_q -> j for every node j, stencil entry q,
+// mode and component (Eq. 28-30, the same rounded operations as the class-pair
+// table), written in row layout (z*nx + x) and, through a shared-memory
+// transpose, in column layout (x*nz + z).  Edges from outside the lattice get
+// +inf.  One 32 x 32 tile of nodes per CTA (32 x 8 threads), all q in turn.
+template <typename T>
+__global__ void node_weights_kernel(const T* __restrict__ selT, const int32_t* __restrict__ cls, int nx,
+                                    int nz, int nk, int n_off, int n_modes, int N, StencilArg st, double dx,
+                                    T* __restrict__ wrow, T* __restrict__ wcol) {
+    __shared__ T tile[32][33];
+    const int mc = blockIdx.z;                       // mode * 2 + component
+    const int mode = mc >> 1, comp = mc & 1;
+    const T* sel = selT + (size_t)(comp * n_modes + mode) * n_off * nk;
+    const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const size_t n = (size_t)nx * nz;
+    int kj[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int x = x0 + tx, z = z0 + ty + 8 * r;
+        kj[r] = (x < nx && z < nz) ? clamp_class(cls[(size_t)z * nx + x], nk) : 0;
+    }
+    for (int q = 0; q < N; ++q) {
+        const int ox = st.x[q], oz = st.z[q];
+        const T L = T(dx * sqrt(double(ox * ox + oz * oz)));
+        const T* so = sel + (size_t)st.map[q] * nk;
+        T* outr = wrow + ((size_t)mc * N + q) * n;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int x = x0 + tx, z = z0 + ty + 8 * r;
+            T w = T(INFINITY);
+            if (x < nx && z < nz) {
+                const int xi = x - ox, zi = z - oz;
+                if (xi >= 0 && xi < nx && zi >= 0 && zi < nz) {
+                    const int ki = clamp_class(cls[(size_t)zi * nx + xi], nk);
+                    w = edge_w<T>(comp, L, so[ki], so[kj[r]]);
+                }
+                outr[(size_t)z * nx + x] = w;
+            }
+            tile[ty + 8 * r][tx] = w;
+        }
+        __syncthreads();
+        T* outc = wcol + ((size_t)mc * N + q) * n;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int x = x0 + ty + 8 * r, z = z0 + tx;
+            if (x < nx && z < nz) outc[(size_t)x * nz + z] = tile[tx][ty + 8 * r];
+        }
+        __syncthreads();
+    }
+}
+
+// Radius of the standard stencil with n_off entries (0 if none).
+static int standard_radius(int n_off) {
+    if (n_off == fast::Stencil<2>::N) return 2;
+    if (n_off == fast::Stencil<3>::N) return 3;
+    if (n_off == fast::Stencil<4>::N) return 4;
+    if (n_off == fast::Stencil<5>::N) return 5;
+    return 0;
+}
+
+static int max_smem() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 227 * 1024;
+    }
+    return v;
+}
+
+template <int R>
+static size_t fast_smem_r(int nk, int nx, int nz, size_t es, bool pn) { return fast_smem<R>(nk, nx, nz, es, pn); }
+
+static size_t fast_smem_any(int R, int nk, int nx, int nz, size_t es, bool pn) {
+    switch (R) {
+        case 2: return fast_smem_r<2>(nk, nx, nz, es, pn);
+        case 3: return fast_smem_r<3>(nk, nx, nz, es, pn);
+        case 4: return fast_smem_r<4>(nk, nx, nz, es, pn);
+        case 5: return fast_smem_r<5>(nk, nx, nz, es, pn);
+        default: return SIZE_MAX;
+    }
+}
+
+struct PnLayout {
+    size_t selT, wrow, wcol, total;    // offsets from the start of the per-node area
+};
+
+// Per-node area of the workspace: used by the specialised kernel when the
+// stencil is the standard one but the class-pair table does not fit in shared
+// memory (e.g. one class per node).  total = 0 when that path does not apply.
+static PnLayout pn_layout(int n_modes, int n_classes, int n_off, int precision, int nx, int nz) {
+    PnLayout L{0, 0, 0, 0};
+    const int R = standard_radius(n_off);
+    if (!R || std::max(nx, nz) > 2048) return L;
+    const size_t es = precision == CHERT_FP64 ? 8 : 4;
+    const int smax = max_smem();
+    if (fast_smem_any(R, n_classes, nx, nz, es, false) <= (size_t)smax) return L;   // pair table fits
+    if (fast_smem_any(R, n_classes, nx, nz, es, true) > (size_t)smax) return L;
+    const size_t m = static_cast<size_t>(n_modes) * n_classes * n_off;
+    const size_t wn = static_cast<size_t>(n_modes) * 2 * n_off * nx * nz * es;
+    L.selT = 0;
+    L.wrow = align256(2 * m * es);
+    L.wcol = L.wrow + align256(wn);
+    L.total = L.wcol + align256(wn);
+    return L;
+}
+
 // Returns 1 if the specialised kernel was launched, 0 if the caller must use
-// the generic one, or a negative status.
+// the generic one, or a negative status.  pn_area (pn_bytes long) is the
+// workspace's per-node area, or null.
 template <typename T, int R>
-static int try_fast_R(fast::Args& a, const Offsets& off, int line_max, int smem_max, int blocks,
-                      cudaStream_t s) {
+static int try_fast_R(fast::Args& a, const Offsets& off, int smem_max, int blocks, const void* Vsel,
+                      unsigned char* pn_area, size_t pn_bytes, int n_modes, cudaStream_t s) {
     if (!standard_map<R>(off, a.map)) return 0;
-    const size_t smem = fast_smem<R>(a.n_classes, line_max, sizeof(T));
-    if (smem > (size_t)smem_max || line_max > 2048) return 0;
+    const int line_max = std::max(a.nx, a.nz);
+    if (line_max > 2048) return 0;
     const int ppt = line_max <= 512 ? 1 : (line_max <= 1024 ? 2 : 4);
     const int threads = ((line_max + ppt - 1) / ppt + 31) / 32 * 32;
-    const int rc = ppt == 1 ? launch_fast_ppt<T, R, 1>(a, smem, blocks, threads, s)
-                 : ppt == 2 ? launch_fast_ppt<T, R, 2>(a, smem, blocks, threads, s)
-                            : launch_fast_ppt<T, R, 4>(a, smem, blocks, threads, s);
+    size_t smem = fast_smem<R>(a.n_classes, a.nx, a.nz, sizeof(T), false);
+    bool pn = false;
+    if (smem > (size_t)smem_max) {
+        const PnLayout L = pn_layout(n_modes, a.n_classes, off.n, sizeof(T) == 8 ? CHERT_FP64 : CHERT_FP32,
+                                     a.nx, a.nz);
+        if (!pn_area || L.total == 0 || pn_bytes < L.total) return 0;
+        smem = fast_smem<R>(a.n_classes, a.nx, a.nz, sizeof(T), true);
+        if (smem > (size_t)smem_max) return 0;
+        pn = true;
+        constexpr int N = fast::Stencil<R>::N;
+        constexpr fast::Stencil<R> st{};
+        StencilArg sa;
+        for (int q = 0; q < N; ++q) { sa.x[q] = (short)st.x[q]; sa.z[q] = (short)st.z[q]; sa.map[q] = a.map[q]; }
+        T* selT = reinterpret_cast<T*>(pn_area + L.selT);
+        transpose_sel_kernel<T><<<dim3((a.n_classes + 31) / 32, (off.n + 31) / 32, 2 * n_modes), dim3(32, 8), 0, s>>>(
+            static_cast<const T*>(Vsel), a.n_classes, off.n, selT);
+        int rc = launch_check("relaxation: edge-table transpose");
+        if (rc) return rc;
+        T* wr = reinterpret_cast<T*>(pn_area + L.wrow);
+        T* wc = reinterpret_cast<T*>(pn_area + L.wcol);
+        node_weights_kernel<T><<<dim3((a.nx + 31) / 32, (a.nz + 31) / 32, 2 * n_modes), dim3(32, 8), 0, s>>>(
+            selT, a.cls, a.nx, a.nz, a.n_classes, off.n, n_modes, N, sa, a.dx, wr, wc);
+        rc = launch_check("relaxation: per-node weights");
+        if (rc) return rc;
+        a.wrow = wr;
+        a.wcol = wc;
+    } else {
+        a.wrow = a.wcol = nullptr;
+    }
+    int rc;
+    if (pn)
+        rc = ppt == 1 ? launch_fast_ppt<T, R, 1, true>(a, smem, blocks, threads, s)
+           : ppt == 2 ? launch_fast_ppt<T, R, 2, true>(a, smem, blocks, threads, s)
+                      : launch_fast_ppt<T, R, 4, true>(a, smem, blocks, threads, s);
+    else
+        rc = ppt == 1 ? launch_fast_ppt<T, R, 1, false>(a, smem, blocks, threads, s)
+           : ppt == 2 ? launch_fast_ppt<T, R, 2, false>(a, smem, blocks, threads, s)
+                      : launch_fast_ppt<T, R, 4, false>(a, smem, blocks, threads, s);
     return rc ? rc : 1;
 }
 
 template <typename T>
-static int try_fast(fast::Args& a, const Offsets& off, int R, int line_max, int smem_max, int blocks,
-                    cudaStream_t s) {
+static int try_fast(fast::Args& a, const Offsets& off, int R, int smem_max, int blocks, const void* Vsel,
+                    unsigned char* pn_area, size_t pn_bytes, int n_modes, cudaStream_t s) {
     switch (R) {
-        case 2: return try_fast_R<T, 2>(a, off, line_max, smem_max, blocks, s);
-        case 3: return try_fast_R<T, 3>(a, off, line_max, smem_max, blocks, s);
-        case 4: return try_fast_R<T, 4>(a, off, line_max, smem_max, blocks, s);
-        case 5: return try_fast_R<T, 5>(a, off, line_max, smem_max, blocks, s);
+        case 2: return try_fast_R<T, 2>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s);
+        case 3: return try_fast_R<T, 3>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s);
+        case 4: return try_fast_R<T, 4>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s);
+        case 5: return try_fast_R<T, 5>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s);
         default: return 0;
     }
+}
+
+extern "C" size_t chert_traveltime_workspace_bytes(int n_modes, int n_classes, int n_off,
+                                                   int precision, int n_sources) {
+    if (n_modes < 1 || n_classes < 1 || n_off < 1 || n_sources < 1) return 0;
+    return ws_layout(n_modes, n_classes, n_off, precision, n_sources).total;
+}
+
+extern "C" size_t chert_traveltime_workspace_bytes_grid(int n_modes, int n_classes, int n_off, int precision,
+                                                        int n_sources, int nx, int ny, int nz) {
+    if (n_modes < 1 || n_classes < 1 || n_off < 1 || n_sources < 1 || nx < 1 || ny != 1 || nz < 1) return 0;
+    return ws_layout(n_modes, n_classes, n_off, precision, n_sources).total +
+           pn_layout(n_modes, n_classes, n_off, precision, nx, nz).total;
 }
 
 // Validates the arguments and enqueues lookup, class check and relaxation on
@@ -535,9 +713,12 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     fa.max_cycles = max_cycles; fa.dx = dx; fa.cls = a.cls; fa.src = a.src;
     fa.tauR = d_tauR; fa.tauI = d_tauI; fa.parR = d_parR; fa.parI = d_parI;
     fa.Vsel = Vsel; fa.Asel = Asel; fa.n_off = n_off; fa.status = a.status;
+    fa.wrow = fa.wcol = nullptr;
+    unsigned char* pn_area = bytes > ws.total ? w + ws.total : nullptr;
+    const size_t pn_bytes = bytes > ws.total ? bytes - ws.total : 0;
     const int fr = precision == CHERT_FP64
-                       ? try_fast<double>(fa, off, R, line_max, smem_max, blocks, s)
-                       : try_fast<float>(fa, off, R, line_max, smem_max, blocks, s);
+                       ? try_fast<double>(fa, off, R, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s)
+                       : try_fast<float>(fa, off, R, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s);
     if (fr < 0) return fr;
     if (fr == 1) rc = CHERT_OK;
     else if (precision == CHERT_FP64)

@@ -88,6 +88,10 @@ struct Args {
     int n_off;
     int* status;
     short map[128];            // stencil index -> caller offset index
+    // Per-node weights (used when the class-pair table does not fit in shared
+    // memory): [n_modes*2 + comp][N][node], node index z*nx + x (row layout)
+    // and x*nz + z (column layout); null for the class-pair table.
+    const void *wrow, *wcol;
 };
 
 // One ring element: the node's tau and its class id pre-multiplied by nk*N,
@@ -98,23 +102,73 @@ struct alignas(2 * sizeof(T)) Cell {
     int ck;
 };
 
+// Dirty tiles.  The lattice is cut into kTile x kTile tiles; stamp[t] is the
+// number of the last pass (counted over the whole run, from 1) in which a node
+// of tile t was lowered.  A pull only reads nodes within R < kTile of the
+// puller, i.e. in the 3 x 3 tiles around it, so a node whose surrounding tiles
+// have not changed since the last pass of the same kind (sweep direction or
+// verification) cannot improve, and its pulls are skipped.  The skip is exact:
+// the results are those of the full passes.
+constexpr int kTile = 32;
+
 template <typename T>
 struct Ctx {
-    T* W;            // [nk][nk][N]: W[(ki*nk + kj)*N + q]
+    T* W;            // [nk][nk][N]: W[(ki*nk + kj)*N + q] (class-pair mode)
     Cell<T>* ring;   // [16][LS]
     short* sx;       // stencil offsets (for decoding the winning parent)
     short* sz;
-    int LS, nx, nz, nk;
+    int* stamp;      // [TZ][TX]
+    const T* wr;     // per-node weights of this (mode, component), row layout
+    const T* wc;     // column layout
+    size_t n;        // nodes
+    int LS, nx, nz, nk, TX, TZ;
 };
 
 __device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
 
+// Whether the tiles around tile (tx, tz) changed in or after pass `since`.
+template <typename T>
+__device__ __forceinline__ bool dirty(const Ctx<T>& c, int tx, int tz, int since) {
+    int m = 0;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int z = tz + dz;
+        if (z < 0 || z >= c.TZ) continue;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int x = tx + dx;
+            if (x < 0 || x >= c.TX) continue;
+            m = max(m, c.stamp[z * c.TX + x]);
+        }
+    }
+    return m >= since;
+}
+
+// Whether any tile of bands b-1..b+1 changed in or after pass `since`; a band
+// is kTile consecutive lines across AXIS (0: rows, tile row b; 1: columns,
+// tile column b).  Block-wide (every thread must call it).
+template <typename T, int AXIS>
+__device__ __forceinline__ bool band_dirty(const Ctx<T>& c, int b, int since) {
+    const int nb = AXIS == 0 ? c.TZ : c.TX;     // bands
+    const int per = AXIS == 0 ? c.TX : c.TZ;    // tiles per band
+    bool d = false;
+    for (int t = threadIdx.x; t < 3 * per; t += blockDim.x) {
+        const int k = b - 1 + t / per, o = t % per;
+        if (k < 0 || k >= nb) continue;
+        const int tile = AXIS == 0 ? k * c.TX + o : o * c.TX + k;
+        if (c.stamp[tile] >= since) d = true;
+    }
+    return __syncthreads_or(d);
+}
+
 // One sweep over lines along AXIS (0: rows in z, 1: columns in x) in
 // direction DIR; every node pulls from its in-neighbours on the previous
-// lines (offsets whose across-line component has the sign of DIR).
-template <typename T, int R, int PPT, int AXIS, int DIR>
-__device__ void sweep(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __restrict__ cls) {
+// lines (offsets whose across-line component has the sign of DIR).  Pass
+// number `pass`; `since` is the number of the previous pass of this sweep.
+template <typename T, int R, int PPT, int AXIS, int DIR, bool PN>
+__device__ void sweep(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __restrict__ cls, int pass,
+                      int since) {
     constexpr int N = Stencil<R>::N;
     const int n_lines = AXIS == 0 ? c.nz : c.nx;
     const int len = AXIS == 0 ? c.nx : c.nz;
@@ -131,13 +185,49 @@ __device__ void sweep(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __res
             if (u < len) {
                 const size_t j = AXIS == 0 ? (size_t)u + (size_t)nx * line : (size_t)line + (size_t)nx * u;
                 t[p] = tau[j];
-                k[p] = min(max(cls[j], 0), c.nk - 1);
+                k[p] = PN ? 0 : min(max(cls[j], 0), c.nk - 1);
             }
         }
     };
+    // Bands whose tiles and neighbouring tiles are all clean are skipped
+    // whole (no node of them can change in this pass); the ring lines that the
+    // next processed line reads are then reloaded from tau.
+    auto ring_line = [&](int line) {
+        Cell<T>* row = c.ring + (line & 7) * c.LS + R;
+        const bool in = line >= 0 && line < n_lines;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int u = tid + p * bd;
+            if (u < len) {
+                if (in) {
+                    const size_t j = AXIS == 0 ? (size_t)u + (size_t)nx * line : (size_t)line + (size_t)nx * u;
+                    row[u] = Cell<T>{tau[j], PN ? 0 : min(max(cls[j], 0), c.nk - 1) * c.nk * N};
+                } else {
+                    row[u] = Cell<T>{T(INFINITY), 0};
+                }
+            }
+        }
+    };
+    bool reload = false;
     load(DIR > 0 ? 0 : n_lines - 1, cur, kr);
     for (int step = 0; step < n_lines; ++step) {
         const int line = DIR > 0 ? step : n_lines - 1 - step;
+        const bool band_start = DIR > 0 ? (line % kTile == 0) : (line == n_lines - 1 || line % kTile == kTile - 1);
+        if (band_start) {
+            const int b = line / kTile;
+            if (!band_dirty<T, AXIS>(c, b, since)) {
+                const int last = DIR > 0 ? min(n_lines - 1, b * kTile + kTile - 1) : b * kTile;
+                step = DIR > 0 ? last : n_lines - 1 - last;      // the loop's ++step moves past it
+                reload = true;
+                continue;
+            }
+            if (reload) {
+                for (int lag = 1; lag <= R; ++lag) ring_line(line - DIR * lag);
+                load(line, cur, kr);
+                __syncthreads();
+                reload = false;
+            }
+        }
         T nxt[PPT];
         int nkr[PPT];
         if (step + 1 < n_lines) load(DIR > 0 ? line + 1 : line - 1, nxt, nkr);
@@ -149,22 +239,39 @@ __device__ void sweep(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __res
         for (int p = 0; p < PPT; ++p) {
             const int u = tid + p * bd;
             if (u < len) {
-                const T* Wj = c.W + kr[p] * N;
+                const int tx = (AXIS == 0 ? u : line) / kTile, tz = (AXIS == 0 ? line : u) / kTile;
                 T best = cur[p];
-                static_for<N>([&](auto qc) {
-                    constexpr int q = decltype(qc)::value;
-                    constexpr int oa = AXIS == 0 ? Table<R>::v.z[q] : Table<R>::v.x[q];
-                    constexpr int ol = AXIS == 0 ? Table<R>::v.x[q] : Table<R>::v.z[q];
-                    if constexpr (oa * DIR > 0) {
-                        constexpr int lag = oa * DIR;
-                        const Cell<T> ci = pt[lag][u - ol];
-                        best = fmin_(best, ci.tau + Wj[ci.ck + q]);
+                if (dirty(c, tx, tz, since)) {          // uniform across the warp (one tile)
+                    if constexpr (PN) {
+                        const T* wl = (AXIS == 0 ? c.wr : c.wc) + (size_t)line * len + u;
+                        static_for<N>([&](auto qc) {
+                            constexpr int q = decltype(qc)::value;
+                            constexpr int oa = AXIS == 0 ? Table<R>::v.z[q] : Table<R>::v.x[q];
+                            constexpr int ol = AXIS == 0 ? Table<R>::v.x[q] : Table<R>::v.z[q];
+                            if constexpr (oa * DIR > 0) {
+                                constexpr int lag = oa * DIR;
+                                best = fmin_(best, pt[lag][u - ol].tau + wl[(size_t)q * c.n]);
+                            }
+                        });
+                    } else {
+                        const T* Wj = c.W + kr[p] * N;
+                        static_for<N>([&](auto qc) {
+                            constexpr int q = decltype(qc)::value;
+                            constexpr int oa = AXIS == 0 ? Table<R>::v.z[q] : Table<R>::v.x[q];
+                            constexpr int ol = AXIS == 0 ? Table<R>::v.x[q] : Table<R>::v.z[q];
+                            if constexpr (oa * DIR > 0) {
+                                constexpr int lag = oa * DIR;
+                                const Cell<T> ci = pt[lag][u - ol];
+                                best = fmin_(best, ci.tau + Wj[ci.ck + q]);
+                            }
+                        });
                     }
-                });
+                }
                 c.ring[own + u] = Cell<T>{best, kr[p] * c.nk * N};
                 if (best < cur[p]) {
                     const size_t j = AXIS == 0 ? (size_t)u + (size_t)nx * line : (size_t)line + (size_t)nx * u;
                     tau[j] = best;
+                    c.stamp[tz * c.TX + tx] = pass;
                 }
             }
         }
@@ -176,10 +283,12 @@ __device__ void sweep(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __res
 
 // Verification pass over rows with a 16-row ring: pulls every in-neighbour in
 // increasing node index; lowers tau where possible (returns whether anything
-// changed) and otherwise writes the argmin parent.
-template <typename T, int R, int PPT>
+// changed) and otherwise writes the argmin parent.  Nodes of clean tiles keep
+// the parent written when they were last verified: none of their
+// in-neighbours has changed since.
+template <typename T, int R, int PPT, bool PN>
 __device__ bool verify(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __restrict__ cls,
-                       int64_t src, int32_t* __restrict__ par) {
+                       int64_t src, int32_t* __restrict__ par, int pass, int since) {
     constexpr int N = Stencil<R>::N;
     const int nx = c.nx, nz = c.nz;
     const int tid = threadIdx.x, bd = blockDim.x;
@@ -191,9 +300,9 @@ __device__ bool verify(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __re
         for (int p = 0; p < PPT; ++p) {
             const int x = tid + p * bd;
             if (x < nx) {
-                if (row < nz) {
+                if (row >= 0 && row < nz) {
                     const size_t j = (size_t)x + (size_t)nx * row;
-                    c.ring[base + x] = Cell<T>{tau[j], min(max(cls[j], 0), c.nk - 1) * c.nk * N};
+                    c.ring[base + x] = Cell<T>{tau[j], PN ? 0 : min(max(cls[j], 0), c.nk - 1) * c.nk * N};
                 } else {
                     c.ring[base + x] = Cell<T>{T(INFINITY), 0};
                 }
@@ -202,7 +311,20 @@ __device__ bool verify(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __re
     };
     for (int row = 0; row < R && row < nz; ++row) store_row(row);
     bool changed = false;
+    bool reload = false;
     for (int z = 0; z < nz; ++z) {
+        if (z % kTile == 0) {                     // skip clean bands of rows whole
+            const int b = z / kTile;
+            if (!band_dirty<T, 0>(c, b, since)) {
+                z = min(nz, z + kTile) - 1;
+                reload = true;
+                continue;
+            }
+            if (reload) {
+                for (int row = z - R; row < z + R; ++row) store_row(row);
+                reload = false;
+            }
+        }
         store_row(z + R);
         __syncthreads();
         const Cell<T>* pt[2 * R + 1];
@@ -212,24 +334,35 @@ __device__ bool verify(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __re
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
             const int x = tid + p * bd;
-            if (x < nx) {
+            if (x < nx && dirty(c, x / kTile, z / kTile, since)) {
                 const Cell<T> me = c.ring[own + x];
                 const T cur = me.tau;
-                const int kj = me.ck / (c.nk * N);
-                const T* Wj = c.W + kj * N;
+                const size_t j = (size_t)x + (size_t)nx * z;
                 T best = T(INFINITY);
                 int bq = -1;
-                static_for<N>([&](auto qc) {
-                    constexpr int q = decltype(qc)::value;
-                    constexpr int oz = Table<R>::v.z[q], ox = Table<R>::v.x[q];
-                    const Cell<T> ci = pt[oz + R][x - ox];
-                    const T cand = ci.tau + Wj[ci.ck + q];
-                    if (cand < best) { best = cand; bq = q; }
-                });
-                const size_t j = (size_t)x + (size_t)nx * z;
+                if constexpr (PN) {
+                    const T* wj = c.wr + j;
+                    static_for<N>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        constexpr int oz = Table<R>::v.z[q], ox = Table<R>::v.x[q];
+                        const T cand = pt[oz + R][x - ox].tau + wj[(size_t)q * c.n];
+                        if (cand < best) { best = cand; bq = q; }
+                    });
+                } else {
+                    const int kj = me.ck / (c.nk * N);
+                    const T* Wj = c.W + kj * N;
+                    static_for<N>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        constexpr int oz = Table<R>::v.z[q], ox = Table<R>::v.x[q];
+                        const Cell<T> ci = pt[oz + R][x - ox];
+                        const T cand = ci.tau + Wj[ci.ck + q];
+                        if (cand < best) { best = cand; bq = q; }
+                    });
+                }
                 if (best < cur) {
                     tau[j] = best;
                     changed = true;
+                    c.stamp[(z / kTile) * c.TX + x / kTile] = pass;
                 } else if (par) {
                     int32_t pj;
                     if ((int64_t)j == src) pj = (int32_t)src;
@@ -243,7 +376,7 @@ __device__ bool verify(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __re
     return __syncthreads_or(changed);
 }
 
-template <typename T, int R, int PPT>
+template <typename T, int R, int PPT, bool PN>
 __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
     constexpr int N = Stencil<R>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -255,14 +388,19 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
     const int line_max = max(a.nx, a.nz);
     Ctx<T> c;
     c.nx = a.nx; c.nz = a.nz; c.nk = nk;
+    c.n = (size_t)a.nx * a.nz;
+    c.TX = (a.nx + kTile - 1) / kTile;
+    c.TZ = (a.nz + kTile - 1) / kTile;
     c.LS = ((line_max + 2 * R) + 3) & ~3;
     unsigned char* p = smem_raw;
-    c.W = reinterpret_cast<T*>(p); p += (size_t)nk * nk * N * sizeof(T);
+    c.W = reinterpret_cast<T*>(p); p += PN ? 0 : (size_t)nk * nk * N * sizeof(T);
     c.ring = reinterpret_cast<Cell<T>*>(p); p += (size_t)16 * c.LS * sizeof(Cell<T>);
+    c.stamp = reinterpret_cast<int*>(p); p += (size_t)c.TX * c.TZ * sizeof(int);
     c.sx = reinterpret_cast<short*>(p); p += N * sizeof(short);
     c.sz = reinterpret_cast<short*>(p);
+    c.wr = PN ? static_cast<const T*>(a.wrow) + (size_t)(mode * 2 + comp) * N * c.n : nullptr;
+    c.wc = PN ? static_cast<const T*>(a.wcol) + (size_t)(mode * 2 + comp) * N * c.n : nullptr;
 
-    const T* sel = static_cast<const T*>(comp == 0 ? a.Vsel : a.Asel) + (size_t)mode * nk * a.n_off;
     if (threadIdx.x == 0)
         static_for<N>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
@@ -270,33 +408,41 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
             c.sx[q] = vx;
             c.sz[q] = vz;
         });
+    for (int t = threadIdx.x; t < c.TX * c.TZ; t += blockDim.x) c.stamp[t] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < nk * nk * N; t += blockDim.x) {
-        const int q = t % N, kj = (t / N) % nk, ki = t / (N * nk);
-        const int o = a.map[q];
-        const double ox = c.sx[q], oz = c.sz[q];
-        const T L = T(a.dx * sqrt(ox * ox + oz * oz));
-        const T vi = sel[ki * a.n_off + o], vj = sel[kj * a.n_off + o];
-        // Eq. 29-30 with the segment averages of Eq. 28 (same rounding as the
-        // generic kernel: no contraction)
-        c.W[t] = comp == 0 ? L / (T(0.5) * (vi + vj)) : L * (T(0.5) * (vi + vj));
+    if constexpr (!PN) {
+        const T* sel = static_cast<const T*>(comp == 0 ? a.Vsel : a.Asel) + (size_t)mode * nk * a.n_off;
+        for (int t = threadIdx.x; t < nk * nk * N; t += blockDim.x) {
+            const int q = t % N, kj = (t / N) % nk, ki = t / (N * nk);
+            const int o = a.map[q];
+            const double ox = c.sx[q], oz = c.sz[q];
+            const T L = T(a.dx * sqrt(ox * ox + oz * oz));
+            const T vi = sel[ki * a.n_off + o], vj = sel[kj * a.n_off + o];
+            // Eq. 29-30 with the segment averages of Eq. 28 (same rounding as the
+            // generic kernel: no contraction)
+            c.W[t] = comp == 0 ? L / (T(0.5) * (vi + vj)) : L * (T(0.5) * (vi + vj));
+        }
     }
 
-    const size_t n = (size_t)a.nx * a.nz;
-    T* tau = static_cast<T*>(comp == 0 ? a.tauR : a.tauI) + (size_t)field * n;
+    T* tau = static_cast<T*>(comp == 0 ? a.tauR : a.tauI) + (size_t)field * c.n;
     int32_t* par = comp == 0 ? a.parR : a.parI;
-    if (par) par += (size_t)field * n;
+    if (par) par += (size_t)field * c.n;
     const int64_t src = a.src[s];
-    for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
+    for (size_t j = threadIdx.x; j < c.n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
     __syncthreads();
 
+    // pass numbers start at 1; every tile starts dirty (stamp 0 >= last 0)
+    int pass = 1;
+    int last[5] = {0, 0, 0, 0, 0};
     int used = -1;
     for (int cycle = 0; cycle < a.max_cycles; ++cycle) {
-        sweep<T, R, PPT, 0, +1>(c, tau, a.cls);
-        sweep<T, R, PPT, 1, +1>(c, tau, a.cls);
-        sweep<T, R, PPT, 1, -1>(c, tau, a.cls);
-        sweep<T, R, PPT, 0, -1>(c, tau, a.cls);
-        if (!verify<T, R, PPT>(c, tau, a.cls, src, par)) {
+        sweep<T, R, PPT, 0, +1, PN>(c, tau, a.cls, pass, last[0]); last[0] = pass++;
+        sweep<T, R, PPT, 1, +1, PN>(c, tau, a.cls, pass, last[1]); last[1] = pass++;
+        sweep<T, R, PPT, 1, -1, PN>(c, tau, a.cls, pass, last[2]); last[2] = pass++;
+        sweep<T, R, PPT, 0, -1, PN>(c, tau, a.cls, pass, last[3]); last[3] = pass++;
+        const bool changed = verify<T, R, PPT, PN>(c, tau, a.cls, src, par, pass, last[4]);
+        last[4] = pass++;
+        if (!changed) {
             used = cycle + 1;
             break;
         }

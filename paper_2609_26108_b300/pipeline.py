@@ -44,7 +44,7 @@ class Tracer:
         self.tau = (torch.empty(fshape, dtype=fd, device=device), torch.empty(fshape, dtype=fd, device=device),
                     torch.empty(fshape, dtype=torch.int32, device=device),
                     torch.empty(fshape, dtype=torch.int32, device=device))
-        wsb = chert.workspace_bytes(nm, n_classes, len(self.offsets), self.prec, n_sources)
+        wsb = chert.workspace_bytes(nm, n_classes, len(self.offsets), self.prec, n_sources, nx, nz)
         self.workspace = torch.empty(wsb, dtype=torch.uint8, device=device)
         nf = n_sources * nm
         self.d_rcv = torch.as_tensor(self.receivers, device=device)

@@ -80,15 +80,16 @@ def train(x, t, steps=2000, batch=4096, lr=2e-3, seed=0, log_every=0):
     return params, history
 
 
-def per_cell_cache(d_classes, n_cells, modes, M, params_per_mode=None, precision="mixed"):
+def per_cell_cache(d_classes, n_cells, modes, M, params_per_mode=None, precision="mixed", out=None):
     """Cache with one class per cell: exact (params_per_mode None) or from the
     networks, with every solve they hand back (flag 2: outside the training
-    range, unsure validity, qSV branch region) recomputed by the exact solver."""
+    range, unsure validity, qSV branch region) recomputed by the exact solver.
+    out: optional preallocated cache arrays (the layout of build_cache)."""
     import torch
     if params_per_mode is None:
-        return chert.build_cache(d_classes, n_cells, modes, M, kernel="MEV", precision=precision)
+        return chert.build_cache(d_classes, n_cells, modes, M, kernel="MEV", precision=precision, out=out)
     cache = chert.surrogate_cache(params_per_mode, d_classes, n_cells, modes, M,
-                                  precision="fp64" if precision == "fp64" else "fp32")
+                                  precision="fp64" if precision == "fp64" else "fp32", out=out)
     # solve j of (mode slot, class) writes entry d = j (d = M for j = M)
     first = cache["flag"][:, :, :M + 1]
     items = torch.nonzero(first.reshape(-1) == 2).flatten()

@@ -63,6 +63,21 @@ def test_workspace_query(lib):
     assert chert.workspace_bytes(0, 8, 80, chert.FP32, 64) == 0
 
 
+def test_workspace_grid_adds_per_node_area(lib):
+    """The lattice-aware query adds the per-node weight area only where the
+    class-pair table cannot hold the classes and the stencil is standard."""
+    base = chert.workspace_bytes(3, 8, 80, chert.FP32, 64)
+    assert chert.workspace_bytes(3, 8, 80, chert.FP32, 64, 401, 401) == base
+    n = 100 * 60
+    small = chert.workspace_bytes(3, n, 80, chert.FP32, 4)
+    big = chert.workspace_bytes(3, n, 80, chert.FP32, 4, 100, 60)
+    assert big - small >= 2 * (3 * 2 * 80 * n * 4)          # row and column layouts
+    assert chert.workspace_bytes(3, n, 80, chert.FP64, 4, 100, 60) - chert.workspace_bytes(3, n, 80, chert.FP64, 4) \
+        >= 2 * (3 * 2 * 80 * n * 8)
+    assert chert.workspace_bytes(3, n, 84, chert.FP32, 4, 100, 60) == chert.workspace_bytes(3, n, 84, chert.FP32, 4)
+    assert lib.chert_traveltime_workspace_bytes_grid(3, n, 80, chert.FP32, 4, 100, 2, 60) == 0
+
+
 def test_null_arguments_are_rejected_without_gpu(lib):
     assert lib.chert_build_cache(None, 1, None, 1, None, None, None) == chert.EINVAL
     assert lib.chert_raypath(None, 1, 10, None, None, 1, 4, None, None, None) == chert.EINVAL
