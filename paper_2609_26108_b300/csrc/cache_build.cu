@@ -26,8 +26,11 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "cplx.cuh"
+#include "ff.cuh"
 
 namespace chert {
 namespace {
@@ -51,6 +54,19 @@ __device__ __forceinline__ Medium<T> load_medium(const chert_class& c) {
     return m;
 }
 
+__device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double shfl(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// Relative precision of each arithmetic (float, float-float, double).
+template <typename T>
+constexpr double unit_eps();
+template <>
+constexpr double unit_eps<float>() { return 1.2e-7; }
+template <>
+constexpr double unit_eps<xf::ff>() { return 3.6e-15; }
+template <>
+constexpr double unit_eps<double>() { return 2.3e-16; }
+
 __device__ __forceinline__ float ch_(float x) { return coshf(x); }
 __device__ __forceinline__ double ch_(double x) { return cosh(x); }
 __device__ __forceinline__ float sh_(float x) { return sinhf(x); }
@@ -59,8 +75,8 @@ __device__ __forceinline__ double sh_(double x) { return sinh(x); }
 // Complex energy velocity (x and z components) at slowness angle theta + i vt,
 // with s = sin(theta), c = cos(theta).
 template <typename T>
-__device__ __forceinline__ void energy_velocity(const Medium<T>& m, T s, T c, T vt, int mode,
-                                                int kernel, cplx<T>& v1, cplx<T>& v3) {
+__device__ __forceinline__ void energy_velocity_body(const Medium<T>& m, T s, T c, T vt, int mode,
+                                                     int kernel, cplx<T>& v1, cplx<T>& v3) {
     const T chv = ch_(vt), shv = sh_(vt);
     const cplx<T> n1 = mk<T>(s * chv, c * shv);     // sin(theta + i vt)
     const cplx<T> n3 = mk<T>(c * chv, -s * shv);    // cos(theta + i vt)
@@ -102,12 +118,36 @@ __device__ __forceinline__ void energy_velocity(const Medium<T>& m, T s, T c, T 
     }
 }
 
+// One out-of-line copy of the evaluation serves every call site outside the
+// float scan loop (the wide-precision refinement, the polish, the ray
+// quantities): inlined everywhere, the kernel's code would not fit the
+// instruction cache.  The float scan keeps its inlined copies.
+template <typename T>
+__device__ __noinline__ void energy_velocity_call(const Medium<T>& m, T s, T c, T vt, int mode, int kernel,
+                                                  cplx<T>& v1, cplx<T>& v3) {
+    energy_velocity_body(m, s, c, vt, mode, kernel, v1, v3);
+}
+template <typename T>
+__device__ __forceinline__ void energy_velocity(const Medium<T>& m, T s, T c, T vt, int mode,
+                                                int kernel, cplx<T>& v1, cplx<T>& v3) {
+    if constexpr (sizeof(T) == 4)
+        energy_velocity_body(m, s, c, vt, mode, kernel, v1, v3);
+    else
+        energy_velocity_call(m, s, c, vt, mode, kernel, v1, v3);
+}
+
 // Sign-carrying residual: (v^R x v^I)_y; the oracle divides by |v^R|^2 > 0,
 // which changes neither its sign nor its zeros.
 template <typename T>
 __device__ __forceinline__ T residual(const Medium<T>& m, T s, T c, T vt, int mode, int kernel) {
     cplx<T> v1, v3;
     energy_velocity(m, s, c, vt, mode, kernel, v1, v3);
+    return v1.re * v3.im - v3.re * v1.im;
+}
+template <typename T>
+__device__ __forceinline__ T residual_cold(const Medium<T>& m, T s, T c, T vt, int mode, int kernel) {
+    cplx<T> v1, v3;
+    energy_velocity_call(m, s, c, vt, mode, kernel, v1, v3);
     return v1.re * v3.im - v3.re * v1.im;
 }
 
@@ -117,12 +157,9 @@ struct RayQ {
     bool ok;
 };
 
-// Eq. 10-11 at a root.
+// Eq. 10-11 from the complex energy velocity at a root.
 template <typename T>
-__device__ __forceinline__ RayQ<T> ray_quantities(const Medium<T>& m, T s, T c, T vt, int mode,
-                                                  int kernel) {
-    cplx<T> v1, v3;
-    energy_velocity(m, s, c, vt, mode, kernel, v1, v3);
+__device__ __forceinline__ RayQ<T> ray_from_velocity(cplx<T> v1, cplx<T> v3) {
     RayQ<T> q;
     const T vr = hyp(v1.re, v3.re);
     q.rx = v1.re / vr;
@@ -138,6 +175,14 @@ __device__ __forceinline__ RayQ<T> ray_quantities(const Medium<T>& m, T s, T c, 
     return q;
 }
 
+template <typename T>
+__device__ __forceinline__ RayQ<T> ray_quantities(const Medium<T>& m, T s, T c, T vt, int mode,
+                                                  int kernel) {
+    cplx<T> v1, v3;
+    energy_velocity_call(m, s, c, vt, mode, kernel, v1, v3);
+    return ray_from_velocity(v1, v3);
+}
+
 // 33-way subdivision of the bracket [lo, hi] (residuals flo, fhi at its ends):
 // every round each lane evaluates one interior point and the warp keeps the
 // first sub-interval with a sign change, until the bracket is narrower than
@@ -147,25 +192,25 @@ __device__ __forceinline__ RayQ<T> ray_quantities(const Medium<T>& m, T s, T c, 
 template <typename T>
 __device__ T polish(const Medium<T>& m, T s, T c, int mode, int kernel, T lo, T hi, T flo, T fhi,
                     int lane, T stop) {
-    const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(2.3e-16);
+    constexpr T eps = T(unit_eps<T>());
     for (int round = 0; round < 12; ++round) {
         const T width = hi - lo;
         if (!(width > stop) || !(width > T(kPolishTol))) break;
         if (width <= T(2) * eps * fmax(fabs(lo), fabs(hi))) break;
         const T x = lo + width * T(lane + 1) / T(33);
-        const T fx = residual(m, s, c, x, mode, kernel);
+        const T fx = residual_cold(m, s, c, x, mode, kernel);
         const bool chg = (fx == T(0)) || (signbit(fx) != signbit(flo));
         const unsigned mask = __ballot_sync(0xffffffffu, chg);
         if (mask == 0u) {
-            lo = __shfl_sync(0xffffffffu, x, 31);
-            flo = __shfl_sync(0xffffffffu, fx, 31);
+            lo = shfl(x, 31);
+            flo = shfl(fx, 31);
             continue;
         }
         const int i = __ffs(mask) - 1;
-        const T xi = __shfl_sync(0xffffffffu, x, i);
-        const T fi = __shfl_sync(0xffffffffu, fx, i);
-        const T xp = __shfl_sync(0xffffffffu, x, i > 0 ? i - 1 : 0);
-        const T fp = __shfl_sync(0xffffffffu, fx, i > 0 ? i - 1 : 0);
+        const T xi = shfl(x, i);
+        const T fi = shfl(fx, i);
+        const T xp = shfl(x, i > 0 ? i - 1 : 0);
+        const T fp = shfl(fx, i > 0 ? i - 1 : 0);
         if (fi == T(0)) return xi;
         if (i > 0) {
             lo = xp;
@@ -181,35 +226,70 @@ __device__ T polish(const Medium<T>& m, T s, T c, int mode, int kernel, T lo, T 
     return T(0.5) * (lo + hi);
 }
 
-// Double refinement of a float root r32 that lies in the grid bracket
-// [glo, ghi]: one 33-point round on [r32 - d, r32 + d] in double (lanes 0 and
-// 32's neighbour evaluate the ends), then a secant step.  If the ends do not
-// bracket a sign change in double, fall back to polishing the grid bracket.
-__device__ double refine_double(const Medium<double>& m, double s, double c, int mode, int kernel,
-                                double r32, double glo, double ghi, int lane) {
-    const double d = 1e-8 + 16.0 * 1.2e-7 * fabs(r32);
-    const double a = fmax(glo, r32 - d), b = fmin(ghi, r32 + d);
-    const double x = a + (b - a) * double(lane) / 31.0;          // lane 0: a, lane 31: b
-    const double fx = residual(m, s, c, x, mode, kernel);
-    const double fa = __shfl_sync(0xffffffffu, fx, 0), fb = __shfl_sync(0xffffffffu, fx, 31);
-    if (fa == 0.0) return a;
-    if (fb == 0.0) return b;
+template <typename TP>
+struct Refined {
+    TP root;
+    RayQ<TP> q;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> shfl_c(cplx<T> v, int src) { return mk<T>(shfl(v.re, src), shfl(v.im, src)); }
+
+// Extended-precision refinement (TP: float-float or double) of a float root
+// r32 that lies in the grid bracket [glo, ghi] of width h.  The float root
+// can be off by the float noise of the residual (it matters most for roots
+// near vartheta = 0), so the window is [r32 - d, r32 + d] with d a quarter of
+// h (at least 16 float ulps of r32), clipped to the bracket: one 32-point
+// round (lanes 0 and 31 at the ends), a secant step between the two lanes
+// around the sign change, and the ray quantities (Eq. 10-11) from the energy
+// velocity interpolated linearly between those lanes (spacing h/62, so the
+// interpolation error, of the order of its square, lies far below the
+// precision of the stored float entries).  If the window shows no sign
+// change, the whole bracket is polished in TP and evaluated there.  Out of
+// line: called once per candidate that passes the float prefilter.
+template <typename TP>
+__device__ __noinline__ Refined<TP> refine(const Medium<TP>& m, TP s, TP c, int mode, int kernel, TP r32,
+                                           TP glo, TP ghi, int lane) {
+    const TP d = fmax(TP(0.25f) * (ghi - glo), TP(1e-8) + TP(16.0 * 1.2e-7) * fabs(r32));
+    const TP a = fmax(glo, r32 - d), b = fmin(ghi, r32 + d);
+    const TP x = a + (b - a) * TP(float(lane) / 31.0f);           // lane 0: a, lane 31: b
+    cplx<TP> v1, v3;
+    energy_velocity_call(m, s, c, x, mode, kernel, v1, v3);
+    const TP fx = v1.re * v3.im - v3.re * v1.im;
+    const TP fa = shfl(fx, 0), fb = shfl(fx, 31);
+    Refined<TP> out;
+    auto at_lane = [&](int l) {
+        out.root = shfl(x, l);
+        out.q = ray_from_velocity(shfl_c(v1, l), shfl_c(v3, l));
+        return out;
+    };
+    if (fa == TP(0)) return at_lane(0);
+    if (fb == TP(0)) return at_lane(31);
     if (signbit(fa) == signbit(fb)) {
-        const double flo = residual(m, s, c, glo, mode, kernel);
-        const double fhi = residual(m, s, c, ghi, mode, kernel);
-        if (flo == 0.0) return glo;
-        if (fhi == 0.0) return ghi;
-        if (signbit(flo) == signbit(fhi)) return r32;        // no double sign change: keep float root
-        return polish(m, s, c, mode, kernel, glo, ghi, flo, fhi, lane, 1e-9);
+        const TP flo = residual_cold(m, s, c, glo, mode, kernel);
+        const TP fhi = residual_cold(m, s, c, ghi, mode, kernel);
+        TP r;
+        if (flo == TP(0)) r = glo;
+        else if (fhi == TP(0)) r = ghi;
+        else if (signbit(flo) == signbit(fhi)) r = r32;       // no sign change in TP: keep the float root
+        else r = polish(m, s, c, mode, kernel, glo, ghi, flo, fhi, lane, TP(1e-9));
+        out.root = r;
+        out.q = ray_quantities(m, s, c, r, mode, kernel);
+        return out;
     }
-    const bool chg = (fx == 0.0) || (signbit(fx) != signbit(fa));
+    const bool chg = (fx == TP(0)) || (signbit(fx) != signbit(fa));
     const unsigned mask = __ballot_sync(0xffffffffu, chg) & ~1u;
     const int i = __ffs(mask) - 1;                             // first lane past a sign change
-    const double xi = __shfl_sync(0xffffffffu, x, i), fi = __shfl_sync(0xffffffffu, fx, i);
-    const double xp = __shfl_sync(0xffffffffu, x, i - 1), fp = __shfl_sync(0xffffffffu, fx, i - 1);
-    if (fi == 0.0) return xi;
-    const double r = xp - fp * (xi - xp) / (fi - fp);
-    return (r >= xp && r <= xi) ? r : 0.5 * (xp + xi);
+    const TP xi = shfl(x, i), fi = shfl(fx, i);
+    const TP xp = shfl(x, i - 1), fp = shfl(fx, i - 1);
+    if (fi == TP(0)) return at_lane(i);
+    TP r = xp - fp * (xi - xp) / (fi - fp);
+    if (!(r >= xp && r <= xi)) r = TP(0.5f) * (xp + xi);
+    const TP t = (r - xp) / (xi - xp);
+    const cplx<TP> a1 = shfl_c(v1, i - 1), b1 = shfl_c(v1, i), a3 = shfl_c(v3, i - 1), b3 = shfl_c(v3, i);
+    out.root = r;
+    out.q = ray_from_velocity(a1 + t * (b1 - a1), a3 + t * (b3 - a3));
+    return out;
 }
 
 struct Outs {
@@ -261,6 +341,16 @@ __device__ __forceinline__ Solve<TS, TP> make_solve(const chert_class* classes, 
     return v;
 }
 
+// Grid point kk*h in the scan precision.  In float it is formed from the
+// two-float split h = hf + hl (hf = float(h), hl = float(h - hf)) as
+// fma(kk, hf, kk*hl): one rounding of kk*h (kk < 2^24 is exact in float) and
+// no double-precision instruction, which on this part issues at a small
+// fraction of the float rate.
+__device__ __forceinline__ float grid_point(float kf, double, float hf, float hl) {
+    return fmaf(kf, hf, kf * hl);
+}
+__device__ __forceinline__ double grid_point(double kf, double h, float, float) { return kf * h; }
+
 // Outward scan of the grid distances kk in [k_begin, k_end] on both sides by
 // one warp.  fb_pos / fb_neg are the residuals at +-(k_begin-1)h.  Candidates
 // are taken in order of |vartheta| (brackets at inner distance kk-1 before the
@@ -272,16 +362,18 @@ __device__ bool scan_window(const Solve<TS, TP>& v, int kernel, double h, int k_
     constexpr bool mixed = sizeof(TS) != sizeof(TP);
     constexpr int P = 4;     // consecutive grid points per lane per step
     const int mode = v.mode;
+    const float hf = float(h), hl = float(h - double(hf));
     TS prev_pos = fb_pos, prev_neg = fb_neg;
     for (int base = k_begin - 1; base < k_end; base += 16 * P) {
         const bool neg = lane >= 16;
         const int l16 = lane & 15;
+        const int k0 = base + 1 + l16 * P;
+        const TS kf0 = TS(k0);
         TS fv[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const int kk = base + 1 + l16 * P + p;
-            const double xk = (neg ? -static_cast<double>(kk) : static_cast<double>(kk)) * h;
-            fv[p] = kk <= k_end ? residual(v.ms, v.ss, v.cs, TS(xk), mode, kernel) : TS(NAN);
+            const TS xk = grid_point(kf0 + TS(p), h, hf, hl);
+            fv[p] = k0 + p <= k_end ? residual(v.ms, v.ss, v.cs, neg ? -xk : xk, mode, kernel) : TS(NAN);
         }
         TS before = __shfl_up_sync(0xffffffffu, fv[P - 1], 1);    // point just inside
         if (l16 == 0) before = neg ? prev_neg : prev_pos;
@@ -318,15 +410,18 @@ __device__ bool scan_window(const Solve<TS, TP>& v, int kernel, double h, int k_
                     // polish in the scan precision (float for FP32 and MIXED)
                     const TS rs = polish(v.ms, v.ss, v.cs, mode, kernel, TS(glo), TS(ghi), fl, fh, lane,
                                          sizeof(TS) == 8 ? TS(1e-9) : TS(0));
-                    TP r = TP(rs);
                     if constexpr (mixed) {
-                        // drop clearly growing roots in float; decide the rest in double
+                        // drop clearly growing roots in float; decide the rest in TP
                         const RayQ<TS> q32 = ray_quantities(v.ms, v.ss, v.cs, rs, mode, kernel);
                         if (!(q32.vi <= TS(1e-4) * q32.vr)) continue;
-                        r = refine_double(v.mp, v.sd, v.cd, mode, kernel, double(rs), glo, ghi, lane);
+                        const Refined<TP> rf = refine<TP>(v.mp, v.sp, v.cp, mode, kernel, TP(rs), TP(glo), TP(ghi),
+                                                          lane);
+                        cq[side] = rf.q;
+                        cand[side] = rf.root;
+                    } else {
+                        cq[side] = ray_quantities(v.mp, v.sp, v.cp, TP(rs), mode, kernel);
+                        cand[side] = TP(rs);
                     }
-                    cq[side] = ray_quantities(v.mp, v.sp, v.cp, r, mode, kernel);
-                    cand[side] = r;
                     cok[side] = cq[side].ok;
                 }
                 if (cok[0] || cok[1]) {
@@ -405,7 +500,7 @@ __device__ void write_entries(const Outs& out, const Solve<TS, TP>& v, int n_cla
 // With a solve list (items != NULL) warp w takes solve items[w]; a solve is
 // numbered mode_slot*n_classes*(M+1) + class*(M+1) + j.
 template <typename TS, typename TP, typename TO>
-__global__ void __launch_bounds__(256) cache_build_kernel(const chert_class* __restrict__ classes,
+__global__ void __launch_bounds__(256, 2) cache_build_kernel(const chert_class* __restrict__ classes,
                                                           int n_classes, ModeList modes, int M,
                                                           double h, int K, int kernel, Outs out,
                                                           const int64_t* __restrict__ items,
@@ -432,27 +527,25 @@ __global__ void __launch_bounds__(256) cache_build_kernel(const chert_class* __r
     write_entries<TS, TP, TO>(out, v, n_classes, M, found, root, fq, lane);
 }
 
-// Second launch: one 1024-thread CTA per pending solve.  Each round its 32
-// warps scan consecutive 64-point slices of grid distance (2048 per side per
-// round); the nearest slice with a decaying root wins.
+// Second launch: one 1024-thread CTA per chunk of `chunk` (<= kFinishChunk)
+// consecutive solves (of the solve list, if any).  It collects the chunk's
+// pending solves in shared memory and finishes them one after another with
+// the whole CTA: each round its 32 warps scan consecutive 64-point slices of
+// grid distance (2048 per side per round); the nearest slice with a decaying
+// root wins.  The host sizes the chunks so that large builds launch few CTAs
+// and small ones still spread their pending solves over every SM; the block
+// scheduler balances the uneven work.
+constexpr int kFinishChunk = 256;
+
 template <typename TS, typename TP, typename TO>
-__global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* __restrict__ classes,
-                                                            int n_classes, ModeList modes, int M,
-                                                            double h, int K, int kernel, Outs out,
-                                                            const int64_t* __restrict__ items) {
-    const long long idx = items ? items[blockIdx.x] : static_cast<long long>(blockIdx.x);
-    const int per = M + 1;
-    {
-        const int j = static_cast<int>(idx % per);
-        const int k = static_cast<int>((idx / per) % n_classes);
-        const int mi = static_cast<int>(idx / (static_cast<long long>(per) * n_classes));
-        if (out.flag[entry_index(mi, k, n_classes, M, j)] != kPending) return;
-    }
+__device__ void finish_one(const chert_class* __restrict__ classes, int n_classes, const ModeList& modes,
+                           int M, double h, int K, int kernel, const Outs& out, long long idx) {
     __shared__ int s_found[32];
     __shared__ double s_root[32];
     __shared__ RayQ<TP> s_q[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, M, idx);
+    const float hf = float(h), hl = float(h - double(hf));
     constexpr int slice = 64;
     int winner = -1;
     for (int r0 = kPhase1Reach; r0 < K && winner < 0; r0 += 32 * slice) {
@@ -461,9 +554,9 @@ __global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* _
         TP root = TP(0);
         RayQ<TP> q{};
         if (kb <= ke) {
-            const double xb = (kb - 1) * h;
-            const TS fp = residual(v.ms, v.ss, v.cs, TS(xb), v.mode, kernel);
-            const TS fn = residual(v.ms, v.ss, v.cs, TS(-xb), v.mode, kernel);
+            const TS xb = grid_point(TS(kb - 1), h, hf, hl);
+            const TS fp = residual(v.ms, v.ss, v.cs, xb, v.mode, kernel);
+            const TS fn = residual(v.ms, v.ss, v.cs, -xb, v.mode, kernel);
             found = scan_window(v, kernel, h, kb, ke, fp, fn, lane, root, q);
         }
         if (lane == 0) {
@@ -482,6 +575,32 @@ __global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* _
         const RayQ<TP> q = found ? s_q[winner] : RayQ<TP>{};
         write_entries<TS, TP, TO>(out, v, n_classes, M, found, root, q, lane);
     }
+    __syncthreads();
+}
+
+template <typename TS, typename TP, typename TO>
+__global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* __restrict__ classes,
+                                                            int n_classes, ModeList modes, int M,
+                                                            double h, int K, int kernel, Outs out,
+                                                            const int64_t* __restrict__ items,
+                                                            long long n_total, int chunk) {
+    __shared__ long long s_list[kFinishChunk];
+    __shared__ int s_count;
+    const int per = M + 1;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    const long long t = (long long)blockIdx.x * chunk + threadIdx.x;
+    if ((int)threadIdx.x < chunk && t < n_total) {
+        const long long idx = items ? items[t] : t;
+        const int j = static_cast<int>(idx % per);
+        const int k = static_cast<int>((idx / per) % n_classes);
+        const int mi = static_cast<int>(idx / (static_cast<long long>(per) * n_classes));
+        if (out.flag[entry_index(mi, k, n_classes, M, j)] == kPending) s_list[atomicAdd(&s_count, 1)] = idx;
+    }
+    __syncthreads();
+    const int cnt = s_count;
+    for (int q = 0; q < cnt; ++q)
+        finish_one<TS, TP, TO>(classes, n_classes, modes, M, h, K, kernel, out, s_list[q]);
 }
 
 }  // namespace
@@ -515,18 +634,26 @@ static int launch_build(const chert_class* d_classes, int n_classes, const int* 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double h = params->scan_step;
     const int K = params->scan_half;
-    const unsigned solves = (unsigned)warps;
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1) {
+        cudaGetLastError();
+        n_sm = 148;
+    }
+    const long long per_cta = (warps + 8LL * n_sm - 1) / (8LL * n_sm);        // ~8 CTAs per SM
+    const int chunk = (int)std::max(1LL, std::min<long long>(kFinishChunk, per_cta));
+    const unsigned finish_blocks = (unsigned)((warps + chunk - 1) / chunk);
     const int Mq = params->M, kern = params->kernel;
 #define CHERT_LAUNCH_BUILD(TS, TP, TO)                                                                  \
     cache_build_kernel<TS, TP, TO><<<(unsigned)blocks, threads, 0, s>>>(d_classes, n_classes, ml, Mq, h, K, \
                                                                        kern, o, d_items, n_items);       \
     if (K > kPhase1Reach)                                                                               \
-        cache_finish_kernel<TS, TP, TO><<<solves, 1024, 0, s>>>(d_classes, n_classes, ml, Mq, h, K, kern, o, \
-                                                                 d_items);
+        cache_finish_kernel<TS, TP, TO><<<finish_blocks, 1024, 0, s>>>(d_classes, n_classes, ml, Mq, h, K, kern, \
+                                                                        o, d_items, warps, chunk);
     switch (params->precision) {
         case CHERT_FP64: CHERT_LAUNCH_BUILD(double, double, double) break;
         case CHERT_FP32: CHERT_LAUNCH_BUILD(float, float, float) break;
-        case CHERT_MIXED: CHERT_LAUNCH_BUILD(float, double, float) break;
+        case CHERT_MIXED: CHERT_LAUNCH_BUILD(float, xf::ff, float) break;
         default: CHERT_REQUIRE(false, "%s: precision=%d", who, params->precision);
     }
 #undef CHERT_LAUNCH_BUILD
