@@ -47,6 +47,10 @@ RADIUS = 5
 N_RECEIVERS = 41
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# relax_fast_kernel<float, 5, 1, class-pair> on the 64-source workload, from
+# one ncu capture of this kernel version (1.051 GB read + 0.761 GB written).
+RELAX_DRAM_BYTES_64SRC = 1.051050e9 + 0.760521e9
 
 
 def workload(n_sources=64):
@@ -399,8 +403,11 @@ def run_chert(args):
     sm_max = clocks.get("sm_max_mhz") or 2032.0
     peak_tops = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     achieved = alg_ops / relax_avg_s / 1e12
+    traffic = RELAX_DRAM_BYTES_64SRC if len(model.sources) == 64 else None
     roofline = {"bound": "alu", "kernel": "relax_fast_kernel<float,5,1,false>", "achieved": achieved,
-                "peak": peak_tops, "unit": "TFLOP/s", "frac": achieved / peak_tops, "traffic": None,
+                "peak": peak_tops, "unit": "TFLOP/s", "frac": achieved / peak_tops, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu)",
+                "alg_bytes_per_launch": 20.0 * model.nx * model.nz * nf,   # class id 4 B + tauR, tauI, parR, parI 4 B each per node per field
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock (non-FMA op rate)",
                 "alg_ops_per_launch": alg_ops, "directed_edges_per_field": edges,
                 "launch_ms": 1e3 * relax_avg_s}
