@@ -29,6 +29,13 @@ against the equations, not for speed:
                symmetry-axis frame, d < 4M; the solve runs at the angle folded
                into [0, pi/2] (the 0-90 deg TI range) and the ray direction is
                mirrored back, then rotated by the tilt theta_0.
+* Eq. 35       3D cache over global slowness directions (polar (i + 1/2) pi/n_pol,
+               azimuth j 2 pi/n_az): each direction is expressed in the local
+               frame (e_x', e_y', e_z') of the class's symmetry axis (theta_0,
+               phi_0); VTI is rotationally symmetric about e_z', so the solve is
+               the sagittal-plane one at the local polar angle folded into
+               [0, pi/2], and its ray is turned to the local azimuth, mirrored
+               back and expressed in the global frame.
 """
 from __future__ import annotations
 
@@ -280,4 +287,56 @@ def build_cache(moduli, tilts, modes, M, kernel="MEV", h=0.001 * DEG, K=30000):
                 out["vartheta"][mi, k, d] = s["vartheta"] * sx * sz
                 out["theta"][mi, k, d] = (math.pi / 2) * d / M + tilts[k]
                 out["flag"][mi, k, d] = s["flag"]
+    return out
+
+
+def local_basis(theta0, phi0):
+    """Rows e_x', e_y', e_z' of the local symmetry-axis frame (Eq. 35)."""
+    ct, st, cp, sp = math.cos(theta0), math.sin(theta0), math.cos(phi0), math.sin(phi0)
+    return np.array([[ct * cp, ct * sp, -st],
+                     [-sp, cp, 0.0],
+                     [st * cp, st * sp, ct]])
+
+
+def build_cache_3d(moduli, tilts, azims, modes, n_az, n_pol, kernel="MEV", h=0.001 * DEG, K=30000):
+    """3D directional cache for classes ``moduli`` [n_classes, 5] with symmetry
+    axes (tilts theta_0, azims phi_0).  Entry d = i*n_az + j is the global
+    slowness direction of polar angle (i + 1/2) pi/n_pol and azimuth j 2 pi/n_az.
+
+    Returns arrays [n_modes, n_classes, n_pol*n_az]: V, A, Q, rx, ry, rz,
+    theta (polar), phi (azimuth), vartheta (as solved, times the z mirror sign),
+    flag."""
+    moduli = np.asarray(moduli, dtype=np.complex128).reshape(-1, 5)
+    tilts = np.asarray(tilts, dtype=np.float64).reshape(-1)
+    azims = np.asarray(azims, dtype=np.float64).reshape(-1)
+    nm, nk, nd = len(modes), moduli.shape[0], n_az * n_pol
+    out = {key: np.zeros((nm, nk, nd)) for key in ("V", "A", "Q", "rx", "ry", "rz", "theta", "phi", "vartheta")}
+    out["flag"] = np.zeros((nm, nk, nd), dtype=np.uint8)
+    for mi, mode in enumerate(modes):
+        for k in range(nk):
+            A = stiffness_tensor(moduli[k])
+            E = local_basis(tilts[k], azims[k])
+            for i in range(n_pol):
+                th = (i + 0.5) * math.pi / n_pol
+                for j in range(n_az):
+                    ph = j * 2.0 * math.pi / n_az
+                    d = i * n_az + j
+                    n = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+                    nl = E @ n                                   # components along e_x', e_y', e_z'
+                    th_l = math.acos(min(1.0, max(-1.0, nl[2])))
+                    ph_l = math.atan2(nl[1], nl[0])
+                    sz = 1.0 if th_l <= math.pi / 2 else -1.0
+                    th_f = th_l if sz > 0 else math.pi - th_l
+                    s = solve_direction(A, th_f, mode, kernel, h, K)
+                    rs, rzl = s["r"][0], s["r"][2]
+                    rl = np.array([rs * math.cos(ph_l), rs * math.sin(ph_l), sz * rzl])
+                    r = E.T @ rl                                 # back to the global frame
+                    out["rx"][mi, k, d], out["ry"][mi, k, d], out["rz"][mi, k, d] = r
+                    out["V"][mi, k, d] = s["V"]
+                    out["A"][mi, k, d] = s["A"]
+                    out["Q"][mi, k, d] = s["Q"]
+                    out["vartheta"][mi, k, d] = s["vartheta"] * sz
+                    out["theta"][mi, k, d] = th
+                    out["phi"][mi, k, d] = ph
+                    out["flag"][mi, k, d] = s["flag"]
     return out
