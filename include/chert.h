@@ -92,7 +92,11 @@ int chert_thomsen_to_classes(int64_t n, const double* vp0, const double* vs0,
  *               as seen from direction d (Eq. 9)
  *   flag        0 = valid, 1 = no acceptable (decaying) root; V, A, Q, rx, rz,
  *               vartheta are NaN then and the lookup skips the entry.
- * Any pointer except flag, V and rx/rz may be NULL to skip that output. */
+ *   ry, phi     3D caches only (chert_build_cache_3d): the y component of r and
+ *               the global slowness azimuth; theta is then the global polar
+ *               angle.  2D builds neither read nor write them (may be NULL).
+ * Any pointer except flag, V and rx/rz (and ry in 3D) may be NULL to skip
+ * that output. */
 typedef struct {
     void*    V;
     void*    A;
@@ -102,6 +106,8 @@ typedef struct {
     void*    theta;
     void*    vartheta;
     uint8_t* flag;
+    void*    ry;
+    void*    phi;
 } chert_cache_arrays;
 
 /* Homogeneity search settings.  The roots of the residual
@@ -142,12 +148,29 @@ int chert_build_cache_items(const chert_class* d_classes, int n_classes,
                             const int64_t* d_items, int64_t n_items,
                             const chert_cache_arrays* out, void* stream);
 
+/* 3D cache (Eq. 35, the 3D TTI extension of the paper's experiments): entry
+ * d = i*n_az + j of class k is the global slowness direction of polar angle
+ * (i + 1/2)*pi/n_pol and azimuth j*2*pi/n_az (arrays [n_modes][n_classes]
+ * [n_az*n_pol]).  Each direction is expressed in the class's symmetry-axis
+ * frame (e_x', e_y', e_z') given by its tilt theta0 and azimuth phi0; the
+ * medium being rotationally symmetric about e_z', the homogeneity search runs
+ * in the sagittal plane at the local polar angle folded into [0, pi/2], and
+ * the ray is turned to the local azimuth, mirrored back and written in the
+ * global frame (rx, ry, rz).  Same search settings and root rule as
+ * chert_build_cache (params->M is ignored); one solve per entry.  Errors:
+ * CHERT_EINVAL (also for a NULL ry), CHERT_ECUDA. */
+int chert_build_cache_3d(const chert_class* d_classes, int n_classes, const int* modes, int n_modes,
+                         int n_az, int n_pol, const chert_cache_params* params,
+                         const chert_cache_arrays* out, void* stream);
+
 /* ---- direction lookup (Eq. 27-28) --------------------------------------- */
 
 /* For every (mode, class, stencil offset o): the cache entry whose ray
  * direction r has the largest dot product with d = o/|o| (both float64 for
  * CHERT_FP64, float32 otherwise; products rounded separately, ties to the
- * lower entry index, flagged entries skipped).  Writes device arrays
+ * lower entry index, flagged entries skipped; the dot product is summed as
+ * ((dx*rx) + (dy*ry)) + (dz*rz), the middle term only when the cache has ry).
+ * Writes device arrays
  * [n_modes][n_classes][n_off]: idx (int32, -1 if a class has no valid
  * entry), Vsel and Asel (the entry's V and A, NaN for idx = -1).
  * offsets: host int32 [n_off][3] = (ox, oy, oz), 1 <= n_off <= 512, oy = 0

@@ -41,7 +41,8 @@ class chert_class(ctypes.Structure):
 class chert_cache_arrays(ctypes.Structure):
     _fields_ = [("V", ctypes.c_void_p), ("A", ctypes.c_void_p), ("Q", ctypes.c_void_p),
                 ("rx", ctypes.c_void_p), ("rz", ctypes.c_void_p), ("theta", ctypes.c_void_p),
-                ("vartheta", ctypes.c_void_p), ("flag", ctypes.c_void_p)]
+                ("vartheta", ctypes.c_void_p), ("flag", ctypes.c_void_p), ("ry", ctypes.c_void_p),
+                ("phi", ctypes.c_void_p)]
 
 
 class chert_cache_params(ctypes.Structure):
@@ -71,6 +72,9 @@ def lib():
     L.chert_build_cache_items.argtypes = [P, I, P, I, ctypes.POINTER(chert_cache_params), P, I64,
                                           ctypes.POINTER(chert_cache_arrays), P]
     L.chert_build_cache_items.restype = ctypes.c_int
+    L.chert_build_cache_3d.argtypes = [P, I, P, I, I, I, ctypes.POINTER(chert_cache_params),
+                                       ctypes.POINTER(chert_cache_arrays), P]
+    L.chert_build_cache_3d.restype = ctypes.c_int
     L.chert_traveltime_workspace_bytes.argtypes = [I, I, I, I, I]
     L.chert_traveltime_workspace_bytes.restype = SZ
     L.chert_traveltime_workspace_bytes_grid.argtypes = [I, I, I, I, I, I, I, I]
@@ -188,19 +192,23 @@ def classes_to_device(classes, device="cuda"):
 
 # ------------------------------------------------------------------ cache
 class Cache:
-    """Device-resident directional cache (torch tensors [n_modes, n_classes, 4M])."""
+    """Device-resident directional cache (torch tensors [n_modes, n_classes,
+    n_dir]): 2D with n_dir = 4M slowness angles, or 3D (n_az, n_pol set) with
+    n_dir = n_az*n_pol global directions."""
 
-    def __init__(self, arrays, modes, n_classes, M, precision):
+    def __init__(self, arrays, modes, n_classes, M, precision, n_az=0, n_pol=0):
         self.arrays, self.modes, self.n_classes, self.M, self.precision = arrays, modes, n_classes, M, precision
+        self.n_az, self.n_pol = n_az, n_pol
 
     @property
     def n_dir(self):
-        return 4 * self.M
+        return self.n_az * self.n_pol if self.n_az else 4 * self.M
 
     def struct(self):
         a = self.arrays
         return chert_cache_arrays(*[None if a.get(k) is None else a[k].data_ptr()
-                                    for k in ("V", "A", "Q", "rx", "rz", "theta", "vartheta", "flag")])
+                                    for k in ("V", "A", "Q", "rx", "rz", "theta", "vartheta", "flag", "ry",
+                                              "phi")])
 
     def __getitem__(self, key):
         return self.arrays[key]
@@ -225,6 +233,28 @@ def build_cache(d_classes, n_classes, modes, M, scan_step=0.001 * math.pi / 180,
     st = cache.struct()
     _check(lib().chert_build_cache(_dev_ptr(d_classes), n_classes, modes_arr, len(mode_ids),
                                    ctypes.byref(params), ctypes.byref(st), _stream_ptr(stream)))
+    return cache
+
+
+def build_cache_3d(d_classes, n_classes, modes, n_az, n_pol, scan_step=0.001 * math.pi / 180, scan_half=30000,
+                   kernel="MEV", precision="fp32", stream=None, out=None):
+    """Enqueue chert_build_cache_3d (global direction grid n_pol x n_az)."""
+    torch = _torch()
+    prec = PRECISION_IDS[precision] if isinstance(precision, str) else precision
+    mode_ids = [MODE_IDS[m] if isinstance(m, str) else m for m in modes]
+    shape = (len(mode_ids), n_classes, n_az * n_pol)
+    dev = d_classes.device
+    if out is None:
+        fd = _fdtype(prec)
+        out = {k: torch.empty(shape, dtype=fd, device=dev)
+               for k in ("V", "A", "Q", "rx", "ry", "rz", "theta", "phi", "vartheta")}
+        out["flag"] = torch.empty(shape, dtype=torch.uint8, device=dev)
+    cache = Cache(out, mode_ids, n_classes, 0, prec, n_az, n_pol)
+    params = chert_cache_params(1, scan_step, scan_half, KERNEL_IDS.get(kernel, kernel), prec)
+    modes_arr = (ctypes.c_int * len(mode_ids))(*mode_ids)
+    st = cache.struct()
+    _check(lib().chert_build_cache_3d(_dev_ptr(d_classes), n_classes, modes_arr, len(mode_ids), n_az, n_pol,
+                                      ctypes.byref(params), ctypes.byref(st), _stream_ptr(stream)))
     return cache
 
 

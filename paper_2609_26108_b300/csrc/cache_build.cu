@@ -295,6 +295,18 @@ __device__ __noinline__ Refined<TP> refine(const Medium<TP>& m, TP s, TP c, int 
 struct Outs {
     void *V, *A, *Q, *rx, *rz, *theta, *vartheta;
     uint8_t* flag;
+    void *ry, *phi;          // 3D only
+};
+
+// Direction set of a cache.  2D (n_az == 0): 4M slowness angles of the local
+// frame, solved as the M+1 folded angles j and mirrored.  3D (n_az > 0): the
+// global directions of polar angle (i + 1/2) pi/n_pol and azimuth
+// j 2 pi/n_az, entry d = i*n_az + j, one solve each (Eq. 35).
+struct Geo {
+    int M, n_az, n_pol;
+    __host__ __device__ bool three_d() const { return n_az > 0; }
+    __host__ __device__ int per_class() const { return n_az > 0 ? n_az * n_pol : M + 1; }   // solves
+    __host__ __device__ int n_dir() const { return n_az > 0 ? n_az * n_pol : 4 * M; }       // entries
 };
 
 struct ModeList {
@@ -314,6 +326,7 @@ constexpr int kPhase1Reach = 2048;   // grid points per side scanned by the firs
 template <typename TS, typename TP>
 struct Solve {
     int mi, k, j, mode;
+    double sz, phl;          // 3D: mirror sign of the local polar angle, local azimuth
     chert_class cls;
     Medium<TS> ms;
     Medium<TP> mp;
@@ -322,11 +335,32 @@ struct Solve {
     TP sp, cp;
 };
 
+// Local frame of Eq. 35: rows e_x', e_y', e_z' of the symmetry axis (theta0, phi0).
+__device__ __forceinline__ void local_basis(double theta0, double phi0, double E[3][3]) {
+    double st, ct, sp, cp;
+    sincos(theta0, &st, &ct);
+    sincos(phi0, &sp, &cp);
+    E[0][0] = ct * cp; E[0][1] = ct * sp; E[0][2] = -st;
+    E[1][0] = -sp;     E[1][1] = cp;      E[1][2] = 0.0;
+    E[2][0] = st * cp; E[2][1] = st * sp; E[2][2] = ct;
+}
+
+// 3D direction d of the global grid: polar and azimuth angles and unit vector.
+__device__ __forceinline__ void global_direction(const Geo& g, int d, double& th, double& ph, double n[3]) {
+    const int i = d / g.n_az, j = d % g.n_az;
+    th = (i + 0.5) * M_PI / g.n_pol;
+    ph = j * 2.0 * M_PI / g.n_az;
+    double st, ct, sp, cp;
+    sincos(th, &st, &ct);
+    sincos(ph, &sp, &cp);
+    n[0] = st * cp; n[1] = st * sp; n[2] = ct;
+}
+
 template <typename TS, typename TP>
 __device__ __forceinline__ Solve<TS, TP> make_solve(const chert_class* classes, int n_classes,
-                                                     const ModeList& modes, int M, long long idx) {
+                                                     const ModeList& modes, const Geo& g, long long idx) {
     Solve<TS, TP> v;
-    const int per = M + 1;
+    const int per = g.per_class();
     v.j = static_cast<int>(idx % per);
     v.k = static_cast<int>((idx / per) % n_classes);
     v.mi = static_cast<int>(idx / (static_cast<long long>(per) * n_classes));
@@ -334,7 +368,23 @@ __device__ __forceinline__ Solve<TS, TP> make_solve(const chert_class* classes, 
     v.cls = classes[v.k];
     v.ms = load_medium<TS>(v.cls);
     v.mp = load_medium<TP>(v.cls);
-    const double theta = (M_PI / 2 * v.j) / M;
+    v.sz = 1.0;
+    v.phl = 0.0;
+    double theta;
+    if (g.three_d()) {
+        // the sagittal-plane solve at the local polar angle folded into [0, pi/2]
+        double th, ph, n[3], E[3][3];
+        global_direction(g, v.j, th, ph, n);
+        local_basis(v.cls.tilt, v.cls.azim, E);
+        double nl[3];
+        for (int r = 0; r < 3; ++r) nl[r] = E[r][0] * n[0] + E[r][1] * n[1] + E[r][2] * n[2];
+        const double thl = acos(fmin(1.0, fmax(-1.0, nl[2])));
+        v.phl = atan2(nl[1], nl[0]);
+        v.sz = thl <= M_PI / 2 ? 1.0 : -1.0;
+        theta = v.sz > 0 ? thl : M_PI - thl;
+    } else {
+        theta = (M_PI / 2 * v.j) / g.M;
+    }
     sincos(theta, &v.sd, &v.cd);
     v.ss = TS(v.sd); v.cs = TS(v.cd);
     v.sp = TP(v.sd); v.cp = TP(v.cd);
@@ -444,17 +494,56 @@ __device__ bool scan_window(const Solve<TS, TP>& v, int kernel, double h, int k_
     return false;
 }
 
-__device__ __forceinline__ size_t entry_index(int mi, int k, int n_classes, int M, int d) {
-    return (static_cast<size_t>(mi) * n_classes + k) * (4 * M) + d;
+__device__ __forceinline__ size_t entry_index(int mi, int k, int n_classes, const Geo& g, int d) {
+    return (static_cast<size_t>(mi) * n_classes + k) * g.n_dir() + d;
 }
 
 // Write the up to four mirrored entries of a folded solve (lanes 0..3), the
 // ray direction reflected into the quadrant of theta_d, then rotated by the
 // tilt (Eq. 36).
 template <typename TS, typename TP, typename TO>
-__device__ void write_entries(const Outs& out, const Solve<TS, TP>& v, int n_classes, int M,
+__device__ void write_entries(const Outs& out, const Solve<TS, TP>& v, int n_classes, const Geo& g,
                               bool found, TP root, const RayQ<TP>& q, int lane) {
     const int j = v.j;
+    if (g.three_d()) {
+        // one entry: the sagittal ray turned to the local azimuth, mirrored in
+        // z' where the local polar angle was folded, expressed globally (Eq. 35)
+        if (lane != 0) return;
+        const size_t e = entry_index(v.mi, v.k, n_classes, g, j);
+        double th, ph, n[3], E[3][3];
+        global_direction(g, j, th, ph, n);
+        put<TO>(out.theta, e, th);
+        put<TO>(out.phi, e, ph);
+        if (found) {
+            local_basis(v.cls.tilt, v.cls.azim, E);
+            double sp, cp;
+            sincos(v.phl, &sp, &cp);
+            const double rs = double(q.rx);
+            const double rl[3] = {rs * cp, rs * sp, v.sz * double(q.rz)};
+            const double r[3] = {E[0][0] * rl[0] + E[1][0] * rl[1] + E[2][0] * rl[2],
+                                 E[0][1] * rl[0] + E[1][1] * rl[1] + E[2][1] * rl[2],
+                                 E[0][2] * rl[0] + E[1][2] * rl[1] + E[2][2] * rl[2]};
+            put<TO>(out.rx, e, r[0]);
+            put<TO>(out.ry, e, r[1]);
+            put<TO>(out.rz, e, r[2]);
+            put<TO>(out.V, e, double(q.V));
+            put<TO>(out.A, e, double(q.A));
+            put<TO>(out.Q, e, double(q.Q));
+            put<TO>(out.vartheta, e, double(root) * v.sz);
+            out.flag[e] = 0;
+        } else {
+            put<TO>(out.rx, e, NAN);
+            put<TO>(out.ry, e, NAN);
+            put<TO>(out.rz, e, NAN);
+            put<TO>(out.V, e, NAN);
+            put<TO>(out.A, e, NAN);
+            put<TO>(out.Q, e, NAN);
+            put<TO>(out.vartheta, e, NAN);
+            out.flag[e] = 1;
+        }
+        return;
+    }
+    const int M = g.M;
     int d, sx, sz, cnt;
     if (j == 0) {
         cnt = 2;
@@ -469,7 +558,7 @@ __device__ void write_entries(const Outs& out, const Solve<TS, TP>& v, int n_cla
         sz = (lane == 0 || lane == 3) ? 1 : -1;
     }
     if (lane >= cnt) return;
-    const size_t e = entry_index(v.mi, v.k, n_classes, M, d);
+    const size_t e = entry_index(v.mi, v.k, n_classes, g, d);
     double ct, st;
     sincos(v.cls.tilt, &st, &ct);
     put<TO>(out.theta, e, (M_PI / 2 * d) / M + v.cls.tilt);
@@ -498,18 +587,19 @@ __device__ void write_entries(const Outs& out, const Solve<TS, TP>& v, int n_cla
 // left marked kPending for the second launch.
 // TS: scan precision, TP: polish + ray-quantity precision, TO: storage.
 // With a solve list (items != NULL) warp w takes solve items[w]; a solve is
-// numbered mode_slot*n_classes*(M+1) + class*(M+1) + j.
+// numbered mode_slot*n_classes*P + class*P + j with P = M+1 (2D) or
+// n_az*n_pol (3D, j the entry d).
 template <typename TS, typename TP, typename TO>
 __global__ void __launch_bounds__(256, 2) cache_build_kernel(const chert_class* __restrict__ classes,
-                                                          int n_classes, ModeList modes, int M,
+                                                          int n_classes, ModeList modes, Geo g,
                                                           double h, int K, int kernel, Outs out,
                                                           const int64_t* __restrict__ items,
                                                           long long n_items) {
     const int lane = threadIdx.x & 31;
     const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const long long total = items ? n_items : static_cast<long long>(modes.n) * n_classes * (M + 1);
+    const long long total = items ? n_items : static_cast<long long>(modes.n) * n_classes * g.per_class();
     if (warp >= total) return;
-    const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, M, items ? items[warp] : warp);
+    const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, g, items ? items[warp] : warp);
     bool found = false;
     TP root = TP(0);
     RayQ<TP> fq{};
@@ -521,10 +611,10 @@ __global__ void __launch_bounds__(256, 2) cache_build_kernel(const chert_class* 
     const int reach = min(K, kPhase1Reach);
     if (!found) found = scan_window(v, kernel, h, 1, reach, f0, f0, lane, root, fq);
     if (!found && K > reach) {
-        if (lane == 0) out.flag[entry_index(v.mi, v.k, n_classes, M, v.j)] = kPending;
+        if (lane == 0) out.flag[entry_index(v.mi, v.k, n_classes, g, v.j)] = kPending;
         return;
     }
-    write_entries<TS, TP, TO>(out, v, n_classes, M, found, root, fq, lane);
+    write_entries<TS, TP, TO>(out, v, n_classes, g, found, root, fq, lane);
 }
 
 // Second launch: one 1024-thread CTA per chunk of `chunk` (<= kFinishChunk)
@@ -539,12 +629,12 @@ constexpr int kFinishChunk = 256;
 
 template <typename TS, typename TP, typename TO>
 __device__ void finish_one(const chert_class* __restrict__ classes, int n_classes, const ModeList& modes,
-                           int M, double h, int K, int kernel, const Outs& out, long long idx) {
+                           const Geo& g, double h, int K, int kernel, const Outs& out, long long idx) {
     __shared__ int s_found[32];
     __shared__ double s_root[32];
     __shared__ RayQ<TP> s_q[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, M, idx);
+    const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, g, idx);
     const float hf = float(h), hl = float(h - double(hf));
     constexpr int slice = 64;
     int winner = -1;
@@ -573,20 +663,20 @@ __device__ void finish_one(const chert_class* __restrict__ classes, int n_classe
         const bool found = winner >= 0;
         const TP root = found ? TP(s_root[winner]) : TP(0);
         const RayQ<TP> q = found ? s_q[winner] : RayQ<TP>{};
-        write_entries<TS, TP, TO>(out, v, n_classes, M, found, root, q, lane);
+        write_entries<TS, TP, TO>(out, v, n_classes, g, found, root, q, lane);
     }
     __syncthreads();
 }
 
 template <typename TS, typename TP, typename TO>
 __global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* __restrict__ classes,
-                                                            int n_classes, ModeList modes, int M,
+                                                            int n_classes, ModeList modes, Geo g,
                                                             double h, int K, int kernel, Outs out,
                                                             const int64_t* __restrict__ items,
                                                             long long n_total, int chunk) {
     __shared__ long long s_list[kFinishChunk];
     __shared__ int s_count;
-    const int per = M + 1;
+    const int per = g.per_class();
     if (threadIdx.x == 0) s_count = 0;
     __syncthreads();
     const long long t = (long long)blockIdx.x * chunk + threadIdx.x;
@@ -595,12 +685,12 @@ __global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* _
         const int j = static_cast<int>(idx % per);
         const int k = static_cast<int>((idx / per) % n_classes);
         const int mi = static_cast<int>(idx / (static_cast<long long>(per) * n_classes));
-        if (out.flag[entry_index(mi, k, n_classes, M, j)] == kPending) s_list[atomicAdd(&s_count, 1)] = idx;
+        if (out.flag[entry_index(mi, k, n_classes, g, j)] == kPending) s_list[atomicAdd(&s_count, 1)] = idx;
     }
     __syncthreads();
     const int cnt = s_count;
     for (int q = 0; q < cnt; ++q)
-        finish_one<TS, TP, TO>(classes, n_classes, modes, M, h, K, kernel, out, s_list[q]);
+        finish_one<TS, TP, TO>(classes, n_classes, modes, g, h, K, kernel, out, s_list[q]);
 }
 
 }  // namespace
@@ -608,12 +698,16 @@ __global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* _
 
 static int launch_build(const chert_class* d_classes, int n_classes, const int* modes, int n_modes,
                         const chert_cache_params* params, const chert_cache_arrays* out,
-                        const int64_t* d_items, long long n_items, void* stream, const char* who) {
+                        const int64_t* d_items, long long n_items, void* stream, const char* who,
+                        int n_az = 0, int n_pol = 0) {
     using namespace chert;
     CHERT_REQUIRE(d_classes && modes && params && out, "%s: NULL argument", who);
     CHERT_REQUIRE(n_classes >= 1, "%s: n_classes=%d", who, n_classes);
     CHERT_REQUIRE(n_modes >= 1 && n_modes <= 3, "%s: n_modes=%d", who, n_modes);
-    CHERT_REQUIRE(params->M >= 1 && params->M <= (1 << 20), "%s: M=%d", who, params->M);
+    CHERT_REQUIRE(n_az > 0 || (params->M >= 1 && params->M <= (1 << 20)), "%s: M=%d", who, params->M);
+    CHERT_REQUIRE(n_az == 0 || (n_az >= 1 && n_pol >= 1 && (long long)n_az * n_pol <= (1 << 24)),
+                  "%s: n_az=%d n_pol=%d", who, n_az, n_pol);
+    CHERT_REQUIRE(n_az == 0 || out->ry, "%s: a 3D cache needs the ry output", who);
     CHERT_REQUIRE(params->scan_step > 0 && params->scan_half >= 1 && params->scan_half <= (1 << 28),
                   "%s: bad scan grid", who);
     CHERT_REQUIRE(params->kernel == CHERT_OEV || params->kernel == CHERT_MEV, "%s: kernel=%d", who,
@@ -625,8 +719,9 @@ static int launch_build(const chert_class* d_classes, int n_classes, const int* 
         for (int j = 0; j < i; j++) CHERT_REQUIRE(modes[j] != modes[i], "%s: repeated mode", who);
         ml.m[i] = modes[i];
     }
-    Outs o{out->V, out->A, out->Q, out->rx, out->rz, out->theta, out->vartheta, out->flag};
-    const long long warps = d_items ? n_items : static_cast<long long>(n_modes) * n_classes * (params->M + 1);
+    Outs o{out->V, out->A, out->Q, out->rx, out->rz, out->theta, out->vartheta, out->flag, out->ry, out->phi};
+    const Geo geo{params->M, n_az, n_pol};
+    const long long warps = d_items ? n_items : static_cast<long long>(n_modes) * n_classes * geo.per_class();
     if (warps == 0) return CHERT_OK;
     const int threads = 256;
     const long long blocks = (warps * 32 + threads - 1) / threads;
@@ -643,12 +738,12 @@ static int launch_build(const chert_class* d_classes, int n_classes, const int* 
     const long long per_cta = (warps + 8LL * n_sm - 1) / (8LL * n_sm);        // ~8 CTAs per SM
     const int chunk = (int)std::max(1LL, std::min<long long>(kFinishChunk, per_cta));
     const unsigned finish_blocks = (unsigned)((warps + chunk - 1) / chunk);
-    const int Mq = params->M, kern = params->kernel;
+    const int kern = params->kernel;
 #define CHERT_LAUNCH_BUILD(TS, TP, TO)                                                                  \
-    cache_build_kernel<TS, TP, TO><<<(unsigned)blocks, threads, 0, s>>>(d_classes, n_classes, ml, Mq, h, K, \
+    cache_build_kernel<TS, TP, TO><<<(unsigned)blocks, threads, 0, s>>>(d_classes, n_classes, ml, geo, h, K, \
                                                                        kern, o, d_items, n_items);       \
     if (K > kPhase1Reach)                                                                               \
-        cache_finish_kernel<TS, TP, TO><<<finish_blocks, 1024, 0, s>>>(d_classes, n_classes, ml, Mq, h, K, kern, \
+        cache_finish_kernel<TS, TP, TO><<<finish_blocks, 1024, 0, s>>>(d_classes, n_classes, ml, geo, h, K, kern, \
                                                                         o, d_items, warps, chunk);
     switch (params->precision) {
         case CHERT_FP64: CHERT_LAUNCH_BUILD(double, double, double) break;
@@ -674,4 +769,12 @@ extern "C" int chert_build_cache_items(const chert_class* d_classes, int n_class
     CHERT_REQUIRE(d_items && n_items >= 0, "chert_build_cache_items: bad item list");
     return launch_build(d_classes, n_classes, modes, n_modes, params, out, d_items, n_items, stream,
                         "chert_build_cache_items");
+}
+
+extern "C" int chert_build_cache_3d(const chert_class* d_classes, int n_classes, const int* modes, int n_modes,
+                                    int n_az, int n_pol, const chert_cache_params* params,
+                                    const chert_cache_arrays* out, void* stream) {
+    CHERT_REQUIRE(n_az >= 1 && n_pol >= 1, "chert_build_cache_3d: n_az=%d n_pol=%d", n_az, n_pol);
+    return launch_build(d_classes, n_classes, modes, n_modes, params, out, nullptr, 0, stream,
+                        "chert_build_cache_3d", n_az, n_pol);
 }

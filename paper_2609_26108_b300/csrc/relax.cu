@@ -46,7 +46,7 @@ __device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(
 
 // One warp per (mode, class, offset): argmax of d.r over the class's entries.
 template <typename T>
-__global__ void edge_table_kernel(const T* __restrict__ rx, const T* __restrict__ rz,
+__global__ void edge_table_kernel(const T* __restrict__ rx, const T* __restrict__ ry, const T* __restrict__ rz,
                                   const T* __restrict__ V, const T* __restrict__ A,
                                   const uint8_t* __restrict__ flag, int n_modes, int n_classes,
                                   int n_dir, Offsets off, int32_t* __restrict__ idx_out,
@@ -59,13 +59,15 @@ __global__ void edge_table_kernel(const T* __restrict__ rx, const T* __restrict_
     const long long mk = w / off.n;                  // mode * n_classes + class
     const double ox = off.x[o], oy = off.y[o], oz = off.z[o];
     const T nrm = T(sqrt(ox * ox + oy * oy + oz * oz));
-    const T dx = div_rn(T(ox), nrm), dz = div_rn(T(oz), nrm);
+    const T dx = div_rn(T(ox), nrm), dy = div_rn(T(oy), nrm), dz = div_rn(T(oz), nrm);
     const size_t base = static_cast<size_t>(mk) * n_dir;
     T best = T(-INFINITY);
     int bi = -1;
     for (int e = lane; e < n_dir; e += 32) {
         if (flag[base + e]) continue;
-        const T dot = add_rn(mul_rn(dx, rx[base + e]), mul_rn(dz, rz[base + e]));
+        T dot = mul_rn(dx, rx[base + e]);
+        if (ry) dot = add_rn(dot, mul_rn(dy, ry[base + e]));
+        dot = add_rn(dot, mul_rn(dz, rz[base + e]));
         if (dot > best) { best = dot; bi = e; }     // increasing e: first max kept
     }
     for (int s = 16; s > 0; s >>= 1) {
@@ -364,14 +366,14 @@ extern "C" int chert_edge_table(const chert_cache_arrays* cache, int n_modes, in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (precision == CHERT_FP64) {
         edge_table_kernel<double><<<blocks, 256, 0, s>>>(
-            (const double*)cache->rx, (const double*)cache->rz, (const double*)cache->V,
+            (const double*)cache->rx, (const double*)cache->ry, (const double*)cache->rz, (const double*)cache->V,
             (const double*)cache->A, cache->flag, n_modes, n_classes, n_dir, off, d_idx,
             (double*)d_Vsel, (double*)d_Asel);
     } else {
         CHERT_REQUIRE(precision == CHERT_FP32 || precision == CHERT_MIXED,
                       "chert_edge_table: precision=%d", precision);
         edge_table_kernel<float><<<blocks, 256, 0, s>>>(
-            (const float*)cache->rx, (const float*)cache->rz, (const float*)cache->V,
+            (const float*)cache->rx, (const float*)cache->ry, (const float*)cache->rz, (const float*)cache->V,
             (const float*)cache->A, cache->flag, n_modes, n_classes, n_dir, off, d_idx,
             (float*)d_Vsel, (float*)d_Asel);
     }

@@ -33,7 +33,9 @@ def cache_to_torch(cache_np, precision_dtype, device):
     """Oracle cache dict (numpy) -> dict of device tensors in the given dtype."""
     import torch
     out = {}
-    for k in ("V", "A", "Q", "rx", "rz", "theta", "vartheta"):
+    for k in ("V", "A", "Q", "rx", "rz", "theta", "vartheta", "ry", "phi"):
+        if k not in cache_np:
+            continue
         out[k] = torch.as_tensor(np.ascontiguousarray(cache_np[k]), dtype=precision_dtype, device=device)
     out["flag"] = torch.as_tensor(np.ascontiguousarray(cache_np["flag"]), dtype=torch.uint8, device=device)
     return out
