@@ -186,8 +186,8 @@ int chert_edge_table(const chert_cache_arrays* cache, int n_modes, int n_classes
 size_t chert_traveltime_workspace_bytes(int n_modes, int n_classes, int n_off,
                                         int precision, int n_sources);
 
-/* Scratch bytes for this problem on an nx x ny x nz lattice (ny = 1), including
- * the per-node weight area: with the standard secondary-node stencil and too
+/* Scratch bytes for this problem on an nx x ny x nz lattice, including (2D,
+ * ny = 1) the per-node weight area: with the standard secondary-node stencil and too
  * many classes for the class-pair table in shared memory (e.g. one class per
  * node), chert_traveltime precomputes each node's directed edge weights in row-
  * and column-major layouts, n_modes x 2 x n_off x nodes values each, when the
@@ -198,8 +198,11 @@ size_t chert_traveltime_workspace_bytes_grid(int n_modes, int n_classes, int n_o
                                              int n_sources, int nx, int ny, int nz);
 
 /* Propagation and attenuation traveltime fields for every (source, mode) of
- * a cache, on a 2D lattice nx x nz (ny must be 1) with spacing dx.
- *   d_class_of_node  device int32 [nz*nx], values in [0, n_classes)
+ * a cache, on a lattice nx x ny x nz with spacing dx: 2D with ny = 1 (cache
+ * from chert_build_cache; offsets with oy = 0), 3D with ny > 1 (cache from
+ * chert_build_cache_3d, whose ry the lookup uses).  Node index
+ * x + nx*(y + ny*z).
+ *   d_class_of_node  device int32 [nz*ny*nx], values in [0, n_classes)
  *   offsets          host int32 [n_off][3], a set closed under negation
  *   sources          host int64 [n_sources] node indices
  * Each directed edge i -> j = i + o costs, with the selected (V, A) of the
@@ -208,7 +211,9 @@ size_t chert_traveltime_workspace_bytes_grid(int n_modes, int n_classes, int n_o
  * solved separately; parR/parI (may be NULL) follow the rule
  * par_j = argmin_i (tau_i + w_ij), ties to the smallest i, par(source) =
  * source, par = -1 and tau = +inf where unreachable (Eq. 33).
- * Outputs are device arrays [n_sources][n_modes][nz*nx].
+ * Outputs are device arrays [n_sources][n_modes][nz*ny*nx].
+ * 2D cycles sweep lines (rows and columns, both ways); 3D cycles sweep planes
+ * of constant z, y and x, both ways.
  * max_cycles caps the sweep cycles per field; a field that has not converged
  * after it returns CHERT_ETIMEOUT (its values are valid upper bounds).
  * Synchronises on `stream` once at the end to read the convergence status.

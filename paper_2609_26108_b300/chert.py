@@ -303,26 +303,28 @@ def workspace_bytes(n_modes, n_classes, n_off, precision, n_sources, nx=None, nz
 
 
 def traveltime(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64, parents=True,
-               stream=None, out=None, workspace=None):
-    """chert_traveltime for all (source, mode) fields of ``cache``.
+               stream=None, out=None, workspace=None, ny=1):
+    """chert_traveltime for all (source, mode) fields of ``cache`` on an
+    nx x ny x nz lattice (ny = 1: 2D).
 
-    Returns (tauR, tauI, parR, parI) torch tensors [n_sources, n_modes, nz*nx]."""
+    Returns (tauR, tauI, parR, parI) torch tensors [n_sources, n_modes, nz*ny*nx]."""
     torch = _torch()
     off, off_p = _offsets_arr(offsets)
     src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64).reshape(-1))
     nm, ns = len(cache.modes), len(src)
     dev = cache["V"].device
-    shape = (ns, nm, nx * nz)
+    shape = (ns, nm, nx * ny * nz)
     if out is None:
         fd = _fdtype(cache.precision)
         out = (torch.empty(shape, dtype=fd, device=dev), torch.empty(shape, dtype=fd, device=dev),
                torch.empty(shape, dtype=torch.int32, device=dev) if parents else None,
                torch.empty(shape, dtype=torch.int32, device=dev) if parents else None)
     if workspace is None:
-        wsb = workspace_bytes(nm, cache.n_classes, len(off), cache.precision, ns, nx, nz)
+        wsb = (workspace_bytes(nm, cache.n_classes, len(off), cache.precision, ns, nx, nz) if ny == 1
+               else workspace_bytes(nm, cache.n_classes, len(off), cache.precision, ns))
         workspace = torch.empty(wsb, dtype=torch.uint8, device=dev)
     st = cache.struct()
-    _check(lib().chert_traveltime(ctypes.byref(st), nm, cache.n_classes, cache.n_dir, nx, 1, nz,
+    _check(lib().chert_traveltime(ctypes.byref(st), nm, cache.n_classes, cache.n_dir, nx, ny, nz,
                                   float(dx), _dev_ptr(d_cls), off_p, len(off),
                                   src.ctypes.data_as(ctypes.c_void_p), ns, cache.precision,
                                   max_cycles, _dev_ptr(out[0]), _dev_ptr(out[1]), _dev_ptr(out[2]),

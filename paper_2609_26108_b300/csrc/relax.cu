@@ -86,6 +86,7 @@ __global__ void edge_table_kernel(const T* __restrict__ rx, const T* __restrict_
 // ------------------------------------------------------------ relaxation
 struct FieldArgs {
     int nx, nz, n_classes, n_modes, n_sources, max_cycles, ring;
+    int ny;                      // 1 for 2D lattices
     double dx;
     const int32_t* cls;
     const int64_t* src;
@@ -282,6 +283,160 @@ __global__ void __launch_bounds__(512) relax_kernel(FieldArgs a, Offsets off) {
     if (threadIdx.x == 0) a.status[blockIdx.x] = used;
 }
 
+// ------------------------------------------------------------ 3D relaxation
+// A 3D lattice (node x + nx*(y + ny*z)) is relaxed by plane sweeps: a cycle
+// runs the planes of constant z upward, of constant y and of constant x in
+// both directions, and of constant z downward; in each, a node pulls from the
+// offsets whose component along the sweep axis has the sweep's sign, i.e. from
+// finished planes, so the nodes of one plane are independent.  A 201 x 201
+// plane does not fit in shared memory, so tau is read from global memory
+// (L1/L2 resident for the planes just behind); the weights sit in shared
+// memory as in 2D.  A pull whose source tau_i is not below the current best is
+// skipped without loading its class or weight (weights are >= 0, so it cannot
+// improve).  The verification pass and the parent rule are those of 2D.
+template <typename T, int WMODE>
+__device__ bool sweep3d(const Smem<T>& sm, const T* __restrict__ gsel, const Offsets& off, int list, int axis,
+                        int dir, T* tau, const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk,
+                        int comp) {
+    const int np = axis == 2 ? nz : axis == 1 ? ny : nx;
+    const long long psize = axis == 2 ? (long long)nx * ny : axis == 1 ? (long long)nx * nz : (long long)ny * nz;
+    const short* lst = sm.lists + list * off.n;
+    const int cnt = sm.counts[list];
+    bool changed = false;
+    for (int step = 0; step < np; ++step) {
+        const int p = dir > 0 ? step : np - 1 - step;
+        for (long long t = threadIdx.x; t < psize; t += blockDim.x) {
+            int x, y, z;
+            if (axis == 2) { x = (int)(t % nx); y = (int)(t / nx); z = p; }
+            else if (axis == 1) { x = (int)(t % nx); z = (int)(t / nx); y = p; }
+            else { y = (int)(t % ny); z = (int)(t / ny); x = p; }
+            const size_t j = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z);
+            const int kj = clamp_class(cls[j], nk);
+            const T cur = tau[j];
+            T best = cur;
+            for (int q = 0; q < cnt; ++q) {
+                const int o = lst[q];
+                const int xi = x - off.x[o], yi = y - off.y[o], zi = z - off.z[o];
+                if (xi < 0 || xi >= nx || yi < 0 || yi >= ny || zi < 0 || zi >= nz) continue;
+                const size_t i = (size_t)xi + (size_t)nx * ((size_t)yi + (size_t)ny * zi);
+                const T ti = tau[i];
+                if (!(ti < best)) continue;
+                const int ki = clamp_class(cls[i], nk);
+                best = fmin(best, ti + pull_weight<T, WMODE>(sm, gsel, off.n, nk, comp, o, ki, kj));
+            }
+            if (best < cur) {
+                tau[j] = best;
+                changed = true;
+            }
+        }
+        __syncthreads();
+    }
+    return __syncthreads_or(changed);
+}
+
+template <typename T, int WMODE>
+__device__ bool verify3d(const Smem<T>& sm, const T* __restrict__ gsel, const Offsets& off, T* tau,
+                         const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk, int comp, int64_t src,
+                         int32_t* par) {
+    bool changed = false;
+    const size_t n = (size_t)nx * ny * nz;
+    for (size_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const int x = (int)(j % nx), y = (int)((j / nx) % ny), z = (int)(j / ((size_t)nx * ny));
+        const int kj = clamp_class(cls[j], nk);
+        const T cur = tau[j];
+        T best = T(INFINITY);
+        long long bi = -1;
+        for (int o = 0; o < off.n; ++o) {
+            const int xi = x - off.x[o], yi = y - off.y[o], zi = z - off.z[o];
+            if (xi < 0 || xi >= nx || yi < 0 || yi >= ny || zi < 0 || zi >= nz) continue;
+            const size_t i = (size_t)xi + (size_t)nx * ((size_t)yi + (size_t)ny * zi);
+            const T ti = tau[i];
+            if (ti > best) continue;
+            const int ki = clamp_class(cls[i], nk);
+            const T c = ti + pull_weight<T, WMODE>(sm, gsel, off.n, nk, comp, o, ki, kj);
+            if (c < best || (c == best && (long long)i < bi)) { best = c; bi = (long long)i; }
+        }
+        if (best < cur) {
+            tau[j] = best;
+            changed = true;
+        } else if (par) {
+            par[j] = ((int64_t)j == src) ? static_cast<int32_t>(src) : (isinf(cur) ? -1 : (int32_t)bi);
+        }
+    }
+    return __syncthreads_or(changed);
+}
+
+template <typename T, int WMODE>
+__global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nk = a.n_classes;
+    const int field = blockIdx.x >> 1;
+    const int comp = blockIdx.x & 1;
+    const int mode = field % a.n_modes;
+    const int s = field / a.n_modes;
+    const size_t n = (size_t)a.nx * a.ny * a.nz;
+
+    Smem<T> sm;
+    unsigned char* p = smem_raw;
+    const size_t wcount = WMODE == 1 ? static_cast<size_t>(off.n) * nk * nk
+                          : WMODE == 0 ? static_cast<size_t>(nk) * off.n : 0;
+    sm.W = reinterpret_cast<T*>(p); p += wcount * sizeof(T);
+    sm.L = reinterpret_cast<T*>(p); p += off.n * sizeof(T);
+    sm.ring = nullptr;
+    sm.cring = nullptr;
+    sm.lists = reinterpret_cast<short*>(p); p += 6 * off.n * sizeof(short);
+    sm.counts = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
+
+    const T* sel = static_cast<const T*>(comp == 0 ? a.Vsel : a.Asel) + static_cast<size_t>(mode) * nk * off.n;
+    for (int o = threadIdx.x; o < off.n; o += blockDim.x) {
+        const double ox = off.x[o], oy = off.y[o], oz = off.z[o];
+        sm.L[o] = T(a.dx * sqrt(ox * ox + oy * oy + oz * oz));
+    }
+    __syncthreads();
+    if (WMODE == 1) {
+        for (int t = threadIdx.x; t < off.n * nk * nk; t += blockDim.x) {
+            const int kj = t % nk, ki = (t / nk) % nk, o = t / (nk * nk);
+            sm.W[t] = edge_w<T>(comp, sm.L[o], sel[ki * off.n + o], sel[kj * off.n + o]);
+        }
+    } else if (WMODE == 0) {
+        for (int t = threadIdx.x; t < nk * off.n; t += blockDim.x) sm.W[t] = sel[t];
+    }
+    if (threadIdx.x == 0) {
+        int c[6] = {0, 0, 0, 0, 0, 0};
+        for (int o = 0; o < off.n; ++o) {
+            if (off.z[o] > 0) sm.lists[0 * off.n + c[0]++] = (short)o;   // z planes upward
+            if (off.y[o] > 0) sm.lists[1 * off.n + c[1]++] = (short)o;   // y planes
+            if (off.x[o] > 0) sm.lists[2 * off.n + c[2]++] = (short)o;   // x planes
+            if (off.x[o] < 0) sm.lists[3 * off.n + c[3]++] = (short)o;
+            if (off.y[o] < 0) sm.lists[4 * off.n + c[4]++] = (short)o;
+            if (off.z[o] < 0) sm.lists[5 * off.n + c[5]++] = (short)o;   // z planes downward
+        }
+        for (int i = 0; i < 6; ++i) sm.counts[i] = c[i];
+    }
+
+    T* tau = static_cast<T*>(comp == 0 ? a.tauR : a.tauI) + static_cast<size_t>(field) * n;
+    int32_t* par = comp == 0 ? a.parR : a.parI;
+    if (par) par += static_cast<size_t>(field) * n;
+    const int64_t src = a.src[s];
+    for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
+    __syncthreads();
+
+    int used = -1;
+    for (int cycle = 0; cycle < a.max_cycles; ++cycle) {
+        sweep3d<T, WMODE>(sm, sel, off, 0, 2, +1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
+        sweep3d<T, WMODE>(sm, sel, off, 1, 1, +1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
+        sweep3d<T, WMODE>(sm, sel, off, 2, 0, +1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
+        sweep3d<T, WMODE>(sm, sel, off, 3, 0, -1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
+        sweep3d<T, WMODE>(sm, sel, off, 4, 1, -1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
+        sweep3d<T, WMODE>(sm, sel, off, 5, 2, -1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
+        if (!verify3d<T, WMODE>(sm, sel, off, tau, a.cls, a.nx, a.ny, a.nz, nk, comp, src, par)) {
+            used = cycle + 1;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) a.status[blockIdx.x] = used;
+}
+
 // ------------------------------------------------------------ raypaths
 // One thread per (field, receiver): walk the parents once to count the path
 // (bounded by cap), then again to write it source-first.
@@ -380,6 +535,15 @@ extern "C" int chert_edge_table(const chert_cache_arrays* cache, int n_modes, in
     return launch_check("chert_edge_table");
 }
 
+
+template <typename T, int WMODE>
+static int launch_relax3d(const FieldArgs& a, const Offsets& off, size_t smem, int blocks, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(relax3d_kernel<T, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
+    relax3d_kernel<T, WMODE><<<blocks, 512, smem, s>>>(a, off);
+    return launch_check("chert_traveltime: relax3d");
+}
 
 template <typename T, int WMODE>
 static int launch_relax(const FieldArgs& a, const Offsets& off, size_t smem, int blocks,
@@ -630,7 +794,8 @@ extern "C" size_t chert_traveltime_workspace_bytes(int n_modes, int n_classes, i
 
 extern "C" size_t chert_traveltime_workspace_bytes_grid(int n_modes, int n_classes, int n_off, int precision,
                                                         int n_sources, int nx, int ny, int nz) {
-    if (n_modes < 1 || n_classes < 1 || n_off < 1 || n_sources < 1 || nx < 1 || ny != 1 || nz < 1) return 0;
+    if (n_modes < 1 || n_classes < 1 || n_off < 1 || n_sources < 1 || nx < 1 || ny < 1 || nz < 1) return 0;
+    if (ny > 1) return ws_layout(n_modes, n_classes, n_off, precision, n_sources).total;   // 3D: no per-node area
     return ws_layout(n_modes, n_classes, n_off, precision, n_sources).total +
            pn_layout(n_modes, n_classes, n_off, precision, nx, nz).total;
 }
@@ -646,9 +811,9 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
                               void* d_tauR, void* d_tauI, int32_t* d_parR, int32_t* d_parI,
                               unsigned char* w, size_t bytes, cudaStream_t s, int* blocks_out,
                               int** status_out) {
-    CHERT_REQUIRE(ny == 1, "%s: only 2D lattices (ny = 1) are supported", who);
-    CHERT_REQUIRE(nx >= 1 && nz >= 1 && (long long)nx * nz < (1LL << 31),
-                  "%s: bad lattice %d x %d", who, nx, nz);
+    CHERT_REQUIRE(nx >= 1 && ny >= 1 && nz >= 1 && (long long)nx * ny * nz < (1LL << 31),
+                  "%s: bad lattice %d x %d x %d", who, nx, ny, nz);
+    const long long n_nodes = (long long)nx * ny * nz;
     CHERT_REQUIRE(dx > 0, "%s: dx must be positive", who);
     CHERT_REQUIRE(d_class_of_node && sources && d_tauR && d_tauI && w, "%s: NULL argument", who);
     CHERT_REQUIRE(n_sources >= 1 && n_modes >= 1 && n_modes <= 3 && n_classes >= 1,
@@ -657,18 +822,18 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     CHERT_REQUIRE(precision == CHERT_FP64 || precision == CHERT_FP32 || precision == CHERT_MIXED,
                   "%s: precision=%d", who, precision);
     for (int i = 0; i < n_sources; i++)
-        CHERT_REQUIRE(sources[i] >= 0 && sources[i] < (int64_t)nx * nz,
+        CHERT_REQUIRE(sources[i] >= 0 && sources[i] < (int64_t)n_nodes,
                       "%s: source %d out of range", who, i);
     Offsets off;
     int rc = fill_offsets(off, offsets, n_off, who);
     if (rc) return rc;
     int R = 0;
     for (int i = 0; i < n_off; i++) {
-        CHERT_REQUIRE(off.y[i] == 0, "%s: 2D offsets need oy = 0", who);
+        CHERT_REQUIRE(ny > 1 || off.y[i] == 0, "%s: 2D offsets need oy = 0", who);
         R = std::max(R, std::max(abs((int)off.x[i]), abs((int)off.z[i])));
         bool has_neg = false;
         for (int j = 0; j < n_off; j++)
-            if (off.x[j] == -off.x[i] && off.z[j] == -off.z[i]) has_neg = true;
+            if (off.x[j] == -off.x[i] && off.y[j] == -off.y[i] && off.z[j] == -off.z[i]) has_neg = true;
         CHERT_REQUIRE(has_neg, "%s: offset set must be closed under negation", who);
     }
     const WsLayout ws = ws_layout(n_modes, n_classes, n_off, precision, n_sources);
@@ -690,26 +855,45 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     int* bad_class = reinterpret_cast<int*>(w + ws.status) + (size_t)n_sources * n_modes * 2;
     e = cudaMemsetAsync(bad_class, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
-    check_classes_kernel<<<296, 256, 0, s>>>(d_class_of_node, (long long)nx * nz, n_classes, bad_class);
+    check_classes_kernel<<<296, 256, 0, s>>>(d_class_of_node, n_nodes, n_classes, bad_class);
     rc = launch_check("class check");
     if (rc) return rc;
 
     FieldArgs a;
-    a.nx = nx; a.nz = nz; a.n_classes = n_classes; a.n_modes = n_modes;
+    a.nx = nx; a.ny = ny; a.nz = nz; a.n_classes = n_classes; a.n_modes = n_modes;
     a.n_sources = n_sources; a.max_cycles = max_cycles; a.ring = R + 2; a.dx = dx;
     a.cls = d_class_of_node; a.src = reinterpret_cast<const int64_t*>(w + ws.src);
     a.tauR = d_tauR; a.tauI = d_tauI; a.parR = d_parR; a.parI = d_parI;
     a.Vsel = Vsel; a.Asel = Asel; a.status = reinterpret_cast<int*>(w + ws.status);
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int blocks = n_sources * n_modes * 2;
+    if (ny > 1) {                                      // 3D: plane sweeps
+        const size_t base3 = n_off * es + 6 * n_off * 2 + 64;
+        const size_t t3 = (size_t)n_off * n_classes * n_classes * es + base3;
+        const size_t r3 = (size_t)n_classes * n_off * es + base3;
+        const int mode3 = t3 <= (size_t)std::min(smem_max, 160 * 1024) ? 1 : r3 <= (size_t)smem_max ? 0 : 2;
+        const size_t sm3 = mode3 == 1 ? t3 : mode3 == 0 ? r3 : base3;
+        if (precision == CHERT_FP64)
+            rc = mode3 == 1 ? launch_relax3d<double, 1>(a, off, sm3, blocks, s)
+               : mode3 == 0 ? launch_relax3d<double, 0>(a, off, sm3, blocks, s)
+                            : launch_relax3d<double, 2>(a, off, sm3, blocks, s);
+        else
+            rc = mode3 == 1 ? launch_relax3d<float, 1>(a, off, sm3, blocks, s)
+               : mode3 == 0 ? launch_relax3d<float, 0>(a, off, sm3, blocks, s)
+                            : launch_relax3d<float, 2>(a, off, sm3, blocks, s);
+        if (rc) return rc;
+        *blocks_out = blocks;
+        *status_out = a.status;
+        return CHERT_OK;
+    }
     const int line_max = std::max(nx, nz);
     const size_t common = n_off * es + (size_t)a.ring * line_max * (es + 4) + 4 * n_off * 2 + 32;
     const size_t smem_table = (size_t)n_off * n_classes * n_classes * es + common;
     const size_t smem_raw = (size_t)n_classes * n_off * es + common;
-    int dev = 0, smem_max = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const bool table = smem_table <= (size_t)std::min(smem_max, 120 * 1024);
     const bool raw_smem = smem_raw <= (size_t)smem_max;
-    const int blocks = n_sources * n_modes * 2;
     fast::Args fa;
     fa.nx = nx; fa.nz = nz; fa.n_classes = n_classes; fa.n_modes = n_modes;
     fa.max_cycles = max_cycles; fa.dx = dx; fa.cls = a.cls; fa.src = a.src;

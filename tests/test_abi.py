@@ -75,7 +75,9 @@ def test_workspace_grid_adds_per_node_area(lib):
     assert chert.workspace_bytes(3, n, 80, chert.FP64, 4, 100, 60) - chert.workspace_bytes(3, n, 80, chert.FP64, 4) \
         >= 2 * (3 * 2 * 80 * n * 8)
     assert chert.workspace_bytes(3, n, 84, chert.FP32, 4, 100, 60) == chert.workspace_bytes(3, n, 84, chert.FP32, 4)
-    assert lib.chert_traveltime_workspace_bytes_grid(3, n, 80, chert.FP32, 4, 100, 2, 60) == 0
+    # 3D lattices have no per-node area: the class tables only
+    assert lib.chert_traveltime_workspace_bytes_grid(3, n, 80, chert.FP32, 4, 100, 2, 60) == small
+    assert lib.chert_traveltime_workspace_bytes_grid(3, n, 80, chert.FP32, 4, 100, 0, 60) == 0
 
 
 def test_null_arguments_are_rejected_without_gpu(lib):

@@ -1,0 +1,131 @@
+"""Parity of the 3D relaxation (plane sweeps) and parents with the oracle's
+binary-heap Dijkstra on the same cache, and of the 3D pipeline (GPU 3D cache,
+lookup, traveltime, raypaths) with the oracle end to end.
+
+Tolerances as in 2D: FP64 tau to 1e-12 relative with identical parents; FP32
+tau per node within max(1e-5, 2 (hops + 2) 2^-24)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import graph_oracle as go
+from paper_2609_26108_b300 import chert, inputs
+
+from helpers import cache_to_torch
+from test_gpu_relax import _check_fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    from paper_2609_26108_b300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def synthetic_cache3d(n_classes, n_az=16, n_pol=9, seed=0):
+    """Lookup-only 3D cache: rays along the slowness directions of the global
+    grid, V and A varying with the polar angle per class."""
+    rng = np.random.default_rng(seed)
+    nd = n_az * n_pol
+    th = (np.arange(n_pol) + 0.5) * math.pi / n_pol
+    ph = np.arange(n_az) * 2 * math.pi / n_az
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    T, P = T.reshape(-1), P.reshape(-1)
+    v0 = rng.uniform(1500, 4500, n_classes)
+    an = rng.uniform(-0.2, 0.2, n_classes)
+    V = v0[:, None] * (1 + an[:, None] * np.cos(2 * T)[None])
+    A = rng.uniform(1e-5, 1e-4, n_classes)[:, None] * (1 + 0.3 * np.sin(T)[None] ** 2)
+    c = {"V": V[None], "A": A[None],
+         "rx": np.tile(np.sin(T) * np.cos(P), (1, n_classes, 1)),
+         "ry": np.tile(np.sin(T) * np.sin(P), (1, n_classes, 1)),
+         "rz": np.tile(np.cos(T), (1, n_classes, 1)),
+         "theta": np.tile(T, (1, n_classes, 1)), "phi": np.tile(P, (1, n_classes, 1)),
+         "vartheta": np.zeros((1, n_classes, nd)), "flag": np.zeros((1, n_classes, nd), np.uint8)}
+    c["Q"] = np.full_like(c["V"], np.inf)
+    return c, n_az, n_pol
+
+
+def run3d(torch, cnp, n_az, n_pol, precision, shape, cls, off, sources):
+    prec = chert.PRECISION_IDS[precision]
+    dt = torch.float64 if prec == chert.FP64 else torch.float32
+    nm, nk, _ = cnp["V"].shape
+    cache = chert.Cache(cache_to_torch(cnp, dt, "cuda"), list(range(nm)), nk, 0, prec, n_az, n_pol)
+    nx, ny, nz = shape
+    d_cls = torch.as_tensor(np.asarray(cls, np.int32), device="cuda")
+    tR, tI, pR, pI = chert.traveltime(cache, nx, nz, 10.0, d_cls, off, sources, max_cycles=64, ny=ny)
+    torch.cuda.synchronize()
+    return tR.cpu().numpy(), tI.cpu().numpy(), pR.cpu().numpy(), pI.cpu().numpy()
+
+
+def oracle3d_fields(cnp, precision, shape, cls, off, sources):
+    dt = np.float64 if precision == "fp64" else np.float32
+    cast = {k: (cnp[k].astype(dt).astype(np.float64) if k != "flag" else cnp[k]) for k in cnp}
+    out = {}
+    for m in range(cnp["V"].shape[0]):
+        _, Vs, As = go.lookup_tables(cast, m, off, dtype=dt)
+        for s in sources:
+            out[(s, m, 0)] = go.dijkstra(shape, 10.0, cls, off, Vs, 0, s)
+            out[(s, m, 1)] = go.dijkstra(shape, 10.0, cls, off, As, 1, s)
+    return out
+
+
+@pytest.mark.parametrize("n_classes", [4, 30, 400])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_relax3d_matches_oracle(torch_dev, precision, n_classes):
+    """4 layers (class-pair table in shared memory), 30 random classes (raw
+    tables in shared memory) and 400 random classes (tables in global
+    memory); a lattice of several planes in each direction, ragged sizes."""
+    shape = (19, 14, 11)
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    if n_classes == 4:
+        z = np.arange(n) // (nx * ny)
+        cls = np.minimum(z * 4 // nz, 3).astype(np.int32)
+    else:
+        cls = np.random.default_rng(n_classes).integers(0, n_classes, n).astype(np.int32)
+    cnp, n_az, n_pol = synthetic_cache3d(n_classes, seed=n_classes)
+    off = inputs.stencil_3d(2)
+    sources = [0, nx // 2 + nx * (ny // 2 + ny * (nz // 2))]
+    g = run3d(torch_dev, cnp, n_az, n_pol, precision, shape, cls, off, sources)
+    ref = oracle3d_fields(cnp, precision, shape, cls, off, sources)
+    _check_fields(g, ref, sources, 1, precision, shape, 10.0, cls, off, cnp)
+
+
+def test_pipeline3d_gpu_cache_to_traveltime_fp64(torch_dev):
+    """GPU 3D cache (tilted, azimuthally rotated TTI classes) -> lookup ->
+    traveltime against the oracle's 3D cache -> Dijkstra, and raypaths that
+    follow the oracle's parents."""
+    from test_gpu_cache3d import H, K, MODES, N_AZ, N_POL, layers3d, oracle3d
+    ls = layers3d()
+    d_cls = chert.classes_to_device(chert.classes_from_layers(ls))
+    cache = chert.build_cache_3d(d_cls, len(ls), MODES, N_AZ, N_POL, H, K, "MEV", "fp64")
+    shape = (13, 11, 9)
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    cls = np.minimum((np.arange(n) // (nx * ny)) * 4 // nz, 3).astype(np.int32)
+    off = inputs.stencil_3d(2)
+    src = [nx // 2 + nx * (ny // 2)]
+    tR, tI, pR, pI = chert.traveltime(cache, nx, nz, 10.0, torch_dev.as_tensor(cls, device="cuda"), off, src,
+                                      ny=ny)
+    torch_dev.cuda.synchronize()
+    o = oracle3d()
+    for m in range(len(MODES)):
+        _, Vs, As = go.lookup_tables(o, m, off)
+        for comp, (t, p, sel) in enumerate([(tR, pR, Vs), (tI, pI, As)]):
+            rt, rp = go.dijkstra(shape, 10.0, cls, off, sel, comp, src[0])
+            gt = t[0, m].cpu().numpy()
+            fin = np.isfinite(rt)
+            assert np.array_equal(np.isfinite(gt), fin)
+            assert np.allclose(gt[fin], rt[fin], rtol=1e-9, atol=0)
+    rcv = [0, n - 1, nx * ny * (nz - 1) + 3]
+    paths, lens = chert.raypath(pR[0, 0], src, rcv, cap=256)
+    paths, lens = paths.cpu().numpy()[0], lens.cpu().numpy()[0]
+    par = pR[0, 0].cpu().numpy()
+    for r, node in enumerate(rcv):
+        want = go.raypath(par, src[0], node)
+        assert lens[r] == len(want) and list(paths[r, :lens[r]]) == want
