@@ -330,6 +330,56 @@ def surrogate_section(n_sources, flush, log=None):
             "tauR_median_rel_error_worst_mode": worst}
 
 
+# --------------------------------------------------------------- 3D
+def section_3d(flush, n_sources=16):
+    """3D layered visco-TTI, 201^3 nodes at dx = 10 m, 12 layers (PCG64 seed
+    1004, symmetry-axis azimuth ~ U(0, 360 deg)), qP and qSV, 1 deg x 1 deg
+    cache of global directions (360 azimuths x 180 polar angles = 64,800 per
+    class and mode), radius-2 3D stencil (98 offsets), 16 sources on a 4 x 4
+    surface grid; cache and traveltimes in FP64.  One run of cache build +
+    relaxation with parents, L2 flushed before each part."""
+    import torch
+    from paper_2609_26108_b300 import chert
+
+    m = inputs.layered_tti_3d(n_sources=n_sources)
+    modes = ["qP", "qSV"]
+    nk = len(m.layers)
+    d_classes = chert.classes_to_device(chert.classes_from_layers(m.layers))
+    d_cls = torch.as_tensor(m.class_of_node, device="cuda")
+    off = inputs.stencil_3d(2)
+    src = [int(v) for v in m.sources]
+    n = m.nx * m.ny * m.nz
+    shape = (len(src), len(modes), n)
+    tau = tuple(torch.empty(shape, dtype=dt, device="cuda")
+                for dt in (torch.float64, torch.float64, torch.int32, torch.int32))
+    ws = torch.empty(chert.workspace_bytes(len(modes), nk, len(off), chert.FP64, len(src)), dtype=torch.uint8,
+                     device="cuda")
+    small = chert.build_cache_3d(d_classes, nk, modes, 36, 18, precision="fp64")        # load the kernels
+    chert.traveltime(small, 9, 9, m.dx, d_cls[:729], off, [0], ny=9, workspace=ws)
+
+    def timed(fn):
+        flush.fill_(3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b) / 1e3
+
+    cache, t_cache = timed(lambda: chert.build_cache_3d(d_classes, nk, modes, 360, 180, precision="fp64"))
+    _, t_relax = timed(lambda: chert.traveltime(cache, m.nx, m.nz, m.dx, d_cls, off, src, max_cycles=64,
+                                                out=tau, workspace=ws, ny=m.ny))
+    nf = len(src) * len(modes)
+    edges = int(sum((m.nx - abs(int(o[0]))) * (m.ny - abs(int(o[1]))) * (m.nz - abs(int(o[2]))) for o in off))
+    return {"workload": "layered_visco_tti_3d_201^3_12layers_%dsrc_qP_qSV_1x1deg_R2" % len(src),
+            "nodes": n, "fields": nf, "precision": "fp64 cache, fp64 traveltimes",
+            "cache_entries": nk * len(modes) * 64800, "cache_s": t_cache,
+            "cache_entries_per_s": nk * len(modes) * 64800 / t_cache,
+            "relax_s": t_relax, "fields_per_s": nf / (t_cache + t_relax),
+            "edge_relaxations_per_s": edges * nf * 2 / t_relax, "directed_edges_per_field": edges}
+
+
 # --------------------------------------------------------------- GPU arm
 def run_chert(args):
     import torch
@@ -430,6 +480,8 @@ def run_chert(args):
            "gpu_launches": tr.launches_per_run * args.steps}
     if world == 1 and args.surrogate_sources > 0:
         out["surrogate"] = surrogate_section(args.surrogate_sources, flush)
+    if world == 1 and args.sources_3d > 0:
+        out["lattice_3d"] = section_3d(flush, args.sources_3d)
     if world == 1 and not args.no_cpu_baseline:
         fps, eps_, desc, _ = oracle_sample(model, off)
         out["cpu_baseline"] = {"value": fps, "unit": "fields/s", "cores": 1, "kind": "oracle",
@@ -449,6 +501,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sources", type=int, default=64,
                     help="surface sources (64 = the benchmark workload; fewer only for profiling)")
+    ap.add_argument("--sources-3d", type=int, default=16,
+                    help="sources of the 201^3 3D section (0: leave it out)")
     ap.add_argument("--surrogate-sources", type=int, default=16,
                     help="sources of the per-cell plain-vs-surrogate comparison (0: leave it out)")
     args = ap.parse_args()

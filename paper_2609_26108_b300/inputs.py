@@ -35,7 +35,7 @@ __all__ = [
 ]
 
 # One seed per workload (PCG64).
-SEEDS = {"homogeneous_vti": 1001, "layered_tti": 1002}
+SEEDS = {"homogeneous_vti": 1001, "layered_tti": 1002, "layered_tti_3d": 1004}
 
 
 @dataclass(frozen=True)
@@ -271,3 +271,38 @@ def folded_faulted(nx: int = 1701, nz: int = 351, n_layers: int = 10, n_sources:
     src = surface_sources_2d(nx, n_sources)
     return CellModel2D("folded_faulted_%dx%d_%dsrc" % (nx, nz, n_sources), nx, nz, dx, params,
                        layer.reshape(-1), src)
+
+
+@dataclass
+class Model3D:
+    """A 3D layered model: classes per layer, node = x + nx*(y + ny*z)."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    layers: list
+    class_of_node: np.ndarray
+    sources: np.ndarray
+
+
+def layered_tti_3d(n: int = 201, n_layers: int = 12, n_sources: int = 16,
+                   seed: int = SEEDS["layered_tti_3d"], vti: bool = False) -> Model3D:
+    """3D layered visco-TTI on an n^3 lattice (dx = 10 m): flat layers of equal
+    thickness with the seeded Thomsen parameters of ``seeded_tti_layers`` and
+    a symmetry-axis azimuth phi0 ~ U(0, 360 deg) per layer (VTI variant: no
+    tilt); sources on a sqrt(n_sources)^2 grid on the surface z = 0."""
+    rng = np.random.default_rng(seed + 1)
+    layers = seeded_tti_layers(n_layers, seed)
+    from dataclasses import replace
+    azim = rng.uniform(0.0, 2 * math.pi, n_layers)
+    layers = [replace(L, tilt=0.0 if vti else L.tilt, azim=0.0 if vti else float(a))
+              for L, a in zip(layers, azim)]
+    z = np.arange(n, dtype=np.float64)
+    bounds = np.arange(1, n_layers) * (n - 1) / n_layers
+    layer_of_z = np.searchsorted(bounds, z, side="right").astype(np.int32)
+    cls = np.repeat(layer_of_z, n * n)
+    m = int(round(math.sqrt(n_sources)))
+    pos = np.round(np.linspace(0, n - 1, m + 2)[1:-1]).astype(np.int64)
+    src = np.array([x + n * y for y in pos for x in pos], dtype=np.int64)
+    return Model3D("layered_tti_3d_%d^3_%dsrc" % (n, len(src)), n, n, n, 10.0, layers, cls, src)
