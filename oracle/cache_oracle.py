@@ -298,6 +298,23 @@ def local_basis(theta0, phi0):
                      [st * cp, st * sp, ct]])
 
 
+def solve_direction_3d(A, theta0, phi0, th, ph, mode, kernel="MEV", h=0.001 * DEG, K=30000):
+    """One 3D entry: the global slowness direction of polar angle ``th`` and
+    azimuth ``ph``, for the class with stiffness ``A`` and symmetry axis
+    (theta0, phi0).  Returns (solve dict, global ray (3,), z mirror sign)."""
+    E = local_basis(theta0, phi0)
+    n = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    nl = E @ n                                   # components along e_x', e_y', e_z'
+    th_l = math.acos(min(1.0, max(-1.0, nl[2])))
+    ph_l = math.atan2(nl[1], nl[0])
+    sz = 1.0 if th_l <= math.pi / 2 else -1.0
+    th_f = th_l if sz > 0 else math.pi - th_l
+    s = solve_direction(A, th_f, mode, kernel, h, K)
+    rs, rzl = s["r"][0], s["r"][2]
+    rl = np.array([rs * math.cos(ph_l), rs * math.sin(ph_l), sz * rzl])
+    return s, E.T @ rl, sz
+
+
 def build_cache_3d(moduli, tilts, azims, modes, n_az, n_pol, kernel="MEV", h=0.001 * DEG, K=30000):
     """3D directional cache for classes ``moduli`` [n_classes, 5] with symmetry
     axes (tilts theta_0, azims phi_0).  Entry d = i*n_az + j is the global
@@ -315,22 +332,12 @@ def build_cache_3d(moduli, tilts, azims, modes, n_az, n_pol, kernel="MEV", h=0.0
     for mi, mode in enumerate(modes):
         for k in range(nk):
             A = stiffness_tensor(moduli[k])
-            E = local_basis(tilts[k], azims[k])
             for i in range(n_pol):
                 th = (i + 0.5) * math.pi / n_pol
                 for j in range(n_az):
                     ph = j * 2.0 * math.pi / n_az
                     d = i * n_az + j
-                    n = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
-                    nl = E @ n                                   # components along e_x', e_y', e_z'
-                    th_l = math.acos(min(1.0, max(-1.0, nl[2])))
-                    ph_l = math.atan2(nl[1], nl[0])
-                    sz = 1.0 if th_l <= math.pi / 2 else -1.0
-                    th_f = th_l if sz > 0 else math.pi - th_l
-                    s = solve_direction(A, th_f, mode, kernel, h, K)
-                    rs, rzl = s["r"][0], s["r"][2]
-                    rl = np.array([rs * math.cos(ph_l), rs * math.sin(ph_l), sz * rzl])
-                    r = E.T @ rl                                 # back to the global frame
+                    s, r, sz = solve_direction_3d(A, tilts[k], azims[k], th, ph, mode, kernel, h, K)
                     out["rx"][mi, k, d], out["ry"][mi, k, d], out["rz"][mi, k, d] = r
                     out["V"][mi, k, d] = s["V"]
                     out["A"][mi, k, d] = s["A"]

@@ -129,3 +129,50 @@ def test_pipeline3d_gpu_cache_to_traveltime_fp64(torch_dev):
     for r, node in enumerate(rcv):
         want = go.raypath(par, src[0], node)
         assert lens[r] == len(want) and list(paths[r, :lens[r]]) == want
+
+
+def test_full_size_3d_sampled(torch_dev):
+    """The 201^3 layered TTI model in the benchmark's launch configuration
+    (1 deg x 1 deg FP64 cache, 98 offsets): sampled cache entries against
+    single oracle solves at the full 0.001 deg scan, and the qP propagation
+    and qSV attenuation fields of one source against the oracle's Dijkstra on
+    the GPU cache's own lookup (FP64 tau to 1e-12, identical parents)."""
+    import math as _m
+    from oracle import cache_oracle as co
+    from helpers import oracle_moduli
+    m = inputs.layered_tti_3d(n_sources=1)
+    modes = ["qP", "qSV"]
+    nk = len(m.layers)
+    d_classes = chert.classes_to_device(chert.classes_from_layers(m.layers))
+    cache = chert.build_cache_3d(d_classes, nk, modes, 360, 180, precision="fp64")
+    torch_dev.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in cache.arrays.items()}
+    mods, tilts = oracle_moduli(m.layers)
+    rng = np.random.default_rng(5)
+    for _ in range(6):
+        mi, k, i, j = rng.integers(0, 2), rng.integers(0, nk), rng.integers(0, 180), rng.integers(0, 360)
+        d = i * 360 + j
+        s, r, _sz = co.solve_direction_3d(co.stiffness_tensor(mods[k]), tilts[k], m.layers[k].azim,
+                                          (i + 0.5) * _m.pi / 180, j * 2 * _m.pi / 360, modes[mi], "MEV")
+        assert g["flag"][mi, k, d] == s["flag"]
+        if s["flag"]:
+            continue
+        assert g["V"][mi, k, d] == pytest.approx(s["V"], rel=1e-9)
+        assert g["A"][mi, k, d] == pytest.approx(s["A"], rel=1e-9)
+        for q, key in enumerate(("rx", "ry", "rz")):
+            assert g[key][mi, k, d] == pytest.approx(r[q], abs=1e-9)
+    cls = m.class_of_node
+    off = inputs.stencil_3d(2)
+    src = int(m.sources[0])
+    tR, tI, pR, pI = chert.traveltime(cache, m.nx, m.nz, m.dx, torch_dev.as_tensor(cls, device="cuda"), off,
+                                      [src], ny=m.ny)
+    torch_dev.cuda.synchronize()
+    shape = (m.nx, m.ny, m.nz)
+    for mi, comp, t, p in ((0, 0, tR, pR), (1, 1, tI, pI)):
+        _, Vs, As = go.lookup_tables(g, mi, off)
+        rt, rp = go.dijkstra(shape, m.dx, cls, off, Vs if comp == 0 else As, comp, src)
+        gt, gp = t[0, mi].cpu().numpy(), p[0, mi].cpu().numpy()
+        fin = np.isfinite(rt)
+        assert np.array_equal(np.isfinite(gt), fin)
+        assert np.allclose(gt[fin], rt[fin], rtol=1e-12, atol=0)
+        assert np.array_equal(gp, rp)
