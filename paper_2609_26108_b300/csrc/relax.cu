@@ -288,48 +288,86 @@ __global__ void __launch_bounds__(512) relax_kernel(FieldArgs a, Offsets off) {
 // runs the planes of constant z upward, of constant y and of constant x in
 // both directions, and of constant z downward; in each, a node pulls from the
 // offsets whose component along the sweep axis has the sweep's sign, i.e. from
-// finished planes, so the nodes of one plane are independent.  A 201 x 201
-// plane does not fit in shared memory, so tau is read from global memory
-// (L1/L2 resident for the planes just behind); the weights sit in shared
-// memory as in 2D.  A pull whose source tau_i is not below the current best is
-// skipped without loading its class or weight (weights are >= 0, so it cannot
-// improve).  The verification pass and the parent rule are those of 2D.
+// finished planes, so the nodes of one plane are independent.  A plane is
+// processed in tiles of TU x TV nodes: the tile plus a halo of H nodes (H =
+// the stencil's largest component) is staged from the planes behind into
+// shared memory (tau and class), so each pull reads shared memory; tau itself
+// lives in global memory.  A pull whose source tau_i is not below the current
+// best is skipped without reading its class or weight (weights are >= 0, so
+// it cannot improve).  The verification pass stages planes z-H..z+H and
+// applies the 2D parent rule.
+constexpr int kTU = 32, kTV = 16;
+
+struct Stage3 {
+    int H, SU, SV;      // halo, staged tile extents
+};
+
+// In-plane coordinates (u, v) and plane p of a sweep along `axis` (0: x, 1: y,
+// 2: z planes) -> node index.
+__device__ __forceinline__ long long node3(int axis, int u, int v, int p, int nx, int ny) {
+    if (axis == 2) return (long long)u + (long long)nx * ((long long)v + (long long)ny * p);
+    if (axis == 1) return (long long)u + (long long)nx * ((long long)p + (long long)ny * v);
+    return (long long)p + (long long)nx * ((long long)u + (long long)ny * v);
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_planes(T* st, int* sk, const T* tau, const int32_t* cls, int nk, int axis,
+                                             int nu, int nv, int np, int p0, int pstep, int nplanes, int tu0,
+                                             int tv0, const Stage3& g, int nx, int ny) {
+    const int per = g.SU * g.SV;
+    for (int e = threadIdx.x; e < nplanes * per; e += blockDim.x) {
+        const int pl = p0 + pstep * (e / per);
+        const int r = e % per;
+        const int u = tu0 - g.H + r % g.SU, v = tv0 - g.H + r / g.SU;
+        if (pl >= 0 && pl < np && u >= 0 && u < nu && v >= 0 && v < nv) {
+            const long long j = node3(axis, u, v, pl, nx, ny);
+            st[e] = tau[j];
+            sk[e] = clamp_class(cls[j], nk);
+        } else {
+            st[e] = T(INFINITY);
+            sk[e] = 0;
+        }
+    }
+}
+
 template <typename T, int WMODE>
-__device__ bool sweep3d(const Smem<T>& sm, const T* __restrict__ gsel, const Offsets& off, int list, int axis,
-                        int dir, T* tau, const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk,
-                        int comp) {
+__device__ bool sweep3d(const Smem<T>& sm, const T* __restrict__ gsel, const Offsets& off, const short* qo,
+                        const short* qu, const short* qv, const short* ql, int cnt, int axis, int dir, T* tau,
+                        const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk, int comp, T* st, int* sk,
+                        const Stage3& g) {
+    const int nu = axis == 0 ? ny : nx;
+    const int nv = axis == 2 ? ny : nz;
     const int np = axis == 2 ? nz : axis == 1 ? ny : nx;
-    const long long psize = axis == 2 ? (long long)nx * ny : axis == 1 ? (long long)nx * nz : (long long)ny * nz;
-    const short* lst = sm.lists + list * off.n;
-    const int cnt = sm.counts[list];
+    const int per = g.SU * g.SV;
     bool changed = false;
     for (int step = 0; step < np; ++step) {
         const int p = dir > 0 ? step : np - 1 - step;
-        for (long long t = threadIdx.x; t < psize; t += blockDim.x) {
-            int x, y, z;
-            if (axis == 2) { x = (int)(t % nx); y = (int)(t / nx); z = p; }
-            else if (axis == 1) { x = (int)(t % nx); z = (int)(t / nx); y = p; }
-            else { y = (int)(t % ny); z = (int)(t / ny); x = p; }
-            const size_t j = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z);
-            const int kj = clamp_class(cls[j], nk);
-            const T cur = tau[j];
-            T best = cur;
-            for (int q = 0; q < cnt; ++q) {
-                const int o = lst[q];
-                const int xi = x - off.x[o], yi = y - off.y[o], zi = z - off.z[o];
-                if (xi < 0 || xi >= nx || yi < 0 || yi >= ny || zi < 0 || zi >= nz) continue;
-                const size_t i = (size_t)xi + (size_t)nx * ((size_t)yi + (size_t)ny * zi);
-                const T ti = tau[i];
-                if (!(ti < best)) continue;
-                const int ki = clamp_class(cls[i], nk);
-                best = fmin(best, ti + pull_weight<T, WMODE>(sm, gsel, off.n, nk, comp, o, ki, kj));
-            }
-            if (best < cur) {
-                tau[j] = best;
-                changed = true;
+        for (int tv0 = 0; tv0 < nv; tv0 += kTV) {
+            for (int tu0 = 0; tu0 < nu; tu0 += kTU) {
+                // planes p - dir*1 .. p - dir*H at stage slots 0 .. H-1
+                stage_planes(st, sk, tau, cls, nk, axis, nu, nv, np, p - dir, -dir, g.H, tu0, tv0, g, nx, ny);
+                __syncthreads();
+                const int u = tu0 + (int)(threadIdx.x % kTU), v = tv0 + (int)(threadIdx.x / kTU);
+                if (threadIdx.x < kTU * kTV && u < nu && v < nv) {
+                    const long long j = node3(axis, u, v, p, nx, ny);
+                    const int kj = clamp_class(cls[j], nk);
+                    const T cur = tau[j];
+                    T best = cur;
+                    const int su = u - tu0 + g.H, sv = v - tv0 + g.H;
+                    for (int q = 0; q < cnt; ++q) {
+                        const int e = (ql[q] - 1) * per + (sv - qv[q]) * g.SU + (su - qu[q]);
+                        const T ti = st[e];
+                        if (!(ti < best)) continue;
+                        best = fmin(best, ti + pull_weight<T, WMODE>(sm, gsel, off.n, nk, comp, qo[q], sk[e], kj));
+                    }
+                    if (best < cur) {
+                        tau[j] = best;
+                        changed = true;
+                    }
+                }
+                __syncthreads();
             }
         }
-        __syncthreads();
     }
     return __syncthreads_or(changed);
 }
@@ -337,37 +375,56 @@ __device__ bool sweep3d(const Smem<T>& sm, const T* __restrict__ gsel, const Off
 template <typename T, int WMODE>
 __device__ bool verify3d(const Smem<T>& sm, const T* __restrict__ gsel, const Offsets& off, T* tau,
                          const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk, int comp, int64_t src,
-                         int32_t* par) {
+                         int32_t* par, T* st, int* sk, const Stage3& g) {
+    const int per = g.SU * g.SV;
     bool changed = false;
-    const size_t n = (size_t)nx * ny * nz;
-    for (size_t j = threadIdx.x; j < n; j += blockDim.x) {
-        const int x = (int)(j % nx), y = (int)((j / nx) % ny), z = (int)(j / ((size_t)nx * ny));
-        const int kj = clamp_class(cls[j], nk);
-        const T cur = tau[j];
-        T best = T(INFINITY);
-        long long bi = -1;
-        for (int o = 0; o < off.n; ++o) {
-            const int xi = x - off.x[o], yi = y - off.y[o], zi = z - off.z[o];
-            if (xi < 0 || xi >= nx || yi < 0 || yi >= ny || zi < 0 || zi >= nz) continue;
-            const size_t i = (size_t)xi + (size_t)nx * ((size_t)yi + (size_t)ny * zi);
-            const T ti = tau[i];
-            if (ti > best) continue;
-            const int ki = clamp_class(cls[i], nk);
-            const T c = ti + pull_weight<T, WMODE>(sm, gsel, off.n, nk, comp, o, ki, kj);
-            if (c < best || (c == best && (long long)i < bi)) { best = c; bi = (long long)i; }
-        }
-        if (best < cur) {
-            tau[j] = best;
-            changed = true;
-        } else if (par) {
-            par[j] = ((int64_t)j == src) ? static_cast<int32_t>(src) : (isinf(cur) ? -1 : (int32_t)bi);
+    for (int z = 0; z < nz; ++z) {
+        for (int ty0 = 0; ty0 < ny; ty0 += kTV) {
+            for (int tx0 = 0; tx0 < nx; tx0 += kTU) {
+                // planes z-H .. z+H at stage slots 0 .. 2H
+                stage_planes(st, sk, tau, cls, nk, 2, nx, ny, nz, z - g.H, 1, 2 * g.H + 1, tx0, ty0, g, nx, ny);
+                __syncthreads();
+                const int x = tx0 + (int)(threadIdx.x % kTU), y = ty0 + (int)(threadIdx.x / kTU);
+                if (threadIdx.x < kTU * kTV && x < nx && y < ny) {
+                    const long long j = node3(2, x, y, z, nx, ny);
+                    const int kj = clamp_class(cls[j], nk);
+                    const T cur = tau[j];
+                    T best = T(INFINITY);
+                    long long bi = -1;
+                    const int sx = x - tx0 + g.H, sy = y - ty0 + g.H;
+                    for (int o = 0; o < off.n; ++o) {
+                        const int xi = x - off.x[o], yi = y - off.y[o], zi = z - off.z[o];
+                        if (xi < 0 || xi >= nx || yi < 0 || yi >= ny || zi < 0 || zi >= nz) continue;
+                        const int e = (g.H - off.z[o]) * per + (sy - off.y[o]) * g.SU + (sx - off.x[o]);
+                        const T ti = st[e];
+                        if (ti > best) continue;
+                        const T c = ti + pull_weight<T, WMODE>(sm, gsel, off.n, nk, comp, o, sk[e], kj);
+                        const long long i = node3(2, xi, yi, zi, nx, ny);
+                        if (c < best || (c == best && i < bi)) { best = c; bi = i; }
+                    }
+                    if (best < cur) {
+                        tau[j] = best;
+                        changed = true;
+                    } else if (par) {
+                        par[j] = (j == src) ? static_cast<int32_t>(src) : (isinf(cur) ? -1 : (int32_t)bi);
+                    }
+                }
+                __syncthreads();
+            }
         }
     }
     return __syncthreads_or(changed);
 }
 
+// Shared memory of relax3d_kernel after the weight table: L [n_off], six
+// per-sweep lists of (offset, in-plane u, in-plane v, lag) as shorts, counts,
+// then the stage (tau, then class) for 2H+1 planes.
+__host__ __device__ inline size_t stage3_elems(int H) {
+    return (size_t)(2 * H + 1) * (kTU + 2 * H) * (kTV + 2 * H);
+}
+
 template <typename T, int WMODE>
-__global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off) {
+__global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, int H) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = a.n_classes;
     const int field = blockIdx.x >> 1;
@@ -382,9 +439,13 @@ __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off) 
                           : WMODE == 0 ? static_cast<size_t>(nk) * off.n : 0;
     sm.W = reinterpret_cast<T*>(p); p += wcount * sizeof(T);
     sm.L = reinterpret_cast<T*>(p); p += off.n * sizeof(T);
+    Stage3 g{H, kTU + 2 * H, kTV + 2 * H};
+    T* st = reinterpret_cast<T*>(p); p += stage3_elems(H) * sizeof(T);
+    int* sk = reinterpret_cast<int*>(p); p += stage3_elems(H) * sizeof(int);
     sm.ring = nullptr;
     sm.cring = nullptr;
-    sm.lists = reinterpret_cast<short*>(p); p += 6 * off.n * sizeof(short);
+    short* lists = reinterpret_cast<short*>(p); p += 4 * 6 * off.n * sizeof(short);
+    sm.lists = lists;
     sm.counts = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
 
     const T* sel = static_cast<const T*>(comp == 0 ? a.Vsel : a.Asel) + static_cast<size_t>(mode) * nk * off.n;
@@ -401,17 +462,26 @@ __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off) 
     } else if (WMODE == 0) {
         for (int t = threadIdx.x; t < nk * off.n; t += blockDim.x) sm.W[t] = sel[t];
     }
-    if (threadIdx.x == 0) {
-        int c[6] = {0, 0, 0, 0, 0, 0};
+    // list l of sweep (axis, dir): 0 (z,+) 1 (y,+) 2 (x,+) 3 (x,-) 4 (y,-) 5 (z,-);
+    // entries: offset index, in-plane components (u, v) and lag along the axis
+    const int ax[6] = {2, 1, 0, 0, 1, 2}, dr[6] = {1, 1, 1, -1, -1, -1};
+    if (threadIdx.x < 6) {
+        const int l = threadIdx.x, axis = ax[l], dir = dr[l];
+        short* qo = lists + (4 * l + 0) * off.n;
+        short* qu = lists + (4 * l + 1) * off.n;
+        short* qv = lists + (4 * l + 2) * off.n;
+        short* ql = lists + (4 * l + 3) * off.n;
+        int c = 0;
         for (int o = 0; o < off.n; ++o) {
-            if (off.z[o] > 0) sm.lists[0 * off.n + c[0]++] = (short)o;   // z planes upward
-            if (off.y[o] > 0) sm.lists[1 * off.n + c[1]++] = (short)o;   // y planes
-            if (off.x[o] > 0) sm.lists[2 * off.n + c[2]++] = (short)o;   // x planes
-            if (off.x[o] < 0) sm.lists[3 * off.n + c[3]++] = (short)o;
-            if (off.y[o] < 0) sm.lists[4 * off.n + c[4]++] = (short)o;
-            if (off.z[o] < 0) sm.lists[5 * off.n + c[5]++] = (short)o;   // z planes downward
+            const int oa = axis == 2 ? off.z[o] : axis == 1 ? off.y[o] : off.x[o];
+            if (oa * dir <= 0) continue;
+            qo[c] = (short)o;
+            qu[c] = axis == 0 ? off.y[o] : off.x[o];
+            qv[c] = axis == 2 ? off.y[o] : off.z[o];
+            ql[c] = (short)(oa * dir);
+            ++c;
         }
-        for (int i = 0; i < 6; ++i) sm.counts[i] = c[i];
+        sm.counts[l] = c;
     }
 
     T* tau = static_cast<T*>(comp == 0 ? a.tauR : a.tauI) + static_cast<size_t>(field) * n;
@@ -423,13 +493,11 @@ __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off) 
 
     int used = -1;
     for (int cycle = 0; cycle < a.max_cycles; ++cycle) {
-        sweep3d<T, WMODE>(sm, sel, off, 0, 2, +1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
-        sweep3d<T, WMODE>(sm, sel, off, 1, 1, +1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
-        sweep3d<T, WMODE>(sm, sel, off, 2, 0, +1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
-        sweep3d<T, WMODE>(sm, sel, off, 3, 0, -1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
-        sweep3d<T, WMODE>(sm, sel, off, 4, 1, -1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
-        sweep3d<T, WMODE>(sm, sel, off, 5, 2, -1, tau, a.cls, a.nx, a.ny, a.nz, nk, comp);
-        if (!verify3d<T, WMODE>(sm, sel, off, tau, a.cls, a.nx, a.ny, a.nz, nk, comp, src, par)) {
+        for (int l = 0; l < 6; ++l)
+            sweep3d<T, WMODE>(sm, sel, off, lists + (4 * l) * off.n, lists + (4 * l + 1) * off.n,
+                              lists + (4 * l + 2) * off.n, lists + (4 * l + 3) * off.n, sm.counts[l], ax[l], dr[l],
+                              tau, a.cls, a.nx, a.ny, a.nz, nk, comp, st, sk, g);
+        if (!verify3d<T, WMODE>(sm, sel, off, tau, a.cls, a.nx, a.ny, a.nz, nk, comp, src, par, st, sk, g)) {
             used = cycle + 1;
             break;
         }
@@ -537,11 +605,11 @@ extern "C" int chert_edge_table(const chert_cache_arrays* cache, int n_modes, in
 
 
 template <typename T, int WMODE>
-static int launch_relax3d(const FieldArgs& a, const Offsets& off, size_t smem, int blocks, cudaStream_t s) {
+static int launch_relax3d(const FieldArgs& a, const Offsets& off, int H, size_t smem, int blocks, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(relax3d_kernel<T, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
-    relax3d_kernel<T, WMODE><<<blocks, 512, smem, s>>>(a, off);
+    relax3d_kernel<T, WMODE><<<blocks, 512, smem, s>>>(a, off, H);
     return launch_check("chert_traveltime: relax3d");
 }
 
@@ -870,19 +938,23 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int blocks = n_sources * n_modes * 2;
     if (ny > 1) {                                      // 3D: plane sweeps
-        const size_t base3 = n_off * es + 6 * n_off * 2 + 64;
+        int H = 0;
+        for (int i = 0; i < n_off; i++)
+            H = std::max(H, std::max(abs((int)off.y[i]), std::max(abs((int)off.x[i]), abs((int)off.z[i]))));
+        CHERT_REQUIRE(H <= 8, "%s: 3D offsets reach %d nodes (at most 8)", who, H);
+        const size_t base3 = n_off * es + stage3_elems(H) * (es + 4) + 4 * 6 * n_off * 2 + 64;
         const size_t t3 = (size_t)n_off * n_classes * n_classes * es + base3;
         const size_t r3 = (size_t)n_classes * n_off * es + base3;
         const int mode3 = t3 <= (size_t)std::min(smem_max, 160 * 1024) ? 1 : r3 <= (size_t)smem_max ? 0 : 2;
         const size_t sm3 = mode3 == 1 ? t3 : mode3 == 0 ? r3 : base3;
         if (precision == CHERT_FP64)
-            rc = mode3 == 1 ? launch_relax3d<double, 1>(a, off, sm3, blocks, s)
-               : mode3 == 0 ? launch_relax3d<double, 0>(a, off, sm3, blocks, s)
-                            : launch_relax3d<double, 2>(a, off, sm3, blocks, s);
+            rc = mode3 == 1 ? launch_relax3d<double, 1>(a, off, H, sm3, blocks, s)
+               : mode3 == 0 ? launch_relax3d<double, 0>(a, off, H, sm3, blocks, s)
+                            : launch_relax3d<double, 2>(a, off, H, sm3, blocks, s);
         else
-            rc = mode3 == 1 ? launch_relax3d<float, 1>(a, off, sm3, blocks, s)
-               : mode3 == 0 ? launch_relax3d<float, 0>(a, off, sm3, blocks, s)
-                            : launch_relax3d<float, 2>(a, off, sm3, blocks, s);
+            rc = mode3 == 1 ? launch_relax3d<float, 1>(a, off, H, sm3, blocks, s)
+               : mode3 == 0 ? launch_relax3d<float, 0>(a, off, H, sm3, blocks, s)
+                            : launch_relax3d<float, 2>(a, off, H, sm3, blocks, s);
         if (rc) return rc;
         *blocks_out = blocks;
         *status_out = a.status;
