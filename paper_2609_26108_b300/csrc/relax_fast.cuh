@@ -381,8 +381,11 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
     constexpr int N = Stencil<R>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = a.n_classes;
-    const int field = blockIdx.x >> 1;
-    const int comp = blockIdx.x & 1;
+    // Attenuation fields (several sweep cycles) launch first and propagation
+    // fields (mostly one cycle) fill the tail of the grid.
+    const int n_fields = gridDim.x >> 1;
+    const int comp = (int)blockIdx.x < n_fields ? 1 : 0;
+    const int field = comp ? (int)blockIdx.x : (int)blockIdx.x - n_fields;
     const int mode = field % a.n_modes;
     const int s = field / a.n_modes;
     const int line_max = max(a.nx, a.nz);
@@ -447,7 +450,7 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
             break;
         }
     }
-    if (threadIdx.x == 0) a.status[blockIdx.x] = used;
+    if (threadIdx.x == 0) a.status[field * 2 + comp] = used;
 }
 
 }  // namespace fast
