@@ -227,6 +227,23 @@ int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes
                      void* d_tauR, void* d_tauI, int32_t* d_parR, int32_t* d_parI,
                      void* d_workspace, size_t workspace_bytes, void* stream);
 
+/* The same relaxation as chert_traveltime, enqueued on `stream` without any
+ * host synchronisation or host-to-device copy: sources are a device int64
+ * array, the offsets travel by value to the kernels, and the convergence
+ * status lands in d_status (device int32[2]): [0] the first index
+ * field*2 + component (field = source*n_modes + mode) that hit max_cycles, or
+ * -1; [1] 1 if the class map held ids outside [0, n_classes), else 0.  A
+ * source outside the lattice yields an all-unreachable field.  Repeated
+ * problems (many sources and modes, several models) can so be recorded once
+ * as a CUDA graph and replayed as one launch.  Errors (host-side argument
+ * checks): CHERT_EINVAL, CHERT_ENOMEM (workspace too small), CHERT_ECUDA. */
+int chert_traveltime_enqueue(const chert_cache_arrays* cache, int n_modes, int n_classes, int n_dir,
+                             int nx, int ny, int nz, double dx, const int32_t* d_class_of_node,
+                             const int32_t* offsets, int n_off, const int64_t* d_sources, int n_sources,
+                             int precision, int max_cycles, void* d_tauR, void* d_tauI, int32_t* d_parR,
+                             int32_t* d_parI, void* d_workspace, size_t workspace_bytes, int32_t* d_status,
+                             void* stream);
+
 /* ---- cache surrogate (a learned stand-in for the cache build; no counterpart in the paper)
  * One MLP per wave mode, 7 -> 256 -> 256 -> 256 -> 256 -> 5 with SiLU hidden
  * activations, BF16 operands, FP32 accumulation and FP32 master weights.  It

@@ -82,6 +82,9 @@ def lib():
     L.chert_traveltime.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P, I,
                                    P, I, I, I, P, P, P, P, P, SZ, P]
     L.chert_raypath.argtypes = [P, I, I64, P, P, I, I64, P, P, P]
+    L.chert_traveltime_enqueue.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P, I,
+                                           P, I, I, I, P, P, P, P, P, SZ, P, P]
+    L.chert_traveltime_enqueue.restype = ctypes.c_int
     L.chert_traveltime_static.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P,
                                           I, P, I, I, I, P, P, P, P, P]
     L.chert_traveltime_static_limit.restype = SZ
@@ -330,6 +333,23 @@ def traveltime(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64, parent
                                   max_cycles, _dev_ptr(out[0]), _dev_ptr(out[1]), _dev_ptr(out[2]),
                                   _dev_ptr(out[3]), _dev_ptr(workspace), workspace.numel(),
                                   _stream_ptr(stream)))
+    return out
+
+
+def traveltime_enqueue(cache, nx, nz, dx, d_cls, offsets, d_sources, out, workspace, d_status, max_cycles=64,
+                       ny=1, stream=None):
+    """chert_traveltime_enqueue: no host synchronisation or copy (capturable
+    in a CUDA graph).  d_sources: device int64 [n_sources]; out: (tauR, tauI,
+    parR, parI) preallocated; d_status: device int32[2] (first field*2+comp that
+    hit the cycle cap or -1, class-map error flag)."""
+    off, off_p = _offsets_arr(offsets)
+    nm, ns = len(cache.modes), int(d_sources.numel())
+    st = cache.struct()
+    _check(lib().chert_traveltime_enqueue(ctypes.byref(st), nm, cache.n_classes, cache.n_dir, nx, ny, nz,
+                                          float(dx), _dev_ptr(d_cls), off_p, len(off), _dev_ptr(d_sources), ns,
+                                          cache.precision, max_cycles, _dev_ptr(out[0]), _dev_ptr(out[1]),
+                                          _dev_ptr(out[2]), _dev_ptr(out[3]), _dev_ptr(workspace),
+                                          workspace.numel(), _dev_ptr(d_status), _stream_ptr(stream)))
     return out
 
 

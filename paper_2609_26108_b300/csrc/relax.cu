@@ -878,18 +878,18 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
                               const int64_t* sources, int n_sources, int precision, int max_cycles,
                               void* d_tauR, void* d_tauI, int32_t* d_parR, int32_t* d_parI,
                               unsigned char* w, size_t bytes, cudaStream_t s, int* blocks_out,
-                              int** status_out) {
+                              int** status_out, const int64_t* d_sources = nullptr) {
     CHERT_REQUIRE(nx >= 1 && ny >= 1 && nz >= 1 && (long long)nx * ny * nz < (1LL << 31),
                   "%s: bad lattice %d x %d x %d", who, nx, ny, nz);
     const long long n_nodes = (long long)nx * ny * nz;
     CHERT_REQUIRE(dx > 0, "%s: dx must be positive", who);
-    CHERT_REQUIRE(d_class_of_node && sources && d_tauR && d_tauI && w, "%s: NULL argument", who);
+    CHERT_REQUIRE(d_class_of_node && (sources || d_sources) && d_tauR && d_tauI && w, "%s: NULL argument", who);
     CHERT_REQUIRE(n_sources >= 1 && n_modes >= 1 && n_modes <= 3 && n_classes >= 1,
                   "%s: bad counts", who);
     CHERT_REQUIRE(max_cycles >= 1, "%s: max_cycles must be >= 1", who);
     CHERT_REQUIRE(precision == CHERT_FP64 || precision == CHERT_FP32 || precision == CHERT_MIXED,
                   "%s: precision=%d", who, precision);
-    for (int i = 0; i < n_sources; i++)
+    for (int i = 0; sources && i < n_sources; i++)
         CHERT_REQUIRE(sources[i] >= 0 && sources[i] < (int64_t)n_nodes,
                       "%s: source %d out of range", who, i);
     Offsets off;
@@ -916,9 +916,11 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     rc = chert_edge_table(cache, n_modes, n_classes, n_dir, precision, offsets, n_off,
                           reinterpret_cast<int32_t*>(w + ws.idx), Vsel, Asel, s);
     if (rc) return rc;
-    cudaError_t e = cudaMemcpyAsync(w + ws.src, sources, sizeof(int64_t) * n_sources,
-                                    cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "sources copy");
+    cudaError_t e = cudaSuccess;
+    if (sources) {
+        e = cudaMemcpyAsync(w + ws.src, sources, sizeof(int64_t) * n_sources, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "sources copy");
+    }
 
     int* bad_class = reinterpret_cast<int*>(w + ws.status) + (size_t)n_sources * n_modes * 2;
     e = cudaMemsetAsync(bad_class, 0, sizeof(int), s);
@@ -930,7 +932,8 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     FieldArgs a;
     a.nx = nx; a.ny = ny; a.nz = nz; a.n_classes = n_classes; a.n_modes = n_modes;
     a.n_sources = n_sources; a.max_cycles = max_cycles; a.ring = R + 2; a.dx = dx;
-    a.cls = d_class_of_node; a.src = reinterpret_cast<const int64_t*>(w + ws.src);
+    a.cls = d_class_of_node;
+    a.src = d_sources ? d_sources : reinterpret_cast<const int64_t*>(w + ws.src);
     a.tauR = d_tauR; a.tauI = d_tauI; a.parR = d_parR; a.parI = d_parI;
     a.Vsel = Vsel; a.Asel = Asel; a.status = reinterpret_cast<int*>(w + ws.status);
     int dev = 0, smem_max = 0;
@@ -1125,6 +1128,27 @@ extern "C" int chert_traveltime_static(const chert_cache_arrays* cache, int n_mo
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime_static: status");
     return status_to_code("chert_traveltime_static", h[0], h[1], n_classes, max_cycles);
+}
+
+// chert_traveltime_enqueue: the same path with device sources and a device
+// status word pair, and no host synchronisation or host-to-device copy.
+extern "C" int chert_traveltime_enqueue(const chert_cache_arrays* cache, int n_modes, int n_classes, int n_dir,
+                                        int nx, int ny, int nz, double dx, const int32_t* d_class_of_node,
+                                        const int32_t* offsets, int n_off, const int64_t* d_sources,
+                                        int n_sources, int precision, int max_cycles, void* d_tauR,
+                                        void* d_tauI, int32_t* d_parR, int32_t* d_parI, void* d_workspace,
+                                        size_t workspace_bytes, int32_t* d_status, void* stream) {
+    CHERT_REQUIRE(d_sources && d_status, "chert_traveltime_enqueue: NULL sources or status");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int blocks = 0;
+    int* status = nullptr;
+    int rc = enqueue_traveltime("chert_traveltime_enqueue", cache, n_modes, n_classes, n_dir, nx, ny, nz, dx,
+                                d_class_of_node, offsets, n_off, nullptr, n_sources, precision, max_cycles,
+                                d_tauR, d_tauI, d_parR, d_parI, static_cast<unsigned char*>(d_workspace),
+                                workspace_bytes, s, &blocks, &status, d_sources);
+    if (rc) return rc;
+    status_summary_kernel<<<1, 256, 0, s>>>(status, blocks, d_status);
+    return launch_check("chert_traveltime_enqueue: status");
 }
 
 extern "C" int chert_raypath(const int32_t* d_par, int n_fields, int64_t n_nodes,

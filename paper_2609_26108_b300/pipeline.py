@@ -110,3 +110,133 @@ class Tracer:
 
     def d2h_bytes(self):
         return self.tau[0].numel() * self.tau[0].element_size() * 2
+
+
+class Problem:
+    """One traveltime problem of a batch: its classes (packed, device), cache
+    geometry (2D: M; 3D: n_az, n_pol), lattice, class map (device int32),
+    stencil, sources and receivers."""
+
+    def __init__(self, d_classes, n_classes, modes, nx, nz, dx, d_cls, offsets, sources, receivers=None,
+                 M=90, n_az=0, n_pol=0, ny=1, cache_precision="mixed", scan_step=0.001 * math.pi / 180,
+                 scan_half=30000, kernel="MEV", max_cycles=64, path_cap=1024):
+        self.d_classes, self.n_classes, self.modes = d_classes, n_classes, list(modes)
+        self.nx, self.ny, self.nz, self.dx = nx, ny, nz, dx
+        self.d_cls = d_cls
+        self.offsets = np.ascontiguousarray(np.asarray(offsets, np.int32).reshape(-1, 3))
+        self.sources = np.asarray(sources, np.int64).reshape(-1)
+        self.receivers = None if receivers is None else np.asarray(receivers, np.int64).reshape(-1)
+        self.M, self.n_az, self.n_pol = M, n_az, n_pol
+        self.cache_precision, self.scan_step, self.scan_half, self.kernel = cache_precision, scan_step, scan_half, kernel
+        self.max_cycles, self.path_cap = max_cycles, path_cap
+
+    @property
+    def n_fields(self):
+        return len(self.sources) * len(self.modes)
+
+
+class GraphBatch:
+    """Many problems (sources x modes on several models, 2D and 3D) recorded
+    once into one CUDA graph and replayed as one launch.  Each problem is
+    captured on its own stream (forked from and joined to the capture
+    stream), so the graph's branches run concurrently and fill the SMs that
+    one problem's fields leave idle.  Every step is libchert's: cache build,
+    lookup + relaxation + parents (``chert_traveltime_enqueue``: device
+    sources, device status, no host synchronisation), raypaths."""
+
+    def __init__(self, problems, device="cuda"):
+        import torch
+        self.torch = torch
+        self.problems = list(problems)
+        self.state = [self._allocate(p, device) for p in self.problems]
+        self.graph = None
+
+    def _allocate(self, p, device):
+        torch = self.torch
+        prec = chert.PRECISION_IDS[p.cache_precision]
+        fd = torch.float64 if prec == chert.FP64 else torch.float32
+        nd = p.n_az * p.n_pol if p.n_az else 4 * p.M
+        shape = (len(p.modes), p.n_classes, nd)
+        keys = ("V", "A", "Q", "rx", "rz", "theta", "vartheta") + (("ry", "phi") if p.n_az else ())
+        cache_out = {k: torch.empty(shape, dtype=fd, device=device) for k in keys}
+        cache_out["flag"] = torch.empty(shape, dtype=torch.uint8, device=device)
+        n = p.nx * p.ny * p.nz
+        fshape = (len(p.sources), len(p.modes), n)
+        tau = (torch.empty(fshape, dtype=fd, device=device), torch.empty(fshape, dtype=fd, device=device),
+               torch.empty(fshape, dtype=torch.int32, device=device),
+               torch.empty(fshape, dtype=torch.int32, device=device))
+        if p.ny == 1:
+            wsb = chert.workspace_bytes(len(p.modes), p.n_classes, len(p.offsets), prec, len(p.sources), p.nx, p.nz)
+        else:
+            wsb = chert.workspace_bytes(len(p.modes), p.n_classes, len(p.offsets), prec, len(p.sources))
+        st = {"cache_out": cache_out, "tau": tau,
+              "ws": torch.empty(wsb, dtype=torch.uint8, device=device),
+              "d_src": torch.as_tensor(p.sources, device=device),
+              "status": torch.zeros(2, dtype=torch.int32, device=device),
+              "stream": torch.cuda.Stream(device=device)}
+        if p.receivers is not None:
+            nf = p.n_fields
+            st["d_fsrc"] = torch.as_tensor(np.repeat(p.sources, len(p.modes)), device=device)
+            st["d_rcv"] = torch.as_tensor(p.receivers, device=device)
+            st["paths"] = (torch.empty((2, nf, len(p.receivers), p.path_cap), dtype=torch.int64, device=device),
+                           torch.empty((2, nf, len(p.receivers)), dtype=torch.int64, device=device))
+        return st
+
+    def _enqueue(self, p, st, stream):
+        if p.n_az:
+            cache = chert.build_cache_3d(p.d_classes, p.n_classes, p.modes, p.n_az, p.n_pol, p.scan_step,
+                                         p.scan_half, p.kernel, p.cache_precision, stream, out=st["cache_out"])
+        else:
+            cache = chert.build_cache(p.d_classes, p.n_classes, p.modes, p.M, p.scan_step, p.scan_half,
+                                      p.kernel, p.cache_precision, stream, out=st["cache_out"])
+        st["cache"] = cache
+        chert.traveltime_enqueue(cache, p.nx, p.nz, p.dx, p.d_cls, p.offsets, st["d_src"], st["tau"], st["ws"],
+                                 st["status"], p.max_cycles, p.ny, stream)
+        if p.receivers is not None:
+            nf = p.n_fields
+            for comp in (0, 1):
+                chert.raypath(st["tau"][2 + comp].reshape(nf, -1), st["d_fsrc"], st["d_rcv"], p.path_cap, stream,
+                              out=(st["paths"][0][comp], st["paths"][1][comp]))
+
+    def run_eager(self):
+        """One pass without the graph (also loads every kernel before capture)."""
+        for p, st in zip(self.problems, self.state):
+            self._enqueue(p, st, None)
+
+    def capture(self):
+        torch = self.torch
+        self.run_eager()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            main = torch.cuda.current_stream()
+            for p, st in zip(self.problems, self.state):
+                s = st["stream"]
+                s.wait_stream(main)
+                with torch.cuda.stream(s):
+                    self._enqueue(p, st, s)
+            for st in self.state:
+                main.wait_stream(st["stream"])
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def check(self):
+        """Host read of every problem's status (one synchronisation); raises
+        like chert_traveltime on a cycle cap or a bad class map."""
+        for p, st in zip(self.problems, self.state):
+            first, bad = (int(v) for v in st["status"].cpu().tolist())
+            if bad:
+                raise chert.ChertError(chert.EINVAL, "class map holds ids outside [0, %d)" % p.n_classes)
+            if first >= 0:
+                raise chert.ChertError(chert.ETIMEOUT, "field %d component %d did not converge in %d cycles"
+                                       % (first // 2, first % 2, p.max_cycles))
+
+    def fields(self, i):
+        return self.state[i]["tau"]
+
+    @property
+    def n_fields(self):
+        return sum(p.n_fields for p in self.problems)
