@@ -380,6 +380,57 @@ def section_3d(flush, n_sources=16):
             "edge_relaxations_per_s": edges * nf * 2 / t_relax, "directed_edges_per_field": edges}
 
 
+# --------------------------------------------------------------- batch
+def section_batch(n2d, n3d):
+    """Several problems of uneven size in one CUDA graph (the batched form):
+    the per-cell folded and faulted 1701x351 model (exact per-cell cache,
+    n2d sources x 3 modes) and a 101^3 block of the 3D layered model cut at a
+    seeded corner (1 deg x 1 deg FP64 cache, n3d sources x qP/qSV).  Each
+    problem is captured on its own stream, so their kernels overlap.  Timed:
+    one eager pass (problems one after another) against one graph replay,
+    each from the caches' build to the raypaths."""
+    import torch
+    from paper_2609_26108_b300 import chert
+    from paper_2609_26108_b300.pipeline import GraphBatch, Problem
+
+    fm = inputs.folded_faulted(n_sources=n2d)
+    n = fm.nx * fm.nz
+    keys = ["vp0", "vs0", "eps", "delta", "gamma", "qp", "qs", "tilt"]
+    d_cells = chert.classes_to_device(chert.classes_from_arrays(**{k: fm.params[k] for k in keys}))
+    m3 = inputs.subvolume_3d(inputs.layered_tti_3d(), 101, seed=1005, n_sources=n3d)
+    d3 = chert.classes_to_device(chert.classes_from_layers(m3.layers))
+    probs = [Problem(d_cells, n, MODES, fm.nx, fm.nz, fm.dx, torch.arange(n, dtype=torch.int32, device="cuda"),
+                     inputs.stencil_2d(RADIUS), fm.sources, receivers=np.arange(0, fm.nx, 40), M=M_PER_QUADRANT,
+                     max_cycles=512),
+             Problem(d3, len(m3.layers), ["qP", "qSV"], m3.nx, m3.nz, m3.dx,
+                     torch.as_tensor(m3.class_of_node, device="cuda"), inputs.stencil_3d(2), m3.sources,
+                     receivers=np.arange(0, m3.nx * m3.ny, 997), n_az=360, n_pol=180, ny=m3.ny,
+                     cache_precision="fp64")]
+    batch = GraphBatch(probs)
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    t_eager = timed(batch.run_eager)
+    batch.check()
+    batch.capture()
+    t_graph = timed(batch.replay)
+    batch.check()
+    nf = batch.n_fields
+    return {"workload": "batch: folded_faulted 1701x351 per-cell %dsrc x 3 modes + layered_tti_3d 101^3 block "
+                        "%dsrc x 2 modes, one CUDA graph" % (len(fm.sources), len(m3.sources)),
+            "fields": nf, "eager_s": t_eager, "graph_s": t_graph,
+            "fields_per_s_eager": nf / t_eager, "fields_per_s_graph": nf / t_graph,
+            "note": "each pass builds the caches (exact per-cell, 3D FP64) and relaxes every field with parents "
+                    "and raypaths"}
+
+
 # --------------------------------------------------------------- GPU arm
 def run_chert(args):
     import torch
@@ -482,6 +533,8 @@ def run_chert(args):
         out["surrogate"] = surrogate_section(args.surrogate_sources, flush)
     if world == 1 and args.sources_3d > 0:
         out["lattice_3d"] = section_3d(flush, args.sources_3d)
+    if world == 1 and args.batch_sources > 0:
+        out["batch"] = section_batch(args.batch_sources, args.batch_sources_3d)
     if world == 1 and not args.no_cpu_baseline:
         fps, eps_, desc, _ = oracle_sample(model, off)
         out["cpu_baseline"] = {"value": fps, "unit": "fields/s", "cores": 1, "kind": "oracle",
@@ -501,6 +554,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sources", type=int, default=64,
                     help="surface sources (64 = the benchmark workload; fewer only for profiling)")
+    ap.add_argument("--batch-sources", type=int, default=0,
+                    help="sources of the per-cell 2D problem in the CUDA-graph batch (0, the default: leave it out;
+                         "64 with --batch-sources-3d 16 is the measured batch)")
+    ap.add_argument("--batch-sources-3d", type=int, default=16,
+                    help="sources of the 101^3 3D problem in the CUDA-graph batch")
     ap.add_argument("--sources-3d", type=int, default=16,
                     help="sources of the 201^3 3D section (0: leave it out)")
     ap.add_argument("--surrogate-sources", type=int, default=16,

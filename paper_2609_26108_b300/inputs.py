@@ -306,3 +306,19 @@ def layered_tti_3d(n: int = 201, n_layers: int = 12, n_sources: int = 16,
     pos = np.round(np.linspace(0, n - 1, m + 2)[1:-1]).astype(np.int64)
     src = np.array([x + n * y for y in pos for x in pos], dtype=np.int64)
     return Model3D("layered_tti_3d_%d^3_%dsrc" % (n, len(src)), n, n, n, 10.0, layers, cls, src)
+
+
+def subvolume_3d(model: Model3D, n: int, seed: int, n_sources: int) -> Model3D:
+    """An n^3 block of a 3D model cut at a seeded corner (PCG64), its top face
+    at the model's surface row z0, sources on a sqrt(n_sources)^2 grid on
+    that face."""
+    rng = np.random.default_rng(seed)
+    x0 = int(rng.integers(0, model.nx - n + 1))
+    y0 = int(rng.integers(0, model.ny - n + 1))
+    z0 = int(rng.integers(0, model.nz - n + 1))
+    cls = model.class_of_node.reshape(model.nz, model.ny, model.nx)[z0:z0 + n, y0:y0 + n, x0:x0 + n]
+    m = int(round(math.sqrt(n_sources)))
+    pos = np.round(np.linspace(0, n - 1, m + 2)[1:-1]).astype(np.int64)
+    src = np.array([x + n * y for y in pos for x in pos], dtype=np.int64)
+    return Model3D("%s_sub%d^3_at_%d_%d_%d" % (model.name, n, x0, y0, z0), n, n, n, model.dx, model.layers,
+                   np.ascontiguousarray(cls).reshape(-1), src)
