@@ -555,8 +555,8 @@ def main():
     ap.add_argument("--sources", type=int, default=64,
                     help="surface sources (64 = the benchmark workload; fewer only for profiling)")
     ap.add_argument("--batch-sources", type=int, default=0,
-                    help="sources of the per-cell 2D problem in the CUDA-graph batch (0, the default: leave it out;
-                         "64 with --batch-sources-3d 16 is the measured batch)")
+                    help="sources of the per-cell 2D problem in the CUDA-graph batch (0, the default: leave it "
+                         "out; the measured batch is --batch-sources 64 --batch-sources-3d 16)")
     ap.add_argument("--batch-sources-3d", type=int, default=16,
                     help="sources of the 101^3 3D problem in the CUDA-graph batch")
     ap.add_argument("--sources-3d", type=int, default=16,
