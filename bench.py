@@ -380,6 +380,63 @@ def section_3d(flush, n_sources=16):
             "edge_relaxations_per_s": edges * nf * 2 / t_relax, "directed_edges_per_field": edges}
 
 
+# --------------------------------------------------------------- angular step
+def section_angular(n_sources=8, steps_deg=(0.5, 1.0, 2.0, 5.0, 10.0)):
+    """Cache angular-step study on the layered 401x401 model: caches of
+    0.5 to 10 deg (MIXED), n_sources surface sources x 3 modes, FP32
+    relaxation.  Per step and mode: RMS of the relative tauR and tauI misfit
+    against the 0.5 deg fields (nodes with tau > 0), and the angle between
+    each stencil offset and the ray of the entry the lookup selects
+    (mean / max over classes and offsets; the lookup's directional error)."""
+    import torch
+    from paper_2609_26108_b300 import chert
+
+    model = inputs.layered_tti(n_sources=n_sources)
+    off = inputs.stencil_2d(RADIUS)
+    d_classes = chert.classes_to_device(chert.classes_from_layers(model.layers))
+    d_cls = torch.as_tensor(model.class_of_node.astype(np.int32), device="cuda")
+    nk = len(model.layers)
+    dirs = torch.as_tensor(off[:, [0, 2]] / np.linalg.norm(off, axis=1)[:, None], device="cuda")
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    rows, ref = [], None
+    for deg in steps_deg:
+        M = int(round(90.0 / deg))
+        cache, t_c = timed(lambda: chert.build_cache(d_classes, nk, MODES, M, SCAN_STEP, SCAN_HALF, "MEV", "mixed"))
+        fields, t_r = timed(lambda: chert.traveltime(cache, model.nx, model.nz, model.dx, d_cls, off,
+                                                     model.sources, max_cycles=128))
+        idx, _, _ = chert.edge_table(cache, off)
+        ix = idx.long().clamp_min(0)
+        rx = torch.gather(cache["rx"].double(), 2, ix)
+        rz = torch.gather(cache["rz"].double(), 2, ix)
+        dot = (rx * dirs[None, None, :, 0] + rz * dirs[None, None, :, 1]).clamp(-1, 1)
+        ang = torch.rad2deg(torch.acos(dot))
+        row = {"step_deg": deg, "cache_ms": t_c, "relax_ms": t_r}
+        for mi, m in enumerate(MODES):
+            a = ang[mi][idx[mi] >= 0]
+            row["lookup_angle_deg_%s" % m] = {"mean": float(a.mean()), "max": float(a.max())}
+        if ref is None:
+            ref = [f.double().clone() for f in fields[:2]]
+        else:
+            for comp, name in ((0, "tauR"), (1, "tauI")):
+                for mi, m in enumerate(MODES):
+                    r = ref[comp][:, mi]
+                    g = fields[comp][:, mi].double()
+                    ok = torch.isfinite(r) & (r > 0) & torch.isfinite(g)
+                    row["rms_rel_misfit_%s_%s" % (name, m)] = float((((g - r) / r)[ok] ** 2).mean().sqrt())
+        rows.append(row)
+    return {"workload": "layered_visco_tti_2d_401x401_8layers_%dsrc_3modes_R5, caches %s deg"
+                        % (len(model.sources), list(steps_deg)), "reference": "0.5 deg fields", "rows": rows}
+
+
 # --------------------------------------------------------------- batch
 def section_batch(n2d, n3d):
     """Several problems of uneven size in one CUDA graph (the batched form):
@@ -533,6 +590,8 @@ def run_chert(args):
         out["surrogate"] = surrogate_section(args.surrogate_sources, flush)
     if world == 1 and args.sources_3d > 0:
         out["lattice_3d"] = section_3d(flush, args.sources_3d)
+    if world == 1 and args.angular_study:
+        out["angular_study"] = section_angular()
     if world == 1 and args.batch_sources > 0:
         out["batch"] = section_batch(args.batch_sources, args.batch_sources_3d)
     if world == 1 and not args.no_cpu_baseline:
@@ -554,6 +613,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sources", type=int, default=64,
                     help="surface sources (64 = the benchmark workload; fewer only for profiling)")
+    ap.add_argument("--angular-study", action="store_true",
+                    help="add the cache angular-step study (0.5-10 deg) on the layered model")
     ap.add_argument("--batch-sources", type=int, default=0,
                     help="sources of the per-cell 2D problem in the CUDA-graph batch (0, the default: leave it "
                          "out; the measured batch is --batch-sources 64 --batch-sources-3d 16)")
