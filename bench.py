@@ -336,7 +336,8 @@ def section_3d(flush, n_sources=16):
     1004, symmetry-axis azimuth ~ U(0, 360 deg)), qP and qSV, 1 deg x 1 deg
     cache of global directions (360 azimuths x 180 polar angles = 64,800 per
     class and mode), radius-2 3D stencil (98 offsets), 16 sources on a 4 x 4
-    surface grid; cache and traveltimes in FP64.  One run of cache build +
+    surface grid; MIXED cache, FP32 edge weights with traveltimes accumulated
+    in float-float (~48-bit) and returned as double.  One run of cache build +
     relaxation with parents, L2 flushed before each part."""
     import torch
     from paper_2609_26108_b300 import chert
@@ -352,10 +353,10 @@ def section_3d(flush, n_sources=16):
     shape = (len(src), len(modes), n)
     tau = tuple(torch.empty(shape, dtype=dt, device="cuda")
                 for dt in (torch.float64, torch.float64, torch.int32, torch.int32))
-    ws = torch.empty(chert.workspace_bytes(len(modes), nk, len(off), chert.FP64, len(src)), dtype=torch.uint8,
-                     device="cuda")
-    small = chert.build_cache_3d(d_classes, nk, modes, 36, 18, precision="fp64")        # load the kernels
-    chert.traveltime(small, 9, 9, m.dx, d_cls[:729], off, [0], ny=9, workspace=ws)
+    ws = torch.empty(chert.workspace_bytes(len(modes), nk, len(off), chert.FP32_ACC64, len(src)),
+                     dtype=torch.uint8, device="cuda")
+    small = chert.build_cache_3d(d_classes, nk, modes, 36, 18, precision="mixed")       # load the kernels
+    chert.traveltime(small, 9, 9, m.dx, d_cls[:729], off, [0], ny=9, workspace=ws, precision="fp32_acc64")
 
     def timed(fn):
         flush.fill_(3)
@@ -367,13 +368,14 @@ def section_3d(flush, n_sources=16):
         torch.cuda.synchronize()
         return r, a.elapsed_time(b) / 1e3
 
-    cache, t_cache = timed(lambda: chert.build_cache_3d(d_classes, nk, modes, 360, 180, precision="fp64"))
+    cache, t_cache = timed(lambda: chert.build_cache_3d(d_classes, nk, modes, 360, 180, precision="mixed"))
     _, t_relax = timed(lambda: chert.traveltime(cache, m.nx, m.nz, m.dx, d_cls, off, src, max_cycles=64,
-                                                out=tau, workspace=ws, ny=m.ny))
+                                                out=tau, workspace=ws, ny=m.ny, precision="fp32_acc64"))
     nf = len(src) * len(modes)
     edges = int(sum((m.nx - abs(int(o[0]))) * (m.ny - abs(int(o[1]))) * (m.nz - abs(int(o[2]))) for o in off))
     return {"workload": "layered_visco_tti_3d_201^3_12layers_%dsrc_qP_qSV_1x1deg_R2" % len(src),
-            "nodes": n, "fields": nf, "precision": "fp64 cache, fp64 traveltimes",
+            "nodes": n, "fields": nf,
+            "precision": "mixed cache (float storage), fp32 weights, float-float traveltime accumulation",
             "cache_entries": nk * len(modes) * 64800, "cache_s": t_cache,
             "cache_entries_per_s": nk * len(modes) * 64800 / t_cache,
             "relax_s": t_relax, "fields_per_s": nf / (t_cache + t_relax),

@@ -16,7 +16,8 @@
  *   - Units are SI: moduli in (m/s)^2 (density normalised), lengths in m,
  *     traveltimes in s, angles in rad.
  *   - Floating-point buffers are double for CHERT_FP64 and float for
- *     CHERT_FP32 / CHERT_MIXED.
+ *     CHERT_FP32 / CHERT_MIXED; with CHERT_FP32_ACC64 (3D traveltimes) the
+ *     cache is float and tauR/tauI are double.
  *   - 2D lattice: node = x + nx*z (z = depth).  3D: node = x + nx*(y + ny*z).
  */
 #ifndef CHERT_H
@@ -46,8 +47,11 @@ extern "C" {
 
 #define CHERT_FP64  0       /* every step in double                            */
 #define CHERT_FP32  1       /* every step in float                             */
-#define CHERT_MIXED 2       /* float scan, double root polish and ray
-                               quantities, float storage and relaxation        */
+#define CHERT_MIXED 2       /* float scan, float-float (~48-bit) root polish and
+                               ray quantities, float storage and relaxation    */
+#define CHERT_FP32_ACC64 3  /* chert_traveltime on 3D lattices only: float
+                               cache and edge weights, traveltimes accumulated
+                               in float-float (~48-bit) and returned as double */
 
 /* One cache class k (a layer, facies, cell or tilt group).  Eq. 2:
  * a = aR - i*aI per Voigt component (a11, a13, a33, a44, a66) of a VTI solid

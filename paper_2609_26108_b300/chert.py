@@ -21,8 +21,8 @@ QP, QSV, QSH = 0, 1, 2
 MODE_IDS = {"qP": QP, "qSV": QSV, "qSH": QSH}
 OEV, MEV = 0, 1
 KERNEL_IDS = {"OEV": OEV, "MEV": MEV}
-FP64, FP32, MIXED = 0, 1, 2
-PRECISION_IDS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
+FP64, FP32, MIXED, FP32_ACC64 = 0, 1, 2, 3
+PRECISION_IDS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED, "fp32_acc64": FP32_ACC64}
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4
 
@@ -138,7 +138,7 @@ def _stream_ptr(stream):
 
 def _fdtype(precision):
     torch = _torch()
-    return torch.float64 if precision == FP64 else torch.float32
+    return torch.float64 if precision in (FP64, FP32_ACC64) else torch.float32
 
 
 # ------------------------------------------------------------------ classes
@@ -306,30 +306,34 @@ def workspace_bytes(n_modes, n_classes, n_off, precision, n_sources, nx=None, nz
 
 
 def traveltime(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64, parents=True,
-               stream=None, out=None, workspace=None, ny=1):
+               stream=None, out=None, workspace=None, ny=1, precision=None):
     """chert_traveltime for all (source, mode) fields of ``cache`` on an
-    nx x ny x nz lattice (ny = 1: 2D).
+    nx x ny x nz lattice (ny = 1: 2D).  precision: the cache's by default;
+    "fp32_acc64" (3D, float cache) accumulates the traveltimes in float-float
+    and returns them as double.
 
     Returns (tauR, tauI, parR, parI) torch tensors [n_sources, n_modes, nz*ny*nx]."""
     torch = _torch()
     off, off_p = _offsets_arr(offsets)
     src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64).reshape(-1))
     nm, ns = len(cache.modes), len(src)
+    prec = cache.precision if precision is None else (PRECISION_IDS[precision] if isinstance(precision, str)
+                                                      else precision)
     dev = cache["V"].device
     shape = (ns, nm, nx * ny * nz)
     if out is None:
-        fd = _fdtype(cache.precision)
+        fd = _fdtype(prec)
         out = (torch.empty(shape, dtype=fd, device=dev), torch.empty(shape, dtype=fd, device=dev),
                torch.empty(shape, dtype=torch.int32, device=dev) if parents else None,
                torch.empty(shape, dtype=torch.int32, device=dev) if parents else None)
     if workspace is None:
-        wsb = (workspace_bytes(nm, cache.n_classes, len(off), cache.precision, ns, nx, nz) if ny == 1
-               else workspace_bytes(nm, cache.n_classes, len(off), cache.precision, ns))
+        wsb = (workspace_bytes(nm, cache.n_classes, len(off), prec, ns, nx, nz) if ny == 1
+               else workspace_bytes(nm, cache.n_classes, len(off), prec, ns))
         workspace = torch.empty(wsb, dtype=torch.uint8, device=dev)
     st = cache.struct()
     _check(lib().chert_traveltime(ctypes.byref(st), nm, cache.n_classes, cache.n_dir, nx, ny, nz,
                                   float(dx), _dev_ptr(d_cls), off_p, len(off),
-                                  src.ctypes.data_as(ctypes.c_void_p), ns, cache.precision,
+                                  src.ctypes.data_as(ctypes.c_void_p), ns, prec,
                                   max_cycles, _dev_ptr(out[0]), _dev_ptr(out[1]), _dev_ptr(out[2]),
                                   _dev_ptr(out[3]), _dev_ptr(workspace), workspace.numel(),
                                   _stream_ptr(stream)))

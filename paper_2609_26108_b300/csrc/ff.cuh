@@ -58,6 +58,12 @@ __device__ __forceinline__ ff operator+(ff a, ff b) {
     return quick_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+// ff + float: the float joins with one two-sum
+__device__ __forceinline__ ff operator+(ff a, float b) {
+    ff s = two_sum(a.hi, b);
+    s.lo += a.lo;
+    return quick_two_sum(s.hi, s.lo);
+}
 
 __device__ __forceinline__ ff operator*(ff a, ff b) {
     ff p = two_prod(a.hi, b.hi);

@@ -21,9 +21,11 @@
 #include <limits.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 #include "common.cuh"
+#include "ff.cuh"
 #include "relax_fast.cuh"
 
 namespace chert {
@@ -330,10 +332,12 @@ __device__ __forceinline__ void stage_planes(T* st, int* sk, const T* tau, const
     }
 }
 
-template <typename T, int WMODE>
-__device__ bool sweep3d(const Smem<T>& sm, const T* __restrict__ gsel, const Offsets& off, const short* qo,
-                        const short* qu, const short* qv, const short* ql, int cnt, int axis, int dir, T* tau,
-                        const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk, int comp, T* st, int* sk,
+// TW: weight type; TA: traveltime accumulation and storage type (double,
+// float, or float-float pairs for float weights with ~48-bit accumulation).
+template <typename TW, typename TA, int WMODE>
+__device__ bool sweep3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const Offsets& off, const short* qo,
+                        const short* qu, const short* qv, const short* ql, int cnt, int axis, int dir, TA* tau,
+                        const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk, int comp, TA* st, int* sk,
                         const Stage3& g) {
     const int nu = axis == 0 ? ny : nx;
     const int nv = axis == 2 ? ny : nz;
@@ -351,14 +355,14 @@ __device__ bool sweep3d(const Smem<T>& sm, const T* __restrict__ gsel, const Off
                 if (threadIdx.x < kTU * kTV && u < nu && v < nv) {
                     const long long j = node3(axis, u, v, p, nx, ny);
                     const int kj = clamp_class(cls[j], nk);
-                    const T cur = tau[j];
-                    T best = cur;
+                    const TA cur = tau[j];
+                    TA best = cur;
                     const int su = u - tu0 + g.H, sv = v - tv0 + g.H;
                     for (int q = 0; q < cnt; ++q) {
                         const int e = (ql[q] - 1) * per + (sv - qv[q]) * g.SU + (su - qu[q]);
-                        const T ti = st[e];
+                        const TA ti = st[e];
                         if (!(ti < best)) continue;
-                        best = fmin(best, ti + pull_weight<T, WMODE>(sm, gsel, off.n, nk, comp, qo[q], sk[e], kj));
+                        best = fmin(best, ti + pull_weight<TW, WMODE>(sm, gsel, off.n, nk, comp, qo[q], sk[e], kj));
                     }
                     if (best < cur) {
                         tau[j] = best;
@@ -372,10 +376,10 @@ __device__ bool sweep3d(const Smem<T>& sm, const T* __restrict__ gsel, const Off
     return __syncthreads_or(changed);
 }
 
-template <typename T, int WMODE>
-__device__ bool verify3d(const Smem<T>& sm, const T* __restrict__ gsel, const Offsets& off, T* tau,
+template <typename TW, typename TA, int WMODE>
+__device__ bool verify3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const Offsets& off, TA* tau,
                          const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk, int comp, int64_t src,
-                         int32_t* par, T* st, int* sk, const Stage3& g) {
+                         int32_t* par, TA* st, int* sk, const Stage3& g) {
     const int per = g.SU * g.SV;
     bool changed = false;
     for (int z = 0; z < nz; ++z) {
@@ -388,17 +392,17 @@ __device__ bool verify3d(const Smem<T>& sm, const T* __restrict__ gsel, const Of
                 if (threadIdx.x < kTU * kTV && x < nx && y < ny) {
                     const long long j = node3(2, x, y, z, nx, ny);
                     const int kj = clamp_class(cls[j], nk);
-                    const T cur = tau[j];
-                    T best = T(INFINITY);
+                    const TA cur = tau[j];
+                    TA best = TA(INFINITY);
                     long long bi = -1;
                     const int sx = x - tx0 + g.H, sy = y - ty0 + g.H;
                     for (int o = 0; o < off.n; ++o) {
                         const int xi = x - off.x[o], yi = y - off.y[o], zi = z - off.z[o];
                         if (xi < 0 || xi >= nx || yi < 0 || yi >= ny || zi < 0 || zi >= nz) continue;
                         const int e = (g.H - off.z[o]) * per + (sy - off.y[o]) * g.SU + (sx - off.x[o]);
-                        const T ti = st[e];
+                        const TA ti = st[e];
                         if (ti > best) continue;
-                        const T c = ti + pull_weight<T, WMODE>(sm, gsel, off.n, nk, comp, o, sk[e], kj);
+                        const TA c = ti + pull_weight<TW, WMODE>(sm, gsel, off.n, nk, comp, o, sk[e], kj);
                         const long long i = node3(2, xi, yi, zi, nx, ny);
                         if (c < best || (c == best && i < bi)) { best = c; bi = i; }
                     }
@@ -406,7 +410,7 @@ __device__ bool verify3d(const Smem<T>& sm, const T* __restrict__ gsel, const Of
                         tau[j] = best;
                         changed = true;
                     } else if (par) {
-                        par[j] = (j == src) ? static_cast<int32_t>(src) : (isinf(cur) ? -1 : (int32_t)bi);
+                        par[j] = (j == src) ? static_cast<int32_t>(src) : (!(cur < TA(INFINITY)) ? -1 : (int32_t)bi);
                     }
                 }
                 __syncthreads();
@@ -423,7 +427,9 @@ __host__ __device__ inline size_t stage3_elems(int H) {
     return (size_t)(2 * H + 1) * (kTU + 2 * H) * (kTV + 2 * H);
 }
 
-template <typename T, int WMODE>
+// TA = xf::ff: float weights, traveltimes accumulated as float-float pairs in
+// the (double) output arrays, converted to double in place at the end.
+template <typename T, typename TA, int WMODE>
 __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, int H) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = a.n_classes;
@@ -440,7 +446,7 @@ __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, 
     sm.W = reinterpret_cast<T*>(p); p += wcount * sizeof(T);
     sm.L = reinterpret_cast<T*>(p); p += off.n * sizeof(T);
     Stage3 g{H, kTU + 2 * H, kTV + 2 * H};
-    T* st = reinterpret_cast<T*>(p); p += stage3_elems(H) * sizeof(T);
+    TA* st = reinterpret_cast<TA*>(p); p += stage3_elems(H) * sizeof(TA);
     int* sk = reinterpret_cast<int*>(p); p += stage3_elems(H) * sizeof(int);
     sm.ring = nullptr;
     sm.cring = nullptr;
@@ -484,22 +490,30 @@ __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, 
         sm.counts[l] = c;
     }
 
-    T* tau = static_cast<T*>(comp == 0 ? a.tauR : a.tauI) + static_cast<size_t>(field) * n;
+    TA* tau = static_cast<TA*>(comp == 0 ? a.tauR : a.tauI) + static_cast<size_t>(field) * n;
     int32_t* par = comp == 0 ? a.parR : a.parI;
     if (par) par += static_cast<size_t>(field) * n;
     const int64_t src = a.src[s];
-    for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
+    for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? TA(0.0f) : TA(INFINITY);
     __syncthreads();
 
     int used = -1;
     for (int cycle = 0; cycle < a.max_cycles; ++cycle) {
         for (int l = 0; l < 6; ++l)
-            sweep3d<T, WMODE>(sm, sel, off, lists + (4 * l) * off.n, lists + (4 * l + 1) * off.n,
+            sweep3d<T, TA, WMODE>(sm, sel, off, lists + (4 * l) * off.n, lists + (4 * l + 1) * off.n,
                               lists + (4 * l + 2) * off.n, lists + (4 * l + 3) * off.n, sm.counts[l], ax[l], dr[l],
                               tau, a.cls, a.nx, a.ny, a.nz, nk, comp, st, sk, g);
-        if (!verify3d<T, WMODE>(sm, sel, off, tau, a.cls, a.nx, a.ny, a.nz, nk, comp, src, par, st, sk, g)) {
+        if (!verify3d<T, TA, WMODE>(sm, sel, off, tau, a.cls, a.nx, a.ny, a.nz, nk, comp, src, par, st, sk, g)) {
             used = cycle + 1;
             break;
+        }
+    }
+    if constexpr (std::is_same<TA, xf::ff>::value) {
+        __syncthreads();
+        double* out = reinterpret_cast<double*>(tau);          // same 8 bytes per node
+        for (size_t j = threadIdx.x; j < n; j += blockDim.x) {
+            const xf::ff v = tau[j];
+            out[j] = double(v.hi) + double(v.lo);
         }
     }
     if (threadIdx.x == 0) a.status[blockIdx.x] = used;
@@ -604,12 +618,12 @@ extern "C" int chert_edge_table(const chert_cache_arrays* cache, int n_modes, in
 }
 
 
-template <typename T, int WMODE>
+template <typename T, int WMODE, typename TA = T>
 static int launch_relax3d(const FieldArgs& a, const Offsets& off, int H, size_t smem, int blocks, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(relax3d_kernel<T, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(relax3d_kernel<T, TA, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
-    relax3d_kernel<T, WMODE><<<blocks, 512, smem, s>>>(a, off, H);
+    relax3d_kernel<T, TA, WMODE><<<blocks, 512, smem, s>>>(a, off, H);
     return launch_check("chert_traveltime: relax3d");
 }
 
@@ -887,8 +901,11 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     CHERT_REQUIRE(n_sources >= 1 && n_modes >= 1 && n_modes <= 3 && n_classes >= 1,
                   "%s: bad counts", who);
     CHERT_REQUIRE(max_cycles >= 1, "%s: max_cycles must be >= 1", who);
-    CHERT_REQUIRE(precision == CHERT_FP64 || precision == CHERT_FP32 || precision == CHERT_MIXED,
+    CHERT_REQUIRE(precision == CHERT_FP64 || precision == CHERT_FP32 || precision == CHERT_MIXED ||
+                      precision == CHERT_FP32_ACC64,
                   "%s: precision=%d", who, precision);
+    CHERT_REQUIRE(precision != CHERT_FP32_ACC64 || ny > 1,
+                  "%s: CHERT_FP32_ACC64 is for 3D lattices (ny > 1)", who);
     for (int i = 0; sources && i < n_sources; i++)
         CHERT_REQUIRE(sources[i] >= 0 && sources[i] < (int64_t)n_nodes,
                       "%s: source %d out of range", who, i);
@@ -913,7 +930,8 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     const size_t m = static_cast<size_t>(n_modes) * n_classes * n_off;
     void* Vsel = w + ws.sel;
     void* Asel = w + ws.sel + m * es;
-    rc = chert_edge_table(cache, n_modes, n_classes, n_dir, precision, offsets, n_off,
+    rc = chert_edge_table(cache, n_modes, n_classes, n_dir, precision == CHERT_FP32_ACC64 ? CHERT_FP32 : precision,
+                          offsets, n_off,
                           reinterpret_cast<int32_t*>(w + ws.idx), Vsel, Asel, s);
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
@@ -945,12 +963,17 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         for (int i = 0; i < n_off; i++)
             H = std::max(H, std::max(abs((int)off.y[i]), std::max(abs((int)off.x[i]), abs((int)off.z[i]))));
         CHERT_REQUIRE(H <= 8, "%s: 3D offsets reach %d nodes (at most 8)", who, H);
-        const size_t base3 = n_off * es + stage3_elems(H) * (es + 4) + 4 * 6 * n_off * 2 + 64;
+        const size_t tas = precision == CHERT_FP32 || precision == CHERT_MIXED ? 4 : 8;   // accumulation type
+        const size_t base3 = n_off * es + stage3_elems(H) * (tas + 4) + 4 * 6 * n_off * 2 + 64;
         const size_t t3 = (size_t)n_off * n_classes * n_classes * es + base3;
         const size_t r3 = (size_t)n_classes * n_off * es + base3;
         const int mode3 = t3 <= (size_t)std::min(smem_max, 160 * 1024) ? 1 : r3 <= (size_t)smem_max ? 0 : 2;
         const size_t sm3 = mode3 == 1 ? t3 : mode3 == 0 ? r3 : base3;
-        if (precision == CHERT_FP64)
+        if (precision == CHERT_FP32_ACC64)
+            rc = mode3 == 1 ? launch_relax3d<float, 1, xf::ff>(a, off, H, sm3, blocks, s)
+               : mode3 == 0 ? launch_relax3d<float, 0, xf::ff>(a, off, H, sm3, blocks, s)
+                            : launch_relax3d<float, 2, xf::ff>(a, off, H, sm3, blocks, s);
+        else if (precision == CHERT_FP64)
             rc = mode3 == 1 ? launch_relax3d<double, 1>(a, off, H, sm3, blocks, s)
                : mode3 == 0 ? launch_relax3d<double, 0>(a, off, H, sm3, blocks, s)
                             : launch_relax3d<double, 2>(a, off, H, sm3, blocks, s);

@@ -176,3 +176,41 @@ def test_full_size_3d_sampled(torch_dev):
         assert np.array_equal(np.isfinite(gt), fin)
         assert np.allclose(gt[fin], rt[fin], rtol=1e-12, atol=0)
         assert np.array_equal(gp, rp)
+
+
+@pytest.mark.parametrize("n_classes", [4, 400])
+def test_relax3d_float_weights_wide_accumulation(torch_dev, n_classes):
+    """CHERT_FP32_ACC64: float cache and weights, float-float accumulation,
+    double output.  Against the oracle's double Dijkstra on the float lookup:
+    each weight carries about two float roundings and the accumulation about
+    2^-47 per hop, so tau is within 4e-7 relative however long the path (FP32
+    accumulation drifts with the hop count); the source and unreachable nodes
+    are exact."""
+    shape = (23, 12, 15)
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    if n_classes == 4:
+        cls = np.minimum((np.arange(n) // (nx * ny)) * 4 // nz, 3).astype(np.int32)
+    else:
+        cls = np.random.default_rng(n_classes + 1).integers(0, n_classes, n).astype(np.int32)
+    cnp, n_az, n_pol = synthetic_cache3d(n_classes, seed=n_classes + 2)
+    nm, nk, _ = cnp["V"].shape
+    cache = chert.Cache(cache_to_torch(cnp, torch_dev.float32, "cuda"), list(range(nm)), nk, 0, chert.FP32,
+                        n_az, n_pol)
+    off = inputs.stencil_3d(2)
+    sources = [3, nx * ny * nz - 5]
+    d_cls = torch_dev.as_tensor(cls, device="cuda")
+    tR, tI, pR, pI = chert.traveltime(cache, nx, nz, 10.0, d_cls, off, sources, ny=ny, precision="fp32_acc64")
+    torch_dev.cuda.synchronize()
+    assert tR.dtype == torch_dev.float64
+    ref = oracle3d_fields(cnp, "fp32", shape, cls, off, sources)
+    for si, s in enumerate(sources):
+        for comp, (t, p) in enumerate([(tR, pR), (tI, pI)]):
+            rt, rp = ref[(s, 0, comp)]
+            gt, gp = t[si, 0].cpu().numpy(), p[si, 0].cpu().numpy()
+            fin = np.isfinite(rt)
+            assert np.array_equal(np.isfinite(gt), fin)
+            pos = fin & (rt > 0)
+            assert np.max(np.abs(gt[pos] - rt[pos]) / rt[pos]) < 4e-7
+            assert gt[s] == 0.0 and gp[s] == s
+            assert np.all(gp[~fin] == -1)
