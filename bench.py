@@ -512,6 +512,8 @@ def run_chert(args):
                 len(model.sources), rcv, scan_step=SCAN_STEP, scan_half=SCAN_HALF)
     tr.set_inputs(d_classes, d_cls, model.sources)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    from paper_2609_26108_b300.pipeline import autotune_points_per_thread
+    ppt, tune_ms = autotune_points_per_thread(tr)          # launch shape of the relaxation (untimed)
 
     def barrier():
         if world > 1:
@@ -579,8 +581,10 @@ def run_chert(args):
     out = {"metric": METRIC, "value": value, "unit": "fields/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": config_dict(model, {"cache_precision": "float scan, double polish, float storage",
-                                         "relax_precision": "fp32", "parallelism": "replicas" if world > 1 else "single"}),
+           "config": config_dict(model, {"cache_precision": "float scan, float-float polish, float storage",
+                                         "relax_precision": "fp32", "parallelism": "replicas" if world > 1 else "single",
+                                         "relax_points_per_thread": ppt,
+                                         "autotune_relax_ms": {str(k): v for k, v in tune_ms.items()}}),
            "cache_entries_per_s": world * entries / cache_avg_s,
            "cache_build_ms": 1e3 * cache_avg_s, "relax_ms": 1e3 * relax_avg_s,
            "edge_relaxations_per_s": world * edges * nf * 2 / relax_avg_s,

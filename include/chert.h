@@ -231,6 +231,14 @@ int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes
                      void* d_tauR, void* d_tauI, int32_t* d_parR, int32_t* d_parI,
                      void* d_workspace, size_t workspace_bytes, void* stream);
 
+/* Launch shape of the 2D relaxation specialised to the standard stencil:
+ * nodes of a line per thread (1, 2 or 4; threads = line length / ppt,
+ * rounded up to a warp, at most 512).  0 (the default) chooses from the line
+ * length; a forced value applies wherever the line fits.  Process-wide (for
+ * an autotuner that times each choice on its problem).  Returns the previous
+ * setting, or CHERT_EINVAL for other values.  Results do not depend on it. */
+int chert_set_relax_points_per_thread(int ppt);
+
 /* The same relaxation as chert_traveltime, enqueued on `stream` without any
  * host synchronisation or host-to-device copy: sources are a device int64
  * array, the offsets travel by value to the kernels, and the convergence

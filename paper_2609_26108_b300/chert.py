@@ -85,6 +85,8 @@ def lib():
     L.chert_traveltime_enqueue.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P, I,
                                            P, I, I, I, P, P, P, P, P, SZ, P, P]
     L.chert_traveltime_enqueue.restype = ctypes.c_int
+    L.chert_set_relax_points_per_thread.argtypes = [I]
+    L.chert_set_relax_points_per_thread.restype = ctypes.c_int
     L.chert_traveltime_static.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P,
                                           I, P, I, I, I, P, P, P, P, P]
     L.chert_traveltime_static_limit.restype = SZ

@@ -21,6 +21,7 @@
 #include <limits.h>
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <mutex>
 
@@ -748,6 +749,11 @@ __global__ void node_weights_kernel(const T* __restrict__ selT, const int32_t* _
     }
 }
 
+// Points per thread of the specialised 2D kernel: 0 = chosen from the line
+// length; 1, 2 or 4 = forced where the line fits in 512 threads (set by
+// chert_set_relax_points_per_thread, e.g. by an autotuner).
+std::atomic<int> g_relax_ppt{0};
+
 // Radius of the standard stencil with n_off entries (0 if none).
 static int standard_radius(int n_off) {
     if (n_off == fast::Stencil<2>::N) return 2;
@@ -813,7 +819,9 @@ static int try_fast_R(fast::Args& a, const Offsets& off, int smem_max, int block
     if (!standard_map<R>(off, a.map)) return 0;
     const int line_max = std::max(a.nx, a.nz);
     if (line_max > 2048) return 0;
-    const int ppt = line_max <= 512 ? 1 : (line_max <= 1024 ? 2 : 4);
+    int ppt = line_max <= 512 ? 1 : (line_max <= 1024 ? 2 : 4);
+    const int forced = g_relax_ppt.load();
+    if ((forced == 1 || forced == 2 || forced == 4) && (line_max + forced - 1) / forced <= 512) ppt = forced;
     const int threads = ((line_max + ppt - 1) / ppt + 31) / 32 * 32;
     size_t smem = fast_smem<R>(a.n_classes, a.nx, a.nz, sizeof(T), false);
     bool pn = false;
@@ -1184,4 +1192,10 @@ extern "C" int chert_raypath(const int32_t* d_par, int n_fields, int64_t n_nodes
     raypath_kernel<<<(unsigned)((n + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
         d_par, n_fields, n_nodes, d_src, d_rcv, n_rcv, cap, d_paths, d_len);
     return launch_check("chert_raypath");
+}
+
+extern "C" int chert_set_relax_points_per_thread(int ppt) {
+    CHERT_REQUIRE(ppt == 0 || ppt == 1 || ppt == 2 || ppt == 4,
+                  "chert_set_relax_points_per_thread: ppt=%d (0, 1, 2 or 4)", ppt);
+    return g_relax_ppt.exchange(ppt);
 }

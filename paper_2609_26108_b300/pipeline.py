@@ -240,3 +240,29 @@ class GraphBatch:
     @property
     def n_fields(self):
         return sum(p.n_fields for p in self.problems)
+
+
+def autotune_points_per_thread(tracer, candidates=(1, 2, 4), repeats=3):
+    """Time the relaxation of ``tracer``'s problem (its full run) with each
+    launch shape of the specialised 2D kernel and keep the fastest for the
+    process (chert_set_relax_points_per_thread).  The results are identical
+    for every shape; only the time differs.  Returns (best, {ppt: ms})."""
+    import torch
+    line = max(tracer.nx, tracer.nz)
+    times = {}
+    for ppt in candidates:
+        if (line + ppt - 1) // ppt > 512:
+            continue
+        chert.lib().chert_set_relax_points_per_thread(ppt)
+        tracer.run()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        best = float("inf")
+        for _ in range(repeats):
+            tracer.run(events=ev)
+            torch.cuda.synchronize()
+            best = min(best, ev[1].elapsed_time(ev[2]))
+        times[ppt] = best
+    choice = min(times, key=times.get)
+    chert.lib().chert_set_relax_points_per_thread(choice)
+    return choice, times

@@ -378,3 +378,25 @@ def test_layered_tti_full_size_sampled_fields(torch_dev):
     assert np.all(tR >= 0)
     for si, s in enumerate(model.sources):
         assert np.all(tR[si, :, s] == 0)
+
+
+def test_launch_shapes_give_identical_fields(torch_dev):
+    """Every points-per-thread choice of the specialised kernel (the
+    autotuner's search space) returns the same fields and parents, bit for
+    bit, including the per-node weight path."""
+    nx, nz = 151, 97
+    cls = inputs.layered_class_map_2d(nx, nz, 5).astype(np.int32)
+    off = inputs.stencil_2d(5)
+    cache = as_cache(torch_dev, small_oracle_cache(), "fp32")
+    lib = chert.lib()
+    outs = {}
+    try:
+        for ppt in (1, 2, 4):
+            lib.chert_set_relax_points_per_thread(ppt)
+            outs[ppt] = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, [0, 77, nx * nz - 1])
+    finally:
+        lib.chert_set_relax_points_per_thread(0)
+    for ppt in (2, 4):
+        for a, b in zip(outs[1], outs[ppt]):
+            assert np.array_equal(a, b)
+    assert lib.chert_set_relax_points_per_thread(3) == chert.EINVAL
