@@ -10,7 +10,12 @@ stencil (80 offsets), 64 surface sources.  One step runs the whole hot path:
 cache build (8,640 entries), direction lookup, propagation and attenuation
 relaxation of 192 (source, mode) fields with parents, and raypaths to 41
 surface receivers per field.  The cache is built with a float scan and a
-double root polish (float storage); lookup and relaxation run in float.
+float-float (~48-bit) root polish (float storage); lookup and relaxation run
+in float.  Before the timed steps the relaxation's launch shape is autotuned.
+
+Further sections (added to the same JSON line): the plain-vs-surrogate
+comparison on the per-cell 1701x351 model, the 201^3 3D model, and, on
+request, the cache angular-step study and the CUDA-graph batch.
 
 `value` is traveltime fields per second (a field = one (source, mode) pair
 with both tau^R and tau^I and their parents); `e2e` is the same through the

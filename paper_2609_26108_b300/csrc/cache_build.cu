@@ -12,6 +12,11 @@
 // first acceptable root returns exactly the root a full scan of the grid
 // would select.  The ray quantities of Eq. 10-11 are then written to the up to
 // four mirrored entries of the full circle and rotated by the tilt (Eq. 36).
+// In 3D (chert_build_cache_3d) each global slowness direction is one solve in
+// the sagittal plane of the class's symmetry-axis frame (Eq. 35), and its ray
+// is turned back to the global frame.  Precisions: FP64 (all double), FP32
+// (all float) and MIXED (float scan and polish, then a float-float refinement
+// of the accepted root and its ray quantities, float storage).
 //
 // Velocity kernels, for n = (sin(theta + i vartheta), 0, cos(theta + i vartheta))
 // (Eq. 7) and the 2x2 x-z block of the Christoffel matrix (Eq. 4):
