@@ -377,6 +377,17 @@ def section_3d(flush, n_sources=16):
     _, t_relax = timed(lambda: chert.traveltime(cache, m.nx, m.nz, m.dx, d_cls, off, src, max_cycles=64,
                                                 out=tau, workspace=ws, ny=m.ny, precision="fp32_acc64"))
     nf = len(src) * len(modes)
+    # receiver gathers (survey NEXT-1): a 21 x 21 surface grid per field, both components
+    g = np.round(np.linspace(0, m.nx - 1, 21)).astype(np.int64)
+    rcv = torch.as_tensor(np.array([x + m.nx * y for y in g for x in g], dtype=np.int64), device="cuda")
+    fsrc = torch.as_tensor(np.repeat(np.asarray(src, np.int64), len(modes)), device="cuda")
+    cap = 3 * m.nx
+
+    def gathers():
+        return [chert.raypath(tau[2 + c].reshape(nf, -1), fsrc, rcv, cap) for c in (0, 1)]
+
+    paths, t_paths = timed(gathers)
+    n_ok = int(sum(int((p[1] > 0).sum()) for p in paths))
     edges = int(sum((m.nx - abs(int(o[0]))) * (m.ny - abs(int(o[1]))) * (m.nz - abs(int(o[2]))) for o in off))
     return {"workload": "layered_visco_tti_3d_201^3_12layers_%dsrc_qP_qSV_1x1deg_R2" % len(src),
             "nodes": n, "fields": nf,
@@ -384,6 +395,8 @@ def section_3d(flush, n_sources=16):
             "cache_entries": nk * len(modes) * 64800, "cache_s": t_cache,
             "cache_entries_per_s": nk * len(modes) * 64800 / t_cache,
             "relax_s": t_relax, "fields_per_s": nf / (t_cache + t_relax),
+            "raypaths": {"receivers_per_field": int(rcv.numel()), "paths": 2 * nf * int(rcv.numel()),
+                         "traced": n_ok, "s": t_paths},
             "edge_relaxations_per_s": edges * nf * 2 / t_relax, "directed_edges_per_field": edges}
 
 
