@@ -457,6 +457,47 @@ def section_angular(n_sources=8, steps_deg=(0.5, 1.0, 2.0, 5.0, 10.0)):
                         % (len(model.sources), list(steps_deg)), "reference": "0.5 deg fields", "rows": rows}
 
 
+# --------------------------------------------------------------- scheduler study
+def section_scheduler(n_sources=16, reps=3):
+    """Block-heap marching (Eq. 32) against the sweep scheduler on the layered
+    401x401 model: n_sources surface sources x 3 modes, MIXED cache, FP32
+    relaxation with parents.  Per scheduler the best of `reps` timed
+    relaxations (after one untimed), and whether the two return the same
+    fields and parents bit for bit."""
+    import torch
+    from paper_2609_26108_b300 import chert
+
+    model = inputs.layered_tti(n_sources=n_sources)
+    off = inputs.stencil_2d(RADIUS)
+    d_classes = chert.classes_to_device(chert.classes_from_layers(model.layers))
+    d_cls = torch.as_tensor(model.class_of_node.astype(np.int32), device="cuda")
+    cache = chert.build_cache(d_classes, len(model.layers), MODES, M_PER_QUADRANT, SCAN_STEP, SCAN_HALF,
+                              "MEV", "mixed")
+    res, outs = {}, {}
+    try:
+        for name in ("sweeps", "block_heap"):
+            chert.set_relax_scheduler(name)
+            run = lambda: chert.traveltime(cache, model.nx, model.nz, model.dx, d_cls, off, model.sources,
+                                           max_cycles=128)
+            outs[name] = [t.clone() for t in run()]
+            best = None
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record()
+                run()
+                b.record()
+                torch.cuda.synchronize()
+                best = a.elapsed_time(b) if best is None else min(best, a.elapsed_time(b))
+            res[name + "_ms"] = best
+    finally:
+        chert.set_relax_scheduler("sweeps")
+    res["identical"] = all(bool(torch.equal(x, y)) for x, y in zip(outs["sweeps"], outs["block_heap"]))
+    res["block_heap_over_sweeps"] = res["block_heap_ms"] / res["sweeps_ms"]
+    res["workload"] = "layered_visco_tti_2d_401x401_8layers_%dsrc_3modes_1deg_R5, fp32 relaxation" % n_sources
+    return res
+
+
 # --------------------------------------------------------------- batch
 def section_batch(n2d, n3d):
     """Several problems of uneven size in one CUDA graph (the batched form):
@@ -616,6 +657,8 @@ def run_chert(args):
         out["lattice_3d"] = section_3d(flush, args.sources_3d)
     if world == 1 and args.angular_study:
         out["angular_study"] = section_angular()
+    if world == 1 and args.scheduler_study > 0:
+        out["scheduler_study"] = section_scheduler(args.scheduler_study)
     if world == 1 and args.batch_sources > 0:
         out["batch"] = section_batch(args.batch_sources, args.batch_sources_3d)
     if world == 1 and not args.no_cpu_baseline:
@@ -648,6 +691,8 @@ def main():
                     help="sources of the 201^3 3D section (0: leave it out)")
     ap.add_argument("--surrogate-sources", type=int, default=16,
                     help="sources of the per-cell plain-vs-surrogate comparison (0: leave it out)")
+    ap.add_argument("--scheduler-study", type=int, default=0,
+                    help="sources of the block-heap vs sweep scheduler comparison on the layered model (0: leave it out)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -239,6 +239,15 @@ int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes
  * setting, or CHERT_EINVAL for other values.  Results do not depend on it. */
 int chert_set_relax_points_per_thread(int ppt);
 
+/* Scheduler of the 2D relaxation, process-wide: 0 (default) ordered sweep
+ * cycles; 1 the paper's block-heap marching (Eq. 32): 32 x 32 node blocks
+ * keyed by the least traveltime that may still propagate from them, the
+ * smallest taken next and relaxed inside to local convergence, its
+ * neighbours re-keyed.  Both return the same fixed point of Eq. 31 and the
+ * same parents; they differ in the work done.  Returns the previous setting,
+ * or CHERT_EINVAL. */
+int chert_set_relax_scheduler(int scheduler);
+
 /* The same relaxation as chert_traveltime, enqueued on `stream` without any
  * host synchronisation or host-to-device copy: sources are a device int64
  * array, the offsets travel by value to the kernels, and the convergence

@@ -87,6 +87,8 @@ def lib():
     L.chert_traveltime_enqueue.restype = ctypes.c_int
     L.chert_set_relax_points_per_thread.argtypes = [I]
     L.chert_set_relax_points_per_thread.restype = ctypes.c_int
+    L.chert_set_relax_scheduler.argtypes = [I]
+    L.chert_set_relax_scheduler.restype = ctypes.c_int
     L.chert_traveltime_static.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P,
                                           I, P, I, I, I, P, P, P, P, P]
     L.chert_traveltime_static_limit.restype = SZ
@@ -382,6 +384,21 @@ def traveltime_static(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64,
                                          max_cycles, _dev_ptr(out[0]), _dev_ptr(out[1]),
                                          _dev_ptr(out[2]), _dev_ptr(out[3]), _stream_ptr(stream)))
     return out
+
+
+SCHEDULERS = {"sweeps": 0, "block_heap": 1}
+
+
+def set_relax_scheduler(name):
+    """Scheduler of every later 2D relaxation in this process: "sweeps" (the
+    default, ordered sweep cycles) or "block_heap" (block-heap marching of
+    Eq. 32).  Both return the same fields and parents.  Returns the previous
+    name."""
+    if name not in SCHEDULERS:
+        raise ValueError("scheduler %r: one of %s" % (name, sorted(SCHEDULERS)))
+    prev = lib().chert_set_relax_scheduler(SCHEDULERS[name])
+    _check(prev if prev < 0 else 0)
+    return {v: k for k, v in SCHEDULERS.items()}[prev]
 
 
 def raypath(par, sources, receivers, cap=4096, stream=None, out=None):

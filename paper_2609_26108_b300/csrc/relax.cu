@@ -286,6 +286,163 @@ __global__ void __launch_bounds__(512) relax_kernel(FieldArgs a, Offsets off) {
     if (threadIdx.x == 0) a.status[blockIdx.x] = used;
 }
 
+// ------------------------------------------------------------ block-heap marching
+// The paper's block scheduler (Eq. 32): a block's key is the least traveltime
+// that may still propagate from it; the block with the smallest key is taken
+// next, relaxed inside (every node pulls all its in-neighbours, repeatedly,
+// until nothing in the block changes), and the 3 x 3 blocks around it are
+// re-keyed with the least value it lowered.  When no block is dirty, every
+// block has been relaxed after its neighbours' last change: the field is the
+// fixed point of Eq. 31 (the same one the sweeps reach).  The verification
+// pass then writes the parents.  Blocks are 32 x 32 tiles; one CTA per field
+// component; the priority queue is a block-wide argmin over the tile keys in
+// shared memory (ties to the lower tile index).
+constexpr int kBT = 32;
+
+template <typename T>
+__device__ __forceinline__ void block_argmin(T v, int i, T* rv, int* ri, T& out_v, int& out_i) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const T v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        if (v2 < v || (v2 == v && i2 >= 0 && (i < 0 || i2 < i))) { v = v2; i = i2; }
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { rv[w] = v; ri[w] = i; }
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? rv[lane] : T(INFINITY);
+        i = lane < (int)(blockDim.x >> 5) ? ri[lane] : -1;
+        for (int o = 16; o > 0; o >>= 1) {
+            const T v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+            if (v2 < v || (v2 == v && i2 >= 0 && (i < 0 || i2 < i))) { v = v2; i = i2; }
+        }
+        if (lane == 0) { rv[0] = v; ri[0] = i; }
+    }
+    __syncthreads();
+    out_v = rv[0];
+    out_i = ri[0];
+    __syncthreads();
+}
+
+template <typename T, int WMODE>
+__global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nk = a.n_classes;
+    const int field = blockIdx.x >> 1;
+    const int comp = blockIdx.x & 1;
+    const int mode = field % a.n_modes;
+    const int s = field / a.n_modes;
+    const int nx = a.nx, nz = a.nz;
+    const size_t n = static_cast<size_t>(nx) * nz;
+    const int TX = (nx + kBT - 1) / kBT, TZ = (nz + kBT - 1) / kBT, nt = TX * TZ;
+
+    Smem<T> sm;
+    unsigned char* p = smem_raw;
+    const size_t wcount = WMODE == 1 ? static_cast<size_t>(off.n) * nk * nk
+                          : WMODE == 0 ? static_cast<size_t>(nk) * off.n : 0;
+    sm.W = reinterpret_cast<T*>(p); p += wcount * sizeof(T);
+    sm.L = reinterpret_cast<T*>(p); p += off.n * sizeof(T);
+    T* key = reinterpret_cast<T*>(p); p += (size_t)nt * sizeof(T);
+    T* rv = reinterpret_cast<T*>(p); p += 32 * sizeof(T);
+    int* ri = reinterpret_cast<int*>(p);
+    sm.ring = nullptr;
+    sm.cring = nullptr;
+    sm.lists = nullptr;
+    sm.counts = nullptr;
+
+    const T* sel = static_cast<const T*>(comp == 0 ? a.Vsel : a.Asel) + static_cast<size_t>(mode) * nk * off.n;
+    for (int o = threadIdx.x; o < off.n; o += blockDim.x) {
+        const double ox = off.x[o], oz = off.z[o];
+        sm.L[o] = T(a.dx * sqrt(ox * ox + oz * oz));
+    }
+    __syncthreads();
+    if (WMODE == 1) {
+        for (int t = threadIdx.x; t < off.n * nk * nk; t += blockDim.x) {
+            const int kj = t % nk, ki = (t / nk) % nk, o = t / (nk * nk);
+            sm.W[t] = edge_w<T>(comp, sm.L[o], sel[ki * off.n + o], sel[kj * off.n + o]);
+        }
+    } else if (WMODE == 0) {
+        for (int t = threadIdx.x; t < nk * off.n; t += blockDim.x) sm.W[t] = sel[t];
+    }
+    T* tau = static_cast<T*>(comp == 0 ? a.tauR : a.tauI) + static_cast<size_t>(field) * n;
+    int32_t* par = comp == 0 ? a.parR : a.parI;
+    if (par) par += static_cast<size_t>(field) * n;
+    const int64_t src = a.src[s];
+    for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
+    for (int t = threadIdx.x; t < nt; t += blockDim.x)
+        key[t] = t == (int)((src % nx) / kBT + (src / nx) / kBT * TX) ? T(0) : T(INFINITY);
+    __syncthreads();
+
+    const long long max_pops = (long long)a.max_cycles * nt * 8;
+    long long pops = 0;
+    int used = -1;
+    for (int cycle = 0; cycle < a.max_cycles && pops <= max_pops; ++cycle) {
+        for (;;) {
+            T bv = T(INFINITY);
+            int bi = -1;
+            for (int t = threadIdx.x; t < nt; t += blockDim.x)
+                if (key[t] < bv) { bv = key[t]; bi = t; }
+            T kv;
+            int kt;
+            block_argmin(bv, bi, rv, ri, kv, kt);
+            if (kt < 0 || ++pops > max_pops) break;
+            if (threadIdx.x == 0) key[kt] = T(INFINITY);
+            __syncthreads();
+            const int x0 = (kt % TX) * kBT, z0 = (kt / TX) * kBT;
+            T lowered = T(INFINITY);
+            bool still = false;
+            for (int it = 0; it < 4 * kBT; ++it) {          // relax the block to local convergence
+                bool any = false;
+                for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
+                    const int x = x0 + q % kBT, z = z0 + q / kBT;
+                    if (x >= nx || z >= nz) continue;
+                    const size_t j = (size_t)x + (size_t)nx * z;
+                    const int kj = clamp_class(a.cls[j], nk);
+                    const T cur = tau[j];
+                    T best = cur;
+                    for (int o = 0; o < off.n; ++o) {
+                        const int xi = x - off.x[o], zi = z - off.z[o];
+                        if (xi < 0 || xi >= nx || zi < 0 || zi >= nz) continue;
+                        const size_t i = (size_t)xi + (size_t)nx * zi;
+                        const T ti = tau[i];
+                        if (!(ti < best)) continue;
+                        const int ki = clamp_class(a.cls[i], nk);
+                        best = fmin(best, ti + pull_weight<T, WMODE>(sm, sel, off.n, nk, comp, o, ki, kj));
+                    }
+                    if (best < cur) {
+                        tau[j] = best;
+                        any = true;
+                        lowered = fmin(lowered, best);
+                    }
+                }
+                still = __syncthreads_or(any);
+                if (!still) break;
+            }
+            T m;
+            int dummy;
+            block_argmin(lowered, 0, rv, ri, m, dummy);
+            if (m < T(INFINITY) && threadIdx.x < 9) {
+                const int tx = kt % TX + (int)threadIdx.x % 3 - 1, tz = kt / TX + (int)threadIdx.x / 3 - 1;
+                const bool self = threadIdx.x == 4;
+                if (tx >= 0 && tx < TX && tz >= 0 && tz < TZ && (!self || still)) {
+                    T* kk = key + tz * TX + tx;
+                    *kk = fmin(*kk, m);
+                }
+            }
+            __syncthreads();
+        }
+        if (pops > max_pops) break;
+        if (!verify<T, WMODE>(sm, sel, off, tau, a.cls, nx, nz, nk, comp, src, par)) {
+            used = cycle + 1;
+            break;
+        }
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) key[t] = T(0);   // rare: start over everywhere
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.status[blockIdx.x] = used;
+}
+
 // ------------------------------------------------------------ 3D relaxation
 // A 3D lattice (node x + nx*(y + ny*z)) is relaxed by plane sweeps: a cycle
 // runs the planes of constant z upward, of constant y and of constant x in
@@ -629,6 +786,15 @@ static int launch_relax3d(const FieldArgs& a, const Offsets& off, int H, size_t 
 }
 
 template <typename T, int WMODE>
+static int launch_bhm(const FieldArgs& a, const Offsets& off, size_t smem, int blocks, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(relax_bhm_kernel<T, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
+    relax_bhm_kernel<T, WMODE><<<blocks, 512, smem, s>>>(a, off);
+    return launch_check("chert_traveltime: block heap");
+}
+
+template <typename T, int WMODE>
 static int launch_relax(const FieldArgs& a, const Offsets& off, size_t smem, int blocks,
                         cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(relax_kernel<T, WMODE>,
@@ -753,6 +919,8 @@ __global__ void node_weights_kernel(const T* __restrict__ selT, const int32_t* _
 // length; 1, 2 or 4 = forced where the line fits in 512 threads (set by
 // chert_set_relax_points_per_thread, e.g. by an autotuner).
 std::atomic<int> g_relax_ppt{0};
+// 2D scheduler: 0 = ordered sweeps (default), 1 = block-heap marching.
+std::atomic<int> g_relax_sched{0};
 
 // Radius of the standard stencil with n_off entries (0 if none).
 static int standard_radius(int n_off) {
@@ -994,6 +1162,25 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         *status_out = a.status;
         return CHERT_OK;
     }
+    if (g_relax_sched.load() == 1 && R < kBT) {      // 2D block-heap marching
+        const size_t nt = (size_t)((nx + kBT - 1) / kBT) * ((nz + kBT - 1) / kBT);
+        const size_t baseb = n_off * es + nt * es + 32 * (es + 4) + 64;
+        const size_t tb = (size_t)n_off * n_classes * n_classes * es + baseb;
+        const size_t rb = (size_t)n_classes * n_off * es + baseb;
+        const int mb = tb <= (size_t)std::min(smem_max, 160 * 1024) ? 1 : rb <= (size_t)smem_max ? 0 : 2;
+        const size_t smb = mb == 1 ? tb : mb == 0 ? rb : baseb;
+        CHERT_REQUIRE(smb <= (size_t)smem_max, "%s: lattice too large for the block scheduler", who);
+        if (precision == CHERT_FP64)
+            rc = mb == 1 ? launch_bhm<double, 1>(a, off, smb, blocks, s)
+               : mb == 0 ? launch_bhm<double, 0>(a, off, smb, blocks, s) : launch_bhm<double, 2>(a, off, smb, blocks, s);
+        else
+            rc = mb == 1 ? launch_bhm<float, 1>(a, off, smb, blocks, s)
+               : mb == 0 ? launch_bhm<float, 0>(a, off, smb, blocks, s) : launch_bhm<float, 2>(a, off, smb, blocks, s);
+        if (rc) return rc;
+        *blocks_out = blocks;
+        *status_out = a.status;
+        return CHERT_OK;
+    }
     const int line_max = std::max(nx, nz);
     const size_t common = n_off * es + (size_t)a.ring * line_max * (es + 4) + 4 * n_off * 2 + 32;
     const size_t smem_table = (size_t)n_off * n_classes * n_classes * es + common;
@@ -1198,4 +1385,9 @@ extern "C" int chert_set_relax_points_per_thread(int ppt) {
     CHERT_REQUIRE(ppt == 0 || ppt == 1 || ppt == 2 || ppt == 4,
                   "chert_set_relax_points_per_thread: ppt=%d (0, 1, 2 or 4)", ppt);
     return g_relax_ppt.exchange(ppt);
+}
+
+extern "C" int chert_set_relax_scheduler(int scheduler) {
+    CHERT_REQUIRE(scheduler == 0 || scheduler == 1, "chert_set_relax_scheduler: scheduler=%d (0 or 1)", scheduler);
+    return g_relax_sched.exchange(scheduler);
 }

@@ -1,0 +1,131 @@
+"""Block-heap marching (Eq. 32) against the sweep scheduler and the oracle.
+
+Both schedulers stop only at the fixed point of Eq. 31, which is unique: a
+node's value is the least rounded path sum, whatever order the edges are
+relaxed in, and its parent the least-index argmin there.  So the two must give
+the same fields and parents bit for bit, in either precision; FP64 is also
+checked against the oracle's Dijkstra."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_26108_b300 import chert, inputs
+
+from test_gpu_relax import (_check_fields, _serpentine, _synthetic_cache, as_cache, oracle_fields, run_gpu,
+                            small_oracle_cache)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    from paper_2609_26108_b300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def both(torch, cache, nx, nz, cls, off, src, max_cycles=256, dx=10.0):
+    out = {}
+    try:
+        for name in ("sweeps", "block_heap"):
+            chert.set_relax_scheduler(name)
+            out[name] = run_gpu(torch, cache, nx, nz, dx, cls, off, src, max_cycles)
+    finally:
+        chert.set_relax_scheduler("sweeps")
+    for a, b in zip(out["sweeps"], out["block_heap"]):
+        assert np.array_equal(a, b)
+    return out["block_heap"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_layered_equals_sweeps(torch_dev, precision):
+    """Five-class layered lattice of 5 x 4 blocks with ragged edges, R = 5
+    stencil (class-pair table in shared memory), sources at a corner, inside
+    and at the opposite corner."""
+    nx, nz = 151, 97
+    cls = inputs.layered_class_map_2d(nx, nz, 5).astype(np.int32)
+    off = inputs.stencil_2d(5)
+    cache = as_cache(torch_dev, small_oracle_cache(), precision)
+    src = [0, 77 + nx * 40, nx * nz - 1]
+    g = both(torch_dev, cache, nx, nz, cls, off, src)
+    if precision == "fp64":
+        ref = oracle_fields(small_oracle_cache(), precision, (nx, 1, nz), 10.0, cls, off, src)
+        _check_fields(g, ref, src, 2, precision, (nx, 1, nz), 10.0, cls, off, small_oracle_cache())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_serpentine_many_block_passes(torch_dev, precision):
+    """A fast channel with 12 bends across 9 x 4 blocks: blocks are taken
+    many times each, in an order set by the keys; the oracle's field and
+    parents all the same."""
+    nx, nz = 280, 120
+    cls = _serpentine(nx, nz, 12)
+    cnp = _synthetic_cache([150.0, 6000.0], [1e-3, 1e-5])
+    off = inputs.stencil_2d(3)
+    src = [2 + nx * 1]
+    g = both(torch_dev, as_cache(torch_dev, cnp, precision), nx, nz, cls, off, src)
+    ref = oracle_fields(cnp, precision, (nx, 1, nz), 10.0, cls, off, src)
+    _check_fields(g, ref, src, 1, precision, (nx, 1, nz), 10.0, cls, off, cnp)
+
+
+def test_one_class_per_node_global_tables(torch_dev):
+    """One class per node: the looked-up tables stay in global memory."""
+    nx, nz = 150, 70
+    n = nx * nz
+    rng = np.random.default_rng(43)
+    M = 6
+    nd = 4 * M
+    th = (math.pi / 2) * np.arange(nd) / M
+    chan = _serpentine(nx, nz, 6).astype(bool)
+    v0 = np.where(chan, 5200.0, 1400.0) * rng.uniform(0.97, 1.03, n)
+    aniso = rng.uniform(-0.15, 0.15, n)
+    V = v0[:, None] * (1 + aniso[:, None] * np.cos(2 * th)[None])
+    a0 = np.where(chan, 1e-5, 3e-4) * rng.uniform(0.9, 1.1, n)
+    cnp = {"V": V[None], "A": (a0[:, None] * np.ones(nd))[None],
+           "rx": np.tile(np.sin(th), (1, n, 1)), "rz": np.tile(np.cos(th), (1, n, 1)),
+           "theta": np.tile(th, (1, n, 1)), "vartheta": np.zeros((1, n, nd)),
+           "flag": np.zeros((1, n, nd), np.uint8)}
+    cnp["Q"] = np.full_like(cnp["V"], np.inf)
+    off = inputs.stencil_2d(5)
+    cls = np.arange(n, dtype=np.int32)
+    src = [2 + nx * 1, 77 + nx * 40]
+    for precision in ("fp64", "fp32"):
+        g = both(torch_dev, as_cache(torch_dev, cnp, precision), nx, nz, cls, off, src)
+        if precision == "fp64":
+            ref = oracle_fields(cnp, precision, (nx, 1, nz), 10.0, cls, off, src)
+            _check_fields(g, ref, src, 1, precision, (nx, 1, nz), 10.0, cls, off, cnp)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 40), (40, 1), (33, 2), (32, 32), (65, 33)])
+def test_degenerate_and_ragged_lattices(torch_dev, shape):
+    """Single node, single row or column, one block plus a one-node tail."""
+    nx, nz = shape
+    cls = (np.arange(nx * nz) % 2).astype(np.int32)
+    cnp = _synthetic_cache([2000.0, 3000.0], [1e-4, 2e-4])
+    off = inputs.stencil_2d(2)
+    src = [0, nx * nz - 1]
+    both(torch_dev, as_cache(torch_dev, cnp, "fp64"), nx, nz, cls, off, src)
+
+
+def test_unreachable_nodes_keep_infinity(torch_dev):
+    """Offsets that move two columns at a time never reach the odd columns:
+    those stay +inf with parent -1 under both schedulers, across several
+    blocks."""
+    nx, nz = 90, 40
+    off = np.array([(2, 0, 0), (-2, 0, 0), (0, 0, 1), (0, 0, -1)], np.int32)
+    cls = np.zeros(nx * nz, np.int32)
+    cnp = _synthetic_cache([3000.0], [2e-5])
+    tR, _, pR, _ = both(torch_dev, as_cache(torch_dev, cnp, "fp64"), nx, nz, cls, off, [4])
+    odd = (np.arange(nx * nz) % nx) % 2 == 1
+    assert np.all(np.isinf(tR[0, 0, odd])) and np.all(pR[0, 0, odd] == -1)
+    assert np.all(np.isfinite(tR[0, 0, ~odd]))
+
+
+def test_scheduler_switch_rejects_unknown(torch_dev):
+    with pytest.raises(ValueError):
+        chert.set_relax_scheduler("heap")
+    assert chert.lib().chert_set_relax_scheduler(2) == chert.EINVAL
+    assert chert.set_relax_scheduler("sweeps") == "sweeps"
