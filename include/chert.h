@@ -243,9 +243,12 @@ int chert_set_relax_points_per_thread(int ppt);
  * cycles; 1 the paper's block-heap marching (Eq. 32): 32 x 32 node blocks
  * keyed by the least traveltime that may still propagate from them, the
  * smallest taken next and relaxed inside to local convergence, its
- * neighbours re-keyed.  Both return the same fixed point of Eq. 31 and the
- * same parents; they differ in the work done.  Returns the previous setting,
- * or CHERT_EINVAL. */
+ * neighbours re-keyed; each block is staged with a halo of the stencil's
+ * reach in shared memory while it is relaxed.  Both return the same fixed
+ * point of Eq. 31 and the same parents; they differ in the work done.  Under
+ * scheduler 1, a 2D chert_traveltime whose stencil reaches more than 8 nodes
+ * returns CHERT_EINVAL (3D lattices always sweep).  Returns the previous
+ * setting, or CHERT_EINVAL. */
 int chert_set_relax_scheduler(int scheduler);
 
 /* The same relaxation as chert_traveltime, enqueued on `stream` without any

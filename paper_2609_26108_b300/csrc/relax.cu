@@ -325,8 +325,13 @@ __device__ __forceinline__ void block_argmin(T v, int i, T* rv, int* ri, T& out_
     __syncthreads();
 }
 
+// Window of one block in shared memory: the block's kBT x kBT nodes and a
+// halo of H nodes (the stencil's reach) on every side, H <= kBH; positions
+// off the lattice hold +inf, so no pull needs a bounds check.
+constexpr int kBH = 8;
+
 template <typename T, int WMODE>
-__global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off) {
+__global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off, int H) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = a.n_classes;
     const int field = blockIdx.x >> 1;
@@ -336,6 +341,7 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
     const int nx = a.nx, nz = a.nz;
     const size_t n = static_cast<size_t>(nx) * nz;
     const int TX = (nx + kBT - 1) / kBT, TZ = (nz + kBT - 1) / kBT, nt = TX * TZ;
+    const int SW = kBT + 2 * H;
 
     Smem<T> sm;
     unsigned char* p = smem_raw;
@@ -345,6 +351,9 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
     sm.L = reinterpret_cast<T*>(p); p += off.n * sizeof(T);
     T* key = reinterpret_cast<T*>(p); p += (size_t)nt * sizeof(T);
     T* rv = reinterpret_cast<T*>(p); p += 32 * sizeof(T);
+    T* wt = reinterpret_cast<T*>(p); p += (size_t)SW * SW * sizeof(T);
+    int* wk = reinterpret_cast<int*>(p); p += (size_t)SW * SW * 4;
+    int* ws = reinterpret_cast<int*>(p); p += off.n * 4;      // window shift of each offset
     int* ri = reinterpret_cast<int*>(p);
     sm.ring = nullptr;
     sm.cring = nullptr;
@@ -355,6 +364,7 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
     for (int o = threadIdx.x; o < off.n; o += blockDim.x) {
         const double ox = off.x[o], oz = off.z[o];
         sm.L[o] = T(a.dx * sqrt(ox * ox + oz * oz));
+        ws[o] = off.x[o] + off.z[o] * SW;
     }
     __syncthreads();
     if (WMODE == 1) {
@@ -387,9 +397,16 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
             int kt;
             block_argmin(bv, bi, rv, ri, kv, kt);
             if (kt < 0 || ++pops > max_pops) break;
+            const int x0 = (kt % TX) * kBT, z0 = (kt / TX) * kBT;
+            for (int q = threadIdx.x; q < SW * SW; q += blockDim.x) {      // stage the window
+                const int x = x0 - H + q % SW, z = z0 - H + q / SW;
+                const bool in = x >= 0 && x < nx && z >= 0 && z < nz;
+                const size_t g = in ? (size_t)x + (size_t)nx * z : 0;
+                wt[q] = in ? tau[g] : T(INFINITY);
+                wk[q] = in ? clamp_class(a.cls[g], nk) : 0;
+            }
             if (threadIdx.x == 0) key[kt] = T(INFINITY);
             __syncthreads();
-            const int x0 = (kt % TX) * kBT, z0 = (kt / TX) * kBT;
             T lowered = T(INFINITY);
             bool still = false;
             for (int it = 0; it < 4 * kBT; ++it) {          // relax the block to local convergence
@@ -397,27 +414,27 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
                 for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
                     const int x = x0 + q % kBT, z = z0 + q / kBT;
                     if (x >= nx || z >= nz) continue;
-                    const size_t j = (size_t)x + (size_t)nx * z;
-                    const int kj = clamp_class(a.cls[j], nk);
-                    const T cur = tau[j];
+                    const int e = (q % kBT + H) + (q / kBT + H) * SW;
+                    const int kj = wk[e];
+                    const T cur = wt[e];
                     T best = cur;
                     for (int o = 0; o < off.n; ++o) {
-                        const int xi = x - off.x[o], zi = z - off.z[o];
-                        if (xi < 0 || xi >= nx || zi < 0 || zi >= nz) continue;
-                        const size_t i = (size_t)xi + (size_t)nx * zi;
-                        const T ti = tau[i];
+                        const T ti = wt[e - ws[o]];
                         if (!(ti < best)) continue;
-                        const int ki = clamp_class(a.cls[i], nk);
-                        best = fmin(best, ti + pull_weight<T, WMODE>(sm, sel, off.n, nk, comp, o, ki, kj));
+                        best = fmin(best, ti + pull_weight<T, WMODE>(sm, sel, off.n, nk, comp, o, wk[e - ws[o]], kj));
                     }
                     if (best < cur) {
-                        tau[j] = best;
+                        wt[e] = best;
                         any = true;
                         lowered = fmin(lowered, best);
                     }
                 }
                 still = __syncthreads_or(any);
                 if (!still) break;
+            }
+            for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {     // write the block back
+                const int x = x0 + q % kBT, z = z0 + q / kBT;
+                if (x < nx && z < nz) tau[(size_t)x + (size_t)nx * z] = wt[(q % kBT + H) + (q / kBT + H) * SW];
             }
             T m;
             int dummy;
@@ -786,11 +803,11 @@ static int launch_relax3d(const FieldArgs& a, const Offsets& off, int H, size_t 
 }
 
 template <typename T, int WMODE>
-static int launch_bhm(const FieldArgs& a, const Offsets& off, size_t smem, int blocks, cudaStream_t s) {
+static int launch_bhm(const FieldArgs& a, const Offsets& off, int H, size_t smem, int blocks, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(relax_bhm_kernel<T, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
-    relax_bhm_kernel<T, WMODE><<<blocks, 512, smem, s>>>(a, off);
+    relax_bhm_kernel<T, WMODE><<<blocks, 512, smem, s>>>(a, off, H);
     return launch_check("chert_traveltime: block heap");
 }
 
@@ -1162,20 +1179,24 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         *status_out = a.status;
         return CHERT_OK;
     }
-    if (g_relax_sched.load() == 1 && R < kBT) {      // 2D block-heap marching
+    if (g_relax_sched.load() == 1) {                  // 2D block-heap marching
+        CHERT_REQUIRE(R <= kBH, "%s: the block scheduler takes stencils of reach <= %d (got %d)", who, kBH, R);
         const size_t nt = (size_t)((nx + kBT - 1) / kBT) * ((nz + kBT - 1) / kBT);
-        const size_t baseb = n_off * es + nt * es + 32 * (es + 4) + 64;
+        const size_t sw = (size_t)(kBT + 2 * R) * (kBT + 2 * R);
+        const size_t baseb = n_off * es + nt * es + 32 * es + sw * (es + 4) + (size_t)n_off * 4 + 32 * 4 + 64;
         const size_t tb = (size_t)n_off * n_classes * n_classes * es + baseb;
         const size_t rb = (size_t)n_classes * n_off * es + baseb;
         const int mb = tb <= (size_t)std::min(smem_max, 160 * 1024) ? 1 : rb <= (size_t)smem_max ? 0 : 2;
         const size_t smb = mb == 1 ? tb : mb == 0 ? rb : baseb;
         CHERT_REQUIRE(smb <= (size_t)smem_max, "%s: lattice too large for the block scheduler", who);
         if (precision == CHERT_FP64)
-            rc = mb == 1 ? launch_bhm<double, 1>(a, off, smb, blocks, s)
-               : mb == 0 ? launch_bhm<double, 0>(a, off, smb, blocks, s) : launch_bhm<double, 2>(a, off, smb, blocks, s);
+            rc = mb == 1 ? launch_bhm<double, 1>(a, off, R, smb, blocks, s)
+               : mb == 0 ? launch_bhm<double, 0>(a, off, R, smb, blocks, s)
+                         : launch_bhm<double, 2>(a, off, R, smb, blocks, s);
         else
-            rc = mb == 1 ? launch_bhm<float, 1>(a, off, smb, blocks, s)
-               : mb == 0 ? launch_bhm<float, 0>(a, off, smb, blocks, s) : launch_bhm<float, 2>(a, off, smb, blocks, s);
+            rc = mb == 1 ? launch_bhm<float, 1>(a, off, R, smb, blocks, s)
+               : mb == 0 ? launch_bhm<float, 0>(a, off, R, smb, blocks, s)
+                         : launch_bhm<float, 2>(a, off, R, smb, blocks, s);
         if (rc) return rc;
         *blocks_out = blocks;
         *status_out = a.status;

@@ -129,3 +129,22 @@ def test_scheduler_switch_rejects_unknown(torch_dev):
         chert.set_relax_scheduler("heap")
     assert chert.lib().chert_set_relax_scheduler(2) == chert.EINVAL
     assert chert.set_relax_scheduler("sweeps") == "sweeps"
+
+
+def test_block_scheduler_rejects_long_stencils(torch_dev):
+    """A stencil that reaches beyond the staged halo (9 > 8 nodes) is refused
+    with CHERT_EINVAL under the block scheduler, and runs under the sweeps."""
+    nx, nz = 40, 30
+    cls = np.zeros(nx * nz, np.int32)
+    cache = as_cache(torch_dev, _synthetic_cache([3000.0], [2e-5]), "fp64")
+    off = np.array([(9, 0, 1), (-9, 0, -1), (1, 0, 0), (-1, 0, 0), (0, 0, 1), (0, 0, -1)], np.int32)
+    d_cls = torch_dev.as_tensor(cls, device="cuda")
+    try:
+        chert.set_relax_scheduler("block_heap")
+        with pytest.raises(chert.ChertError) as e:
+            chert.traveltime(cache, nx, nz, 10.0, d_cls, off, [0])
+        assert e.value.code == chert.EINVAL
+    finally:
+        chert.set_relax_scheduler("sweeps")
+    chert.traveltime(cache, nx, nz, 10.0, d_cls, off, [0])
+    torch_dev.cuda.synchronize()
