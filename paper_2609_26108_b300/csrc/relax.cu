@@ -329,6 +329,12 @@ __device__ __forceinline__ void block_argmin(T v, int i, T* rv, int* ri, T& out_
 // halo of H nodes (the stencil's reach) on every side, H <= kBH; positions
 // off the lattice hold +inf, so no pull needs a bounds check.
 constexpr int kBH = 8;
+// Inside a block, 8 x 8 sub-blocks record whether a node of theirs changed in
+// an iteration; the next iteration re-evaluates only the nodes whose 3 x 3
+// sub-block neighbourhood (which covers a reach of kBH) saw a change.  Three
+// flag sets rotate: read (previous iteration), written (this one), cleared
+// (the next one), so no barrier is needed between clearing and writing.
+constexpr int kSB = 8, kNSB = kBT / kSB;
 
 template <typename T, int WMODE>
 __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off, int H) {
@@ -354,7 +360,8 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
     T* wt = reinterpret_cast<T*>(p); p += (size_t)SW * SW * sizeof(T);
     int* wk = reinterpret_cast<int*>(p); p += (size_t)SW * SW * 4;
     int* ws = reinterpret_cast<int*>(p); p += off.n * 4;      // window shift of each offset
-    int* ri = reinterpret_cast<int*>(p);
+    int* ri = reinterpret_cast<int*>(p); p += 32 * 4;
+    int* chg = reinterpret_cast<int*>(p);                      // [3][kNSB * kNSB]
     sm.ring = nullptr;
     sm.cring = nullptr;
     sm.lists = nullptr;
@@ -406,14 +413,26 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
                 wk[q] = in ? clamp_class(a.cls[g], nk) : 0;
             }
             if (threadIdx.x == 0) key[kt] = T(INFINITY);
+            for (int t = threadIdx.x; t < 3 * kNSB * kNSB; t += blockDim.x) chg[t] = 0;
             __syncthreads();
             T lowered = T(INFINITY);
             bool still = false;
             for (int it = 0; it < 4 * kBT; ++it) {          // relax the block to local convergence
                 bool any = false;
+                const int* prev = chg + ((it + 2) % 3) * kNSB * kNSB;
+                int* now = chg + (it % 3) * kNSB * kNSB;
+                if (it > 0 && threadIdx.x < kNSB * kNSB) chg[((it + 1) % 3) * kNSB * kNSB + threadIdx.x] = 0;
                 for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
                     const int x = x0 + q % kBT, z = z0 + q / kBT;
                     if (x >= nx || z >= nz) continue;
+                    const int bx = (q % kBT) / kSB, bz = (q / kBT) / kSB;
+                    bool near = it == 0;
+                    for (int dz = -1; dz <= 1 && !near; ++dz)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int cx = bx + dx, cz = bz + dz;
+                            if (cx >= 0 && cx < kNSB && cz >= 0 && cz < kNSB && prev[cz * kNSB + cx]) near = true;
+                        }
+                    if (!near) continue;
                     const int e = (q % kBT + H) + (q / kBT + H) * SW;
                     const int kj = wk[e];
                     const T cur = wt[e];
@@ -427,6 +446,7 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
                         wt[e] = best;
                         any = true;
                         lowered = fmin(lowered, best);
+                        now[bz * kNSB + bx] = 1;
                     }
                 }
                 still = __syncthreads_or(any);
@@ -1183,7 +1203,8 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         CHERT_REQUIRE(R <= kBH, "%s: the block scheduler takes stencils of reach <= %d (got %d)", who, kBH, R);
         const size_t nt = (size_t)((nx + kBT - 1) / kBT) * ((nz + kBT - 1) / kBT);
         const size_t sw = (size_t)(kBT + 2 * R) * (kBT + 2 * R);
-        const size_t baseb = n_off * es + nt * es + 32 * es + sw * (es + 4) + (size_t)n_off * 4 + 32 * 4 + 64;
+        const size_t baseb = n_off * es + nt * es + 32 * es + sw * (es + 4) + (size_t)n_off * 4 + 32 * 4 +
+                             3 * 16 * 4 + 64;
         const size_t tb = (size_t)n_off * n_classes * n_classes * es + baseb;
         const size_t rb = (size_t)n_classes * n_off * es + baseb;
         const int mb = tb <= (size_t)std::min(smem_max, 160 * 1024) ? 1 : rb <= (size_t)smem_max ? 0 : 2;
