@@ -299,6 +299,17 @@ __global__ void __launch_bounds__(512) relax_kernel(FieldArgs a, Offsets off) {
 // shared memory (ties to the lower tile index).
 constexpr int kBT = 32;
 
+template <typename T, typename B>
+__device__ __forceinline__ B to_bits(T v) {
+    if constexpr (sizeof(T) == 8) return static_cast<B>(__double_as_longlong(v));
+    else return static_cast<B>(__float_as_uint(v));
+}
+template <typename T, typename B>
+__device__ __forceinline__ T from_bits(B b) {
+    if constexpr (sizeof(T) == 8) return __longlong_as_double(static_cast<long long>(b));
+    else return __uint_as_float(static_cast<unsigned int>(b));
+}
+
 template <typename T>
 __device__ __forceinline__ void block_argmin(T v, int i, T* rv, int* ri, T& out_v, int& out_i) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -361,7 +372,12 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
     int* wk = reinterpret_cast<int*>(p); p += (size_t)SW * SW * 4;
     int* ws = reinterpret_cast<int*>(p); p += off.n * 4;      // window shift of each offset
     int* ri = reinterpret_cast<int*>(p); p += 32 * 4;
-    int* chg = reinterpret_cast<int*>(p);                      // [3][kNSB * kNSB]
+    int* chg = reinterpret_cast<int*>(p); p += 3 * kNSB * kNSB * 4;   // [3][kNSB * kNSB]
+    // least new value among the changed nodes within reach of each of the 3 x 3
+    // blocks around the current one (the centre: all changed nodes), as the
+    // bit patterns of non-negative values, which order like the values
+    using Bits = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
+    Bits* m9 = reinterpret_cast<Bits*>((reinterpret_cast<uintptr_t>(p) + 7) & ~uintptr_t(7));
     sm.ring = nullptr;
     sm.cring = nullptr;
     sm.lists = nullptr;
@@ -414,15 +430,16 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
             }
             if (threadIdx.x == 0) key[kt] = T(INFINITY);
             for (int t = threadIdx.x; t < 3 * kNSB * kNSB; t += blockDim.x) chg[t] = 0;
+            if (threadIdx.x < 9) m9[threadIdx.x] = to_bits<T, Bits>(T(INFINITY));
             __syncthreads();
-            T lowered = T(INFINITY);
+            unsigned changed = 0;                            // bit k: node threadIdx.x + k * blockDim.x
             bool still = false;
             for (int it = 0; it < 4 * kBT; ++it) {          // relax the block to local convergence
                 bool any = false;
                 const int* prev = chg + ((it + 2) % 3) * kNSB * kNSB;
                 int* now = chg + (it % 3) * kNSB * kNSB;
                 if (it > 0 && threadIdx.x < kNSB * kNSB) chg[((it + 1) % 3) * kNSB * kNSB + threadIdx.x] = 0;
-                for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {
+                for (int q = threadIdx.x, k = 0; q < kBT * kBT; q += blockDim.x, ++k) {
                     const int x = x0 + q % kBT, z = z0 + q / kBT;
                     if (x >= nx || z >= nz) continue;
                     const int bx = (q % kBT) / kSB, bz = (q / kBT) / kSB;
@@ -445,24 +462,34 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
                     if (best < cur) {
                         wt[e] = best;
                         any = true;
-                        lowered = fmin(lowered, best);
+                        changed |= 1u << k;
                         now[bz * kNSB + bx] = 1;
                     }
                 }
                 still = __syncthreads_or(any);
                 if (!still) break;
             }
-            for (int q = threadIdx.x; q < kBT * kBT; q += blockDim.x) {     // write the block back
-                const int x = x0 + q % kBT, z = z0 + q / kBT;
-                if (x < nx && z < nz) tau[(size_t)x + (size_t)nx * z] = wt[(q % kBT + H) + (q / kBT + H) * SW];
+            for (int q = threadIdx.x, k = 0; q < kBT * kBT; q += blockDim.x, ++k) {   // write back, re-key
+                const int lx = q % kBT, lz = q / kBT;
+                const int x = x0 + lx, z = z0 + lz;
+                if (x >= nx || z >= nz) continue;
+                const T v = wt[(lx + H) + (lz + H) * SW];
+                tau[(size_t)x + (size_t)nx * z] = v;
+                if (!((changed >> k) & 1u)) continue;
+                const Bits b = to_bits<T, Bits>(v);
+                const int sx = lx < H ? 0 : lx >= kBT - H ? 2 : 1;          // side within reach in x
+                const int sz = lz < H ? 0 : lz >= kBT - H ? 2 : 1;
+                atomicMin(&m9[4], b);
+                if (sx != 1) atomicMin(&m9[3 + sx], b);                     // block left or right
+                if (sz != 1) atomicMin(&m9[sz * 3 + 1], b);                 // block above or below
+                if (sx != 1 && sz != 1) atomicMin(&m9[sz * 3 + sx], b);     // diagonal block
             }
-            T m;
-            int dummy;
-            block_argmin(lowered, 0, rv, ri, m, dummy);
-            if (m < T(INFINITY) && threadIdx.x < 9) {
+            __syncthreads();
+            if (threadIdx.x < 9) {
+                const T m = from_bits<T, Bits>(m9[threadIdx.x]);
                 const int tx = kt % TX + (int)threadIdx.x % 3 - 1, tz = kt / TX + (int)threadIdx.x / 3 - 1;
                 const bool self = threadIdx.x == 4;
-                if (tx >= 0 && tx < TX && tz >= 0 && tz < TZ && (!self || still)) {
+                if (m < T(INFINITY) && tx >= 0 && tx < TX && tz >= 0 && tz < TZ && (!self || still)) {
                     T* kk = key + tz * TX + tx;
                     *kk = fmin(*kk, m);
                 }
@@ -1204,7 +1231,7 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         const size_t nt = (size_t)((nx + kBT - 1) / kBT) * ((nz + kBT - 1) / kBT);
         const size_t sw = (size_t)(kBT + 2 * R) * (kBT + 2 * R);
         const size_t baseb = n_off * es + nt * es + 32 * es + sw * (es + 4) + (size_t)n_off * 4 + 32 * 4 +
-                             3 * 16 * 4 + 64;
+                             3 * 16 * 4 + 9 * 8 + 64;
         const size_t tb = (size_t)n_off * n_classes * n_classes * es + baseb;
         const size_t rb = (size_t)n_classes * n_off * es + baseb;
         const int mb = tb <= (size_t)std::min(smem_max, 160 * 1024) ? 1 : rb <= (size_t)smem_max ? 0 : 2;
