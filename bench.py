@@ -458,14 +458,18 @@ def section_angular(n_sources=8, steps_deg=(0.5, 1.0, 2.0, 5.0, 10.0)):
 
 
 # --------------------------------------------------------------- scheduler study
-def section_scheduler(n_sources=16, reps=3):
-    """Block-heap marching (Eq. 32) against the sweep scheduler on the layered
+def section_scheduler(n_sources=16, reps=3, percell_sources=2):
+    """Block-heap marching (Eq. 32) and the hybrid scheduler (at most 8
+    sweep cycles, then block-heap marching for unconverged fields) against
+    the sweep scheduler.  Layered
     401x401 model: n_sources surface sources x 3 modes, MIXED cache, FP32
-    relaxation with parents.  Per scheduler the best of `reps` timed
-    relaxations (after one untimed), and whether the two return the same
-    fields and parents bit for bit."""
+    relaxation with parents, per scheduler the best of `reps` timed
+    relaxations (after one untimed).  Per-cell folded and faulted 1701x351
+    model (exact per-cell FP32 cache): percell_sources sources x 3 modes, one
+    timed relaxation per scheduler, per mode.  Each case also reports whether
+    the two schedulers return the same fields and parents bit for bit."""
     import torch
-    from paper_2609_26108_b300 import chert
+    from paper_2609_26108_b300 import chert, surrogate
 
     model = inputs.layered_tti(n_sources=n_sources)
     off = inputs.stencil_2d(RADIUS)
@@ -475,7 +479,7 @@ def section_scheduler(n_sources=16, reps=3):
                               "MEV", "mixed")
     res, outs = {}, {}
     try:
-        for name in ("sweeps", "block_heap"):
+        for name in ("sweeps", "block_heap", "hybrid"):
             chert.set_relax_scheduler(name)
             run = lambda: chert.traveltime(cache, model.nx, model.nz, model.dx, d_cls, off, model.sources,
                                            max_cycles=128)
@@ -492,9 +496,41 @@ def section_scheduler(n_sources=16, reps=3):
             res[name + "_ms"] = best
     finally:
         chert.set_relax_scheduler("sweeps")
-    res["identical"] = all(bool(torch.equal(x, y)) for x, y in zip(outs["sweeps"], outs["block_heap"]))
+    res["identical"] = all(bool(torch.equal(x, y)) for o in ("block_heap", "hybrid")
+                           for x, y in zip(outs["sweeps"], outs[o]))
     res["block_heap_over_sweeps"] = res["block_heap_ms"] / res["sweeps_ms"]
     res["workload"] = "layered_visco_tti_2d_401x401_8layers_%dsrc_3modes_1deg_R5, fp32 relaxation" % n_sources
+    if percell_sources <= 0:
+        return res
+    del outs, cache
+    pc = inputs.folded_faulted(n_sources=percell_sources)
+    n = pc.nx * pc.nz
+    keys = ["vp0", "vs0", "eps", "delta", "gamma", "qp", "qs", "tilt"]
+    d_cells = chert.classes_to_device(chert.classes_from_arrays(**{k: pc.params[k] for k in keys}))
+    d_pcls = torch.arange(n, dtype=torch.int32, device="cuda")
+    per = {"workload": "folded_faulted_visco_tti_2d_1701x351_per_cell_%dsrc_R5, fp32 relaxation, per mode"
+                       % percell_sources}
+    src = [int(v) for v in pc.sources]
+    for mode in MODES:
+        pcache = surrogate.per_cell_cache(d_cells, n, [mode], M_PER_QUADRANT)
+        got = {}
+        try:
+            for name in ("sweeps", "block_heap", "hybrid"):
+                chert.set_relax_scheduler(name)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record()
+                got[name] = chert.traveltime(pcache, pc.nx, pc.nz, pc.dx, d_pcls, off, src,
+                                             max_cycles=SURR_MAX_CYCLES)
+                b.record()
+                torch.cuda.synchronize()
+                per["%s_%s_ms" % (mode, name)] = a.elapsed_time(b)
+        finally:
+            chert.set_relax_scheduler("sweeps")
+        per["%s_identical" % mode] = all(bool(torch.equal(x, y)) for o in ("block_heap", "hybrid")
+                                         for x, y in zip(got["sweeps"], got[o]))
+        del pcache, got
+    res["per_cell"] = per
     return res
 
 

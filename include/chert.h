@@ -239,16 +239,22 @@ int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes
  * setting, or CHERT_EINVAL for other values.  Results do not depend on it. */
 int chert_set_relax_points_per_thread(int ppt);
 
-/* Scheduler of the 2D relaxation, process-wide: 0 (default) ordered sweep
- * cycles; 1 the paper's block-heap marching (Eq. 32): 32 x 32 node blocks
- * keyed by the least traveltime that may still propagate from them, the
- * smallest taken next and relaxed inside to local convergence, its
- * neighbours re-keyed; each block is staged with a halo of the stencil's
- * reach in shared memory while it is relaxed.  Both return the same fixed
- * point of Eq. 31 and the same parents; they differ in the work done.  Under
- * scheduler 1, a 2D chert_traveltime whose stencil reaches more than 8 nodes
- * returns CHERT_EINVAL (3D lattices always sweep).  Returns the previous
- * setting, or CHERT_EINVAL. */
+/* Scheduler of the 2D relaxation, process-wide:
+ *   0 (default) ordered sweep cycles;
+ *   1 the paper's block-heap marching (Eq. 32): 32 x 32 node blocks keyed by
+ *     the least traveltime that may still propagate from them, the smallest
+ *     taken next and relaxed inside to local convergence (staged with a halo
+ *     of the stencil's reach in shared memory), the neighbours within reach
+ *     of a changed node re-keyed;
+ *   2 hybrid: at most 8 sweep cycles, then block-heap marching, continuing
+ *     from the swept traveltimes, for the fields that have not converged
+ *     (one more launch, whose CTAs of converged fields return at once).
+ * All return the same fixed point of Eq. 31 and the same parents; they
+ * differ in the work done.  Under scheduler 1, a 2D chert_traveltime whose
+ * stencil reaches more than 8 nodes returns CHERT_EINVAL; under 2 it sweeps
+ * only, as it does when max_cycles <= 8.  3D lattices always sweep.
+ * scheduler < 0 queries without changing.  Returns the previous (or current)
+ * setting, or CHERT_EINVAL for scheduler > 2. */
 int chert_set_relax_scheduler(int scheduler);
 
 /* The same relaxation as chert_traveltime, enqueued on `stream` without any

@@ -386,19 +386,25 @@ def traveltime_static(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64,
     return out
 
 
-SCHEDULERS = {"sweeps": 0, "block_heap": 1}
+SCHEDULERS = {"sweeps": 0, "block_heap": 1, "hybrid": 2}
 
 
 def set_relax_scheduler(name):
     """Scheduler of every later 2D relaxation in this process: "sweeps" (the
-    default, ordered sweep cycles) or "block_heap" (block-heap marching of
-    Eq. 32).  Both return the same fields and parents.  Returns the previous
-    name."""
+    default, ordered sweep cycles), "block_heap" (block-heap marching of
+    Eq. 32) or "hybrid" (at most 8 sweep cycles, then block-heap marching for
+    the fields that have not converged).  All return the same fields and
+    parents.  Returns the previous name."""
     if name not in SCHEDULERS:
         raise ValueError("scheduler %r: one of %s" % (name, sorted(SCHEDULERS)))
     prev = lib().chert_set_relax_scheduler(SCHEDULERS[name])
     _check(prev if prev < 0 else 0)
     return {v: k for k, v in SCHEDULERS.items()}[prev]
+
+
+def relax_scheduler():
+    """Name of the current 2D relaxation scheduler."""
+    return {v: k for k, v in SCHEDULERS.items()}[lib().chert_set_relax_scheduler(-1)]
 
 
 def raypath(par, sources, receivers, cap=4096, stream=None, out=None):

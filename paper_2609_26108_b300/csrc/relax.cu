@@ -348,7 +348,12 @@ constexpr int kBH = 8;
 constexpr int kSB = 8, kNSB = kBT / kSB;
 
 template <typename T, int WMODE>
-__global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off, int H) {
+// warm > 0: a continuation.  The fields were swept for `warm` cycles first;
+// the CTAs whose field converged there (status >= 0) return at once, the
+// others start from the swept traveltimes (valid upper bounds, each a path
+// sum) with every block keyed by its least traveltime.
+__global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off, int H, int warm) {
+    if (warm > 0 && a.status[blockIdx.x] >= 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = a.n_classes;
     const int field = blockIdx.x >> 1;
@@ -402,9 +407,19 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
     int32_t* par = comp == 0 ? a.parR : a.parI;
     if (par) par += static_cast<size_t>(field) * n;
     const int64_t src = a.src[s];
-    for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
-    for (int t = threadIdx.x; t < nt; t += blockDim.x)
-        key[t] = t == (int)((src % nx) / kBT + (src / nx) / kBT * TX) ? T(0) : T(INFINITY);
+    if (warm > 0) {
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) key[t] = T(INFINITY);
+        __syncthreads();
+        Bits* kb = reinterpret_cast<Bits*>(key);
+        for (size_t j = threadIdx.x; j < n; j += blockDim.x) {
+            const T v = tau[j];
+            if (v < T(INFINITY)) atomicMin(&kb[(int)((j % nx) / kBT + (j / nx) / kBT * TX)], to_bits<T, Bits>(v));
+        }
+    } else {
+        for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
+        for (int t = threadIdx.x; t < nt; t += blockDim.x)
+            key[t] = t == (int)((src % nx) / kBT + (src / nx) / kBT * TX) ? T(0) : T(INFINITY);
+    }
     __syncthreads();
 
     const long long max_pops = (long long)a.max_cycles * nt * 8;
@@ -498,7 +513,7 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
         }
         if (pops > max_pops) break;
         if (!verify<T, WMODE>(sm, sel, off, tau, a.cls, nx, nz, nk, comp, src, par)) {
-            used = cycle + 1;
+            used = warm + cycle + 1;
             break;
         }
         for (int t = threadIdx.x; t < nt; t += blockDim.x) key[t] = T(0);   // rare: start over everywhere
@@ -850,11 +865,12 @@ static int launch_relax3d(const FieldArgs& a, const Offsets& off, int H, size_t 
 }
 
 template <typename T, int WMODE>
-static int launch_bhm(const FieldArgs& a, const Offsets& off, int H, size_t smem, int blocks, cudaStream_t s) {
+static int launch_bhm(const FieldArgs& a, const Offsets& off, int H, int warm, size_t smem, int blocks,
+                      cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(relax_bhm_kernel<T, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
-    relax_bhm_kernel<T, WMODE><<<blocks, 512, smem, s>>>(a, off, H);
+    relax_bhm_kernel<T, WMODE><<<blocks, 512, smem, s>>>(a, off, H, warm);
     return launch_check("chert_traveltime: block heap");
 }
 
@@ -983,8 +999,10 @@ __global__ void node_weights_kernel(const T* __restrict__ selT, const int32_t* _
 // length; 1, 2 or 4 = forced where the line fits in 512 threads (set by
 // chert_set_relax_points_per_thread, e.g. by an autotuner).
 std::atomic<int> g_relax_ppt{0};
-// 2D scheduler: 0 = ordered sweeps (default), 1 = block-heap marching.
+// 2D scheduler: 0 = ordered sweeps (default), 1 = block-heap marching,
+// 2 = sweeps, then block-heap marching for the fields still changing.
 std::atomic<int> g_relax_sched{0};
+constexpr int kHybridSweeps = 8;
 
 // Radius of the standard stencil with n_off entries (0 if none).
 static int standard_radius(int n_off) {
@@ -1226,8 +1244,14 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         *status_out = a.status;
         return CHERT_OK;
     }
-    if (g_relax_sched.load() == 1) {                  // 2D block-heap marching
-        CHERT_REQUIRE(R <= kBH, "%s: the block scheduler takes stencils of reach <= %d (got %d)", who, kBH, R);
+    // 2D schedulers: 0 sweeps; 1 block-heap marching; 2 sweeps for at most
+    // kHybridSweeps cycles, then block-heap marching for the fields that did
+    // not converge (continuing from their swept traveltimes).
+    const int sched = g_relax_sched.load();
+    CHERT_REQUIRE(sched != 1 || R <= kBH, "%s: the block scheduler takes stencils of reach <= %d (got %d)", who,
+                  kBH, R);
+    const bool hybrid = sched == 2 && R <= kBH && max_cycles > kHybridSweeps;
+    auto block_heap = [&](int warm) -> int {
         const size_t nt = (size_t)((nx + kBT - 1) / kBT) * ((nz + kBT - 1) / kBT);
         const size_t sw = (size_t)(kBT + 2 * R) * (kBT + 2 * R);
         const size_t baseb = n_off * es + nt * es + 32 * es + sw * (es + 4) + (size_t)n_off * 4 + 32 * 4 +
@@ -1238,18 +1262,22 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         const size_t smb = mb == 1 ? tb : mb == 0 ? rb : baseb;
         CHERT_REQUIRE(smb <= (size_t)smem_max, "%s: lattice too large for the block scheduler", who);
         if (precision == CHERT_FP64)
-            rc = mb == 1 ? launch_bhm<double, 1>(a, off, R, smb, blocks, s)
-               : mb == 0 ? launch_bhm<double, 0>(a, off, R, smb, blocks, s)
-                         : launch_bhm<double, 2>(a, off, R, smb, blocks, s);
-        else
-            rc = mb == 1 ? launch_bhm<float, 1>(a, off, R, smb, blocks, s)
-               : mb == 0 ? launch_bhm<float, 0>(a, off, R, smb, blocks, s)
-                         : launch_bhm<float, 2>(a, off, R, smb, blocks, s);
+            return mb == 1 ? launch_bhm<double, 1>(a, off, R, warm, smb, blocks, s)
+                 : mb == 0 ? launch_bhm<double, 0>(a, off, R, warm, smb, blocks, s)
+                           : launch_bhm<double, 2>(a, off, R, warm, smb, blocks, s);
+        return mb == 1 ? launch_bhm<float, 1>(a, off, R, warm, smb, blocks, s)
+             : mb == 0 ? launch_bhm<float, 0>(a, off, R, warm, smb, blocks, s)
+                       : launch_bhm<float, 2>(a, off, R, warm, smb, blocks, s);
+    };
+    if (sched == 1) {
+        rc = block_heap(0);
         if (rc) return rc;
         *blocks_out = blocks;
         *status_out = a.status;
         return CHERT_OK;
     }
+    const int sweep_cycles = hybrid ? kHybridSweeps : max_cycles;
+    a.max_cycles = sweep_cycles;
     const int line_max = std::max(nx, nz);
     const size_t common = n_off * es + (size_t)a.ring * line_max * (es + 4) + 4 * n_off * 2 + 32;
     const size_t smem_table = (size_t)n_off * n_classes * n_classes * es + common;
@@ -1258,7 +1286,7 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     const bool raw_smem = smem_raw <= (size_t)smem_max;
     fast::Args fa;
     fa.nx = nx; fa.nz = nz; fa.n_classes = n_classes; fa.n_modes = n_modes;
-    fa.max_cycles = max_cycles; fa.dx = dx; fa.cls = a.cls; fa.src = a.src;
+    fa.max_cycles = sweep_cycles; fa.dx = dx; fa.cls = a.cls; fa.src = a.src;
     fa.tauR = d_tauR; fa.tauI = d_tauI; fa.parR = d_parR; fa.parI = d_parI;
     fa.Vsel = Vsel; fa.Asel = Asel; fa.n_off = n_off; fa.status = a.status;
     fa.wrow = fa.wcol = nullptr;
@@ -1278,6 +1306,11 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
            : raw_smem ? launch_relax<float, 0>(a, off, smem_raw, blocks, s)
                       : launch_relax<float, 2>(a, off, common, blocks, s);
     if (rc) return rc;
+    if (hybrid) {
+        a.max_cycles = max_cycles;
+        rc = block_heap(kHybridSweeps);
+        if (rc) return rc;
+    }
     *blocks_out = blocks;
     *status_out = a.status;
     return CHERT_OK;
@@ -1457,6 +1490,7 @@ extern "C" int chert_set_relax_points_per_thread(int ppt) {
 }
 
 extern "C" int chert_set_relax_scheduler(int scheduler) {
-    CHERT_REQUIRE(scheduler == 0 || scheduler == 1, "chert_set_relax_scheduler: scheduler=%d (0 or 1)", scheduler);
+    if (scheduler < 0) return g_relax_sched.load();
+    CHERT_REQUIRE(scheduler <= 2, "chert_set_relax_scheduler: scheduler=%d (0, 1 or 2)", scheduler);
     return g_relax_sched.exchange(scheduler);
 }

@@ -54,7 +54,15 @@ class Tracer:
         self.d_cls = torch.empty(n, dtype=torch.int32, device=device)
         self.sources = np.zeros(n_sources, np.int64)
         self.d_field_src = torch.empty(2 * nf, dtype=torch.int64, device=device)
-        self.launches_per_run = 6   # cache build, lookup, class check, relaxation, 2 x raypaths
+
+    @property
+    def launches_per_run(self):
+        """Kernels of one run: cache build, lookup, class check, relaxation,
+        2 x raypaths; the hybrid scheduler adds the block-heap continuation
+        (launched always, returning at once for converged fields)."""
+        hybrid = chert.relax_scheduler() == "hybrid" and self.max_cycles > 8 and \
+            int(np.max(np.abs(self.offsets[:, [0, 2]]))) <= 8
+        return 6 + int(hybrid)
 
     # -- inputs --------------------------------------------------------------
     def set_inputs(self, d_classes, d_cls, sources):

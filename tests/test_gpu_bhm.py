@@ -1,8 +1,9 @@
-"""Block-heap marching (Eq. 32) against the sweep scheduler and the oracle.
+"""Block-heap marching (Eq. 32) and the hybrid scheduler (sweeps, then
+block-heap marching from the swept state) against the sweeps and the oracle.
 
-Both schedulers stop only at the fixed point of Eq. 31, which is unique: a
+Every scheduler stops only at the fixed point of Eq. 31, which is unique: a
 node's value is the least rounded path sum, whatever order the edges are
-relaxed in, and its parent the least-index argmin there.  So the two must give
+relaxed in, and its parent the least-index argmin there.  So all must give
 the same fields and parents bit for bit, in either precision; FP64 is also
 checked against the oracle's Dijkstra."""
 import math
@@ -30,13 +31,14 @@ def torch_dev():
 def both(torch, cache, nx, nz, cls, off, src, max_cycles=256, dx=10.0):
     out = {}
     try:
-        for name in ("sweeps", "block_heap"):
+        for name in ("sweeps", "block_heap", "hybrid"):
             chert.set_relax_scheduler(name)
             out[name] = run_gpu(torch, cache, nx, nz, dx, cls, off, src, max_cycles)
     finally:
         chert.set_relax_scheduler("sweeps")
-    for a, b in zip(out["sweeps"], out["block_heap"]):
-        assert np.array_equal(a, b)
+    for other in ("block_heap", "hybrid"):
+        for a, b in zip(out["sweeps"], out[other]):
+            assert np.array_equal(a, b), other
     return out["block_heap"]
 
 
@@ -127,8 +129,11 @@ def test_unreachable_nodes_keep_infinity(torch_dev):
 def test_scheduler_switch_rejects_unknown(torch_dev):
     with pytest.raises(ValueError):
         chert.set_relax_scheduler("heap")
-    assert chert.lib().chert_set_relax_scheduler(2) == chert.EINVAL
-    assert chert.set_relax_scheduler("sweeps") == "sweeps"
+    assert chert.lib().chert_set_relax_scheduler(3) == chert.EINVAL
+    assert chert.relax_scheduler() == "sweeps"
+    assert chert.set_relax_scheduler("hybrid") == "sweeps"
+    assert chert.relax_scheduler() == "hybrid"
+    assert chert.set_relax_scheduler("sweeps") == "hybrid"
 
 
 def test_block_scheduler_rejects_long_stencils(torch_dev):
@@ -144,7 +149,34 @@ def test_block_scheduler_rejects_long_stencils(torch_dev):
         with pytest.raises(chert.ChertError) as e:
             chert.traveltime(cache, nx, nz, 10.0, d_cls, off, [0])
         assert e.value.code == chert.EINVAL
+        chert.set_relax_scheduler("hybrid")          # sweeps only
+        hy = [t.cpu() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, [0])]
     finally:
         chert.set_relax_scheduler("sweeps")
-    chert.traveltime(cache, nx, nz, 10.0, d_cls, off, [0])
-    torch_dev.cuda.synchronize()
+    sw = [t.cpu() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, [0])]
+    for a, b in zip(sw, hy):
+        assert torch_dev.equal(a, b)
+
+
+def test_hybrid_continues_unconverged_fields(torch_dev):
+    """A serpentine channel that needs more than 8 sweep cycles: under the
+    hybrid scheduler, with max_cycles = 9 (8 sweep cycles, then the
+    continuation with a budget of 9), the block-heap continuation finishes it
+    with the sweeps' fixed point and parents."""
+    nx, nz = 280, 120
+    cls = _serpentine(nx, nz, 12)
+    cache = as_cache(torch_dev, _synthetic_cache([150.0, 6000.0], [1e-3, 1e-5]), "fp64")
+    off = inputs.stencil_2d(3)
+    src = [2 + nx * 1]
+    d_cls = torch_dev.as_tensor(cls, device="cuda")
+    with pytest.raises(chert.ChertError) as e:       # the sweeps alone need more than 8 cycles
+        chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=8)
+    assert e.value.code == chert.ETIMEOUT
+    try:
+        chert.set_relax_scheduler("hybrid")
+        g = [t.cpu().numpy() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=9)]
+    finally:
+        chert.set_relax_scheduler("sweeps")
+    ref = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, src, max_cycles=256)
+    for a, b in zip(ref, g):
+        assert np.array_equal(a, b)
