@@ -351,8 +351,10 @@ template <typename T, int WMODE>
 // warm > 0: a continuation.  The fields were swept for `warm` cycles first;
 // the CTAs whose field converged there (status >= 0) return at once, the
 // others start from the swept traveltimes (valid upper bounds, each a path
-// sum) with every block keyed by its least traveltime.
-__global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off, int H, int warm) {
+// sum).  One pull of every node finds the nodes that an in-neighbour can
+// still improve; only their blocks are keyed, by the least improved value.
+// Every violated edge then ends in a keyed block, as in a cold start.
+__global__ void __launch_bounds__(1024) relax_bhm_kernel(FieldArgs a, Offsets off, int H, int warm) {
     if (warm > 0 && a.status[blockIdx.x] >= 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = a.n_classes;
@@ -411,9 +413,20 @@ __global__ void __launch_bounds__(512) relax_bhm_kernel(FieldArgs a, Offsets off
         for (int t = threadIdx.x; t < nt; t += blockDim.x) key[t] = T(INFINITY);
         __syncthreads();
         Bits* kb = reinterpret_cast<Bits*>(key);
-        for (size_t j = threadIdx.x; j < n; j += blockDim.x) {
-            const T v = tau[j];
-            if (v < T(INFINITY)) atomicMin(&kb[(int)((j % nx) / kBT + (j / nx) / kBT * TX)], to_bits<T, Bits>(v));
+        for (int j = threadIdx.x; j < (int)n; j += blockDim.x) {
+            const int x = j % nx, z = j / nx;
+            const int kj = clamp_class(a.cls[j], nk);
+            const T cur = tau[j];
+            T best = cur;
+            for (int o = 0; o < off.n; ++o) {
+                const int xi = x - off.x[o], zi = z - off.z[o];
+                if (xi < 0 || xi >= nx || zi < 0 || zi >= nz) continue;
+                const T ti = tau[xi + nx * zi];
+                if (!(ti < best)) continue;
+                best = fmin(best, ti + pull_weight<T, WMODE>(sm, sel, off.n, nk, comp, o,
+                                                             clamp_class(a.cls[xi + nx * zi], nk), kj));
+            }
+            if (best < cur) atomicMin(&kb[x / kBT + (z / kBT) * TX], to_bits<T, Bits>(best));
         }
     } else {
         for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
@@ -870,7 +883,7 @@ static int launch_bhm(const FieldArgs& a, const Offsets& off, int H, int warm, s
     cudaError_t e = cudaFuncSetAttribute(relax_bhm_kernel<T, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
-    relax_bhm_kernel<T, WMODE><<<blocks, 512, smem, s>>>(a, off, H, warm);
+    relax_bhm_kernel<T, WMODE><<<blocks, 1024, smem, s>>>(a, off, H, warm);
     return launch_check("chert_traveltime: block heap");
 }
 
