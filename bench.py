@@ -459,9 +459,9 @@ def section_angular(n_sources=8, steps_deg=(0.5, 1.0, 2.0, 5.0, 10.0)):
 
 # --------------------------------------------------------------- scheduler study
 def section_scheduler(n_sources=16, reps=3, percell_sources=2):
-    """Block-heap marching (Eq. 32) and the hybrid scheduler (at most 8
-    sweep cycles, then block-heap marching for unconverged fields) against
-    the sweep scheduler.  Layered
+    """Block-heap marching (Eq. 32) and the hybrid scheduler (at most 6
+    sweep cycles, then block-heap marching from the source for unconverged
+    fields) against the sweep scheduler.  Layered
     401x401 model: n_sources surface sources x 3 modes, MIXED cache, FP32
     relaxation with parents, per scheduler the best of `reps` timed
     relaxations (after one untimed).  Per-cell folded and faulted 1701x351

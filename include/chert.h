@@ -246,13 +246,13 @@ int chert_set_relax_points_per_thread(int ppt);
  *     taken next and relaxed inside to local convergence (staged with a halo
  *     of the stencil's reach in shared memory), the neighbours within reach
  *     of a changed node re-keyed;
- *   2 hybrid: at most 8 sweep cycles, then block-heap marching, continuing
- *     from the swept traveltimes, for the fields that have not converged
- *     (one more launch, whose CTAs of converged fields return at once).
+ *   2 hybrid: at most 6 sweep cycles, then block-heap marching, from the
+ *     source, for the fields that have not converged (one more launch,
+ *     whose CTAs of converged fields return at once).
  * All return the same fixed point of Eq. 31 and the same parents; they
  * differ in the work done.  Under scheduler 1, a 2D chert_traveltime whose
  * stencil reaches more than 8 nodes returns CHERT_EINVAL; under 2 it sweeps
- * only, as it does when max_cycles <= 8.  3D lattices always sweep.
+ * only, as it does when max_cycles <= 6.  3D lattices always sweep.
  * scheduler < 0 queries without changing.  Returns the previous (or current)
  * setting, or CHERT_EINVAL for scheduler > 2. */
 int chert_set_relax_scheduler(int scheduler);

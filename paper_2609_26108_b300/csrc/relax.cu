@@ -348,14 +348,14 @@ constexpr int kBH = 8;
 constexpr int kSB = 8, kNSB = kBT / kSB;
 
 template <typename T, int WMODE>
-// warm > 0: a continuation.  The fields were swept for `warm` cycles first;
-// the CTAs whose field converged there (status >= 0) return at once, the
-// others start from the swept traveltimes (valid upper bounds, each a path
-// sum).  One pull of every node finds the nodes that an in-neighbour can
-// still improve; only their blocks are keyed, by the least improved value.
-// Every violated edge then ends in a keyed block, as in a cold start.
-__global__ void __launch_bounds__(1024) relax_bhm_kernel(FieldArgs a, Offsets off, int H, int warm) {
-    if (warm > 0 && a.status[blockIdx.x] >= 0) return;
+// swept > 0: the fields were swept for `swept` cycles first; the CTAs whose
+// field converged there (status >= 0) return at once, the others solve their
+// field again from the source.  (Continuing from the swept traveltimes was
+// measured slower: fields that have not converged after a few cycles still
+// have improvable nodes almost everywhere, and the blocks' keys then give a
+// poor order.)
+__global__ void __launch_bounds__(1024) relax_bhm_kernel(FieldArgs a, Offsets off, int H, int swept) {
+    if (swept > 0 && a.status[blockIdx.x] >= 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = a.n_classes;
     const int field = blockIdx.x >> 1;
@@ -409,30 +409,9 @@ __global__ void __launch_bounds__(1024) relax_bhm_kernel(FieldArgs a, Offsets of
     int32_t* par = comp == 0 ? a.parR : a.parI;
     if (par) par += static_cast<size_t>(field) * n;
     const int64_t src = a.src[s];
-    if (warm > 0) {
-        for (int t = threadIdx.x; t < nt; t += blockDim.x) key[t] = T(INFINITY);
-        __syncthreads();
-        Bits* kb = reinterpret_cast<Bits*>(key);
-        for (int j = threadIdx.x; j < (int)n; j += blockDim.x) {
-            const int x = j % nx, z = j / nx;
-            const int kj = clamp_class(a.cls[j], nk);
-            const T cur = tau[j];
-            T best = cur;
-            for (int o = 0; o < off.n; ++o) {
-                const int xi = x - off.x[o], zi = z - off.z[o];
-                if (xi < 0 || xi >= nx || zi < 0 || zi >= nz) continue;
-                const T ti = tau[xi + nx * zi];
-                if (!(ti < best)) continue;
-                best = fmin(best, ti + pull_weight<T, WMODE>(sm, sel, off.n, nk, comp, o,
-                                                             clamp_class(a.cls[xi + nx * zi], nk), kj));
-            }
-            if (best < cur) atomicMin(&kb[x / kBT + (z / kBT) * TX], to_bits<T, Bits>(best));
-        }
-    } else {
-        for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
-        for (int t = threadIdx.x; t < nt; t += blockDim.x)
-            key[t] = t == (int)((src % nx) / kBT + (src / nx) / kBT * TX) ? T(0) : T(INFINITY);
-    }
+    for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
+    for (int t = threadIdx.x; t < nt; t += blockDim.x)
+        key[t] = t == (int)((src % nx) / kBT + (src / nx) / kBT * TX) ? T(0) : T(INFINITY);
     __syncthreads();
 
     const long long max_pops = (long long)a.max_cycles * nt * 8;
@@ -526,7 +505,7 @@ __global__ void __launch_bounds__(1024) relax_bhm_kernel(FieldArgs a, Offsets of
         }
         if (pops > max_pops) break;
         if (!verify<T, WMODE>(sm, sel, off, tau, a.cls, nx, nz, nk, comp, src, par)) {
-            used = warm + cycle + 1;
+            used = swept + cycle + 1;
             break;
         }
         for (int t = threadIdx.x; t < nt; t += blockDim.x) key[t] = T(0);   // rare: start over everywhere
@@ -878,12 +857,12 @@ static int launch_relax3d(const FieldArgs& a, const Offsets& off, int H, size_t 
 }
 
 template <typename T, int WMODE>
-static int launch_bhm(const FieldArgs& a, const Offsets& off, int H, int warm, size_t smem, int blocks,
+static int launch_bhm(const FieldArgs& a, const Offsets& off, int H, int swept, size_t smem, int blocks,
                       cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(relax_bhm_kernel<T, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
-    relax_bhm_kernel<T, WMODE><<<blocks, 1024, smem, s>>>(a, off, H, warm);
+    relax_bhm_kernel<T, WMODE><<<blocks, 1024, smem, s>>>(a, off, H, swept);
     return launch_check("chert_traveltime: block heap");
 }
 
@@ -1013,9 +992,9 @@ __global__ void node_weights_kernel(const T* __restrict__ selT, const int32_t* _
 // chert_set_relax_points_per_thread, e.g. by an autotuner).
 std::atomic<int> g_relax_ppt{0};
 // 2D scheduler: 0 = ordered sweeps (default), 1 = block-heap marching,
-// 2 = sweeps, then block-heap marching for the fields still changing.
+// 2 = sweeps, then block-heap marching for the fields not yet converged.
 std::atomic<int> g_relax_sched{0};
-constexpr int kHybridSweeps = 8;
+constexpr int kHybridSweeps = 6;
 
 // Radius of the standard stencil with n_off entries (0 if none).
 static int standard_radius(int n_off) {
@@ -1258,13 +1237,13 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         return CHERT_OK;
     }
     // 2D schedulers: 0 sweeps; 1 block-heap marching; 2 sweeps for at most
-    // kHybridSweeps cycles, then block-heap marching for the fields that did
-    // not converge (continuing from their swept traveltimes).
+    // kHybridSweeps cycles, then block-heap marching, from the source, for
+    // the fields that did not converge.
     const int sched = g_relax_sched.load();
     CHERT_REQUIRE(sched != 1 || R <= kBH, "%s: the block scheduler takes stencils of reach <= %d (got %d)", who,
                   kBH, R);
     const bool hybrid = sched == 2 && R <= kBH && max_cycles > kHybridSweeps;
-    auto block_heap = [&](int warm) -> int {
+    auto block_heap = [&](int swept) -> int {
         const size_t nt = (size_t)((nx + kBT - 1) / kBT) * ((nz + kBT - 1) / kBT);
         const size_t sw = (size_t)(kBT + 2 * R) * (kBT + 2 * R);
         const size_t baseb = n_off * es + nt * es + 32 * es + sw * (es + 4) + (size_t)n_off * 4 + 32 * 4 +
@@ -1275,12 +1254,12 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         const size_t smb = mb == 1 ? tb : mb == 0 ? rb : baseb;
         CHERT_REQUIRE(smb <= (size_t)smem_max, "%s: lattice too large for the block scheduler", who);
         if (precision == CHERT_FP64)
-            return mb == 1 ? launch_bhm<double, 1>(a, off, R, warm, smb, blocks, s)
-                 : mb == 0 ? launch_bhm<double, 0>(a, off, R, warm, smb, blocks, s)
-                           : launch_bhm<double, 2>(a, off, R, warm, smb, blocks, s);
-        return mb == 1 ? launch_bhm<float, 1>(a, off, R, warm, smb, blocks, s)
-             : mb == 0 ? launch_bhm<float, 0>(a, off, R, warm, smb, blocks, s)
-                       : launch_bhm<float, 2>(a, off, R, warm, smb, blocks, s);
+            return mb == 1 ? launch_bhm<double, 1>(a, off, R, swept, smb, blocks, s)
+                 : mb == 0 ? launch_bhm<double, 0>(a, off, R, swept, smb, blocks, s)
+                           : launch_bhm<double, 2>(a, off, R, swept, smb, blocks, s);
+        return mb == 1 ? launch_bhm<float, 1>(a, off, R, swept, smb, blocks, s)
+             : mb == 0 ? launch_bhm<float, 0>(a, off, R, swept, smb, blocks, s)
+                       : launch_bhm<float, 2>(a, off, R, swept, smb, blocks, s);
     };
     if (sched == 1) {
         rc = block_heap(0);

@@ -60,7 +60,7 @@ class Tracer:
         """Kernels of one run: cache build, lookup, class check, relaxation,
         2 x raypaths; the hybrid scheduler adds the block-heap continuation
         (launched always, returning at once for converged fields)."""
-        hybrid = chert.relax_scheduler() == "hybrid" and self.max_cycles > 8 and \
+        hybrid = chert.relax_scheduler() == "hybrid" and self.max_cycles > 6 and \
             int(np.max(np.abs(self.offsets[:, [0, 2]]))) <= 8
         return 6 + int(hybrid)
 

@@ -1,5 +1,6 @@
-"""Block-heap marching (Eq. 32) and the hybrid scheduler (sweeps, then
-block-heap marching from the swept state) against the sweeps and the oracle.
+"""Block-heap marching (Eq. 32) and the hybrid scheduler (a few sweep cycles,
+then block-heap marching for the fields not yet converged) against the sweeps
+and the oracle.
 
 Every scheduler stops only at the fixed point of Eq. 31, which is unique: a
 node's value is the least rounded path sum, whatever order the edges are
@@ -159,22 +160,22 @@ def test_block_scheduler_rejects_long_stencils(torch_dev):
 
 
 def test_hybrid_continues_unconverged_fields(torch_dev):
-    """A serpentine channel that needs more than 8 sweep cycles: under the
-    hybrid scheduler, with max_cycles = 9 (8 sweep cycles, then the
-    continuation with a budget of 9), the block-heap continuation finishes it
-    with the sweeps' fixed point and parents."""
+    """A serpentine channel that needs more than 6 sweep cycles: under the
+    hybrid scheduler with max_cycles = 7 (6 sweep cycles, then block-heap
+    marching with a budget of 7) the continuation finishes it with the
+    sweeps' fixed point and parents."""
     nx, nz = 280, 120
     cls = _serpentine(nx, nz, 12)
     cache = as_cache(torch_dev, _synthetic_cache([150.0, 6000.0], [1e-3, 1e-5]), "fp64")
     off = inputs.stencil_2d(3)
     src = [2 + nx * 1]
     d_cls = torch_dev.as_tensor(cls, device="cuda")
-    with pytest.raises(chert.ChertError) as e:       # the sweeps alone need more than 8 cycles
-        chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=8)
+    with pytest.raises(chert.ChertError) as e:       # the sweeps alone need more than 6 cycles
+        chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=6)
     assert e.value.code == chert.ETIMEOUT
     try:
         chert.set_relax_scheduler("hybrid")
-        g = [t.cpu().numpy() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=9)]
+        g = [t.cpu().numpy() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=7)]
     finally:
         chert.set_relax_scheduler("sweeps")
     ref = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, src, max_cycles=256)
