@@ -495,7 +495,7 @@ def section_scheduler(n_sources=16, reps=3, percell_sources=2):
                 best = a.elapsed_time(b) if best is None else min(best, a.elapsed_time(b))
             res[name + "_ms"] = best
     finally:
-        chert.set_relax_scheduler("sweeps")
+        chert.set_relax_scheduler("hybrid")
     res["identical"] = all(bool(torch.equal(x, y)) for o in ("block_heap", "hybrid")
                            for x, y in zip(outs["sweeps"], outs[o]))
     res["block_heap_over_sweeps"] = res["block_heap_ms"] / res["sweeps_ms"]
@@ -526,7 +526,7 @@ def section_scheduler(n_sources=16, reps=3, percell_sources=2):
                 torch.cuda.synchronize()
                 per["%s_%s_ms" % (mode, name)] = a.elapsed_time(b)
         finally:
-            chert.set_relax_scheduler("sweeps")
+            chert.set_relax_scheduler("hybrid")
         per["%s_identical" % mode] = all(bool(torch.equal(x, y)) for o in ("block_heap", "hybrid")
                                          for x, y in zip(got["sweeps"], got[o]))
         del pcache, got

@@ -240,13 +240,13 @@ int chert_traveltime(const chert_cache_arrays* cache, int n_modes, int n_classes
 int chert_set_relax_points_per_thread(int ppt);
 
 /* Scheduler of the 2D relaxation, process-wide:
- *   0 (default) ordered sweep cycles;
+ *   0 ordered sweep cycles;
  *   1 the paper's block-heap marching (Eq. 32): 32 x 32 node blocks keyed by
  *     the least traveltime that may still propagate from them, the smallest
  *     taken next and relaxed inside to local convergence (staged with a halo
  *     of the stencil's reach in shared memory), the neighbours within reach
  *     of a changed node re-keyed;
- *   2 hybrid: at most 6 sweep cycles, then block-heap marching, from the
+ *   2 (default) hybrid: at most 6 sweep cycles, then block-heap marching, from the
  *     source, for the fields that have not converged (one more launch,
  *     whose CTAs of converged fields return at once).
  * All return the same fixed point of Eq. 31 and the same parents; they

@@ -390,11 +390,11 @@ SCHEDULERS = {"sweeps": 0, "block_heap": 1, "hybrid": 2}
 
 
 def set_relax_scheduler(name):
-    """Scheduler of every later 2D relaxation in this process: "sweeps" (the
-    default, ordered sweep cycles), "block_heap" (block-heap marching of
-    Eq. 32) or "hybrid" (at most 6 sweep cycles, then block-heap marching,
-    from the source, for the fields that have not converged).  All return the same fields and
-    parents.  Returns the previous name."""
+    """Scheduler of every later 2D relaxation in this process: "sweeps"
+    (ordered sweep cycles), "block_heap" (block-heap marching of Eq. 32) or
+    "hybrid" (the default: at most 6 sweep cycles, then block-heap marching,
+    from the source, for the fields that have not converged).  All return the
+    same fields and parents.  Returns the previous name."""
     if name not in SCHEDULERS:
         raise ValueError("scheduler %r: one of %s" % (name, sorted(SCHEDULERS)))
     prev = lib().chert_set_relax_scheduler(SCHEDULERS[name])

@@ -991,9 +991,9 @@ __global__ void node_weights_kernel(const T* __restrict__ selT, const int32_t* _
 // length; 1, 2 or 4 = forced where the line fits in 512 threads (set by
 // chert_set_relax_points_per_thread, e.g. by an autotuner).
 std::atomic<int> g_relax_ppt{0};
-// 2D scheduler: 0 = ordered sweeps (default), 1 = block-heap marching,
-// 2 = sweeps, then block-heap marching for the fields not yet converged.
-std::atomic<int> g_relax_sched{0};
+// 2D scheduler: 0 = ordered sweeps, 1 = block-heap marching, 2 (default) =
+// sweeps, then block-heap marching for the fields not yet converged.
+std::atomic<int> g_relax_sched{2};
 constexpr int kHybridSweeps = 6;
 
 // Radius of the standard stencil with n_off entries (0 if none).

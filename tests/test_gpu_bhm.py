@@ -31,12 +31,13 @@ def torch_dev():
 
 def both(torch, cache, nx, nz, cls, off, src, max_cycles=256, dx=10.0):
     out = {}
+    prev = chert.relax_scheduler()
     try:
         for name in ("sweeps", "block_heap", "hybrid"):
             chert.set_relax_scheduler(name)
             out[name] = run_gpu(torch, cache, nx, nz, dx, cls, off, src, max_cycles)
     finally:
-        chert.set_relax_scheduler("sweeps")
+        chert.set_relax_scheduler(prev)
     for other in ("block_heap", "hybrid"):
         for a, b in zip(out["sweeps"], out[other]):
             assert np.array_equal(a, b), other
@@ -131,10 +132,10 @@ def test_scheduler_switch_rejects_unknown(torch_dev):
     with pytest.raises(ValueError):
         chert.set_relax_scheduler("heap")
     assert chert.lib().chert_set_relax_scheduler(3) == chert.EINVAL
+    assert chert.relax_scheduler() == "hybrid"                 # the default
+    assert chert.set_relax_scheduler("sweeps") == "hybrid"
     assert chert.relax_scheduler() == "sweeps"
     assert chert.set_relax_scheduler("hybrid") == "sweeps"
-    assert chert.relax_scheduler() == "hybrid"
-    assert chert.set_relax_scheduler("sweeps") == "hybrid"
 
 
 def test_block_scheduler_rejects_long_stencils(torch_dev):
@@ -152,9 +153,10 @@ def test_block_scheduler_rejects_long_stencils(torch_dev):
         assert e.value.code == chert.EINVAL
         chert.set_relax_scheduler("hybrid")          # sweeps only
         hy = [t.cpu() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, [0])]
-    finally:
         chert.set_relax_scheduler("sweeps")
-    sw = [t.cpu() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, [0])]
+        sw = [t.cpu() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, [0])]
+    finally:
+        chert.set_relax_scheduler("hybrid")
     for a, b in zip(sw, hy):
         assert torch_dev.equal(a, b)
 
@@ -170,14 +172,14 @@ def test_hybrid_continues_unconverged_fields(torch_dev):
     off = inputs.stencil_2d(3)
     src = [2 + nx * 1]
     d_cls = torch_dev.as_tensor(cls, device="cuda")
-    with pytest.raises(chert.ChertError) as e:       # the sweeps alone need more than 6 cycles
-        chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=6)
-    assert e.value.code == chert.ETIMEOUT
     try:
-        chert.set_relax_scheduler("hybrid")
-        g = [t.cpu().numpy() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=7)]
-    finally:
         chert.set_relax_scheduler("sweeps")
-    ref = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, src, max_cycles=256)
+        with pytest.raises(chert.ChertError) as e:   # the sweeps alone need more than 6 cycles
+            chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=6)
+        assert e.value.code == chert.ETIMEOUT
+        ref = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, src, max_cycles=256)
+    finally:
+        chert.set_relax_scheduler("hybrid")
+    g = [t.cpu().numpy() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=7)]
     for a, b in zip(ref, g):
         assert np.array_equal(a, b)

@@ -34,6 +34,16 @@ def torch_dev():
     return torch
 
 
+@pytest.fixture(autouse=True)
+def sweep_scheduler(torch_dev):
+    """These tests pin down the sweep kernels themselves (launch shapes,
+    per-node weights, cycle caps), so they run under the sweep scheduler;
+    the other schedulers are checked against it elsewhere."""
+    prev = chert.set_relax_scheduler("sweeps")
+    yield
+    chert.set_relax_scheduler(prev)
+
+
 _small = {}
 
 
