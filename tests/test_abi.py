@@ -83,3 +83,28 @@ def test_workspace_grid_adds_per_node_area(lib):
 def test_null_arguments_are_rejected_without_gpu(lib):
     assert lib.chert_build_cache(None, 1, None, 1, None, None, None) == chert.EINVAL
     assert lib.chert_raypath(None, 1, 10, None, None, 1, 4, None, None, None) == chert.EINVAL
+
+
+def test_relax_scheduler_switch_host_only(lib):
+    """The 2D scheduler switch is host state: the hybrid is the default, a
+    negative argument queries, out-of-range values are refused, and every
+    change returns the previous setting."""
+    assert lib.chert_set_relax_scheduler(-1) == 2
+    assert chert.relax_scheduler() == "hybrid"
+    assert lib.chert_set_relax_scheduler(3) == chert.EINVAL
+    assert lib.chert_set_relax_scheduler(-1) == 2                # unchanged by the refusal
+    try:
+        assert chert.set_relax_scheduler("block_heap") == "hybrid"
+        assert lib.chert_set_relax_scheduler(0) == 1
+        assert chert.relax_scheduler() == "sweeps"
+        with pytest.raises(ValueError):
+            chert.set_relax_scheduler("dijkstra")
+    finally:
+        chert.set_relax_scheduler("hybrid")
+    assert chert.relax_scheduler() == "hybrid"
+
+
+def test_relax_points_per_thread_switch_host_only(lib):
+    assert lib.chert_set_relax_points_per_thread(3) == chert.EINVAL
+    prev = lib.chert_set_relax_points_per_thread(2)
+    assert lib.chert_set_relax_points_per_thread(prev) == 2
