@@ -65,6 +65,52 @@ def workload(n_sources=64):
     return model, off, rcv
 
 
+def measured_hbm_gbs():
+    """HBM copy bandwidth of this machine's B300s (MEASURED_PEAKS.json at the
+    repository root), else the fallback figure of one earlier measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "of fallback"
+
+
+# Instructions a warp issues per pull in the relaxation's inner loop, counted
+# from its source: one 8-byte shared load of (tau, class), an index add, a
+# shared load of the weight, an add and a min.
+INSTR_PER_PULL = 5
+
+
+def hbm_roofline(alg_bytes, dram_bytes, launch_s):
+    """The relaxation against HBM: algorithmic bytes (class id read, tauR,
+    tauI, parR, parI written) and, when captured, the DRAM bytes ncu counted,
+    per launch time, over the measured copy bandwidth."""
+    peak, src = measured_hbm_gbs()
+    a = alg_bytes / launch_s / 1e9
+    out = {"achieved_gbs": a, "peak_gbs": peak, "peak_source": src, "frac": a / peak}
+    if dram_bytes:
+        out["dram_gbs"] = dram_bytes / launch_s / 1e9
+        out["dram_frac"] = out["dram_gbs"] / peak
+    return out
+
+
+def issue_rate_peak(sm_max_mhz):
+    """Pulls per second if every scheduler issued one pull instruction per
+    cycle: 148 SMs x 4 schedulers x clock x 32 lanes / instructions per pull."""
+    return SM_COUNT * 4 * sm_max_mhz * 1e6 * 32 / INSTR_PER_PULL
+
+
+def issue_roofline(alg_pulls, launch_s, sm_max_mhz):
+    """The relaxation against the issue rate: algorithmic pulls (one per
+    directed edge per field component) per second over the rate at which the
+    schedulers could issue the pull loop."""
+    peak = issue_rate_peak(sm_max_mhz)
+    a = alg_pulls / launch_s
+    return {"achieved_pulls_per_s": a, "peak_pulls_per_s": peak, "frac": a / peak,
+            "instructions_per_pull": INSTR_PER_PULL,
+            "peak_source": "derived: 148 SMs x 4 schedulers x max SM clock x 32 lanes / instructions per pull"}
+
+
 def directed_edges(nx, nz, off):
     return int(sum((nx - abs(int(o[0]))) * (nz - abs(int(o[2]))) for o in off
                    if abs(int(o[0])) < nx and abs(int(o[2])) < nz))
@@ -667,7 +713,9 @@ def run_chert(args):
                 "alg_bytes_per_launch": 20.0 * model.nx * model.nz * nf,   # class id 4 B + tauR, tauI, parR, parI 4 B each per node per field
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x max SM clock (non-FMA op rate)",
                 "alg_ops_per_launch": alg_ops, "directed_edges_per_field": edges,
-                "launch_ms": 1e3 * relax_avg_s}
+                "launch_ms": 1e3 * relax_avg_s,
+                "hbm": hbm_roofline(20.0 * model.nx * model.nz * nf, traffic, relax_avg_s),
+                "issue": issue_roofline(edges * nf * 2, relax_avg_s, sm_max)}
     cache_avg_s = statistics.mean(cache_ms) / 1e3
     if rank != 0:
         if world > 1:
