@@ -514,6 +514,181 @@ __global__ void __launch_bounds__(1024) relax_bhm_kernel(FieldArgs a, Offsets of
     if (threadIdx.x == 0) a.status[blockIdx.x] = used;
 }
 
+// The same block-heap marching on the standard stencil of radius R (the
+// offsets of the specialised sweep kernel): the window shifts are compile-time
+// immediates, and each pull reads its weight either from a class-pair table
+// in shared memory in stencil order, W[(q*nk + k_i)*nk + k_j], or (PN) from
+// the per-node weights that the sweeps computed, wrow[(mode*2+comp)][q][node].
+// Weights, keys, order and results are those of relax_bhm_kernel.
+struct BhmStd {
+    short map[128];        // stencil index -> caller offset index
+    const void* wrow;      // per-node weights (PN), row layout
+};
+
+template <typename T, int R, bool PN>
+__global__ void __launch_bounds__(1024) relax_bhm_std_kernel(FieldArgs a, Offsets off, BhmStd b, int swept) {
+    if (swept > 0 && a.status[blockIdx.x] >= 0) return;
+    constexpr int N = fast::Stencil<R>::N;
+    constexpr int H = R, SW = kBT + 2 * R;
+    using Bits = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nk = a.n_classes;
+    const int field = blockIdx.x >> 1;
+    const int comp = blockIdx.x & 1;
+    const int mode = field % a.n_modes;
+    const int s = field / a.n_modes;
+    const int nx = a.nx, nz = a.nz;
+    const size_t n = static_cast<size_t>(nx) * nz;
+    const int TX = (nx + kBT - 1) / kBT, TZ = (nz + kBT - 1) / kBT, nt = TX * TZ;
+
+    unsigned char* p = smem_raw;
+    T* W = reinterpret_cast<T*>(p); p += PN ? 0 : (size_t)N * nk * nk * sizeof(T);
+    T* Lc = reinterpret_cast<T*>(p); p += (size_t)off.n * sizeof(T);     // lengths, caller order
+    T* key = reinterpret_cast<T*>(p); p += (size_t)nt * sizeof(T);
+    T* rv = reinterpret_cast<T*>(p); p += 32 * sizeof(T);
+    T* wt = reinterpret_cast<T*>(p); p += (size_t)SW * SW * sizeof(T);
+    int* wk = reinterpret_cast<int*>(p); p += PN ? 0 : (size_t)SW * SW * 4;
+    int* ri = reinterpret_cast<int*>(p); p += 32 * 4;
+    int* chg = reinterpret_cast<int*>(p); p += 3 * kNSB * kNSB * 4;
+    Bits* m9 = reinterpret_cast<Bits*>((reinterpret_cast<uintptr_t>(p) + 7) & ~uintptr_t(7));
+
+    const T* sel = static_cast<const T*>(comp == 0 ? a.Vsel : a.Asel) + static_cast<size_t>(mode) * nk * off.n;
+    for (int o = threadIdx.x; o < off.n; o += blockDim.x) {
+        const double ox = off.x[o], oz = off.z[o];
+        Lc[o] = T(a.dx * sqrt(ox * ox + oz * oz));
+    }
+    if constexpr (!PN) {
+        for (int t = threadIdx.x; t < N * nk * nk; t += blockDim.x) {
+            const int kj = t % nk, ki = (t / nk) % nk, q = t / (nk * nk);
+            const int o = b.map[q];
+            const double ox = off.x[o], oz = off.z[o];
+            const T L = T(a.dx * sqrt(ox * ox + oz * oz));
+            W[t] = edge_w<T>(comp, L, sel[ki * off.n + o], sel[kj * off.n + o]);
+        }
+    }
+    const T* wrow = PN ? static_cast<const T*>(b.wrow) + (size_t)(mode * 2 + comp) * N * n : nullptr;
+    T* tau = static_cast<T*>(comp == 0 ? a.tauR : a.tauI) + static_cast<size_t>(field) * n;
+    int32_t* par = comp == 0 ? a.parR : a.parI;
+    if (par) par += static_cast<size_t>(field) * n;
+    const int64_t src = a.src[s];
+    for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
+    for (int t = threadIdx.x; t < nt; t += blockDim.x)
+        key[t] = t == (int)((src % nx) / kBT + (src / nx) / kBT * TX) ? T(0) : T(INFINITY);
+    __syncthreads();
+
+    Smem<T> sm{};                                    // for the generic verification pass (global tables)
+    sm.L = Lc;
+    const long long max_pops = (long long)a.max_cycles * nt * 8;
+    long long pops = 0;
+    int used = -1;
+    for (int cycle = 0; cycle < a.max_cycles && pops <= max_pops; ++cycle) {
+        for (;;) {
+            T bv = T(INFINITY);
+            int bi = -1;
+            for (int t = threadIdx.x; t < nt; t += blockDim.x)
+                if (key[t] < bv) { bv = key[t]; bi = t; }
+            T kv;
+            int kt;
+            block_argmin(bv, bi, rv, ri, kv, kt);
+            if (kt < 0 || ++pops > max_pops) break;
+            const int x0 = (kt % TX) * kBT, z0 = (kt / TX) * kBT;
+            for (int q = threadIdx.x; q < SW * SW; q += blockDim.x) {      // stage the window
+                const int x = x0 - H + q % SW, z = z0 - H + q / SW;
+                const bool in = x >= 0 && x < nx && z >= 0 && z < nz;
+                const size_t g = in ? (size_t)x + (size_t)nx * z : 0;
+                wt[q] = in ? tau[g] : T(INFINITY);
+                if constexpr (!PN) wk[q] = in ? clamp_class(a.cls[g], nk) * nk : 0;
+            }
+            if (threadIdx.x == 0) key[kt] = T(INFINITY);
+            for (int t = threadIdx.x; t < 3 * kNSB * kNSB; t += blockDim.x) chg[t] = 0;
+            if (threadIdx.x < 9) m9[threadIdx.x] = to_bits<T, Bits>(T(INFINITY));
+            __syncthreads();
+            unsigned changed = 0;
+            bool still = false;
+            for (int it = 0; it < 4 * kBT; ++it) {
+                bool any = false;
+                const int* prev = chg + ((it + 2) % 3) * kNSB * kNSB;
+                int* now = chg + (it % 3) * kNSB * kNSB;
+                if (it > 0 && threadIdx.x < kNSB * kNSB) chg[((it + 1) % 3) * kNSB * kNSB + threadIdx.x] = 0;
+                for (int q = threadIdx.x, k = 0; q < kBT * kBT; q += blockDim.x, ++k) {
+                    const int x = x0 + q % kBT, z = z0 + q / kBT;
+                    if (x >= nx || z >= nz) continue;
+                    const int bx = (q % kBT) / kSB, bz = (q / kBT) / kSB;
+                    bool near = it == 0;
+                    for (int dz = -1; dz <= 1 && !near; ++dz)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int cx = bx + dx, cz = bz + dz;
+                            if (cx >= 0 && cx < kNSB && cz >= 0 && cz < kNSB && prev[cz * kNSB + cx]) near = true;
+                        }
+                    if (!near) continue;
+                    const int e = (q % kBT + H) + (q / kBT + H) * SW;
+                    const T cur = wt[e];
+                    T best = cur;
+                    if constexpr (PN) {
+                        const T* wj = wrow + (size_t)x + (size_t)nx * z;
+                        fast::static_for<N>([&](auto qc) {
+                            constexpr int qq = decltype(qc)::value;
+                            constexpr int sh = fast::Table<R>::v.x[qq] + fast::Table<R>::v.z[qq] * SW;
+                            const T ti = wt[e - sh];
+                            if (ti < best) best = fmin(best, ti + wj[(size_t)qq * n]);
+                        });
+                    } else {
+                        const T* Wj = W + wk[e] / nk;      // + q*nk*nk + k_i*nk
+                        fast::static_for<N>([&](auto qc) {
+                            constexpr int qq = decltype(qc)::value;
+                            constexpr int sh = fast::Table<R>::v.x[qq] + fast::Table<R>::v.z[qq] * SW;
+                            const T ti = wt[e - sh];
+                            if (ti < best) best = fmin(best, ti + Wj[qq * nk * nk + wk[e - sh]]);
+                        });
+                    }
+                    if (best < cur) {
+                        wt[e] = best;
+                        any = true;
+                        changed |= 1u << k;
+                        now[bz * kNSB + bx] = 1;
+                    }
+                }
+                still = __syncthreads_or(any);
+                if (!still) break;
+            }
+            for (int q = threadIdx.x, k = 0; q < kBT * kBT; q += blockDim.x, ++k) {   // write back, re-key
+                const int lx = q % kBT, lz = q / kBT;
+                const int x = x0 + lx, z = z0 + lz;
+                if (x >= nx || z >= nz) continue;
+                const T v = wt[(lx + H) + (lz + H) * SW];
+                tau[(size_t)x + (size_t)nx * z] = v;
+                if (!((changed >> k) & 1u)) continue;
+                const Bits bb = to_bits<T, Bits>(v);
+                const int sx = lx < H ? 0 : lx >= kBT - H ? 2 : 1;
+                const int sz = lz < H ? 0 : lz >= kBT - H ? 2 : 1;
+                atomicMin(&m9[4], bb);
+                if (sx != 1) atomicMin(&m9[3 + sx], bb);
+                if (sz != 1) atomicMin(&m9[sz * 3 + 1], bb);
+                if (sx != 1 && sz != 1) atomicMin(&m9[sz * 3 + sx], bb);
+            }
+            __syncthreads();
+            if (threadIdx.x < 9) {
+                const T m = from_bits<T, Bits>(m9[threadIdx.x]);
+                const int tx = kt % TX + (int)threadIdx.x % 3 - 1, tz = kt / TX + (int)threadIdx.x / 3 - 1;
+                const bool self = threadIdx.x == 4;
+                if (m < T(INFINITY) && tx >= 0 && tx < TX && tz >= 0 && tz < TZ && (!self || still)) {
+                    T* kk = key + tz * TX + tx;
+                    *kk = fmin(*kk, m);
+                }
+            }
+            __syncthreads();
+        }
+        if (pops > max_pops) break;
+        if (!verify<T, 2>(sm, sel, off, tau, a.cls, nx, nz, nk, comp, src, par)) {
+            used = swept + cycle + 1;
+            break;
+        }
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) key[t] = T(0);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.status[blockIdx.x] = used;
+}
+
 // ------------------------------------------------------------ 3D relaxation
 // A 3D lattice (node x + nx*(y + ny*z)) is relaxed by plane sweeps: a cycle
 // runs the planes of constant z upward, of constant y and of constant x in
@@ -893,6 +1068,54 @@ static bool standard_map(const Offsets& off, short* map) {
     return true;
 }
 
+template <typename T, int R, bool PN>
+static int launch_bhm_std(const FieldArgs& a, const Offsets& off, const BhmStd& b, int swept, size_t smem,
+                          int blocks, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(relax_bhm_std_kernel<T, R, PN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
+    relax_bhm_std_kernel<T, R, PN><<<blocks, 1024, smem, s>>>(a, off, b, swept);
+    return launch_check("chert_traveltime: block heap");
+}
+
+// Block-heap marching on the standard stencil of radius R, if the offsets are
+// that stencil and its tables fit: 1 launched, 0 not applicable, < 0 error.
+// wrow: the per-node weights of the sweeps, or null (class-pair table).
+template <typename T, int R>
+static int try_bhm_std_R(const FieldArgs& a, const Offsets& off, const void* wrow, int swept, int smem_max,
+                         int blocks, cudaStream_t s) {
+    BhmStd b;
+    if (!standard_map<R>(off, b.map)) return 0;
+    b.wrow = wrow;
+    constexpr int N = fast::Stencil<R>::N;
+    const size_t es = sizeof(T);
+    const size_t nt = (size_t)((a.nx + kBT - 1) / kBT) * ((a.nz + kBT - 1) / kBT);
+    const size_t sw = (size_t)(kBT + 2 * R) * (kBT + 2 * R);
+    const size_t base = (size_t)off.n * es + nt * es + 32 * es + sw * es + 32 * 4 + 3 * kNSB * kNSB * 4 + 9 * 8 + 64;
+    int rc;
+    if (wrow) {
+        if (base > (size_t)smem_max) return 0;
+        rc = launch_bhm_std<T, R, true>(a, off, b, swept, base, blocks, s);
+    } else {
+        const size_t smem = base + (size_t)N * a.n_classes * a.n_classes * es + sw * 4;
+        if (smem > (size_t)std::min(smem_max, 160 * 1024)) return 0;
+        rc = launch_bhm_std<T, R, false>(a, off, b, swept, smem, blocks, s);
+    }
+    return rc ? rc : 1;
+}
+
+template <typename T>
+static int try_bhm_std(const FieldArgs& a, const Offsets& off, int R, const void* wrow, int swept, int smem_max,
+                       int blocks, cudaStream_t s) {
+    switch (R) {
+        case 2: return try_bhm_std_R<T, 2>(a, off, wrow, swept, smem_max, blocks, s);
+        case 3: return try_bhm_std_R<T, 3>(a, off, wrow, swept, smem_max, blocks, s);
+        case 4: return try_bhm_std_R<T, 4>(a, off, wrow, swept, smem_max, blocks, s);
+        case 5: return try_bhm_std_R<T, 5>(a, off, wrow, swept, smem_max, blocks, s);
+        default: return 0;
+    }
+}
+
 template <int R>
 static size_t fast_smem(int nk, int nx, int nz, size_t es, bool pn) {
     const int line_max = std::max(nx, nz);
@@ -1243,7 +1466,13 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     CHERT_REQUIRE(sched != 1 || R <= kBH, "%s: the block scheduler takes stencils of reach <= %d (got %d)", who,
                   kBH, R);
     const bool hybrid = sched == 2 && R <= kBH && max_cycles > kHybridSweeps;
+    const void* swept_wrow = nullptr;                  // per-node weights the sweeps computed, if any
     auto block_heap = [&](int swept) -> int {
+        const int r = precision == CHERT_FP64
+                          ? try_bhm_std<double>(a, off, R, swept_wrow, swept, smem_max, blocks, s)
+                          : try_bhm_std<float>(a, off, R, swept_wrow, swept, smem_max, blocks, s);
+        if (r < 0) return r;
+        if (r == 1) return CHERT_OK;
         const size_t nt = (size_t)((nx + kBT - 1) / kBT) * ((nz + kBT - 1) / kBT);
         const size_t sw = (size_t)(kBT + 2 * R) * (kBT + 2 * R);
         const size_t baseb = n_off * es + nt * es + 32 * es + sw * (es + 4) + (size_t)n_off * 4 + 32 * 4 +
@@ -1300,6 +1529,7 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     if (rc) return rc;
     if (hybrid) {
         a.max_cycles = max_cycles;
+        swept_wrow = fa.wrow;
         rc = block_heap(kHybridSweeps);
         if (rc) return rc;
     }

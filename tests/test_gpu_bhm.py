@@ -183,3 +183,41 @@ def test_hybrid_continues_unconverged_fields(torch_dev):
     g = [t.cpu().numpy() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=7)]
     for a, b in zip(ref, g):
         assert np.array_equal(a, b)
+
+
+def test_hybrid_continuation_on_per_node_weights(torch_dev):
+    """One class per node on the 12-bend serpentine: the sweeps use per-node
+    weights and need more than 6 cycles, so the hybrid's continuation runs
+    the standard-stencil block-heap kernel on those per-node weights; the
+    fields and parents equal the sweeps'."""
+    nx, nz = 280, 120
+    n = nx * nz
+    chan = _serpentine(nx, nz, 12).astype(bool)
+    rng = np.random.default_rng(47)
+    M = 6
+    nd = 4 * M
+    th = (math.pi / 2) * np.arange(nd) / M
+    v0 = np.where(chan, 6000.0, 150.0) * rng.uniform(0.98, 1.02, n)
+    a0 = np.where(chan, 1e-5, 1e-3) * rng.uniform(0.9, 1.1, n)
+    cnp = {"V": np.repeat(v0[None, :, None], nd, 2), "A": np.repeat(a0[None, :, None], nd, 2),
+           "rx": np.tile(np.sin(th), (1, n, 1)), "rz": np.tile(np.cos(th), (1, n, 1)),
+           "theta": np.tile(th, (1, n, 1)), "vartheta": np.zeros((1, n, nd)),
+           "flag": np.zeros((1, n, nd), np.uint8)}
+    cnp["Q"] = np.full_like(cnp["V"], np.inf)
+    off = inputs.stencil_2d(3)
+    cls = np.arange(n, dtype=np.int32)
+    src = [2 + nx * 1]
+    d_cls = torch_dev.as_tensor(cls, device="cuda")
+    for precision in ("fp64", "fp32"):
+        cache = as_cache(torch_dev, cnp, precision)
+        try:
+            chert.set_relax_scheduler("sweeps")
+            with pytest.raises(chert.ChertError) as e:
+                chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=6)
+            assert e.value.code == chert.ETIMEOUT
+            ref = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, src, max_cycles=256)
+        finally:
+            chert.set_relax_scheduler("hybrid")
+        g = [t.cpu().numpy() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=7)]
+        for a, b in zip(ref, g):
+            assert np.array_equal(a, b)
