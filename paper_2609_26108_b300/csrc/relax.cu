@@ -347,77 +347,30 @@ constexpr int kBH = 8;
 // (the next one), so no barrier is needed between clearing and writing.
 constexpr int kSB = 8, kNSB = kBT / kSB;
 
-template <typename T, int WMODE>
-// swept > 0: the fields were swept for `swept` cycles first; the CTAs whose
-// field converged there (status >= 0) return at once, the others solve their
-// field again from the source.  (Continuing from the swept traveltimes was
-// measured slower: fields that have not converged after a few cycles still
-// have improvable nodes almost everywhere, and the blocks' keys then give a
-// poor order.)
-__global__ void __launch_bounds__(1024) relax_bhm_kernel(FieldArgs a, Offsets off, int H, int swept) {
-    if (swept > 0 && a.status[blockIdx.x] >= 0) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nk = a.n_classes;
-    const int field = blockIdx.x >> 1;
-    const int comp = blockIdx.x & 1;
-    const int mode = field % a.n_modes;
-    const int s = field / a.n_modes;
-    const int nx = a.nx, nz = a.nz;
+// One field component by block-heap marching, shared by both kernels below.
+// The window of the block being relaxed is wt (SW x SW, halo H); stage(q, g,
+// in) stages what the pulls need besides tau at window position q (lattice
+// node g, in = on the lattice); pull(e, x, z, cur) returns the least of cur
+// and the pulls of the node at window position e (lattice x, z); verify()
+// is the verification pass (true: something improved).  Returns the cycles
+// used (swept + verification passes), or -1 when a cap ran out.
+template <typename T, typename Stage, typename Pull, typename Verify>
+__device__ __forceinline__ int bhm_field(T* tau, int nx, int nz, int64_t src, int max_cycles, int swept, int H,
+                                         T* key, T* rv, int* ri, T* wt, int* chg, unsigned char* m9raw,
+                                         Stage stage, Pull pull, Verify verify_pass) {
+    using Bits = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
+    Bits* m9 = reinterpret_cast<Bits*>(m9raw);
     const size_t n = static_cast<size_t>(nx) * nz;
     const int TX = (nx + kBT - 1) / kBT, TZ = (nz + kBT - 1) / kBT, nt = TX * TZ;
     const int SW = kBT + 2 * H;
-
-    Smem<T> sm;
-    unsigned char* p = smem_raw;
-    const size_t wcount = WMODE == 1 ? static_cast<size_t>(off.n) * nk * nk
-                          : WMODE == 0 ? static_cast<size_t>(nk) * off.n : 0;
-    sm.W = reinterpret_cast<T*>(p); p += wcount * sizeof(T);
-    sm.L = reinterpret_cast<T*>(p); p += off.n * sizeof(T);
-    T* key = reinterpret_cast<T*>(p); p += (size_t)nt * sizeof(T);
-    T* rv = reinterpret_cast<T*>(p); p += 32 * sizeof(T);
-    T* wt = reinterpret_cast<T*>(p); p += (size_t)SW * SW * sizeof(T);
-    int* wk = reinterpret_cast<int*>(p); p += (size_t)SW * SW * 4;
-    int* ws = reinterpret_cast<int*>(p); p += off.n * 4;      // window shift of each offset
-    int* ri = reinterpret_cast<int*>(p); p += 32 * 4;
-    int* chg = reinterpret_cast<int*>(p); p += 3 * kNSB * kNSB * 4;   // [3][kNSB * kNSB]
-    // least new value among the changed nodes within reach of each of the 3 x 3
-    // blocks around the current one (the centre: all changed nodes), as the
-    // bit patterns of non-negative values, which order like the values
-    using Bits = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
-    Bits* m9 = reinterpret_cast<Bits*>((reinterpret_cast<uintptr_t>(p) + 7) & ~uintptr_t(7));
-    sm.ring = nullptr;
-    sm.cring = nullptr;
-    sm.lists = nullptr;
-    sm.counts = nullptr;
-
-    const T* sel = static_cast<const T*>(comp == 0 ? a.Vsel : a.Asel) + static_cast<size_t>(mode) * nk * off.n;
-    for (int o = threadIdx.x; o < off.n; o += blockDim.x) {
-        const double ox = off.x[o], oz = off.z[o];
-        sm.L[o] = T(a.dx * sqrt(ox * ox + oz * oz));
-        ws[o] = off.x[o] + off.z[o] * SW;
-    }
-    __syncthreads();
-    if (WMODE == 1) {
-        for (int t = threadIdx.x; t < off.n * nk * nk; t += blockDim.x) {
-            const int kj = t % nk, ki = (t / nk) % nk, o = t / (nk * nk);
-            sm.W[t] = edge_w<T>(comp, sm.L[o], sel[ki * off.n + o], sel[kj * off.n + o]);
-        }
-    } else if (WMODE == 0) {
-        for (int t = threadIdx.x; t < nk * off.n; t += blockDim.x) sm.W[t] = sel[t];
-    }
-    T* tau = static_cast<T*>(comp == 0 ? a.tauR : a.tauI) + static_cast<size_t>(field) * n;
-    int32_t* par = comp == 0 ? a.parR : a.parI;
-    if (par) par += static_cast<size_t>(field) * n;
-    const int64_t src = a.src[s];
     for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
     for (int t = threadIdx.x; t < nt; t += blockDim.x)
         key[t] = t == (int)((src % nx) / kBT + (src / nx) / kBT * TX) ? T(0) : T(INFINITY);
     __syncthreads();
 
-    const long long max_pops = (long long)a.max_cycles * nt * 8;
+    const long long max_pops = (long long)max_cycles * nt * 8;
     long long pops = 0;
-    int used = -1;
-    for (int cycle = 0; cycle < a.max_cycles && pops <= max_pops; ++cycle) {
+    for (int cycle = 0; cycle < max_cycles && pops <= max_pops; ++cycle) {
         for (;;) {
             T bv = T(INFINITY);
             int bi = -1;
@@ -433,7 +386,7 @@ __global__ void __launch_bounds__(1024) relax_bhm_kernel(FieldArgs a, Offsets of
                 const bool in = x >= 0 && x < nx && z >= 0 && z < nz;
                 const size_t g = in ? (size_t)x + (size_t)nx * z : 0;
                 wt[q] = in ? tau[g] : T(INFINITY);
-                wk[q] = in ? clamp_class(a.cls[g], nk) : 0;
+                stage(q, g, in);
             }
             if (threadIdx.x == 0) key[kt] = T(INFINITY);
             for (int t = threadIdx.x; t < 3 * kNSB * kNSB; t += blockDim.x) chg[t] = 0;
@@ -458,14 +411,8 @@ __global__ void __launch_bounds__(1024) relax_bhm_kernel(FieldArgs a, Offsets of
                         }
                     if (!near) continue;
                     const int e = (q % kBT + H) + (q / kBT + H) * SW;
-                    const int kj = wk[e];
                     const T cur = wt[e];
-                    T best = cur;
-                    for (int o = 0; o < off.n; ++o) {
-                        const T ti = wt[e - ws[o]];
-                        if (!(ti < best)) continue;
-                        best = fmin(best, ti + pull_weight<T, WMODE>(sm, sel, off.n, nk, comp, o, wk[e - ws[o]], kj));
-                    }
+                    const T best = pull(e, x, z, cur);
                     if (best < cur) {
                         wt[e] = best;
                         any = true;
@@ -504,13 +451,102 @@ __global__ void __launch_bounds__(1024) relax_bhm_kernel(FieldArgs a, Offsets of
             __syncthreads();
         }
         if (pops > max_pops) break;
-        if (!verify<T, WMODE>(sm, sel, off, tau, a.cls, nx, nz, nk, comp, src, par)) {
-            used = swept + cycle + 1;
-            break;
-        }
+        if (!verify_pass()) return swept + cycle + 1;
         for (int t = threadIdx.x; t < nt; t += blockDim.x) key[t] = T(0);   // rare: start over everywhere
         __syncthreads();
     }
+    return -1;
+}
+
+// Shared memory of both kernels after their weight tables: key [nt], rv [32],
+// window tau [SW*SW], window class [SW*SW] (if staged), ri [32], chg
+// [3][kNSB^2], m9 [9] (8-byte aligned).
+struct BhmTail {
+    size_t key, rv, wt, wk, ri, chg, m9, end;
+};
+__host__ __device__ inline BhmTail bhm_tail(size_t at, int nt, int SW, size_t es, bool class_window) {
+    BhmTail t;
+    t.key = at;
+    t.rv = t.key + (size_t)nt * es;
+    t.wt = t.rv + 32 * es;
+    t.wk = t.wt + (size_t)SW * SW * es;
+    t.ri = t.wk + (class_window ? (size_t)SW * SW * 4 : 0);
+    t.chg = t.ri + 32 * 4;
+    t.m9 = (t.chg + 3 * kNSB * kNSB * 4 + 7) & ~size_t(7);
+    t.end = t.m9 + 9 * 8;
+    return t;
+}
+
+// swept > 0: the fields were swept for `swept` cycles first; the CTAs whose
+// field converged there (status >= 0) return at once, the others solve their
+// field again from the source.  (Continuing from the swept traveltimes was
+// measured slower: fields that have not converged after a few cycles still
+// have improvable nodes almost everywhere, and the blocks' keys then give a
+// poor order.)
+template <typename T, int WMODE>
+__global__ void __launch_bounds__(1024) relax_bhm_kernel(FieldArgs a, Offsets off, int H, int swept) {
+    if (swept > 0 && a.status[blockIdx.x] >= 0) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nk = a.n_classes;
+    const int field = blockIdx.x >> 1;
+    const int comp = blockIdx.x & 1;
+    const int mode = field % a.n_modes;
+    const int s = field / a.n_modes;
+    const int nx = a.nx, nz = a.nz;
+    const size_t n = static_cast<size_t>(nx) * nz;
+    const int nt = ((nx + kBT - 1) / kBT) * ((nz + kBT - 1) / kBT);
+    const int SW = kBT + 2 * H;
+
+    Smem<T> sm;
+    unsigned char* p = smem_raw;
+    const size_t wcount = WMODE == 1 ? static_cast<size_t>(off.n) * nk * nk
+                          : WMODE == 0 ? static_cast<size_t>(nk) * off.n : 0;
+    sm.W = reinterpret_cast<T*>(p); p += wcount * sizeof(T);
+    sm.L = reinterpret_cast<T*>(p); p += off.n * sizeof(T);
+    int* ws = reinterpret_cast<int*>(p); p += off.n * 4;      // window shift of each offset
+    sm.ring = nullptr;
+    sm.cring = nullptr;
+    sm.lists = nullptr;
+    sm.counts = nullptr;
+    const BhmTail tl = bhm_tail((size_t)(p - smem_raw + 15) & ~size_t(15), nt, SW, sizeof(T), true);
+    T* wt = reinterpret_cast<T*>(smem_raw + tl.wt);
+    int* wk = reinterpret_cast<int*>(smem_raw + tl.wk);
+
+    const T* sel = static_cast<const T*>(comp == 0 ? a.Vsel : a.Asel) + static_cast<size_t>(mode) * nk * off.n;
+    for (int o = threadIdx.x; o < off.n; o += blockDim.x) {
+        const double ox = off.x[o], oz = off.z[o];
+        sm.L[o] = T(a.dx * sqrt(ox * ox + oz * oz));
+        ws[o] = off.x[o] + off.z[o] * SW;
+    }
+    __syncthreads();
+    if (WMODE == 1) {
+        for (int t = threadIdx.x; t < off.n * nk * nk; t += blockDim.x) {
+            const int kj = t % nk, ki = (t / nk) % nk, o = t / (nk * nk);
+            sm.W[t] = edge_w<T>(comp, sm.L[o], sel[ki * off.n + o], sel[kj * off.n + o]);
+        }
+    } else if (WMODE == 0) {
+        for (int t = threadIdx.x; t < nk * off.n; t += blockDim.x) sm.W[t] = sel[t];
+    }
+    T* tau = static_cast<T*>(comp == 0 ? a.tauR : a.tauI) + static_cast<size_t>(field) * n;
+    int32_t* par = comp == 0 ? a.parR : a.parI;
+    if (par) par += static_cast<size_t>(field) * n;
+    const int64_t src = a.src[s];
+    const int used = bhm_field<T>(
+        tau, nx, nz, src, a.max_cycles, swept, H, reinterpret_cast<T*>(smem_raw + tl.key),
+        reinterpret_cast<T*>(smem_raw + tl.rv), reinterpret_cast<int*>(smem_raw + tl.ri), wt,
+        reinterpret_cast<int*>(smem_raw + tl.chg), smem_raw + tl.m9,
+        [&](int q, size_t g, bool in) { wk[q] = in ? clamp_class(a.cls[g], nk) : 0; },
+        [&](int e, int, int, T cur) {
+            const int kj = wk[e];
+            T best = cur;
+            for (int o = 0; o < off.n; ++o) {
+                const T ti = wt[e - ws[o]];
+                if (!(ti < best)) continue;
+                best = fmin(best, ti + pull_weight<T, WMODE>(sm, sel, off.n, nk, comp, o, wk[e - ws[o]], kj));
+            }
+            return best;
+        },
+        [&]() { return verify<T, WMODE>(sm, sel, off, tau, a.cls, nx, nz, nk, comp, src, par); });
     if (threadIdx.x == 0) a.status[blockIdx.x] = used;
 }
 
@@ -529,8 +565,7 @@ template <typename T, int R, bool PN>
 __global__ void __launch_bounds__(1024) relax_bhm_std_kernel(FieldArgs a, Offsets off, BhmStd b, int swept) {
     if (swept > 0 && a.status[blockIdx.x] >= 0) return;
     constexpr int N = fast::Stencil<R>::N;
-    constexpr int H = R, SW = kBT + 2 * R;
-    using Bits = typename std::conditional<sizeof(T) == 8, unsigned long long, unsigned int>::type;
+    constexpr int SW = kBT + 2 * R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = a.n_classes;
     const int field = blockIdx.x >> 1;
@@ -539,18 +574,14 @@ __global__ void __launch_bounds__(1024) relax_bhm_std_kernel(FieldArgs a, Offset
     const int s = field / a.n_modes;
     const int nx = a.nx, nz = a.nz;
     const size_t n = static_cast<size_t>(nx) * nz;
-    const int TX = (nx + kBT - 1) / kBT, TZ = (nz + kBT - 1) / kBT, nt = TX * TZ;
+    const int nt = ((nx + kBT - 1) / kBT) * ((nz + kBT - 1) / kBT);
 
     unsigned char* p = smem_raw;
     T* W = reinterpret_cast<T*>(p); p += PN ? 0 : (size_t)N * nk * nk * sizeof(T);
     T* Lc = reinterpret_cast<T*>(p); p += (size_t)off.n * sizeof(T);     // lengths, caller order
-    T* key = reinterpret_cast<T*>(p); p += (size_t)nt * sizeof(T);
-    T* rv = reinterpret_cast<T*>(p); p += 32 * sizeof(T);
-    T* wt = reinterpret_cast<T*>(p); p += (size_t)SW * SW * sizeof(T);
-    int* wk = reinterpret_cast<int*>(p); p += PN ? 0 : (size_t)SW * SW * 4;
-    int* ri = reinterpret_cast<int*>(p); p += 32 * 4;
-    int* chg = reinterpret_cast<int*>(p); p += 3 * kNSB * kNSB * 4;
-    Bits* m9 = reinterpret_cast<Bits*>((reinterpret_cast<uintptr_t>(p) + 7) & ~uintptr_t(7));
+    const BhmTail tl = bhm_tail((size_t)(p - smem_raw + 15) & ~size_t(15), nt, SW, sizeof(T), !PN);
+    T* wt = reinterpret_cast<T*>(smem_raw + tl.wt);
+    int* wk = reinterpret_cast<int*>(smem_raw + tl.wk);      // class id * nk (class-pair table only)
 
     const T* sel = static_cast<const T*>(comp == 0 ? a.Vsel : a.Asel) + static_cast<size_t>(mode) * nk * off.n;
     for (int o = threadIdx.x; o < off.n; o += blockDim.x) {
@@ -571,121 +602,37 @@ __global__ void __launch_bounds__(1024) relax_bhm_std_kernel(FieldArgs a, Offset
     int32_t* par = comp == 0 ? a.parR : a.parI;
     if (par) par += static_cast<size_t>(field) * n;
     const int64_t src = a.src[s];
-    for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
-    for (int t = threadIdx.x; t < nt; t += blockDim.x)
-        key[t] = t == (int)((src % nx) / kBT + (src / nx) / kBT * TX) ? T(0) : T(INFINITY);
-    __syncthreads();
-
     Smem<T> sm{};                                    // for the generic verification pass (global tables)
     sm.L = Lc;
-    const long long max_pops = (long long)a.max_cycles * nt * 8;
-    long long pops = 0;
-    int used = -1;
-    for (int cycle = 0; cycle < a.max_cycles && pops <= max_pops; ++cycle) {
-        for (;;) {
-            T bv = T(INFINITY);
-            int bi = -1;
-            for (int t = threadIdx.x; t < nt; t += blockDim.x)
-                if (key[t] < bv) { bv = key[t]; bi = t; }
-            T kv;
-            int kt;
-            block_argmin(bv, bi, rv, ri, kv, kt);
-            if (kt < 0 || ++pops > max_pops) break;
-            const int x0 = (kt % TX) * kBT, z0 = (kt / TX) * kBT;
-            for (int q = threadIdx.x; q < SW * SW; q += blockDim.x) {      // stage the window
-                const int x = x0 - H + q % SW, z = z0 - H + q / SW;
-                const bool in = x >= 0 && x < nx && z >= 0 && z < nz;
-                const size_t g = in ? (size_t)x + (size_t)nx * z : 0;
-                wt[q] = in ? tau[g] : T(INFINITY);
-                if constexpr (!PN) wk[q] = in ? clamp_class(a.cls[g], nk) * nk : 0;
+    const int used = bhm_field<T>(
+        tau, nx, nz, src, a.max_cycles, swept, R, reinterpret_cast<T*>(smem_raw + tl.key),
+        reinterpret_cast<T*>(smem_raw + tl.rv), reinterpret_cast<int*>(smem_raw + tl.ri), wt,
+        reinterpret_cast<int*>(smem_raw + tl.chg), smem_raw + tl.m9,
+        [&](int q, size_t g, bool in) {
+            if constexpr (!PN) wk[q] = in ? clamp_class(a.cls[g], nk) * nk : 0;
+        },
+        [&](int e, int x, int z, T cur) {
+            T best = cur;
+            if constexpr (PN) {
+                const T* wj = wrow + (size_t)x + (size_t)nx * z;
+                fast::static_for<N>([&](auto qc) {
+                    constexpr int qq = decltype(qc)::value;
+                    constexpr int sh = fast::Table<R>::v.x[qq] + fast::Table<R>::v.z[qq] * SW;
+                    const T ti = wt[e - sh];
+                    if (ti < best) best = fmin(best, ti + wj[(size_t)qq * n]);
+                });
+            } else {
+                const T* Wj = W + wk[e] / nk;          // + q*nk*nk + k_i*nk
+                fast::static_for<N>([&](auto qc) {
+                    constexpr int qq = decltype(qc)::value;
+                    constexpr int sh = fast::Table<R>::v.x[qq] + fast::Table<R>::v.z[qq] * SW;
+                    const T ti = wt[e - sh];
+                    if (ti < best) best = fmin(best, ti + Wj[qq * nk * nk + wk[e - sh]]);
+                });
             }
-            if (threadIdx.x == 0) key[kt] = T(INFINITY);
-            for (int t = threadIdx.x; t < 3 * kNSB * kNSB; t += blockDim.x) chg[t] = 0;
-            if (threadIdx.x < 9) m9[threadIdx.x] = to_bits<T, Bits>(T(INFINITY));
-            __syncthreads();
-            unsigned changed = 0;
-            bool still = false;
-            for (int it = 0; it < 4 * kBT; ++it) {
-                bool any = false;
-                const int* prev = chg + ((it + 2) % 3) * kNSB * kNSB;
-                int* now = chg + (it % 3) * kNSB * kNSB;
-                if (it > 0 && threadIdx.x < kNSB * kNSB) chg[((it + 1) % 3) * kNSB * kNSB + threadIdx.x] = 0;
-                for (int q = threadIdx.x, k = 0; q < kBT * kBT; q += blockDim.x, ++k) {
-                    const int x = x0 + q % kBT, z = z0 + q / kBT;
-                    if (x >= nx || z >= nz) continue;
-                    const int bx = (q % kBT) / kSB, bz = (q / kBT) / kSB;
-                    bool near = it == 0;
-                    for (int dz = -1; dz <= 1 && !near; ++dz)
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            const int cx = bx + dx, cz = bz + dz;
-                            if (cx >= 0 && cx < kNSB && cz >= 0 && cz < kNSB && prev[cz * kNSB + cx]) near = true;
-                        }
-                    if (!near) continue;
-                    const int e = (q % kBT + H) + (q / kBT + H) * SW;
-                    const T cur = wt[e];
-                    T best = cur;
-                    if constexpr (PN) {
-                        const T* wj = wrow + (size_t)x + (size_t)nx * z;
-                        fast::static_for<N>([&](auto qc) {
-                            constexpr int qq = decltype(qc)::value;
-                            constexpr int sh = fast::Table<R>::v.x[qq] + fast::Table<R>::v.z[qq] * SW;
-                            const T ti = wt[e - sh];
-                            if (ti < best) best = fmin(best, ti + wj[(size_t)qq * n]);
-                        });
-                    } else {
-                        const T* Wj = W + wk[e] / nk;      // + q*nk*nk + k_i*nk
-                        fast::static_for<N>([&](auto qc) {
-                            constexpr int qq = decltype(qc)::value;
-                            constexpr int sh = fast::Table<R>::v.x[qq] + fast::Table<R>::v.z[qq] * SW;
-                            const T ti = wt[e - sh];
-                            if (ti < best) best = fmin(best, ti + Wj[qq * nk * nk + wk[e - sh]]);
-                        });
-                    }
-                    if (best < cur) {
-                        wt[e] = best;
-                        any = true;
-                        changed |= 1u << k;
-                        now[bz * kNSB + bx] = 1;
-                    }
-                }
-                still = __syncthreads_or(any);
-                if (!still) break;
-            }
-            for (int q = threadIdx.x, k = 0; q < kBT * kBT; q += blockDim.x, ++k) {   // write back, re-key
-                const int lx = q % kBT, lz = q / kBT;
-                const int x = x0 + lx, z = z0 + lz;
-                if (x >= nx || z >= nz) continue;
-                const T v = wt[(lx + H) + (lz + H) * SW];
-                tau[(size_t)x + (size_t)nx * z] = v;
-                if (!((changed >> k) & 1u)) continue;
-                const Bits bb = to_bits<T, Bits>(v);
-                const int sx = lx < H ? 0 : lx >= kBT - H ? 2 : 1;
-                const int sz = lz < H ? 0 : lz >= kBT - H ? 2 : 1;
-                atomicMin(&m9[4], bb);
-                if (sx != 1) atomicMin(&m9[3 + sx], bb);
-                if (sz != 1) atomicMin(&m9[sz * 3 + 1], bb);
-                if (sx != 1 && sz != 1) atomicMin(&m9[sz * 3 + sx], bb);
-            }
-            __syncthreads();
-            if (threadIdx.x < 9) {
-                const T m = from_bits<T, Bits>(m9[threadIdx.x]);
-                const int tx = kt % TX + (int)threadIdx.x % 3 - 1, tz = kt / TX + (int)threadIdx.x / 3 - 1;
-                const bool self = threadIdx.x == 4;
-                if (m < T(INFINITY) && tx >= 0 && tx < TX && tz >= 0 && tz < TZ && (!self || still)) {
-                    T* kk = key + tz * TX + tx;
-                    *kk = fmin(*kk, m);
-                }
-            }
-            __syncthreads();
-        }
-        if (pops > max_pops) break;
-        if (!verify<T, 2>(sm, sel, off, tau, a.cls, nx, nz, nk, comp, src, par)) {
-            used = swept + cycle + 1;
-            break;
-        }
-        for (int t = threadIdx.x; t < nt; t += blockDim.x) key[t] = T(0);
-        __syncthreads();
-    }
+            return best;
+        },
+        [&]() { return verify<T, 2>(sm, sel, off, tau, a.cls, nx, nz, nk, comp, src, par); });
     if (threadIdx.x == 0) a.status[blockIdx.x] = used;
 }
 
@@ -1090,14 +1037,14 @@ static int try_bhm_std_R(const FieldArgs& a, const Offsets& off, const void* wro
     constexpr int N = fast::Stencil<R>::N;
     const size_t es = sizeof(T);
     const size_t nt = (size_t)((a.nx + kBT - 1) / kBT) * ((a.nz + kBT - 1) / kBT);
-    const size_t sw = (size_t)(kBT + 2 * R) * (kBT + 2 * R);
-    const size_t base = (size_t)off.n * es + nt * es + 32 * es + sw * es + 32 * 4 + 3 * kNSB * kNSB * 4 + 9 * 8 + 64;
     int rc;
     if (wrow) {
-        if (base > (size_t)smem_max) return 0;
-        rc = launch_bhm_std<T, R, true>(a, off, b, swept, base, blocks, s);
+        const size_t smem = bhm_tail(((size_t)off.n * es + 15) & ~size_t(15), (int)nt, kBT + 2 * R, es, false).end;
+        if (smem > (size_t)smem_max) return 0;
+        rc = launch_bhm_std<T, R, true>(a, off, b, swept, smem, blocks, s);
     } else {
-        const size_t smem = base + (size_t)N * a.n_classes * a.n_classes * es + sw * 4;
+        const size_t head = (size_t)N * a.n_classes * a.n_classes * es + (size_t)off.n * es;
+        const size_t smem = bhm_tail((head + 15) & ~size_t(15), (int)nt, kBT + 2 * R, es, true).end;
         if (smem > (size_t)std::min(smem_max, 160 * 1024)) return 0;
         rc = launch_bhm_std<T, R, false>(a, off, b, swept, smem, blocks, s);
     }
@@ -1474,11 +1421,13 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         if (r < 0) return r;
         if (r == 1) return CHERT_OK;
         const size_t nt = (size_t)((nx + kBT - 1) / kBT) * ((nz + kBT - 1) / kBT);
-        const size_t sw = (size_t)(kBT + 2 * R) * (kBT + 2 * R);
-        const size_t baseb = n_off * es + nt * es + 32 * es + sw * (es + 4) + (size_t)n_off * 4 + 32 * 4 +
-                             3 * 16 * 4 + 9 * 8 + 64;
-        const size_t tb = (size_t)n_off * n_classes * n_classes * es + baseb;
-        const size_t rb = (size_t)n_classes * n_off * es + baseb;
+        auto tail = [&](size_t wbytes) {
+            const size_t head = wbytes + n_off * es + (size_t)n_off * 4;
+            return bhm_tail((head + 15) & ~size_t(15), (int)nt, kBT + 2 * R, es, true).end;
+        };
+        const size_t baseb = tail(0);
+        const size_t tb = tail((size_t)n_off * n_classes * n_classes * es);
+        const size_t rb = tail((size_t)n_classes * n_off * es);
         const int mb = tb <= (size_t)std::min(smem_max, 160 * 1024) ? 1 : rb <= (size_t)smem_max ? 0 : 2;
         const size_t smb = mb == 1 ? tb : mb == 0 ? rb : baseb;
         CHERT_REQUIRE(smb <= (size_t)smem_max, "%s: lattice too large for the block scheduler", who);
