@@ -423,7 +423,7 @@ def section_3d(flush, n_sources=16):
     _, t_relax = timed(lambda: chert.traveltime(cache, m.nx, m.nz, m.dx, d_cls, off, src, max_cycles=64,
                                                 out=tau, workspace=ws, ny=m.ny, precision="fp32_acc64"))
     nf = len(src) * len(modes)
-    # receiver gathers (survey NEXT-1): a 21 x 21 surface grid per field, both components
+    # receiver gathers: a 21 x 21 surface grid per field, both components
     g = np.round(np.linspace(0, m.nx - 1, 21)).astype(np.int64)
     rcv = torch.as_tensor(np.array([x + m.nx * y for y in g for x in g], dtype=np.int64), device="cuda")
     fsrc = torch.as_tensor(np.repeat(np.asarray(src, np.int64), len(modes)), device="cuda")
