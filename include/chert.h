@@ -217,9 +217,14 @@ size_t chert_traveltime_workspace_bytes_grid(int n_modes, int n_classes, int n_o
  * source, par = -1 and tau = +inf where unreachable (Eq. 33).
  * Outputs are device arrays [n_sources][n_modes][nz*ny*nx].
  * 2D cycles sweep lines (rows and columns, both ways); 3D cycles sweep planes
- * of constant z, y and x, both ways.
- * max_cycles caps the sweep cycles per field; a field that has not converged
- * after it returns CHERT_ETIMEOUT (its values are valid upper bounds).
+ * of constant z, y and x, both ways.  Which 2D scheduler runs (sweeps, the
+ * paper's block-heap marching, or the default hybrid of the two) is set by
+ * chert_set_relax_scheduler; all give the same fields and parents.
+ * max_cycles caps the sweep cycles per field (under block-heap marching: the
+ * verification passes, and max_cycles x blocks x 8 block relaxations); a
+ * field that has not converged after it returns CHERT_ETIMEOUT (its values
+ * are valid upper bounds, except for a block-heap field cut off mid-way,
+ * whose unreached nodes hold +inf).
  * Synchronises on `stream` once at the end to read the convergence status.
  * Errors: CHERT_EINVAL, CHERT_ENOMEM (workspace too small), CHERT_ECUDA,
  * CHERT_ETIMEOUT. */
