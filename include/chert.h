@@ -223,8 +223,8 @@ size_t chert_traveltime_workspace_bytes_grid(int n_modes, int n_classes, int n_o
  * max_cycles caps the sweep cycles per field (under block-heap marching: the
  * verification passes, and max_cycles x blocks x 8 block relaxations); a
  * field that has not converged after it returns CHERT_ETIMEOUT (its values
- * are valid upper bounds, except for a block-heap field cut off mid-way,
- * whose unreached nodes hold +inf).
+ * are valid upper bounds; the nodes that a block-heap field cut off mid-way
+ * has not reached hold +inf).
  * Synchronises on `stream` once at the end to read the convergence status.
  * Errors: CHERT_EINVAL, CHERT_ENOMEM (workspace too small), CHERT_ECUDA,
  * CHERT_ETIMEOUT. */
