@@ -108,3 +108,27 @@ def test_relax_points_per_thread_switch_host_only(lib):
     assert lib.chert_set_relax_points_per_thread(3) == chert.EINVAL
     prev = lib.chert_set_relax_points_per_thread(2)
     assert lib.chert_set_relax_points_per_thread(prev) == 2
+
+
+def test_tracer_counts_the_hybrid_continuation(lib):
+    """The launch count a Tracer reports follows the scheduler: the hybrid
+    adds its continuation only where the library launches it (stencil reach
+    <= 8 and max_cycles > 6)."""
+    import numpy as np
+    from paper_2609_26108_b300 import inputs
+    from paper_2609_26108_b300.pipeline import Tracer
+    tr = Tracer.__new__(Tracer)                     # host state only, no device buffers
+    tr.offsets = np.asarray(inputs.stencil_2d(5), np.int32).reshape(-1, 3)
+    tr.max_cycles = 64
+    try:
+        chert.set_relax_scheduler("hybrid")
+        assert tr.launches_per_run == 7
+        tr.max_cycles = 6
+        assert tr.launches_per_run == 6
+        tr.max_cycles = 64
+        chert.set_relax_scheduler("sweeps")
+        assert tr.launches_per_run == 6
+        chert.set_relax_scheduler("block_heap")
+        assert tr.launches_per_run == 6
+    finally:
+        chert.set_relax_scheduler("hybrid")
