@@ -19,3 +19,21 @@ def test_reference_arm_json_line():
         assert key in line
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+
+
+def test_relaxation_rooflines_arithmetic():
+    """The HBM and issue-rate rooflines of the bench line: achieved over peak,
+    the peak from the unit counts and the clock, and the HBM peak from the
+    measured file when present."""
+    sys.path.insert(0, ROOT)
+    import bench
+    peak, src = bench.measured_hbm_gbs()
+    assert peak > 0 and src in ("of measured", "of fallback")
+    h = bench.hbm_roofline(2.0e9, 4.0e9, 0.5)
+    assert abs(h["achieved_gbs"] - 4.0) < 1e-12 and abs(h["dram_gbs"] - 8.0) < 1e-12
+    assert abs(h["frac"] - 4.0 / peak) < 1e-15
+    assert "dram_gbs" not in bench.hbm_roofline(2.0e9, None, 0.5)
+    i = bench.issue_roofline(1.0e12, 1.0, 2000.0)
+    want = 148 * 4 * 2000e6 * 32 / bench.INSTR_PER_PULL
+    assert abs(i["peak_pulls_per_s"] - want) < 1e-3 * want
+    assert abs(i["frac"] - 1.0e12 / want) < 1e-12
