@@ -250,34 +250,35 @@ def solve_direction(A, theta, mode, kernel, h=0.001 * DEG, K=30000):
 
 
 # --------------------------------------------------------------- cache (Eq. 26)
-def build_cache(moduli, tilts, modes, M, kernel="MEV", h=0.001 * DEG, K=30000):
-    """Directional cache for classes ``moduli`` [n_classes, 5] (complex) with
-    tilts theta_0 [n_classes] (rad), wave modes ``modes`` (names from MODES) and
-    M slowness angles per quadrant.
+def folded_solves(A, mode, M, kernel="MEV", h=0.001 * DEG, K=30000):
+    """The M+1 solves of one (mode, class) at the folded slowness angles
+    theta_j = j*(pi/2)/M, j = 0..M (the 0-90 deg TI range of Eq. 26)."""
+    return [solve_direction(A, (math.pi / 2) * j / M, mode, kernel, h, K) for j in range(M + 1)]
 
-    Returns a dict of arrays shaped [n_modes, n_classes, 4M]: V, A, Q, rx, rz,
-    theta (global slowness angle, from +z toward +x), vartheta (signed as seen
-    from that direction), flag.  Directions d of the local frame are
-    theta_d = d*(pi/2)/M; the solve runs at the folded angle and the ray
-    direction is mirrored back to the quadrant of theta_d, then rotated by the
-    tilt (Eq. 36)."""
-    moduli = np.asarray(moduli, dtype=np.complex128).reshape(-1, 5)
+
+def assemble_cache(folded, tilts, M):
+    """Cache arrays [n_modes, n_classes, 4M] from folded solves.
+
+    folded[mi][k] is the list of M+1 solve dicts of mode slot mi and class k
+    (keys V, A, Q, r, vartheta, flag).  Direction d of the local frame is the
+    slowness angle theta_d = d*(pi/2)/M; it takes the solve at its folded
+    angle, with the ray direction mirrored into the quadrant of theta_d and
+    rotated by the tilt theta_0 (Eq. 36).  Returns V, A, Q, rx, rz, theta
+    (global slowness angle, from +z toward +x), vartheta (signed as seen from
+    that direction) and flag."""
     tilts = np.asarray(tilts, dtype=np.float64).reshape(-1)
-    nm, nk, nd = len(modes), moduli.shape[0], 4 * M
+    nm, nk, nd = len(folded), len(folded[0]), 4 * M
     out = {key: np.zeros((nm, nk, nd)) for key in ("V", "A", "Q", "rx", "rz", "theta", "vartheta")}
     out["flag"] = np.zeros((nm, nk, nd), dtype=np.uint8)
     signs = [(1.0, 1.0), (1.0, -1.0), (-1.0, -1.0), (-1.0, 1.0)]
-    for mi, mode in enumerate(modes):
+    for mi in range(nm):
         for k in range(nk):
-            A = stiffness_tensor(moduli[k])
-            folded = [solve_direction(A, (math.pi / 2) * j / M, mode, kernel, h, K)
-                      for j in range(M + 1)]
             ct, st = math.cos(tilts[k]), math.sin(tilts[k])
             for d in range(nd):
                 quad, rem = divmod(d, M)
                 j = rem if quad in (0, 2) else M - rem
                 sx, sz = signs[quad]
-                s = folded[j]
+                s = folded[mi][k][j]
                 lx, lz = sx * s["r"][0], sz * s["r"][2]
                 out["rx"][mi, k, d] = lx * ct + lz * st          # Eq. 36
                 out["rz"][mi, k, d] = -lx * st + lz * ct
@@ -288,6 +289,17 @@ def build_cache(moduli, tilts, modes, M, kernel="MEV", h=0.001 * DEG, K=30000):
                 out["theta"][mi, k, d] = (math.pi / 2) * d / M + tilts[k]
                 out["flag"][mi, k, d] = s["flag"]
     return out
+
+
+def build_cache(moduli, tilts, modes, M, kernel="MEV", h=0.001 * DEG, K=30000):
+    """Directional cache for classes ``moduli`` [n_classes, 5] (complex) with
+    tilts theta_0 [n_classes] (rad), wave modes ``modes`` (names from MODES) and
+    M slowness angles per quadrant: the folded solves of every (mode, class),
+    assembled by ``assemble_cache`` (arrays shaped [n_modes, n_classes, 4M])."""
+    moduli = np.asarray(moduli, dtype=np.complex128).reshape(-1, 5)
+    folded = [[folded_solves(stiffness_tensor(moduli[k]), mode, M, kernel, h, K) for k in range(moduli.shape[0])]
+              for mode in modes]
+    return assemble_cache(folded, tilts, M)
 
 
 def local_basis(theta0, phi0):
