@@ -78,10 +78,15 @@ __device__ __forceinline__ float sh_(float x) { return sinhf(x); }
 __device__ __forceinline__ double sh_(double x) { return sinh(x); }
 
 // Complex energy velocity (x and z components) at slowness angle theta + i vt,
-// with s = sin(theta), c = cos(theta).
+// with s = sin(theta), c = cos(theta).  If cond is not null it receives the
+// squared amplification of rounding errors in v: (|tr|/|D|)^2 (the eigen-gap
+// of the 2x2 block, tr its trace, D the square root of its discriminant) times
+// (|g|^2/|g.g|)^2 (the bilinear norm that divides v), 1 for qSH, and +inf
+// where the qP/qSV labels are ambiguous (Re D within 2^-14 |tr| of 0: the two
+// eigenvalues' real parts, which order the labels, nearly coincide).
 template <typename T>
 __device__ __forceinline__ void energy_velocity_body(const Medium<T>& m, T s, T c, T vt, int mode,
-                                                     int kernel, cplx<T>& v1, cplx<T>& v3) {
+                                                     int kernel, cplx<T>& v1, cplx<T>& v3, T* cond) {
     const T chv = ch_(vt), shv = sh_(vt);
     const cplx<T> n1 = mk<T>(s * chv, c * shv);     // sin(theta + i vt)
     const cplx<T> n3 = mk<T>(c * chv, -s * shv);    // cos(theta + i vt)
@@ -90,6 +95,7 @@ __device__ __forceinline__ void energy_velocity_body(const Medium<T>& m, T s, T 
         const cplx<T> cc = csqrt(m.a66 * n11 + m.a44 * n33);
         v1 = m.a66 * (n1 / cc);
         v3 = m.a44 * (n3 / cc);
+        if (cond) *cond = T(1);
         return;
     }
     const cplx<T> b = m.a13 + m.a44;
@@ -121,6 +127,15 @@ __device__ __forceinline__ void energy_velocity_body(const Medium<T>& m, T s, T 
         v1 = v1 + e * p3;
         v3 = v3 - e * p1;
     }
+    if (cond) {
+        const T trn = norm2(tr);
+        if (D.re * D.re < T(0x1p-28) * trn) {
+            *cond = T(INFINITY);
+        } else {
+            const T hh = norm2(g1) + norm2(g3);
+            *cond = (trn / norm2(D)) * (hh * hh / norm2(bb));
+        }
+    }
 }
 
 // One out-of-line copy of the evaluation, per precision, serves every call
@@ -131,8 +146,8 @@ __device__ __forceinline__ void energy_velocity_body(const Medium<T>& m, T s, T 
 // 26% and 17% faster.
 template <typename T>
 __device__ __noinline__ void energy_velocity_call(const Medium<T>& m, T s, T c, T vt, int mode, int kernel,
-                                                  cplx<T>& v1, cplx<T>& v3) {
-    energy_velocity_body(m, s, c, vt, mode, kernel, v1, v3);
+                                                  cplx<T>& v1, cplx<T>& v3, T* cond = nullptr) {
+    energy_velocity_body(m, s, c, vt, mode, kernel, v1, v3, cond);
 }
 template <typename T>
 __device__ __forceinline__ void energy_velocity(const Medium<T>& m, T s, T c, T vt, int mode,
@@ -153,6 +168,38 @@ __device__ __forceinline__ T residual_cold(const Medium<T>& m, T s, T c, T vt, i
     cplx<T> v1, v3;
     energy_velocity_call(m, s, c, vt, mode, kernel, v1, v3);
     return v1.re * v3.im - v3.re * v1.im;
+}
+
+// Noise guard of the MIXED scan.  The float residual's rounding error stays
+// below about 1.1e-6 kappa |v|^2 (kappa^2 = the cond factor of
+// energy_velocity_body; measured against float-float evaluations over the
+// whole [-30, 30] deg grid of 3,024 media in every mode), so its sign is
+// trusted only where |f| >= 2^-13 kappa |v|^2, a margin of about 100.  Below
+// that (about 5e-4 of the grid points) the sign is taken from a float-float
+// evaluation at the exact grid point k*h, which is what a double scan sees.
+constexpr float kGuard2 = 0x1p-26f;          // (2^-13)^2
+
+// Float residual with its guard: returns f; need = whether |f| is within the
+// guard of zero (or the mode labels are ambiguous).
+__device__ __forceinline__ float residual_guarded(const Medium<float>& m, float s, float c, float vt, int mode,
+                                                  int kernel, bool& need) {
+    cplx<float> v1, v3;
+    float cond;
+    energy_velocity_call(m, s, c, vt, mode, kernel, v1, v3, &cond);
+    const float f = v1.re * v3.im - v3.re * v1.im;
+    const float sc = norm2(v1) + norm2(v3);
+    need = !(f * f >= kGuard2 * cond * (sc * sc));    // NaN or inf bounds also re-evaluate
+    return f;
+}
+
+// A residual of the refinement precision narrowed to the scan precision with
+// its sign kept (0 only for an exact zero).
+template <typename TP>
+__device__ __forceinline__ float narrow_sign(TP r) {
+    const double d = double(r);
+    if (d == 0.0) return 0.0f;
+    const float f = float(d);
+    return f != 0.0f ? f : copysignf(1.17549435e-38f, float(d > 0.0 ? 1 : -1));
 }
 
 template <typename T>
@@ -405,6 +452,62 @@ __device__ __forceinline__ float grid_point(float kf, double, float hf, float hl
 }
 __device__ __forceinline__ double grid_point(double kf, double h, float, float) { return kf * h; }
 
+// Re-evaluation of the guarded grid points of one scan step in the
+// refinement precision: the P points of lane l lie at grid distance
+// base + 1 + (l & 15)*P + p, on the negative side for l >= 16.  The pending
+// points of the whole warp are dealt out one per lane, so a step costs one
+// refinement-precision evaluation per 32 pending points.
+template <typename TP, typename TS, typename TSolve, int P>
+__device__ __forceinline__ void guard_points(const TSolve& v, int kernel, double h, int base, TS (&fv)[P],
+                                             const bool (&need)[P], int lane) {
+    unsigned pm[P];
+    int cum[P + 1];
+    cum[0] = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        pm[p] = __ballot_sync(0xffffffffu, need[p]);
+        cum[p + 1] = cum[p] + __popc(pm[p]);
+    }
+    const int total = cum[P];
+    for (int first = 0; first < total; first += 32) {
+        const int t = first + lane;
+        TS r = TS(0);
+        if (t < total) {
+            int p = 0;
+            while (t >= cum[p + 1]) ++p;
+            unsigned m = pm[p];
+            for (int i = cum[p]; i < t; ++i) m &= m - 1;          // drop the set bits before item t
+            const int l = __ffs(m) - 1;
+            const int kk = base + 1 + (l & 15) * P + p;
+            const double x = (l >= 16 ? -1.0 : 1.0) * (double(kk) * h);
+            r = narrow_sign(residual_cold(v.mp, v.sp, v.cp, TP(x), v.mode, kernel));
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int src = cum[p] + __popc(pm[p] & ((1u << lane) - 1u)) - first;
+            const TS got = __shfl_sync(0xffffffffu, r, src & 31);
+            if (need[p] && src >= 0 && src < 32) fv[p] = got;
+        }
+    }
+}
+
+// The residual at one grid distance kk (>= 0) on side sgn (+1 or -1), in the
+// scan precision; in MIXED, guarded like the scan's points.  Every lane of the
+// warp computes the same value.
+template <typename TS, typename TP>
+__device__ __forceinline__ TS scan_point(const Solve<TS, TP>& v, int kernel, double h, int kk, int sgn) {
+    const float hf = float(h), hl = float(h - double(hf));
+    const TS x = grid_point(TS(kk), h, hf, hl);
+    if constexpr (sizeof(TS) != sizeof(TP)) {
+        bool need = false;
+        const TS f = residual_guarded(v.ms, v.ss, v.cs, sgn < 0 ? -x : x, v.mode, kernel, need);
+        if (!need) return f;
+        return narrow_sign(residual_cold(v.mp, v.sp, v.cp, TP(double(sgn) * (double(kk) * h)), v.mode, kernel));
+    } else {
+        return residual(v.ms, v.ss, v.cs, sgn < 0 ? -x : x, v.mode, kernel);
+    }
+}
+
 // Outward scan of the grid distances kk in [k_begin, k_end] on both sides by
 // one warp.  fb_pos / fb_neg are the residuals at +-(k_begin-1)h.  Candidates
 // are taken in order of |vartheta| (brackets at inner distance kk-1 before the
@@ -424,10 +527,22 @@ __device__ bool scan_window(const Solve<TS, TP>& v, int kernel, double h, int k_
         const int k0 = base + 1 + l16 * P;
         const TS kf0 = TS(k0);
         TS fv[P];
+        if constexpr (mixed) {
+            bool need[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const TS xk = grid_point(kf0 + TS(p), h, hf, hl);
-            fv[p] = k0 + p <= k_end ? residual(v.ms, v.ss, v.cs, neg ? -xk : xk, mode, kernel) : TS(NAN);
+            for (int p = 0; p < P; ++p) {
+                const TS xk = grid_point(kf0 + TS(p), h, hf, hl);
+                need[p] = false;
+                fv[p] = k0 + p <= k_end ? residual_guarded(v.ms, v.ss, v.cs, neg ? -xk : xk, mode, kernel, need[p])
+                                        : TS(NAN);
+            }
+            guard_points<TP>(v, kernel, h, base, fv, need, lane);
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const TS xk = grid_point(kf0 + TS(p), h, hf, hl);
+                fv[p] = k0 + p <= k_end ? residual(v.ms, v.ss, v.cs, neg ? -xk : xk, mode, kernel) : TS(NAN);
+            }
         }
         TS before = __shfl_up_sync(0xffffffffu, fv[P - 1], 1);    // point just inside
         if (l16 == 0) before = neg ? prev_neg : prev_pos;
@@ -435,7 +550,9 @@ __device__ bool scan_window(const Solve<TS, TP>& v, int kernel, double h, int k_
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const TS fprev = p == 0 ? before : fv[p - 1];
-            bm[p] = __ballot_sync(0xffffffffu, fprev * fv[p] < TS(0));
+            // strict sign change (a product could underflow for the tiny
+            // guarded values that narrow_sign returns)
+            bm[p] = __ballot_sync(0xffffffffu, (fprev < TS(0) && fv[p] > TS(0)) || (fprev > TS(0) && fv[p] < TS(0)));
             zm[p] = __ballot_sync(0xffffffffu, fv[p] == TS(0));
         }
         prev_pos = __shfl_sync(0xffffffffu, fv[P - 1], 15);
@@ -607,7 +724,7 @@ __global__ void __launch_bounds__(256, 2) cache_build_kernel(const chert_class* 
     bool found = false;
     TP root = TP(0);
     RayQ<TP> fq{};
-    const TS f0 = residual(v.ms, v.ss, v.cs, TS(0), v.mode, kernel);
+    const TS f0 = scan_point(v, kernel, h, 0, 1);
     if (f0 == TS(0)) {
         const RayQ<TP> q = ray_quantities(v.mp, v.sp, v.cp, TP(0), v.mode, kernel);
         if (q.ok) { found = true; fq = q; }
@@ -639,7 +756,6 @@ __device__ void finish_one(const chert_class* __restrict__ classes, int n_classe
     __shared__ RayQ<TP> s_q[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, g, idx);
-    const float hf = float(h), hl = float(h - double(hf));
     constexpr int slice = 64;
     int winner = -1;
     for (int r0 = kPhase1Reach; r0 < K && winner < 0; r0 += 32 * slice) {
@@ -648,9 +764,8 @@ __device__ void finish_one(const chert_class* __restrict__ classes, int n_classe
         TP root = TP(0);
         RayQ<TP> q{};
         if (kb <= ke) {
-            const TS xb = grid_point(TS(kb - 1), h, hf, hl);
-            const TS fp = residual(v.ms, v.ss, v.cs, xb, v.mode, kernel);
-            const TS fn = residual(v.ms, v.ss, v.cs, -xb, v.mode, kernel);
+            const TS fp = scan_point(v, kernel, h, kb - 1, 1);
+            const TS fn = scan_point(v, kernel, h, kb - 1, -1);
             found = scan_window(v, kernel, h, kb, ke, fp, fn, lane, root, q);
         }
         if (lane == 0) {
