@@ -45,3 +45,39 @@ def rel_err(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.abspath(__file__)), "golden")
+THOMSEN_KEYS = ("vp0", "vs0", "eps", "delta", "gamma", "qp", "qs", "tilt")
+
+
+def load_cache_golden(name):
+    """A cache golden written by tests/golden/make_cache_golden.py: returns
+    {"folded": {(mode, class): [solve dict] * (M+1)}, "tilts": [...] or None,
+     "cells": [(node, {thomsen key: value})] or []} with solve dicts holding
+    flag, vartheta, V, A, Q and r = (r_x, 0, r_z) as the oracle returns them."""
+    import os
+    folded, tilts, cells = {}, None, []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.startswith("# tilts:"):
+                tilts = [float(v) for v in line.split(":", 1)[1].split()]
+                continue
+            if line.startswith("# cell "):
+                parts = line.split()
+                cells.append((int(parts[3]), dict(zip(THOMSEN_KEYS, map(float, parts[4:])))))
+                continue
+            if line.startswith("#") or not line.strip():
+                continue
+            mode, k, j, flag, vt, V, A, Q, rx, rz = line.split()
+            folded.setdefault((mode, int(k)), []).append(
+                {"flag": int(flag), "vartheta": float(vt), "V": float(V), "A": float(A), "Q": float(Q),
+                 "r": np.array([float(rx), 0.0, float(rz)])})
+            assert len(folded[(mode, int(k))]) == int(j) + 1
+    return {"folded": folded, "tilts": tilts, "cells": cells}
+
+
+def golden_cache(g, modes, n_classes, tilts, M=90):
+    """The oracle's cache arrays [n_modes, n_classes, 4M] from a loaded golden."""
+    folded = [[g["folded"][(m, k)] for k in range(n_classes)] for m in modes]
+    return co.assemble_cache(folded, tilts, M)
