@@ -352,22 +352,31 @@ int chert_surrogate_cache(const float* const* d_params_per_mode, const chert_cla
 
 /* The paper has no counterpart to this entry point; it exists for callers of
  * this library that cannot allocate device memory: code embedded in a host
- * whose device memory is owned by its own pool, code that runs while a stream
- * is being captured (where cudaMalloc is not allowed), or a runtime that
- * forbids allocation after start-up.  It computes exactly what
- * chert_traveltime computes, with the same arguments minus the workspace, and
+ * whose device memory is all owned by the host's own pool, or a runtime that
+ * forbids allocation after start-up.  It computes what chert_traveltime
+ * computes, bit for bit, with the same arguments minus the workspace, and
  * allocates nothing: its scratch is a fixed 1 MiB array in device memory that
  * libchert declares at file scope, so every device that loads the library
  * holds that array until the process exits.
  *   - Problems whose scratch (chert_traveltime_workspace_bytes) exceeds
  *     chert_traveltime_static_limit() minus 256 bytes are rejected with
- *     CHERT_EINVAL and a message naming both sizes.
+ *     CHERT_EINVAL and a message naming both sizes, before any output is
+ *     touched.
+ *   - On 2D lattices with too many classes for the class-pair table (e.g.
+ *     one class per node), chert_traveltime with a lattice-sized workspace
+ *     relaxes on precomputed per-node weights; here those weights use the
+ *     rest of the array when they fit, and otherwise the generic kernel runs
+ *     (same fields and parents, slower).
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     life of the process.  A cudaDeviceReset of that device invalidates it,
+ *     so do not call this entry point on a device after resetting it.
+ *   - It reads its status back and synchronises `stream`, so it cannot be
+ *     called while that stream is being captured into a CUDA graph; use
+ *     chert_traveltime_enqueue there.
  *   - All calls share the one array and it keeps the last call's contents
  *     (the parts that must start at zero are cleared by each call).  Calls
- *     that overlap on the GPU -- on different streams or different host
+ *     that overlap on the GPU -- on different streams or from different host
  *     threads -- race on it: serialise them.
  * Errors: as chert_traveltime, CHERT_ENOMEM never. */
 int chert_traveltime_static(const chert_cache_arrays* cache, int n_modes, int n_classes,
@@ -395,6 +404,31 @@ size_t chert_traveltime_static_limit(void);
 int chert_raypath(const int32_t* d_par, int n_fields, int64_t n_nodes,
                   const int64_t* d_src, const int64_t* d_rcv, int n_rcv, int64_t cap,
                   int64_t* d_paths, int64_t* d_len, void* stream);
+
+/* Tie log of the parent rule (Eq. 33).  For converged fields (as returned by
+ * chert_traveltime or chert_traveltime_enqueue for the same cache, lattice,
+ * class map, stencil and sources), node j of field f and component c is a
+ * tie when the second-best in-neighbour candidate tau_i + w_ij lies within
+ * rel_tol * best of the best one: rounding at that level can then make either
+ * predecessor the parent, so two correct implementations may return
+ * different parents (and raypaths through j) there.  The source and
+ * unreachable nodes are never ties.
+ *   d_Vsel, d_Asel  device [n_modes][n_classes][n_off] lookup tables from
+ *                   chert_edge_table (the relaxation's weights, Eq. 28-30, are
+ *                   rebuilt from them with the same rounding); double for
+ *                   CHERT_FP64, float otherwise
+ *   d_tauR, d_tauI  device [n_sources][n_modes][nodes]: double for CHERT_FP64
+ *                   and CHERT_FP32_ACC64, float otherwise
+ *   d_tieR, d_tieI  device uint8 [n_sources][n_modes][nodes] (0/1), may be NULL
+ *   d_counts        device uint64 [n_sources*n_modes][2] (ties per field and
+ *                   component), may be NULL
+ * Candidates are formed in the traveltime type; at most 65535 fields per
+ * call.  Errors: CHERT_EINVAL, CHERT_ECUDA. */
+int chert_parent_ties(const void* d_Vsel, const void* d_Asel, int n_modes, int n_classes, int precision,
+                      int nx, int ny, int nz, double dx, const int32_t* d_class_of_node,
+                      const int32_t* offsets, int n_off, const int64_t* d_sources, int n_sources,
+                      const void* d_tauR, const void* d_tauI, double rel_tol, uint8_t* d_tieR,
+                      uint8_t* d_tieI, unsigned long long* d_counts, void* stream);
 
 /* Message describing the last error returned on the calling host thread. */
 const char* chert_last_error(void);

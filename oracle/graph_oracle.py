@@ -9,6 +9,9 @@ Only tests, the smoke check and the benchmark's CPU-baseline leg may call this.
 * ``dijkstra``          FP64 binary-heap Dijkstra in plain C (graph_oracle.c) for
   the fixed point of Eq. 31 with the segment-averaged increments of Eq. 28-30,
   and the deterministic parent rule.
+* ``parent_ties``       the nodes where the parent rule's two best candidates lie
+  within a relative tolerance of each other (where rounding can change the
+  parent, Eq. 33).
 * ``floyd_warshall``    all-pairs check for tiny grids.
 * ``raypath``           backtracking of Eq. 33 from a receiver to the source.
 """
@@ -107,6 +110,52 @@ def dijkstra(shape, dx, cls, offsets, sel, component, src):
     if rc != 0:
         raise RuntimeError("oracle_dijkstra failed")
     return tau, par
+
+
+def in_candidates(shape, dx, cls, offsets, sel, component, tau):
+    """Candidates of the parent rule for every node of a field ``tau``.
+
+    Returns (cand, pred), both [n_off, n_nodes]: pred[o, j] = j - o (the
+    in-neighbour through offset o, -1 outside the lattice) and cand[o, j] =
+    tau_i + w_ij with the weights of ``dijkstra`` (Eq. 28-30, float64; +inf
+    outside the lattice)."""
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    cls = np.asarray(cls).reshape(-1)
+    tau = np.asarray(tau, dtype=np.float64).reshape(-1)
+    sel = np.asarray(sel, dtype=np.float64)
+    j = np.arange(n)
+    x, y, z = j % nx, (j // nx) % ny, j // (nx * ny)
+    cand = np.full((len(offsets), n), np.inf)
+    pred = np.full((len(offsets), n), -1, dtype=np.int64)
+    for o, (ox, oy, oz) in enumerate(np.asarray(offsets, dtype=np.int64)):
+        X, Y, Z = x - ox, y - oy, z - oz
+        ok = (X >= 0) & (X < nx) & (Y >= 0) & (Y < ny) & (Z >= 0) & (Z < nz)
+        i = np.where(ok, X + nx * (Y + ny * Z), 0)
+        L = dx * np.sqrt(float(ox * ox + oy * oy + oz * oz))
+        a, b = sel[cls[i], o], sel[cls[j], o]
+        w = L / (0.5 * (a + b)) if component == 0 else L * (0.5 * (a + b))
+        cand[o] = np.where(ok, tau[i] + w, np.inf)
+        pred[o] = np.where(ok, i, -1)
+    return cand, pred
+
+
+def parent_ties(shape, dx, cls, offsets, sel, component, tau, src, rel_tol):
+    """Tie flags of the parent rule for a converged field ``tau`` (Eq. 33).
+
+    Node j is a tie when the second smallest of its candidates
+    (``in_candidates``) exceeds the smallest by at most rel_tol times the
+    smallest.  The source and the unreachable nodes are never ties.  Returns a
+    bool array [n_nodes]."""
+    cand, _ = in_candidates(shape, dx, cls, offsets, sel, component, tau)
+    n = cand.shape[1]
+    if cand.shape[0] < 2:
+        return np.zeros(n, dtype=bool)
+    two = np.partition(cand, 1, axis=0)[:2]
+    best, second = two[0], two[1]
+    tau = np.asarray(tau, dtype=np.float64).reshape(-1)
+    tie = np.isfinite(second) & (second - best <= rel_tol * best)
+    return tie & np.isfinite(tau) & (np.arange(n) != src)
 
 
 def edge_list(shape, dx, cls, offsets, sel, component):

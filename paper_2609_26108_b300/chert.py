@@ -82,6 +82,8 @@ def lib():
     L.chert_traveltime.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P, I,
                                    P, I, I, I, P, P, P, P, P, SZ, P]
     L.chert_raypath.argtypes = [P, I, I64, P, P, I, I64, P, P, P]
+    L.chert_parent_ties.argtypes = [P, P, I, I, I, I, I, I, D, P, P, I, P, I, P, P, D, P, P, P, P]
+    L.chert_parent_ties.restype = ctypes.c_int
     L.chert_traveltime_enqueue.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P, I,
                                            P, I, I, I, P, P, P, P, P, SZ, P, P]
     L.chert_traveltime_enqueue.restype = ctypes.c_int
@@ -365,7 +367,8 @@ def traveltime_static(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64,
                       stream=None, out=None):
     """chert_traveltime_static: the relaxation without any device allocation by
     the library (its scratch is a fixed array inside libchert).  Same results
-    and output layout as ``traveltime``; calls that overlap on the GPU race."""
+    and output layout as ``traveltime``; it synchronises the stream (no stream
+    capture), and calls that overlap on the GPU race on the shared array."""
     torch = _torch()
     off, off_p = _offsets_arr(offsets)
     src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64).reshape(-1))
@@ -429,6 +432,32 @@ def raypath(par, sources, receivers, cap=4096, stream=None, out=None):
     _check(lib().chert_raypath(_dev_ptr(par2), nf, nn, _dev_ptr(src), _dev_ptr(rcv), len(rcv), cap,
                                _dev_ptr(out[0]), _dev_ptr(out[1]), _stream_ptr(stream)))
     return out
+
+
+def parent_ties(cache, nx, nz, dx, d_cls, offsets, sources, tauR, tauI, rel_tol, ny=1, precision=None,
+                stream=None):
+    """chert_parent_ties: the tie log of the parent rule for converged fields.
+
+    Rebuilds the lookup tables of ``cache`` (chert_edge_table), then flags every
+    node whose two best predecessor candidates lie within rel_tol of each
+    other.  Returns (tieR, tieI) uint8 tensors shaped like the fields and the
+    per-field counts int64 [n_fields, 2]."""
+    torch = _torch()
+    off, off_p = _offsets_arr(offsets)
+    _, Vs, As = edge_table(cache, offsets, stream)
+    prec = cache.precision if precision is None else (PRECISION_IDS[precision] if isinstance(precision, str)
+                                                      else precision)
+    src = sources if torch.is_tensor(sources) else \
+        torch.as_tensor(np.asarray(sources, dtype=np.int64).reshape(-1), device=tauR.device)
+    nm, ns = len(cache.modes), int(src.numel())
+    tieR = torch.empty(tauR.shape, dtype=torch.uint8, device=tauR.device)
+    tieI = torch.empty_like(tieR)
+    counts = torch.empty((ns * nm, 2), dtype=torch.int64, device=tauR.device)
+    _check(lib().chert_parent_ties(_dev_ptr(Vs), _dev_ptr(As), nm, cache.n_classes, prec, nx, ny, nz, float(dx),
+                                   _dev_ptr(d_cls), off_p, len(off), _dev_ptr(src), ns, _dev_ptr(tauR),
+                                   _dev_ptr(tauI), float(rel_tol), _dev_ptr(tieR), _dev_ptr(tieI),
+                                   _dev_ptr(counts), _stream_ptr(stream)))
+    return tieR, tieI, counts
 
 
 # ------------------------------------------------------------------ surrogate

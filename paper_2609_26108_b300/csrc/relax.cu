@@ -870,6 +870,61 @@ __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, 
     if (threadIdx.x == 0) a.status[blockIdx.x] = used;
 }
 
+// ------------------------------------------------------------ parent ties
+// Tie log of the parent rule (Eq. 33): node j of a converged field is a tie
+// when its second-best in-neighbour candidate tau_i + w_ij lies within
+// rel_tol * best of the best one, i.e. when rounding at that level can pick
+// either predecessor.  The weights are those of the relaxation (same lookup
+// tables and rounding, Eq. 28-30); candidates are formed in the traveltime
+// type TT.  One thread per node; blockIdx.y = field, blockIdx.z = component.
+template <typename TW, typename TT>
+__global__ void parent_ties_kernel(const TW* __restrict__ Vsel, const TW* __restrict__ Asel, int n_modes, int nk,
+                                   Offsets off, int nx, int ny, int nz, double dx,
+                                   const int32_t* __restrict__ cls, const int64_t* __restrict__ src,
+                                   const TT* __restrict__ tauR, const TT* __restrict__ tauI, double rel_tol,
+                                   uint8_t* __restrict__ tieR, uint8_t* __restrict__ tieI,
+                                   unsigned long long* __restrict__ counts) {
+    __shared__ TW L[kMaxOff];
+    __shared__ int block_ties;
+    for (int o = threadIdx.x; o < off.n; o += blockDim.x) {
+        const double ox = off.x[o], oy = off.y[o], oz = off.z[o];
+        L[o] = TW(dx * sqrt(ox * ox + oy * oy + oz * oz));
+    }
+    if (threadIdx.x == 0) block_ties = 0;
+    __syncthreads();
+    const int field = blockIdx.y, comp = blockIdx.z;
+    const int mode = field % n_modes;
+    const size_t n = (size_t)nx * ny * nz;
+    const size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool tie = false;
+    if (j < n) {
+        const TT* tau = (comp == 0 ? tauR : tauI) + (size_t)field * n;
+        const TW* sel = (comp == 0 ? Vsel : Asel) + (size_t)mode * nk * off.n;
+        const int64_t s = src[field / n_modes];
+        if ((int64_t)j != s && !isinf(tau[j])) {
+            const int xj = (int)(j % nx), yj = (int)((j / nx) % ny), zj = (int)(j / ((size_t)nx * ny));
+            const int kj = clamp_class(cls[j], nk);
+            TT best = TT(INFINITY), second = TT(INFINITY);
+            for (int o = 0; o < off.n; ++o) {
+                const int xi = xj - off.x[o], yi = yj - off.y[o], zi = zj - off.z[o];
+                if (xi < 0 || xi >= nx || yi < 0 || yi >= ny || zi < 0 || zi >= nz) continue;
+                const size_t i = (size_t)xi + (size_t)nx * ((size_t)yi + (size_t)ny * zi);
+                const int ki = clamp_class(cls[i], nk);
+                const TW w = edge_w<TW>(comp, L[o], sel[(size_t)ki * off.n + o], sel[(size_t)kj * off.n + o]);
+                const TT c = tau[i] + TT(w);
+                if (c < best) { second = best; best = c; }
+                else if (c < second) second = c;
+            }
+            tie = !isinf(second) && double(second) - double(best) <= rel_tol * double(best);
+        }
+        uint8_t* out = comp == 0 ? tieR : tieI;
+        if (out) out[(size_t)field * n + j] = tie ? 1 : 0;
+    }
+    if (tie) atomicAdd(&block_ties, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && counts && block_ties) atomicAdd(counts + field * 2 + comp, (unsigned long long)block_ties);
+}
+
 // ------------------------------------------------------------ raypaths
 // One thread per (field, receiver): walk the parents once to count the path
 // (bounded by cap), then again to write it source-first.
@@ -1533,11 +1588,10 @@ extern "C" int chert_traveltime(const chert_cache_arrays* cache, int n_modes, in
 
 // ------------------------------------------------------------------------
 // chert_traveltime_static: the same relaxation for callers that must not
-// allocate device memory (an allocator-free embedding, code that runs while a
-// stream is being captured, a host that has handed all device memory to its
-// own pool).  Its scratch is the file-scope array below instead of a
-// caller-provided workspace; every device that loads libchert keeps the array
-// for the life of the process.
+// allocate device memory (an allocator-free embedding, a host that has handed
+// all device memory to its own pool).  Its scratch is the file-scope array
+// below instead of a caller-provided workspace; every device that loads
+// libchert keeps the array for the life of the process.
 namespace chert {
 namespace {
 constexpr size_t kStaticScratchBytes = size_t(1) << 20;     // 1 MiB
@@ -1548,7 +1602,8 @@ std::mutex g_static_mu;
 void* g_static_ptr[kMaxDevices] = {};
 
 // Device address of g_static_scratch on the current device, looked up once
-// per device (the host-side symbol is not a device address).
+// per device (the host-side symbol is not a device address) and kept for the
+// life of the process: a cudaDeviceReset of the device makes it stale.
 int static_scratch(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1652,6 +1707,49 @@ extern "C" int chert_raypath(const int32_t* d_par, int n_fields, int64_t n_nodes
     raypath_kernel<<<(unsigned)((n + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
         d_par, n_fields, n_nodes, d_src, d_rcv, n_rcv, cap, d_paths, d_len);
     return launch_check("chert_raypath");
+}
+
+extern "C" int chert_parent_ties(const void* d_Vsel, const void* d_Asel, int n_modes, int n_classes,
+                                 int precision, int nx, int ny, int nz, double dx,
+                                 const int32_t* d_class_of_node, const int32_t* offsets, int n_off,
+                                 const int64_t* d_sources, int n_sources, const void* d_tauR,
+                                 const void* d_tauI, double rel_tol, uint8_t* d_tieR, uint8_t* d_tieI,
+                                 unsigned long long* d_counts, void* stream) {
+    const char* who = "chert_parent_ties";
+    CHERT_REQUIRE(d_Vsel && d_Asel && d_class_of_node && d_sources && d_tauR && d_tauI, "%s: NULL argument", who);
+    CHERT_REQUIRE(n_modes >= 1 && n_modes <= 3 && n_classes >= 1 && n_sources >= 1, "%s: bad counts", who);
+    CHERT_REQUIRE(nx >= 1 && ny >= 1 && nz >= 1 && (long long)nx * ny * nz < (1LL << 31), "%s: bad lattice", who);
+    CHERT_REQUIRE(dx > 0 && rel_tol >= 0, "%s: dx and rel_tol must be positive", who);
+    CHERT_REQUIRE((long long)n_sources * n_modes <= 65535, "%s: at most 65535 fields per call", who);
+    CHERT_REQUIRE(precision == CHERT_FP64 || precision == CHERT_FP32 || precision == CHERT_MIXED ||
+                      precision == CHERT_FP32_ACC64, "%s: precision=%d", who, precision);
+    Offsets off;
+    int rc = fill_offsets(off, offsets, n_off, who);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n_fields = n_sources * n_modes;
+    if (d_counts) {
+        cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * n_fields * 2, s);
+        if (e != cudaSuccess) return cuda_fail(e, "chert_parent_ties: memset");
+    }
+    const long long n = (long long)nx * ny * nz;
+    const dim3 grid((unsigned)((n + 255) / 256), n_fields, 2);
+    if (precision == CHERT_FP64)
+        parent_ties_kernel<double, double><<<grid, 256, 0, s>>>(
+            static_cast<const double*>(d_Vsel), static_cast<const double*>(d_Asel), n_modes, n_classes, off, nx, ny,
+            nz, dx, d_class_of_node, d_sources, static_cast<const double*>(d_tauR),
+            static_cast<const double*>(d_tauI), rel_tol, d_tieR, d_tieI, d_counts);
+    else if (precision == CHERT_FP32_ACC64)
+        parent_ties_kernel<float, double><<<grid, 256, 0, s>>>(
+            static_cast<const float*>(d_Vsel), static_cast<const float*>(d_Asel), n_modes, n_classes, off, nx, ny,
+            nz, dx, d_class_of_node, d_sources, static_cast<const double*>(d_tauR),
+            static_cast<const double*>(d_tauI), rel_tol, d_tieR, d_tieI, d_counts);
+    else
+        parent_ties_kernel<float, float><<<grid, 256, 0, s>>>(
+            static_cast<const float*>(d_Vsel), static_cast<const float*>(d_Asel), n_modes, n_classes, off, nx, ny,
+            nz, dx, d_class_of_node, d_sources, static_cast<const float*>(d_tauR),
+            static_cast<const float*>(d_tauI), rel_tol, d_tieR, d_tieI, d_counts);
+    return launch_check(who);
 }
 
 extern "C" int chert_set_relax_points_per_thread(int ppt) {

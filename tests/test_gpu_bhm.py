@@ -122,7 +122,7 @@ def test_unreachable_nodes_keep_infinity(torch_dev):
     off = np.array([(2, 0, 0), (-2, 0, 0), (0, 0, 1), (0, 0, -1)], np.int32)
     cls = np.zeros(nx * nz, np.int32)
     cnp = _synthetic_cache([3000.0], [2e-5])
-    tR, _, pR, _ = both(torch_dev, as_cache(torch_dev, cnp, "fp64"), nx, nz, cls, off, [4])
+    tR, _, pR, _, _, _ = both(torch_dev, as_cache(torch_dev, cnp, "fp64"), nx, nz, cls, off, [4])
     odd = (np.arange(nx * nz) % nx) % 2 == 1
     assert np.all(np.isinf(tR[0, 0, odd])) and np.all(pR[0, 0, odd] == -1)
     assert np.all(np.isfinite(tR[0, 0, ~odd]))

@@ -5,11 +5,22 @@ so every discrete decision -- the looked-up entry of each (mode, class, offset)
 -- is taken in the same precision on both sides and must agree exactly.
 Tolerances: FP64 traveltimes equal the oracle's to 1e-12 relative (the fixed
 point is unique; both sides add the same double increments) and parents are
-identical.  FP32 traveltimes: each weight is rounded about twice (the segment
-average and the quotient or product) and each of the k additions along a path
-of k edges once, so the relative error is at most about (k + 2) u with
-u = 2^-24; the bound is max(1e-5, 2 (k + 2) u) with k the node's hop count on
-the oracle's tree (1e-5 up to k = 81).
+identical.  FP32 traveltimes: relative to the oracle's at every reachable
+node, 1e-5 (the requirement for float traveltimes) for paths of up to 81
+edges; beyond that 2 (k + 2) u with k the node's hop count on the oracle's
+tree and u = 2^-24.  A float traveltime is the float sum of its path's k
+weights (Eq. 31), each weight itself rounded about twice, and a float sum of
+k terms is only guaranteed to (k + 2) u of its value, so no float
+relaxation can promise 1e-5 beyond about 80 edges; only the synthetic
+many-bend channels here have such paths (the benchmark's lattices are
+checked at a flat 1e-5 in test_gpu_fullsize).  FP32 parents (Eq. 33): identical to the oracle's at
+every node that chert_parent_ties does not log as a tie at TIE_FP32 = 1e-5;
+at a logged tie the GPU's parent must be a predecessor whose oracle candidate
+is within that tolerance of the oracle's traveltime, and every node that the
+oracle's own tie rule finds within TIE_FP32/4 must be logged.  With float
+traveltimes within 1e-6 of the oracle's, two candidates more than TIE_FP32
+apart keep their order on both sides, so this compares everything that is
+unique.
 """
 import math
 
@@ -63,8 +74,13 @@ def as_cache(torch, cnp, precision):
     return chert.Cache(arr, list(range(nm)), nk, nd // 4, prec)
 
 
+TIE_FP32 = 1e-5
+TIE_FP64 = 1e-12
+
+
 def oracle_fields(cnp, precision, shape, dx, cls, off, sources):
-    """tau and parents of the oracle, with the lookup taken in the path's precision."""
+    """tau, parents and lookup values of the oracle, with the lookup taken in
+    the path's precision: {(source, mode, component): (tau, par, sel)}."""
     dt = np.float64 if precision == "fp64" else np.float32
     cast = {k: (cnp[k].astype(dt).astype(np.float64) if k != "flag" else cnp[k]) for k in cnp}
     nm = cnp["V"].shape[0]
@@ -72,16 +88,36 @@ def oracle_fields(cnp, precision, shape, dx, cls, off, sources):
     for m in range(nm):
         idx, Vs, As = go.lookup_tables(cast, m, off, dtype=dt)
         for s in sources:
-            out[(s, m, 0)] = go.dijkstra(shape, dx, cls, off, Vs, 0, s)
-            out[(s, m, 1)] = go.dijkstra(shape, dx, cls, off, As, 1, s)
+            out[(s, m, 0)] = go.dijkstra(shape, dx, cls, off, Vs, 0, s) + (Vs,)
+            out[(s, m, 1)] = go.dijkstra(shape, dx, cls, off, As, 1, s) + (As,)
     return out
 
 
 def run_gpu(torch, cache, nx, nz, dx, cls, off, sources, max_cycles=64):
+    """GPU fields, parents and tie flags: (tauR, tauI, parR, parI, tieR, tieI)."""
     d_cls = torch.as_tensor(np.asarray(cls, dtype=np.int32), device="cuda")
     tR, tI, pR, pI = chert.traveltime(cache, nx, nz, dx, d_cls, off, sources, max_cycles)
+    tol = TIE_FP64 if cache.precision == chert.FP64 else TIE_FP32
+    kR, kI, _ = chert.parent_ties(cache, nx, nz, dx, d_cls, off, sources, tR, tI, tol)
     torch.cuda.synchronize()
-    return tR.cpu().numpy(), tI.cpu().numpy(), pR.cpu().numpy(), pI.cpu().numpy()
+    return tuple(t.cpu().numpy() for t in (tR, tI, pR, pI, kR, kI))
+
+
+def check_parents_fp32(gp, gtie, rt, rp, sel, comp, s, shape, dx, cls, off):
+    """FP32 parents against the oracle's outside logged ties; logged ties valid
+    and complete (module docstring)."""
+    fin = np.isfinite(rt)
+    tie = gtie.astype(bool)
+    assert not tie[s] and not np.any(tie & ~fin)
+    assert np.array_equal(gp[fin & ~tie], rp[fin & ~tie]), int(np.sum((gp != rp) & fin & ~tie))
+    cand, pred = go.in_candidates(shape, dx, cls, off, sel, comp, rt)
+    for j in np.nonzero(tie & (gp != rp))[0]:
+        hit = pred[:, j] == gp[j]
+        assert hit.any(), j
+        assert cand[hit, j][0] <= rt[j] * (1 + TIE_FP32), j
+    near = go.parent_ties(shape, dx, cls, off, sel, comp, rt, s, TIE_FP32 / 4)
+    assert np.all(tie[near]), int(np.sum(near & ~tie))
+    return int(tie.sum())
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -102,8 +138,7 @@ def test_edge_table_matches_oracle(torch_dev, precision):
 def _hops(tau, par):
     """Edges from the source along the parent tree (0 where unreachable)."""
     hops = np.zeros(tau.shape, np.int64)
-    order = np.argsort(tau, kind="stable")
-    for j in order:
+    for j in np.argsort(tau, kind="stable"):
         p = par[j]
         if np.isfinite(tau[j]) and p >= 0 and p != j:
             hops[j] = hops[p] + 1
@@ -111,11 +146,12 @@ def _hops(tau, par):
 
 
 def _check_fields(g, ref, sources, nm, precision, shape, dx, cls, off, cnp):
-    tR, tI, pR, pI = g
+    tR, tI, pR, pI, kR, kI = g
+    worst = 0.0
     for si, s in enumerate(sources):
         for m in range(nm):
-            for comp, (t, p) in enumerate([(tR, pR), (tI, pI)]):
-                rt, rp = ref[(s, m, comp)]
+            for comp, (t, p, k) in enumerate([(tR, pR, kR), (tI, pI, kI)]):
+                rt, rp, sel = ref[(s, m, comp)]
                 gt, gp = t[si, m], p[si, m]
                 fin = np.isfinite(rt)
                 assert np.array_equal(np.isfinite(gt), fin)
@@ -124,11 +160,15 @@ def _check_fields(g, ref, sources, nm, precision, shape, dx, cls, off, cnp):
                     assert np.allclose(gt[fin], rt[fin], rtol=1e-12, atol=0)
                     assert np.array_equal(gp, rp)
                 else:
-                    scale = np.max(rt[fin])
-                    err = np.abs(gt[fin] - rt[fin]) / np.maximum(rt[fin], 1e-3 * scale)
-                    tol = np.maximum(1e-5, 2.0 * (_hops(rt, rp) + 2) * 2.0 ** -24)[fin]
-                    assert np.all(err < tol), (s, m, comp, np.max(err), np.max(err / tol))
+                    pos = fin & (rt > 0)
+                    assert np.all(gt[fin & (rt == 0)] == 0)
+                    err = np.abs(gt[pos] - rt[pos]) / rt[pos]
+                    tol = np.maximum(1e-5, 2.0 * (_hops(rt, rp) + 2) * 2.0 ** -24)[pos]
+                    assert np.all(err <= tol), (s, m, comp, float(np.max(err)), float(np.max(err / tol)))
+                    worst = max(worst, float(np.max(err, initial=0.0)))
                     assert gp[s] == s
+                    check_parents_fp32(gp, k[si, m], rt, rp, sel, comp, s, shape, dx, cls, off)
+    return worst
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -263,7 +303,10 @@ def test_per_node_weights_match_global_class_lookup(torch_dev):
             assert np.array_equal(a, b)
         if precision == "fp64":
             ref = oracle_fields(cnp, precision, (nx, 1, nz), 10.0, cls, off, src)
-            _check_fields(tuple(outs[0]), ref, src, 1, precision, (nx, 1, nz), 10.0, cls, off, cnp)
+            g = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, src, max_cycles=256)
+            for a, b in zip(outs[0], g):
+                assert np.array_equal(a, b)
+            _check_fields(g, ref, src, 1, precision, (nx, 1, nz), 10.0, cls, off, cnp)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -312,7 +355,7 @@ def test_unreachable_nodes_and_raypaths(torch_dev):
     cls = np.zeros(nx * nz, np.int32)
     cnp = _synthetic_cache([3000.0], [2e-5])
     g = run_gpu(torch_dev, as_cache(torch_dev, cnp, "fp64"), nx, nz, 10.0, cls, off, [4])
-    tR, _, pR, _ = g
+    tR, _, pR, _, _, _ = g
     odd = (np.arange(nx * nz) % nx) % 2 == 1
     assert np.all(np.isinf(tR[0, 0, odd])) and np.all(pR[0, 0, odd] == -1)
     assert np.all(np.isfinite(tR[0, 0, ~odd]))
@@ -339,12 +382,12 @@ def test_pipeline_gpu_cache_to_traveltime_fp64(torch_dev):
     cls = inputs.layered_class_map_2d(nx, nz, 5).astype(np.int32)
     off = inputs.stencil_2d(5)
     sources = [0, 25]
-    tR, tI, pR, pI = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, sources)
+    tR, tI, pR, pI, _, _ = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, sources)
     ref = oracle_fields(cnp, "fp64", (nx, 1, nz), 10.0, cls, off, sources)
     for si, s in enumerate(sources):
         for m in range(2):
             for comp, t in enumerate([tR, tI]):
-                rt, _ = ref[(s, m, comp)]
+                rt = ref[(s, m, comp)][0]
                 assert np.allclose(t[si, m], rt, rtol=1e-9, atol=0)
     # the two caches differ by rounding, so parents may differ where two
     # predecessors tie to that level; every GPU raypath must still be a
@@ -354,7 +397,7 @@ def test_pipeline_gpu_cache_to_traveltime_fp64(torch_dev):
                                 [0, 0, 25, 25], rcv, cap=256)
     offs = {tuple(o): i for i, o in enumerate(off)}
     for f, (s, m) in enumerate([(0, 0), (0, 1), (25, 0), (25, 1)]):
-        rt, rp = ref[(s, m, 0)]
+        rt, rp, _ = ref[(s, m, 0)]
         _, Vs, _ = go.lookup_tables(cnp, m, off)
         for r, node in enumerate(rcv):
             path = list(paths[f, r, :lens[f, r]].cpu().numpy())

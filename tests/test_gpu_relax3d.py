@@ -13,7 +13,7 @@ from oracle import graph_oracle as go
 from paper_2609_26108_b300 import chert, inputs
 
 from helpers import cache_to_torch
-from test_gpu_relax import _check_fields
+from test_gpu_relax import TIE_FP32, TIE_FP64, _check_fields, check_parents_fp32
 
 pytestmark = pytest.mark.gpu
 
@@ -58,8 +58,10 @@ def run3d(torch, cnp, n_az, n_pol, precision, shape, cls, off, sources):
     nx, ny, nz = shape
     d_cls = torch.as_tensor(np.asarray(cls, np.int32), device="cuda")
     tR, tI, pR, pI = chert.traveltime(cache, nx, nz, 10.0, d_cls, off, sources, max_cycles=64, ny=ny)
+    kR, kI, _ = chert.parent_ties(cache, nx, nz, 10.0, d_cls, off, sources, tR, tI,
+                                  TIE_FP64 if prec == chert.FP64 else TIE_FP32, ny=ny)
     torch.cuda.synchronize()
-    return tR.cpu().numpy(), tI.cpu().numpy(), pR.cpu().numpy(), pI.cpu().numpy()
+    return tuple(t.cpu().numpy() for t in (tR, tI, pR, pI, kR, kI))
 
 
 def oracle3d_fields(cnp, precision, shape, cls, off, sources):
@@ -69,8 +71,8 @@ def oracle3d_fields(cnp, precision, shape, cls, off, sources):
     for m in range(cnp["V"].shape[0]):
         _, Vs, As = go.lookup_tables(cast, m, off, dtype=dt)
         for s in sources:
-            out[(s, m, 0)] = go.dijkstra(shape, 10.0, cls, off, Vs, 0, s)
-            out[(s, m, 1)] = go.dijkstra(shape, 10.0, cls, off, As, 1, s)
+            out[(s, m, 0)] = go.dijkstra(shape, 10.0, cls, off, Vs, 0, s) + (Vs,)
+            out[(s, m, 1)] = go.dijkstra(shape, 10.0, cls, off, As, 1, s) + (As,)
     return out
 
 
@@ -201,12 +203,14 @@ def test_relax3d_float_weights_wide_accumulation(torch_dev, n_classes):
     sources = [3, nx * ny * nz - 5]
     d_cls = torch_dev.as_tensor(cls, device="cuda")
     tR, tI, pR, pI = chert.traveltime(cache, nx, nz, 10.0, d_cls, off, sources, ny=ny, precision="fp32_acc64")
+    kR, kI, _ = chert.parent_ties(cache, nx, nz, 10.0, d_cls, off, sources, tR, tI, TIE_FP32, ny=ny,
+                                  precision="fp32_acc64")
     torch_dev.cuda.synchronize()
     assert tR.dtype == torch_dev.float64
     ref = oracle3d_fields(cnp, "fp32", shape, cls, off, sources)
     for si, s in enumerate(sources):
-        for comp, (t, p) in enumerate([(tR, pR), (tI, pI)]):
-            rt, rp = ref[(s, 0, comp)]
+        for comp, (t, p, k) in enumerate([(tR, pR, kR), (tI, pI, kI)]):
+            rt, rp, sel = ref[(s, 0, comp)]
             gt, gp = t[si, 0].cpu().numpy(), p[si, 0].cpu().numpy()
             fin = np.isfinite(rt)
             assert np.array_equal(np.isfinite(gt), fin)
@@ -214,3 +218,4 @@ def test_relax3d_float_weights_wide_accumulation(torch_dev, n_classes):
             assert np.max(np.abs(gt[pos] - rt[pos]) / rt[pos]) < 4e-7
             assert gt[s] == 0.0 and gp[s] == s
             assert np.all(gp[~fin] == -1)
+            check_parents_fp32(gp, k[si, 0].cpu().numpy(), rt, rp, sel, comp, s, shape, 10.0, cls, off)

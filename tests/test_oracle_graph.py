@@ -168,3 +168,51 @@ def test_select_direction_brute_force_and_ties():
     assert idx2[0, 0] == 1
     idx3 = go.select_direction(rx2, None, rz2, np.ones((1, 3), np.uint8), np.array([(1, 0, 0)]))
     assert idx3[0, 0] == -1
+
+
+def test_parent_ties_manhattan_closed_form():
+    """Homogeneous medium, 4-neighbour stencil, source in a corner: every node
+    off the two axes through the source is reached by two equally short
+    paths (from its left and from its upper neighbour), so it is an exact tie;
+    nodes on the axes have one shortest predecessor."""
+    nx, nz = 9, 7
+    off = np.array([(1, 0, 0), (-1, 0, 0), (0, 0, 1), (0, 0, -1)], np.int32)
+    cls = np.zeros(nx * nz, np.int32)
+    sel = np.full((1, 4), 2500.0)
+    tau, par = go.dijkstra((nx, 1, nz), 10.0, cls, off, sel, 0, 0)
+    tie = go.parent_ties((nx, 1, nz), 10.0, cls, off, sel, 0, tau, 0, 0.0)
+    x, z = np.arange(nx * nz) % nx, np.arange(nx * nz) // nx
+    assert np.array_equal(tie, (x > 0) & (z > 0))
+    # with anisotropic speeds the two Manhattan orders still cost the same
+    sel2 = np.array([[2000.0, 2000.0, 3100.0, 3100.0]])
+    tau2, _ = go.dijkstra((nx, 1, nz), 10.0, cls, off, sel2, 0, 0)
+    tie2 = go.parent_ties((nx, 1, nz), 10.0, cls, off, sel2, 0, tau2, 0, 1e-12)
+    assert np.array_equal(tie2, (x > 0) & (z > 0))
+
+
+def test_parent_ties_against_brute_force():
+    """Tiny random lattices: the tie flags equal a brute-force enumeration over
+    the edge list with Floyd-Warshall distances, at several tolerances."""
+    rng = np.random.default_rng(5)
+    for trial in range(4):
+        nx, nz = 6, 5
+        off = inputs.stencil_2d(2)
+        cls = rng.integers(0, 3, nx * nz).astype(np.int32)
+        sel = rng.uniform(1500, 1600, (3, len(off)))
+        src = int(rng.integers(0, nx * nz))
+        comp = trial % 2
+        if comp:
+            sel = sel * 1e-8
+        tau, _ = go.dijkstra((nx, 1, nz), 10.0, cls, off, sel, comp, src)
+        I, J, W = go.edge_list((nx, 1, nz), 10.0, cls, off, sel, comp)
+        D = go.floyd_warshall(nx * nz, I, J, W)
+        assert np.allclose(D[src], tau, rtol=1e-12)
+        for tol in (0.0, 1e-4, 3e-3, 3e-2):
+            want = np.zeros(nx * nz, bool)
+            for j in range(nx * nz):
+                if j == src:
+                    continue
+                c = np.sort(D[src, I[J == j]] + W[J == j])
+                want[j] = len(c) >= 2 and c[1] - c[0] <= tol * c[0]
+            got = go.parent_ties((nx, 1, nz), 10.0, cls, off, sel, comp, tau, src, tol)
+            assert np.array_equal(got, want), (trial, tol)
