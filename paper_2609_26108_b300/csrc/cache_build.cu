@@ -86,7 +86,8 @@ __device__ __forceinline__ double sh_(double x) { return sinh(x); }
 // eigenvalues' real parts, which order the labels, nearly coincide).
 template <typename T>
 __device__ __forceinline__ void energy_velocity_body(const Medium<T>& m, T s, T c, T vt, int mode,
-                                                     int kernel, cplx<T>& v1, cplx<T>& v3, T* cond) {
+                                                     int kernel, cplx<T>& v1, cplx<T>& v3, bool want_cond,
+                                                     T& cond) {
     const T chv = ch_(vt), shv = sh_(vt);
     const cplx<T> n1 = mk<T>(s * chv, c * shv);     // sin(theta + i vt)
     const cplx<T> n3 = mk<T>(c * chv, -s * shv);    // cos(theta + i vt)
@@ -95,7 +96,7 @@ __device__ __forceinline__ void energy_velocity_body(const Medium<T>& m, T s, T 
         const cplx<T> cc = csqrt(m.a66 * n11 + m.a44 * n33);
         v1 = m.a66 * (n1 / cc);
         v3 = m.a44 * (n3 / cc);
-        if (cond) *cond = T(1);
+        cond = T(1);
         return;
     }
     const cplx<T> b = m.a13 + m.a44;
@@ -127,13 +128,14 @@ __device__ __forceinline__ void energy_velocity_body(const Medium<T>& m, T s, T 
         v1 = v1 + e * p3;
         v3 = v3 - e * p1;
     }
-    if (cond) {
+    cond = T(1);
+    if (want_cond) {
         const T trn = norm2(tr);
         if (D.re * D.re < T(0x1p-28) * trn) {
-            *cond = T(INFINITY);
+            cond = T(INFINITY);
         } else {
             const T hh = norm2(g1) + norm2(g3);
-            *cond = (trn / norm2(D)) * (hh * hh / norm2(bb));
+            cond = (trn / norm2(D)) * (hh * hh / norm2(bb));
         }
     }
 }
@@ -143,11 +145,28 @@ __device__ __forceinline__ void energy_velocity_body(const Medium<T>& m, T s, T 
 // quantities).  Inlined, the scan loop alone held four copies and the kernel
 // stalled on instruction fetch (ncu: ~16 cycles of "no instruction" per issue
 // on the per-cell builds); out of line, the per-cell qP and qSV builds run
-// 26% and 17% faster.
+// 26% and 17% faster.  The medium goes in and the velocities come out by
+// value, so the call passes them in registers rather than through a stack
+// frame in local memory.
 template <typename T>
-__device__ __noinline__ void energy_velocity_call(const Medium<T>& m, T s, T c, T vt, int mode, int kernel,
-                                                  cplx<T>& v1, cplx<T>& v3, T* cond = nullptr) {
-    energy_velocity_body(m, s, c, vt, mode, kernel, v1, v3, cond);
+struct EnergyVelocity {
+    cplx<T> v1, v3;
+    T cond;
+};
+template <typename T>
+__device__ __noinline__ EnergyVelocity<T> energy_velocity_val(Medium<T> m, T s, T c, T vt, int mode, int kernel,
+                                                              bool want_cond) {
+    EnergyVelocity<T> r;
+    energy_velocity_body(m, s, c, vt, mode, kernel, r.v1, r.v3, want_cond, r.cond);
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ void energy_velocity_call(const Medium<T>& m, T s, T c, T vt, int mode, int kernel,
+                                                     cplx<T>& v1, cplx<T>& v3, T* cond = nullptr) {
+    const EnergyVelocity<T> r = energy_velocity_val(m, s, c, vt, mode, kernel, cond != nullptr);
+    v1 = r.v1;
+    v3 = r.v3;
+    if (cond) *cond = r.cond;
 }
 template <typename T>
 __device__ __forceinline__ void energy_velocity(const Medium<T>& m, T s, T c, T vt, int mode,
@@ -170,14 +189,18 @@ __device__ __forceinline__ T residual_cold(const Medium<T>& m, T s, T c, T vt, i
     return v1.re * v3.im - v3.re * v1.im;
 }
 
-// Noise guard of the MIXED scan.  The float residual's rounding error stays
-// below about 1.1e-6 kappa |v|^2 (kappa^2 = the cond factor of
-// energy_velocity_body; measured against float-float evaluations over the
-// whole [-30, 30] deg grid of 3,024 media in every mode), so its sign is
-// trusted only where |f| >= 2^-13 kappa |v|^2, a margin of about 100.  Below
-// that (about 5e-4 of the grid points) the sign is taken from a float-float
-// evaluation at the exact grid point k*h, which is what a double scan sees.
-constexpr float kGuard2 = 0x1p-26f;          // (2^-13)^2
+// Noise guard of the MIXED scan.  The float residual's rounding error,
+// measured against float-float evaluations over the whole [-30, 30] deg grid
+// of 1,008 media (the layered benchmark's and 1,000 per-cell ones), stays
+// below 2.7e-7 (qP), 1.1e-6 (qSV) and 4.8e-7 (qSH) times kappa |v|^2
+// (kappa^2 = the cond factor of energy_velocity_body).  A float sign is
+// trusted only where |f| >= G kappa |v|^2 with G = 2^-18, 2^-16 and 2^-17 for
+// the three modes, a margin of about 14 over that noise; below it (under
+// 1e-4 of the grid points) the sign is taken from a float-float evaluation
+// at the exact grid point k*h, which is what a double scan sees.
+__device__ __forceinline__ float guard2(int mode) {
+    return mode == CHERT_QP ? 0x1p-36f : mode == CHERT_QSV ? 0x1p-32f : 0x1p-34f;   // G^2
+}
 
 // Float residual with its guard: returns f; need = whether |f| is within the
 // guard of zero (or the mode labels are ambiguous).
@@ -188,7 +211,7 @@ __device__ __forceinline__ float residual_guarded(const Medium<float>& m, float 
     energy_velocity_call(m, s, c, vt, mode, kernel, v1, v3, &cond);
     const float f = v1.re * v3.im - v3.re * v1.im;
     const float sc = norm2(v1) + norm2(v3);
-    need = !(f * f >= kGuard2 * cond * (sc * sc));    // NaN or inf bounds also re-evaluate
+    need = !(f * f >= guard2(mode) * cond * (sc * sc));    // NaN or inf bounds also re-evaluate
     return f;
 }
 
@@ -578,9 +601,11 @@ __device__ bool scan_window(const Solve<TS, TP>& v, int kernel, double h, int k_
                     const TS fl = side ? fin : fcur, fh = side ? fcur : fin;
                     const double glo = side ? (kkl - 1.0) * h : -kkl * h;
                     const double ghi = side ? kkl * h : -(kkl - 1.0) * h;
-                    // polish in the scan precision (float for FP32 and MIXED)
-                    const TS rs = polish(v.ms, v.ss, v.cs, mode, kernel, TS(glo), TS(ghi), fl, fh, lane,
-                                         sizeof(TS) == 8 ? TS(1e-9) : TS(0));
+                    // polish in the scan precision (float for FP32 and MIXED); in
+                    // MIXED it only seeds the refinement window of +-h/4, so
+                    // h/64 is enough
+                    const TS stop = sizeof(TS) == 8 ? TS(1e-9) : mixed ? TS(h / 64) : TS(0);
+                    const TS rs = polish(v.ms, v.ss, v.cs, mode, kernel, TS(glo), TS(ghi), fl, fh, lane, stop);
                     if constexpr (mixed) {
                         // drop clearly growing roots in float; decide the rest in TP
                         const RayQ<TS> q32 = ray_quantities(v.ms, v.ss, v.cs, rs, mode, kernel);
