@@ -26,8 +26,11 @@ Parity status: forward and backward are pinned by finite differences and by
 explicit loops; the elastic baseline is pinned by the oracle's own exact cache
 in the elastic limit, the attenuation baseline by the exact cache where the
 exact wave is homogeneous (isotropic media, and the symmetry axis of a VTI
-medium).  The learned weights have no pin: they are an approximation
-whose error the tests measure against the exact cache.
+medium); ``bf16`` by an independent round-to-nearest-even cast (exact
+halfway cases, signed zeros, subnormals, the top of the range) and two
+halfway cases by hand; ``encode_targets`` and ``decode`` by hand-computed
+cases and by their round trip.  The learned weights have no pin: they are an
+approximation whose error the tests measure against the exact cache.
 """
 from __future__ import annotations
 

@@ -149,3 +149,85 @@ def test_features_scale_and_range():
     _, out2 = mo.features(np.array([0.1]), np.array([0.7]), np.array([0.1]), np.array([0.0]),
                           np.array([0.1]), np.array([0.01]), np.array([0.01]))
     assert out2[0]
+
+
+def test_bf16_matches_an_independent_rounding():
+    """bf16 against torch's float32 -> bfloat16 cast (round to nearest even),
+    on random values over many binades, exact halfway cases, signed zeros,
+    subnormals and values near the top of the range; and two halfway cases by
+    hand: 1 + 2^-8 rounds down to the even 1, 1 + 3*2^-8 up to the even
+    1 + 2^-6."""
+    import torch
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(20000) * np.exp(rng.uniform(-60, 60, 20000))
+    # float32 patterns whose low 16 bits are exactly 0x8000: halfway between
+    # two bfloat16 values, half with an even and half with an odd upper part
+    expo = rng.integers(1, 254, 4000).astype(np.uint32)
+    mant = rng.integers(0, 128, 4000).astype(np.uint32)
+    bits = (((expo << np.uint32(7)) | mant) << np.uint32(16)) | np.uint32(0x8000)
+    halfway = bits.view(np.float32).astype(np.float64) * np.where(rng.random(4000) < 0.5, -1.0, 1.0)
+    subnormal = np.array([1e-40, -3e-42, 1.17e-38, 5e-45, 2.3e-39], np.float64)
+    special = np.array([0.0, -0.0, 3.3e38, -3.3e38, 3.39e38, 1.0, -1.0, 65504.0, np.inf, -np.inf])
+    for vals in (x, halfway, subnormal, special):
+        f32 = vals.astype(np.float32)
+        want = torch.tensor(f32).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+        got = mo.bf16(f32)
+        assert np.array_equal(got, want)
+        assert np.array_equal(np.signbit(got), np.signbit(want))
+    assert mo.bf16(np.float32(1 + 2.0 ** -8)) == 1.0
+    assert mo.bf16(np.float32(1 + 3 * 2.0 ** -8)) == 1 + 2.0 ** -6
+    assert mo.bf16(np.float32(1 + 2.0 ** -8 + 2.0 ** -20)) == 1 + 2.0 ** -7   # just past halfway rounds up
+
+
+def test_encode_targets_hand_cases():
+    """Each output by hand: V/Vg - 1, log(A/A0) (with the 1e-30 floor), the ray
+    angle difference wrapped into (-pi, pi], the validity, vartheta, and the
+    NaN mask of far qSV roots."""
+    V = np.array([2100.0, 2000.0, 1500.0, 1800.0])
+    Vg = np.array([2000.0, 2000.0, 1500.0, 2000.0])
+    A = np.array([2e-5, 1e-5, 3e-6, 0.0])
+    A0 = np.array([1e-5, 1e-5, 3e-6, 1e-5])
+    psi = np.array([0.3, 3.1, -3.1, 0.0])
+    psi_el = np.array([0.1, -3.1, 3.1, 0.0])
+    flag = np.array([0, 0, 0, 1])
+    vt = np.array([0.01, -0.02, 0.05, np.nan])
+    t = mo.encode_targets(V, A, psi, flag, vt, Vg, psi_el, A0, vt_max=0.03)
+    assert np.allclose(t[0], [0.05, math.log(2.0), 0.2, 1.0, 0.01], rtol=1e-14, atol=1e-15)
+    assert np.allclose(t[1], [0.0, 0.0, 6.2 - 2 * math.pi, 1.0, -0.02], rtol=0, atol=1e-14)
+    assert np.all(np.isnan(t[2, :3])) and t[2, 3] == 1.0 and t[2, 4] == 0.05
+    assert np.array_equal(t[3], [0.0, 0.0, 0.0, 0.0, 0.0])
+    tiny = mo.encode_targets(np.array([1.0]), np.array([1e-40]), np.array([0.0]), np.array([0]),
+                             np.array([0.0]), np.array([1.0]), np.array([0.0]), np.array([1e-30]))
+    assert tiny[0, 1] == 0.0                                     # both floored at 1e-30
+
+
+def test_decode_hand_cases_and_round_trip():
+    """decode by hand (logit 0 -> p = 1/2, log 3 -> p = 3/4) and as the inverse
+    of encode_targets followed by the standardisation y = (t - mean)/std."""
+    out_mean = np.array([0.02, 0.1, -0.01, 0.0, 0.003])
+    out_std = np.array([0.05, 0.3, 0.02, 1.0, 0.01])
+    y = np.array([[0.0, 0.0, 0.0, 0.0, 0.0], [1.0, -1.0, 2.0, math.log(3.0), -0.5]])
+    V, A, psi, p, vt = mo.decode(y, out_mean, out_std, np.array([2000.0, 2000.0]), np.array([0.4, 0.4]),
+                                 np.array([1e-5, 1e-5]))
+    assert np.allclose(V, [2000.0 * 1.02, 2000.0 * 1.07], rtol=1e-14)
+    assert np.allclose(A, [1e-5 * math.exp(0.1), 1e-5 * math.exp(-0.2)], rtol=1e-14)
+    assert np.allclose(psi, [0.39, 0.43], rtol=0, atol=1e-15)
+    assert np.allclose(p, [0.5, 0.75], rtol=1e-14)
+    assert np.allclose(vt, [0.003, -0.002], rtol=0, atol=1e-16)
+    rng = np.random.default_rng(8)
+    n = 500
+    Vg = rng.uniform(1500, 4500, n)
+    psi_el = rng.uniform(-math.pi, math.pi, n)
+    A0 = rng.uniform(1e-6, 1e-4, n)
+    V = Vg * rng.uniform(0.9, 1.1, n)
+    A = A0 * rng.uniform(0.5, 2.0, n)
+    psi = np.angle(np.exp(1j * (psi_el + rng.uniform(-0.3, 0.3, n))))
+    vt = rng.uniform(-0.05, 0.05, n)
+    t = mo.encode_targets(V, A, psi, np.zeros(n, int), vt, Vg, psi_el, A0)
+    y = (t - out_mean) / out_std
+    V2, A2, psi2, p2, vt2 = mo.decode(y, out_mean, out_std, Vg, psi_el, A0)
+    assert np.allclose(V2, V, rtol=1e-12)
+    assert np.allclose(A2, A, rtol=1e-12)
+    assert np.allclose(np.angle(np.exp(1j * (psi2 - psi))), 0.0, atol=1e-12)
+    assert np.allclose(vt2, vt, rtol=0, atol=1e-15)
+    assert np.all(p2 > 0.73)                         # validity 1 -> logit (1 - 0)/1 = 1 -> p = 0.731
