@@ -961,8 +961,10 @@ __global__ void raypath_kernel(const int32_t* __restrict__ par, int n_fields, in
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct WsLayout {
-    size_t sel, idx, src, status, total;
+    size_t sel, idx, src, status, rowk, total;
 };
+
+constexpr int kRowkMax = 2048;       // rows of a 2D lattice the row-class path handles
 
 WsLayout ws_layout(int n_modes, int n_classes, int n_off, int precision, int n_sources) {
     const size_t es = precision == CHERT_FP64 ? 8 : 4;
@@ -972,7 +974,8 @@ WsLayout ws_layout(int n_modes, int n_classes, int n_off, int precision, int n_s
     w.idx = align256(2 * m * es);
     w.src = w.idx + align256(m * 4);
     w.status = w.src + align256(static_cast<size_t>(n_sources) * 8);
-    w.total = w.status + align256((static_cast<size_t>(n_sources) * n_modes * 2 + 1) * 4);
+    w.rowk = w.status + align256((static_cast<size_t>(n_sources) * n_modes * 2 + 1) * 4);
+    w.total = w.rowk + align256(static_cast<size_t>(kRowkMax) * 4);
     return w;
 }
 
@@ -1124,7 +1127,19 @@ static size_t fast_smem(int nk, int nx, int nz, size_t es, bool pn) {
     const size_t LS = ((line_max + 2 * R) + 3) & ~3;
     const size_t tiles = (size_t)((nx + fast::kTile - 1) / fast::kTile) * ((nz + fast::kTile - 1) / fast::kTile);
     return (pn ? 0 : (size_t)nk * nk * fast::Stencil<R>::N * es) + 16 * LS * (2 * es) + 4 * tiles +
-           4 * fast::Stencil<R>::N + 64;
+           4 * fast::Stencil<R>::N + 4 * (size_t)nz + 64;
+}
+
+// Row classes of a 2D class map: rowk[z] = the class of every node of row z,
+// or -1 if the row holds more than one class.  One CTA per row.
+__global__ void row_classes_kernel(const int32_t* __restrict__ cls, int nx, int nz, int* __restrict__ rowk) {
+    const int z = blockIdx.x;
+    const int32_t* row = cls + (size_t)z * nx;
+    const int k0 = row[0];
+    bool same = true;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) same = same && row[x] == k0;
+    same = __syncthreads_and(same);
+    if (threadIdx.x == 0) rowk[z] = same ? k0 : -1;
 }
 
 template <typename T, int R, int PPT, bool PN>
@@ -1282,7 +1297,7 @@ static PnLayout pn_layout(int n_modes, int n_classes, int n_off, int precision, 
 // workspace's per-node area, or null.
 template <typename T, int R>
 static int try_fast_R(fast::Args& a, const Offsets& off, int smem_max, int blocks, const void* Vsel,
-                      unsigned char* pn_area, size_t pn_bytes, int n_modes, cudaStream_t s) {
+                      unsigned char* pn_area, size_t pn_bytes, int n_modes, int* rowk_area, cudaStream_t s) {
     if (!standard_map<R>(off, a.map)) return 0;
     const int line_max = std::max(a.nx, a.nz);
     if (line_max > 2048) return 0;
@@ -1319,6 +1334,13 @@ static int try_fast_R(fast::Args& a, const Offsets& off, int smem_max, int block
     } else {
         a.wrow = a.wcol = nullptr;
     }
+    a.rowk = nullptr;
+    if (!pn && ppt == 1 && rowk_area && a.nz <= kRowkMax) {        // row-class path, if every row is one class
+        row_classes_kernel<<<a.nz, 128, 0, s>>>(a.cls, a.nx, a.nz, rowk_area);
+        const int rc0 = launch_check("relaxation: row classes");
+        if (rc0) return rc0;
+        a.rowk = rowk_area;
+    }
     int rc;
     if (pn)
         rc = ppt == 1 ? launch_fast_ppt<T, R, 1, true>(a, smem, blocks, threads, s)
@@ -1333,12 +1355,12 @@ static int try_fast_R(fast::Args& a, const Offsets& off, int smem_max, int block
 
 template <typename T>
 static int try_fast(fast::Args& a, const Offsets& off, int R, int smem_max, int blocks, const void* Vsel,
-                    unsigned char* pn_area, size_t pn_bytes, int n_modes, cudaStream_t s) {
+                    unsigned char* pn_area, size_t pn_bytes, int n_modes, int* rowk_area, cudaStream_t s) {
     switch (R) {
-        case 2: return try_fast_R<T, 2>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s);
-        case 3: return try_fast_R<T, 3>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s);
-        case 4: return try_fast_R<T, 4>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s);
-        case 5: return try_fast_R<T, 5>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s);
+        case 2: return try_fast_R<T, 2>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s);
+        case 3: return try_fast_R<T, 3>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s);
+        case 4: return try_fast_R<T, 4>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s);
+        case 5: return try_fast_R<T, 5>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s);
         default: return 0;
     }
 }
@@ -1517,9 +1539,10 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     fa.wrow = fa.wcol = nullptr;
     unsigned char* pn_area = bytes > ws.total ? w + ws.total : nullptr;
     const size_t pn_bytes = bytes > ws.total ? bytes - ws.total : 0;
+    int* rowk_area = reinterpret_cast<int*>(w + ws.rowk);
     const int fr = precision == CHERT_FP64
-                       ? try_fast<double>(fa, off, R, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s)
-                       : try_fast<float>(fa, off, R, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, s);
+                       ? try_fast<double>(fa, off, R, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s)
+                       : try_fast<float>(fa, off, R, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s);
     if (fr < 0) return fr;
     if (fr == 1) rc = CHERT_OK;
     else if (precision == CHERT_FP64)

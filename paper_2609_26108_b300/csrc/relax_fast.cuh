@@ -92,6 +92,10 @@ struct Args {
     // memory): [n_modes*2 + comp][N][node], node index z*nx + x (row layout)
     // and x*nz + z (column layout); null for the class-pair table.
     const void *wrow, *wcol;
+    // Row classes [nz]: rowk[z] = the class of every node of row z, or -1 if
+    // the row holds several classes (written by row_classes_kernel); null
+    // when the launch cannot use the row-class path.
+    const int* rowk;
 };
 
 // One ring element: the node's tau and its class id pre-multiplied by nk*N,
@@ -113,6 +117,7 @@ constexpr int kTile = 32;
 
 template <typename T>
 struct Ctx {
+    const int* rowk; // [nz] class of each row (row-class path), shared memory
     T* W;            // [nk][nk][N]: W[(ki*nk + kj)*N + q] (class-pair mode)
     Cell<T>* ring;   // [16][LS]
     short* sx;       // stencil offsets (for decoding the winning parent)
@@ -376,6 +381,171 @@ __device__ bool verify(const Ctx<T>& c, T* __restrict__ tau, const int32_t* __re
     return __syncthreads_or(changed);
 }
 
+// ---- row-class path --------------------------------------------------------
+// When every lattice row holds one class (flat layers, the paper's layered
+// models), the weight of an edge depends only on the rows of its two ends:
+// w_q(z) = W[k(z - o_z)][k(z)][q].  Then
+//   * in a row sweep and in the verification pass every thread of a line reads
+//     the same weights (one broadcast per shared load), at offsets in the
+//     class-pair table fixed per line;
+//   * in a column sweep each thread owns one depth z for the whole sweep, so
+//     its weight offsets are fixed per sweep;
+//   * the ring holds tau only, so a pull is a 4-byte (8-byte in double)
+//     shared load of tau and an independent load of the weight, an add and a
+//     min -- the class loads of the class-pair path, and the weight load that
+//     had to wait for them, are gone.
+// Same pulls in the same order with the same rounded weights as the class-
+// pair path, so the fields and parents are bit-identical.
+
+__device__ __forceinline__ int row_class(const int* rowk, int z, int nz, int fallback) {
+    return (z >= 0 && z < nz) ? rowk[z] : fallback;
+}
+
+template <typename T, int R, int AXIS, int DIR>
+__device__ void sweep_rows(const Ctx<T>& c, T* __restrict__ tau, int pass, int since) {
+    constexpr int N = Stencil<R>::N;
+    const int n_lines = AXIS == 0 ? c.nz : c.nx;
+    const int len = AXIS == 0 ? c.nx : c.nz;
+    const int nx = c.nx, nk = c.nk;
+    const int u = threadIdx.x;
+    T* ring = reinterpret_cast<T*>(c.ring);
+    for (int i = u; i < 8 * c.LS; i += blockDim.x) ring[i] = T(INFINITY);
+    __syncthreads();
+    // wo[oz + R]: offset in W of the class pair (row of i = j - o, row of j)
+    // for the entries with z component oz.  Column sweeps: fixed per thread
+    // (its depth z = u); row sweeps: fixed per line, the same for all threads.
+    int wo[2 * R + 1];
+    auto set_wo = [&](int zj) {
+        const int kj = row_class(c.rowk, zj, c.nz, 0);
+#pragma unroll
+        for (int d = -R; d <= R; ++d) wo[d + R] = (row_class(c.rowk, zj - d, c.nz, kj) * nk + kj) * N;
+    };
+    if constexpr (AXIS == 1) set_wo(u < len ? u : 0);
+    auto gidx = [&](int line) {
+        return AXIS == 0 ? (size_t)u + (size_t)nx * line : (size_t)line + (size_t)nx * u;
+    };
+    auto ring_line = [&](int line) {
+        if (u < len) ring[(line & 7) * c.LS + R + u] = (line >= 0 && line < n_lines) ? tau[gidx(line)] : T(INFINITY);
+    };
+    bool reload = false;
+    T cur = (u < len) ? tau[gidx(DIR > 0 ? 0 : n_lines - 1)] : T(INFINITY);
+    for (int step = 0; step < n_lines; ++step) {
+        const int line = DIR > 0 ? step : n_lines - 1 - step;
+        const bool band_start = DIR > 0 ? (line % kTile == 0) : (line == n_lines - 1 || line % kTile == kTile - 1);
+        if (band_start) {
+            const int b = line / kTile;
+            if (!band_dirty<T, AXIS>(c, b, since)) {
+                const int last = DIR > 0 ? min(n_lines - 1, b * kTile + kTile - 1) : b * kTile;
+                step = DIR > 0 ? last : n_lines - 1 - last;
+                reload = true;
+                continue;
+            }
+            if (reload) {
+                for (int lag = 1; lag <= R; ++lag) ring_line(line - DIR * lag);
+                cur = (u < len) ? tau[gidx(line)] : T(INFINITY);
+                __syncthreads();
+                reload = false;
+            }
+        }
+        if constexpr (AXIS == 0) set_wo(line);
+        const T nxt = (step + 1 < n_lines && u < len) ? tau[gidx(DIR > 0 ? line + 1 : line - 1)] : T(INFINITY);
+        int po[R + 1];                      // ring offsets of the previous lines (32-bit shared indices)
+#pragma unroll
+        for (int lag = 1; lag <= R; ++lag) po[lag] = ((line - DIR * lag) & 7) * c.LS + R + u;
+        const int own = (line & 7) * c.LS + R;
+        if (u < len) {
+            const int tx = (AXIS == 0 ? u : line) / kTile, tz = (AXIS == 0 ? line : u) / kTile;
+            T best = cur;
+            if (dirty(c, tx, tz, since)) {
+                static_for<N>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    constexpr int oa = AXIS == 0 ? Table<R>::v.z[q] : Table<R>::v.x[q];
+                    constexpr int ol = AXIS == 0 ? Table<R>::v.x[q] : Table<R>::v.z[q];
+                    if constexpr (oa * DIR > 0) {
+                        constexpr int lag = oa * DIR;
+                        constexpr int oz = Table<R>::v.z[q];
+                        best = fmin_(best, ring[po[lag] - ol] + c.W[wo[oz + R] + q]);
+                    }
+                });
+            }
+            ring[own + u] = best;
+            if (best < cur) {
+                tau[gidx(line)] = best;
+                c.stamp[tz * c.TX + tx] = pass;
+            }
+        }
+        __syncthreads();
+        cur = nxt;
+    }
+}
+
+// Verification pass of the row-class path: rows, a 16-row ring of tau; the
+// weights of the row's in-neighbours are read from the class-pair table at
+// addresses that are the same for every thread (one broadcast per load).
+template <typename T, int R>
+__device__ bool verify_rows(const Ctx<T>& c, T* __restrict__ tau, int64_t src, int32_t* __restrict__ par,
+                            int pass, int since) {
+    constexpr int N = Stencil<R>::N;
+    const int nx = c.nx, nz = c.nz, nk = c.nk;
+    const int x = threadIdx.x;
+    T* ring = reinterpret_cast<T*>(c.ring);
+    for (int i = x; i < 16 * c.LS; i += blockDim.x) ring[i] = T(INFINITY);
+    __syncthreads();
+    auto store_row = [&](int row) {
+        if (x < nx) ring[(row & 15) * c.LS + R + x] = (row >= 0 && row < nz) ? tau[(size_t)x + (size_t)nx * row]
+                                                                              : T(INFINITY);
+    };
+    for (int row = 0; row < R && row < nz; ++row) store_row(row);
+    bool changed = false, reload = false;
+    for (int z = 0; z < nz; ++z) {
+        if (z % kTile == 0) {
+            const int b = z / kTile;
+            if (!band_dirty<T, 0>(c, b, since)) {
+                z = min(nz, z + kTile) - 1;
+                reload = true;
+                continue;
+            }
+            if (reload) {
+                for (int row = z - R; row < z + R; ++row) store_row(row);
+                reload = false;
+            }
+        }
+        store_row(z + R);
+        __syncthreads();
+        int po[2 * R + 1], wo[2 * R + 1];   // ring offsets of rows z - d, weight-table offsets
+        const int kj = c.rowk[z];
+#pragma unroll
+        for (int d = -R; d <= R; ++d) {
+            po[d + R] = ((z - d) & 15) * c.LS + R + x;
+            wo[d + R] = (row_class(c.rowk, z - d, nz, kj) * nk + kj) * N;
+        }
+        if (x < nx && dirty(c, x / kTile, z / kTile, since)) {
+            const T cur = ring[po[R]];
+            const size_t j = (size_t)x + (size_t)nx * z;
+            T best = T(INFINITY);
+            int bq = -1;
+            static_for<N>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                constexpr int oz = Table<R>::v.z[q], ox = Table<R>::v.x[q];
+                const T cand = ring[po[oz + R] - ox] + c.W[wo[oz + R] + q];
+                if (cand < best) { best = cand; bq = q; }
+            });
+            if (best < cur) {
+                tau[j] = best;
+                changed = true;
+                c.stamp[(z / kTile) * c.TX + x / kTile] = pass;
+            } else if (par) {
+                int32_t pj;
+                if ((int64_t)j == src) pj = (int32_t)src;
+                else if (isinf(cur) || bq < 0) pj = -1;
+                else pj = (int32_t)((long long)j - ((long long)c.sz[bq] * nx + c.sx[bq]));
+                par[j] = pj;
+            }
+        }
+    }
+    return __syncthreads_or(changed);
+}
+
 template <typename T, int R, int PPT, bool PN>
 __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
     constexpr int N = Stencil<R>::N;
@@ -400,7 +570,9 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
     c.ring = reinterpret_cast<Cell<T>*>(p); p += (size_t)16 * c.LS * sizeof(Cell<T>);
     c.stamp = reinterpret_cast<int*>(p); p += (size_t)c.TX * c.TZ * sizeof(int);
     c.sx = reinterpret_cast<short*>(p); p += N * sizeof(short);
-    c.sz = reinterpret_cast<short*>(p);
+    c.sz = reinterpret_cast<short*>(p); p += N * sizeof(short);
+    int* rowk_s = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
+    c.rowk = rowk_s;
     c.wr = PN ? static_cast<const T*>(a.wrow) + (size_t)(mode * 2 + comp) * N * c.n : nullptr;
     c.wc = PN ? static_cast<const T*>(a.wcol) + (size_t)(mode * 2 + comp) * N * c.n : nullptr;
 
@@ -434,10 +606,43 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
     for (size_t j = threadIdx.x; j < c.n; j += blockDim.x) tau[j] = (j == (size_t)src) ? T(0) : T(INFINITY);
     __syncthreads();
 
+    // Row-class path: every row one class (checked on the row classes that
+    // row_classes_kernel wrote), one node of a line per thread.
+    bool rows = false;
+    if constexpr (!PN && PPT == 1) {
+        if (a.rowk) {
+            bool ok = true;
+            for (int z = threadIdx.x; z < a.nz; z += blockDim.x) {
+                const int k = a.rowk[z];
+                rowk_s[z] = k;
+                ok = ok && k >= 0 && k < nk;
+            }
+            rows = __syncthreads_and(ok);
+        }
+    }
+
     // pass numbers start at 1; every tile starts dirty (stamp 0 >= last 0)
     int pass = 1;
     int last[5] = {0, 0, 0, 0, 0};
     int used = -1;
+    if constexpr (!PN && PPT == 1) {
+        if (rows) {
+            for (int cycle = 0; cycle < a.max_cycles; ++cycle) {
+                sweep_rows<T, R, 0, +1>(c, tau, pass, last[0]); last[0] = pass++;
+                sweep_rows<T, R, 1, +1>(c, tau, pass, last[1]); last[1] = pass++;
+                sweep_rows<T, R, 1, -1>(c, tau, pass, last[2]); last[2] = pass++;
+                sweep_rows<T, R, 0, -1>(c, tau, pass, last[3]); last[3] = pass++;
+                const bool changed = verify_rows<T, R>(c, tau, src, par, pass, last[4]);
+                last[4] = pass++;
+                if (!changed) {
+                    used = cycle + 1;
+                    break;
+                }
+            }
+            if (threadIdx.x == 0) a.status[field * 2 + comp] = used;
+            return;
+        }
+    }
     for (int cycle = 0; cycle < a.max_cycles; ++cycle) {
         sweep<T, R, PPT, 0, +1, PN>(c, tau, a.cls, pass, last[0]); last[0] = pass++;
         sweep<T, R, PPT, 1, +1, PN>(c, tau, a.cls, pass, last[1]); last[1] = pass++;
