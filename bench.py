@@ -52,10 +52,15 @@ RADIUS = 5
 N_RECEIVERS = 41
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# relax_fast_kernel<float, 5, 1, class-pair> on the 64-source workload, from
-# one ncu capture of this kernel version (1.059 GB read + 0.743 GB written).
-RELAX_DRAM_BYTES_64SRC = 1.059124e9 + 0.743181e9
+# FP32 operations (adds, multiplies, 2 per fused multiply-add) of one
+# energy-velocity evaluation of the cache build: the ncu count of FP32
+# instructions of the all-float layered build divided by its counted
+# evaluations (float); and of one float-float evaluation, from the same count
+# for the MIXED build less its float evaluations (bench.py --cache-only;
+# profiles/cache_build_kernel_layered_tti_401x401.md, part C).
+F_EVAL_F32 = 368.4
+F_EVAL_FF = 5945.0
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "relax_fast_kernel_layered_tti_401x401_64src.md")
 
 
 def workload(n_sources=64):
@@ -73,6 +78,16 @@ def measured_hbm_gbs():
             return float(json.load(f)["hbm_gbs"]), "of measured"
     except (OSError, KeyError, ValueError):
         return 6400.0, "of fallback"
+
+
+def measured_bf16_tflops():
+    """Sustained dense BF16 rate of this machine's B300s (MEASURED_PEAKS.json),
+    else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "of measured (sustained)"
+    except (OSError, KeyError, ValueError):
+        return 1400.0, "of fallback (sustained)"
 
 
 # Instructions a warp issues per pull in the relaxation's inner loop, counted
@@ -109,6 +124,53 @@ def issue_roofline(alg_pulls, launch_s, sm_max_mhz):
     return {"achieved_pulls_per_s": a, "peak_pulls_per_s": peak, "frac": a / peak,
             "instructions_per_pull": INSTR_PER_PULL,
             "peak_source": "derived: 148 SMs x 4 schedulers x max SM clock x 32 lanes / instructions per pull"}
+
+
+def relax_sources_sha():
+    """Digest of the 2D relaxation's sources, to tie a DRAM capture to the
+    kernel version it measured."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("relax_fast.cuh", "relax.cu"):
+        with open(os.path.join(ROOT, "paper_2609_26108_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic():
+    """DRAM bytes per launch of the relaxation from the committed ncu summary,
+    or None when that capture measured another version of the kernel."""
+    try:
+        with open(TRAFFIC_PROFILE) as f:
+            for line in f:
+                if line.startswith("traffic_bytes_per_launch:"):
+                    fields = dict(kv.split("=") for kv in line.split(":", 1)[1].split())
+                    if fields.get("sources_sha256_16") == relax_sources_sha():
+                        return float(fields["bytes"])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def cache_roofline(build_once, entries, build_s, counter):
+    """The cache build against the measured FP32 multiply-add rate: work =
+    counted energy-velocity evaluations x FP32 operations per evaluation."""
+    from paper_2609_26108_b300 import chert
+    with counter() as ec:
+        build_once()
+    n_f32, n_ff, n_f64 = ec.counts
+    flops = n_f32 * F_EVAL_F32 + n_ff * F_EVAL_FF
+    peak32 = max(chert.fma_rate("fp32", 1 << 15) for _ in range(3))
+    peak64 = max(chert.fma_rate("fp64", 1 << 12) for _ in range(2))
+    achieved = flops / build_s
+    return {"bound": "fp32", "achieved": achieved / 1e12, "peak": peak32 / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak32, "peak_source": "measured: chert_fma_rate (FP32 FMA chains, all SMs)",
+            "fp64_fma_peak_tflops": peak64 / 1e12,
+            "evaluations": {"float": n_f32, "float_float": n_ff, "double": n_f64},
+            "evaluations_per_entry": (n_f32 + n_ff + n_f64) / entries,
+            "flops_per_evaluation": {"float": F_EVAL_F32, "float_float": F_EVAL_FF},
+            "flops_per_entry": flops / entries,
+            "roofline_entries_per_s": peak32 / (flops / entries), "entries_per_s": entries / build_s}
 
 
 def directed_edges(nx, nz, off):
@@ -188,76 +250,143 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- CPU oracle
-def oracle_sample(model, off, n_solves=3, n_fields=2, seed=0):
-    """Time the FP64 oracle on a bounded sample of the workload (single thread).
-
-    Returns (fields_per_s, entries_per_s, description).  The cache part times
-    `n_solves` distinct (mode, class, angle) solves at the full scan grid and
-    scales to the 2,184 distinct solves of the 8,640-entry cache; the
-    relaxation part times `n_fields` (source, mode) fields, each tau^R and
-    tau^I by binary-heap Dijkstra with parents."""
+def cpu_info():
+    """CPU model and the cores this process may use."""
+    model = "unknown"
     try:
-        from threadpoolctl import threadpool_limits
-    except ImportError:                    # the oracle's numpy calls are 2x2 solves
-        import contextlib
-        threadpool_limits = lambda n: contextlib.nullcontext()   # noqa: E731
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    return model, cores
+
+
+def _oracle_task(task):
+    """One unit of oracle work on one core: ("solve", seed) times one cache
+    solve at the full scan grid, ("field", seed) one source's tauR and tauI by
+    Dijkstra; returns its wall time."""
+    kind, seed = task
+    from threadpoolctl import threadpool_limits
     from oracle import cache_oracle as co
     from oracle import graph_oracle as go
+    model, off, _ = workload()
     rng = np.random.default_rng(seed)
-    mods, tilts = [], []
-    for L in model.layers:
-        mods.append(co.moduli_from_thomsen(L.vp0, L.vs0, L.eps, L.delta, L.gamma, L.qp, L.qs))
-        tilts.append(L.tilt)
-    n_cls = len(model.layers)
     with threadpool_limits(1):
         t0 = time.perf_counter()
-        for _ in range(n_solves):
-            mi, k, j = rng.integers(0, 3), rng.integers(0, n_cls), rng.integers(0, M_PER_QUADRANT + 1)
-            co.solve_direction(co.stiffness_tensor(mods[k]), (math.pi / 2) * j / M_PER_QUADRANT,
-                               MODES[mi], "MEV", SCAN_STEP, SCAN_HALF)
-        t_solve = (time.perf_counter() - t0) / n_solves
-        # a cheap stand-in cache for the lookup (timed: lookup is per mode)
-        Vsel = rng.uniform(1500, 4500, (n_cls, len(off)))
-        Asel = rng.uniform(1e-6, 1e-4, (n_cls, len(off)))
-        cls = model.class_of_node.astype(np.int32)
-        go.build()
-        t0 = time.perf_counter()
-        for f in range(n_fields):
+        if kind == "solve":
+            mi, k, j = rng.integers(0, 3), rng.integers(0, len(model.layers)), rng.integers(0, M_PER_QUADRANT + 1)
+            L = model.layers[k]
+            a = co.moduli_from_thomsen(L.vp0, L.vs0, L.eps, L.delta, L.gamma, L.qp, L.qs)
+            co.solve_direction(co.stiffness_tensor(a), (math.pi / 2) * j / M_PER_QUADRANT, MODES[mi], "MEV",
+                               SCAN_STEP, SCAN_HALF)
+        else:
+            Vsel = rng.uniform(1500, 4500, (len(model.layers), len(off)))
+            Asel = rng.uniform(1e-6, 1e-4, (len(model.layers), len(off)))
+            cls = model.class_of_node.astype(np.int32)
             s = int(model.sources[rng.integers(0, len(model.sources))])
             go.dijkstra((model.nx, 1, model.nz), model.dx, cls, off, Vsel, 0, s)
             go.dijkstra((model.nx, 1, model.nz), model.dx, cls, off, Asel, 1, s)
-        t_field = (time.perf_counter() - t0) / n_fields
-    n_solves_total = n_cls * 3 * (M_PER_QUADRANT + 1)
+        return time.perf_counter() - t0
+
+
+def oracle_sample(model, off, n_solves=3, n_fields=2, seed=0, parallel=True):
+    """Time the FP64 oracle on a bounded sample of the workload.
+
+    The cache part times distinct (mode, class, angle) solves at the full scan
+    grid and scales to the 2,184 distinct solves of the 8,640-entry cache; the
+    relaxation part times (source, mode) fields, each tau^R and tau^I by
+    binary-heap Dijkstra with parents.  Single thread: n_solves solves and
+    n_fields fields one after another.  Parallel (parallel=True): a process
+    pool with one worker per core runs one solve and one field per worker at
+    once, and the wall time of each batch gives the whole machine's rate.
+    Returns a dict with fields/s and entries/s, single-thread and parallel."""
+    from oracle import graph_oracle as go
+    go.build()
+    model_name, cores = cpu_info()
+    rng = np.random.default_rng(seed)
+    t_solve = sum(_oracle_task(("solve", int(rng.integers(1 << 30)))) for _ in range(n_solves)) / n_solves
+    t_field = sum(_oracle_task(("field", int(rng.integers(1 << 30)))) for _ in range(n_fields)) / n_fields
+    n_solves_total = len(model.layers) * 3 * (M_PER_QUADRANT + 1)
     n_fields_total = len(model.sources) * 3
+    entries = len(model.layers) * 3 * 4 * M_PER_QUADRANT
     t_step = n_solves_total * t_solve + n_fields_total * t_field
-    entries = n_cls * 3 * 4 * M_PER_QUADRANT
-    desc = ("%d cache solves at the full 0.001 deg scan (%.2f s each, scaled to %d solves) + %d fields "
-            "of tauR+tauI Dijkstra on 401x401 (%.2f s each, scaled to %d fields); 1 thread"
-            % (n_solves, t_solve, n_solves_total, n_fields, t_field, n_fields_total))
-    return n_fields_total / t_step, entries / (n_solves_total * t_solve), desc, t_step
+    out = {"cpu_model": model_name, "nproc": cores,
+           "single": {"fields_per_s": n_fields_total / t_step, "entries_per_s": entries / (n_solves_total * t_solve),
+                      "s_per_solve": t_solve, "s_per_field": t_field, "cores": 1},
+           "sample": "%d cache solves at the full 0.001 deg scan (scaled to %d solves) + %d fields of tauR+tauI "
+                     "Dijkstra on 401x401 (scaled to %d fields)" % (n_solves, n_solves_total, n_fields,
+                                                                    n_fields_total)}
+    if parallel and cores > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_oracle_task, [("field", 0)] * cores)                 # start-up, imports
+            t0 = time.perf_counter()
+            pool.map(_oracle_task, [("solve", seed + 1 + i) for i in range(cores)], chunksize=1)
+            t_solves = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            pool.map(_oracle_task, [("field", seed + 1 + i) for i in range(cores)], chunksize=1)
+            t_fields = time.perf_counter() - t0
+        solve_rate = cores / t_solves                  # solves/s over the machine
+        field_rate = cores / t_fields
+        t_par = n_solves_total / solve_rate + n_fields_total / field_rate
+        out["parallel"] = {"fields_per_s": n_fields_total / t_par,
+                           "entries_per_s": entries * solve_rate / n_solves_total, "cores": cores,
+                           "sample": "%d solves and %d fields at once, one per worker process" % (cores, cores)}
+    best = out.get("parallel", out["single"])
+    out["fields_per_s"], out["entries_per_s"], out["cores"] = best["fields_per_s"], best["entries_per_s"], best["cores"]
+    out["t_step_s"] = n_fields_total / out["fields_per_s"]
+    return out
 
 
 def run_reference(args):
+    """The oracle on the host's cores: per step, one cache solve and one field
+    per core at once (a spawn process pool, one worker per core), scaled to
+    the workload's 2,184 solves and 192 fields."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    import multiprocessing as mp
+    from oracle import graph_oracle as go
+    go.build()
     model, off, _ = workload()
-    for _ in range(args.warmup):
-        oracle_sample(model, off, 1, 1)
+    model_name, cores = cpu_info()
+    n_solves_total = len(model.layers) * 3 * (M_PER_QUADRANT + 1)
+    n_fields_total = len(model.sources) * 3
     vals, times = [], []
-    for s in range(args.steps):
-        fps, eps_, desc, t_step = oracle_sample(model, off, 1, 1, seed=s + 1)
-        vals.append(fps)
-        times.append(t_step)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for step in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_task, [("solve", 1000 * step + i) for i in range(cores)], chunksize=1)
+            t_solves = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            pool.map(_oracle_task, [("field", 1000 * step + i) for i in range(cores)], chunksize=1)
+            t_fields = time.perf_counter() - t0
+            if step < args.warmup:
+                continue
+            t_step = n_solves_total * t_solves / cores + n_fields_total * t_fields / cores
+            vals.append(n_fields_total / t_step)
+            times.append(t_step)
     value = statistics.median(vals)
+    sample = ("per step: %d cache solves at the full 0.001 deg scan and %d fields of tauR+tauI Dijkstra on "
+              "401x401, one of each per worker process at once, scaled to %d solves and %d fields"
+              % (cores, cores, n_solves_total, n_fields_total))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "fields/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": config_dict(model),
-           "cpu_baseline": {"value": value, "unit": "fields/s", "cores": 1, "kind": "oracle",
-                            "sample": "per step: " + desc},
-           "e2e": {"value": value, "unit": "fields/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "cpu_baseline": {"value": value, "unit": "fields/s", "cores": cores, "kind": "oracle",
+                            "cpu_model": model_name, "nproc": cores, "sample": sample},
+           "e2e": {"value": value, "unit": "fields/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "note": "each step times a bounded sample of the oracle and scales it to the whole workload; "
+                   "ms_per_step is that scaled time, not the step's wall time"}
     print(json.dumps(out))
     return 0
 
@@ -310,6 +439,25 @@ def surrogate_section(n_sources, flush, log=None):
     del train
     if log:
         log("training set %.1f s, training %.1f s" % (t_data, t_train))
+    # BF16 roofline of inference: 2 flops per parameter per row
+    rows = 1 << 22
+    xin = torch.rand((rows, 8), device="cuda") * 2 - 1
+    ws_f = torch.empty(int(chert.lib().chert_mlp_workspace_bytes(rows, 0)), dtype=torch.uint8, device="cuda")
+    chert.mlp_forward(params[0], xin, workspace=ws_f)
+    t_inf = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        chert.mlp_forward(params[0], xin, workspace=ws_f)
+        b.record()
+        torch.cuda.synchronize()
+        t_inf.append(a.elapsed_time(b) / 1e3)
+    inf_s = statistics.median(t_inf)
+    n_par = chert.mlp_param_count() - 10                     # weights and biases (out_mean/out_std excluded)
+    bf16_peak = measured_bf16_tflops()
+    inf_tflops = 2.0 * n_par * rows / inf_s / 1e12
+    del xin, ws_f
 
     shape = (len(MODES), n, 4 * M)
     bufs = []
@@ -375,6 +523,9 @@ def surrogate_section(n_sources, flush, log=None):
                          "steps_per_mode": SURR_TRAIN_STEPS, "batch": SURR_BATCH,
                          "dataset_s": t_data, "train_s": t_train, "one_off": True},
             "plain": res["plain"], "surrogate": res["surrogate"],
+            "roofline_inference": {"bound": "tensor", "achieved": inf_tflops, "peak": bf16_peak[0],
+                                   "unit": "TFLOP/s", "frac": inf_tflops / bf16_peak[0], "peak_source": bf16_peak[1],
+                                   "rows": rows, "rows_per_s": rows / inf_s, "flops_per_row": 2 * n_par},
             "speedup_fields_per_s": res["surrogate"]["fields_per_s"] / res["plain"]["fields_per_s"],
             "speedup_cache": res["plain"]["cache_s"] / res["surrogate"]["cache_s"],
             "traveltime_rel_error_vs_plain": errs,
@@ -706,7 +857,7 @@ def run_chert(args):
     sm_max = clocks.get("sm_max_mhz") or 2032.0
     peak_tops = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     achieved = alg_ops / relax_avg_s / 1e12
-    traffic = RELAX_DRAM_BYTES_64SRC if len(model.sources) == 64 else None
+    traffic = captured_traffic() if len(model.sources) == 64 else None
     roofline = {"bound": "alu", "kernel": "relax_fast_kernel<float,5,1,false>", "achieved": achieved,
                 "peak": peak_tops, "unit": "TFLOP/s", "frac": achieved / peak_tops, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu)",
@@ -717,6 +868,10 @@ def run_chert(args):
                 "hbm": hbm_roofline(20.0 * model.nx * model.nz * nf, traffic, relax_avg_s),
                 "issue": issue_roofline(edges * nf * 2, relax_avg_s, sm_max)}
     cache_avg_s = statistics.mean(cache_ms) / 1e3
+    roof_cache = cache_roofline(
+        lambda: chert.build_cache(tr.d_classes, len(classes), MODES, M_PER_QUADRANT, SCAN_STEP, SCAN_HALF, "MEV",
+                                  "mixed", out=tr.cache_out),
+        entries, cache_avg_s, chert.EvalCounter)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -731,7 +886,7 @@ def run_chert(args):
            "cache_entries_per_s": world * entries / cache_avg_s,
            "cache_build_ms": 1e3 * cache_avg_s, "relax_ms": 1e3 * relax_avg_s,
            "edge_relaxations_per_s": world * edges * nf * 2 / relax_avg_s,
-           "roofline": roofline, "clocks": clocks,
+           "roofline": roofline, "roofline_cache_build": roof_cache, "clocks": clocks,
            "e2e": {"value": e2e_value, "unit": "fields/s", "h2d_bytes_per_step": tr.h2d_bytes(),
                    "d2h_bytes_per_step": tr.d2h_bytes()},
            "gpu_launches": tr.launches_per_run * args.steps}
@@ -746,12 +901,31 @@ def run_chert(args):
     if world == 1 and args.batch_sources > 0:
         out["batch"] = section_batch(args.batch_sources, args.batch_sources_3d)
     if world == 1 and not args.no_cpu_baseline:
-        fps, eps_, desc, _ = oracle_sample(model, off)
-        out["cpu_baseline"] = {"value": fps, "unit": "fields/s", "cores": 1, "kind": "oracle",
-                               "sample": desc, "cache_entries_per_s": eps_}
+        cb = oracle_sample(model, off)
+        out["cpu_baseline"] = {"value": cb["fields_per_s"], "unit": "fields/s", "cores": cb["cores"],
+                               "kind": "oracle", "cpu_model": cb["cpu_model"], "nproc": cb["nproc"],
+                               "sample": cb["sample"], "cache_entries_per_s": cb["entries_per_s"],
+                               "single_thread": cb["single"], "parallel": cb.get("parallel")}
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_cache_only(precision):
+    """The layered workload's cache build alone, twice (the second with the
+    evaluation counter), for profiling its kernels; prints the counts."""
+    import torch
+    from paper_2609_26108_b300 import build, chert
+    build.build()
+    model, _, _ = workload(1)
+    d = chert.classes_to_device(chert.classes_from_layers(model.layers))
+    chert.build_cache(d, len(model.layers), MODES, M_PER_QUADRANT, SCAN_STEP, SCAN_HALF, "MEV", precision)
+    torch.cuda.synchronize()
+    with chert.EvalCounter() as ec:
+        chert.build_cache(d, len(model.layers), MODES, M_PER_QUADRANT, SCAN_STEP, SCAN_HALF, "MEV", precision)
+    print(json.dumps({"cache_only": precision, "solves": len(model.layers) * 3 * (M_PER_QUADRANT + 1),
+                      "evaluations_float_floatfloat_double": ec.counts}))
     return 0
 
 
@@ -777,7 +951,11 @@ def main():
                     help="sources of the per-cell plain-vs-surrogate comparison (0: leave it out)")
     ap.add_argument("--scheduler-study", type=int, default=0,
                     help="sources of the block-heap vs sweep scheduler comparison on the layered model (0: leave it out)")
+    ap.add_argument("--cache-only", default=None, choices=["fp32", "mixed", "fp64"],
+                    help="profiling aid: build the layered workload's cache twice in this precision and exit")
     args = ap.parse_args()
+    if args.cache_only:
+        return run_cache_only(args.cache_only)
     if args.impl == "reference":
         return run_reference(args)
     return run_chert(args)

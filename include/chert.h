@@ -430,6 +430,25 @@ int chert_parent_ties(const void* d_Vsel, const void* d_Asel, int n_modes, int n
                       const void* d_tauR, const void* d_tauI, double rel_tol, uint8_t* d_tieR,
                       uint8_t* d_tieI, unsigned long long* d_counts, void* stream);
 
+/* ---- measurement helpers (no counterpart in the paper) ---------------------- */
+
+/* Measured multiply-add rate of this device in flop/s (2 per FMA), for the
+ * roofline of the cache build: CTAs of 256 threads, 8 per SM, each thread
+ * running 8 independent chains of `iters` FMAs in float (CHERT_FP32) or
+ * double (CHERT_FP64), timed with events on `stream` (synchronises it).
+ * Errors: CHERT_EINVAL, CHERT_ECUDA. */
+int chert_fma_rate(int precision, int iters, double* flops_per_s, void* stream);
+
+/* Counter of energy-velocity evaluations in the cache build (Eq. 12-14; one
+ * per thread and evaluation: scan grid points, polish and refinement points,
+ * ray quantities), process-wide, off by default.  enable = 1 zeroes the
+ * counts and switches counting on for the current device; enable = 0
+ * synchronises the device, switches it off and writes the counts of float,
+ * float-float and double evaluations to counts_out[3] (may be NULL).
+ * Counting adds one atomic per warp and evaluation; time builds with it off.
+ * Errors: CHERT_ECUDA. */
+int chert_cache_eval_counter(int enable, unsigned long long* counts_out);
+
 /* Message describing the last error returned on the calling host thread. */
 const char* chert_last_error(void);
 

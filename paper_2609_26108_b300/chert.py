@@ -84,6 +84,10 @@ def lib():
     L.chert_raypath.argtypes = [P, I, I64, P, P, I, I64, P, P, P]
     L.chert_parent_ties.argtypes = [P, P, I, I, I, I, I, I, D, P, P, I, P, I, P, P, D, P, P, P, P]
     L.chert_parent_ties.restype = ctypes.c_int
+    L.chert_fma_rate.argtypes = [I, I, ctypes.POINTER(ctypes.c_double), P]
+    L.chert_fma_rate.restype = ctypes.c_int
+    L.chert_cache_eval_counter.argtypes = [I, P]
+    L.chert_cache_eval_counter.restype = ctypes.c_int
     L.chert_traveltime_enqueue.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P, I,
                                            P, I, I, I, P, P, P, P, P, SZ, P, P]
     L.chert_traveltime_enqueue.restype = ctypes.c_int
@@ -458,6 +462,30 @@ def parent_ties(cache, nx, nz, dx, d_cls, offsets, sources, tauR, tauI, rel_tol,
                                    _dev_ptr(tauI), float(rel_tol), _dev_ptr(tieR), _dev_ptr(tieI),
                                    _dev_ptr(counts), _stream_ptr(stream)))
     return tieR, tieI, counts
+
+
+def fma_rate(precision="fp32", iters=1 << 16, stream=None):
+    """Measured FMA throughput of the current device in flop/s (chert_fma_rate)."""
+    out = ctypes.c_double(0.0)
+    prec = PRECISION_IDS[precision] if isinstance(precision, str) else precision
+    _check(lib().chert_fma_rate(prec, int(iters), ctypes.byref(out), _stream_ptr(stream)))
+    return out.value
+
+
+class EvalCounter:
+    """Context manager around chert_cache_eval_counter: counts the energy
+    velocity evaluations of the cache builds run inside it (.counts =
+    [float, float-float, double] after exit)."""
+
+    def __enter__(self):
+        _check(lib().chert_cache_eval_counter(1, None))
+        return self
+
+    def __exit__(self, *exc):
+        c = (ctypes.c_ulonglong * 3)()
+        _check(lib().chert_cache_eval_counter(0, ctypes.cast(c, ctypes.c_void_p)))
+        self.counts = [int(v) for v in c]
+        return False
 
 
 # ------------------------------------------------------------------ surrogate

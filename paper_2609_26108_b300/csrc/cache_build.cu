@@ -32,6 +32,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "cplx.cuh"
@@ -153,9 +154,26 @@ struct EnergyVelocity {
     cplx<T> v1, v3;
     T cond;
 };
+
+// Evaluation counter (instrumentation, off by default): evaluations of the
+// energy velocity in float, float-float and double, one per thread and call.
+__device__ int g_eval_count_on = 0;
+__device__ unsigned long long g_eval_count[3] = {0, 0, 0};
+
+template <typename T>
+__device__ __forceinline__ void count_eval() {
+    if (g_eval_count_on) {
+        const unsigned active = __activemask();
+        if ((threadIdx.x & 31) == __ffs(active) - 1)
+            atomicAdd(&g_eval_count[sizeof(T) == 4 ? 0 : (sizeof(T) == 8 && !std::is_same<T, double>::value) ? 1 : 2],
+                      (unsigned long long)__popc(active));
+    }
+}
+
 template <typename T>
 __device__ __noinline__ EnergyVelocity<T> energy_velocity_val(Medium<T> m, T s, T c, T vt, int mode, int kernel,
                                                               bool want_cond) {
+    count_eval<T>();
     EnergyVelocity<T> r;
     energy_velocity_body(m, s, c, vt, mode, kernel, r.v1, r.v3, want_cond, r.cond);
     return r;
@@ -921,4 +939,26 @@ extern "C" int chert_build_cache_3d(const chert_class* d_classes, int n_classes,
     CHERT_REQUIRE(n_az >= 1 && n_pol >= 1, "chert_build_cache_3d: n_az=%d n_pol=%d", n_az, n_pol);
     return launch_build(d_classes, n_classes, modes, n_modes, params, out, nullptr, 0, stream,
                         "chert_build_cache_3d", n_az, n_pol);
+}
+
+extern "C" int chert_cache_eval_counter(int enable, unsigned long long* counts_out) {
+    using namespace chert;
+    cudaError_t e;
+    if (enable) {
+        const unsigned long long zero[3] = {0, 0, 0};
+        const int on = 1;
+        e = cudaMemcpyToSymbol(g_eval_count, zero, sizeof(zero));
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_eval_count_on, &on, sizeof(on));
+        if (e != cudaSuccess) return cuda_fail(e, "chert_cache_eval_counter: enable");
+        return CHERT_OK;
+    }
+    const int off = 0;
+    e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_eval_count_on, &off, sizeof(off));
+    unsigned long long c[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(c, g_eval_count, sizeof(c));
+    if (e != cudaSuccess) return cuda_fail(e, "chert_cache_eval_counter: read");
+    if (counts_out)
+        for (int i = 0; i < 3; ++i) counts_out[i] = c[i];
+    return CHERT_OK;
 }
