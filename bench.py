@@ -50,6 +50,7 @@ SCAN_STEP = 0.001 * math.pi / 180
 SCAN_HALF = 30000
 RADIUS = 5
 N_RECEIVERS = 41
+E2E_PATH_CAP = 512          # nodes per returned raypath (longer ones come back with length 0)
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 # FP32 operations (adds, multiplies, 2 per fused multiply-add) of one
@@ -833,21 +834,27 @@ def run_chert(args):
     value, slowest_s = replicas.job_throughput(sum(step_ms) / 1e3, nf * args.steps, device="cuda")
     total_ms = 1e3 * slowest_s
 
-    # end to end: pinned host inputs in, both traveltime fields out, per step
+    # end to end through one library call on host buffers (chert_trace_host):
+    # page-locked classes, class map and sources in; both traveltime fields
+    # and the raypaths of both components to every receiver out
+    from paper_2609_26108_b300.pipeline import HostTracer
     h_classes = d_classes.cpu().pin_memory()
     h_cls = d_cls.cpu().pin_memory()
-    h_tauR = torch.empty(tr.tau[0].shape, dtype=tr.tau[0].dtype).pin_memory()
-    h_tauI = torch.empty_like(h_tauR).pin_memory()
-    tr.run_host(h_classes, h_cls, model.sources, h_tauR, h_tauI)
+    h_src = torch.as_tensor(np.asarray(model.sources, np.int64)).pin_memory()
+    ht = HostTracer(len(classes), MODES, M_PER_QUADRANT, model.nx, model.nz, model.dx, off, len(model.sources), rcv,
+                    scan_step=SCAN_STEP, scan_half=SCAN_HALF, path_cap=E2E_PATH_CAP)
+    ht.run(h_classes, h_cls, h_src)
     barrier()
     e2e_times = []
     for k in range(args.steps):
         flush.fill_(k & 0xff)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tr.run_host(h_classes, h_cls, model.sources, h_tauR, h_tauI)
+        ht.run(h_classes, h_cls, h_src)
         e2e_times.append(time.perf_counter() - t0)
     e2e_value, _ = replicas.job_throughput(sum(e2e_times), nf * args.steps, device="cuda")
+    e2e_h2d, e2e_d2h = ht.h2d_bytes(h_classes, h_cls, h_src), ht.d2h_bytes()
+    del ht
 
     # roofline of the dominant kernel (relaxation): algorithmic work = one
     # relaxation (add + min: 2 FP32 ops) per directed edge per field component
@@ -887,8 +894,9 @@ def run_chert(args):
            "cache_build_ms": 1e3 * cache_avg_s, "relax_ms": 1e3 * relax_avg_s,
            "edge_relaxations_per_s": world * edges * nf * 2 / relax_avg_s,
            "roofline": roofline, "roofline_cache_build": roof_cache, "clocks": clocks,
-           "e2e": {"value": e2e_value, "unit": "fields/s", "h2d_bytes_per_step": tr.h2d_bytes(),
-                   "d2h_bytes_per_step": tr.d2h_bytes()},
+           "e2e": {"value": e2e_value, "unit": "fields/s", "h2d_bytes_per_step": e2e_h2d,
+                   "d2h_bytes_per_step": e2e_d2h, "call": "chert_trace_host (one C-ABI call on page-locked host "
+                   "buffers: inputs in, cache, traveltimes with parents, raypaths, fields and raypaths out)"},
            "gpu_launches": tr.launches_per_run * args.steps}
     if world == 1 and args.surrogate_sources > 0:
         out["surrogate"] = surrogate_section(args.surrogate_sources, flush)

@@ -430,6 +430,38 @@ int chert_parent_ties(const void* d_Vsel, const void* d_Asel, int n_modes, int n
                       const void* d_tauR, const void* d_tauI, double rel_tol, uint8_t* d_tieR,
                       uint8_t* d_tieI, unsigned long long* d_counts, void* stream);
 
+/* ---- the whole path on host buffers (Algorithm 2) ------------------------- */
+
+/* Device scratch bytes chert_trace_host needs (0 for invalid sizes). */
+size_t chert_trace_host_scratch_bytes(int n_classes, int n_modes, int M, int nx, int nz, int n_off,
+                                      int n_sources, int n_rcv, int64_t path_cap, int precision);
+
+/* Algorithm 2 on a 2D lattice as one call on host buffers: copies the classes,
+ * class map, sources and receivers to the device, builds the cache
+ * (chert_build_cache with `params`; CHERT_FP64 gives double fields, CHERT_FP32
+ * and CHERT_MIXED float ones), relaxes every (source, mode) field with parents
+ * (chert_traveltime_enqueue), traces the raypaths of both components to every
+ * receiver (chert_raypath), copies the traveltime fields and raypaths back,
+ * and synchronises `stream` once.
+ *   h_classes        host [n_classes]; modes host [n_modes]
+ *   h_class_of_node  host int32 [nz*nx]; offsets host int32 [n_off][3] (oy = 0)
+ *   h_sources        host int64 [n_sources]; h_receivers host int64 [n_rcv]
+ *   h_tauR, h_tauI   host [n_sources][n_modes][nz*nx] (float or double)
+ *   h_paths          host int64 [2][n_sources*n_modes][n_rcv][path_cap]
+ *                    (component 0 = propagation, 1 = attenuation; source first)
+ *   h_path_len       host int64 [2][n_sources*n_modes][n_rcv] (0: unreachable
+ *                    or longer than path_cap)
+ *   d_scratch        device, at least chert_trace_host_scratch_bytes()
+ * Host buffers should be page-locked for the copies to overlap nothing else
+ * but run at full speed.  Errors: as the entry points it chains, CHERT_ENOMEM
+ * (scratch too small). */
+int chert_trace_host(const chert_class* h_classes, int n_classes, const int* modes, int n_modes,
+                     const chert_cache_params* params, int nx, int nz, double dx,
+                     const int32_t* h_class_of_node, const int32_t* offsets, int n_off,
+                     const int64_t* h_sources, int n_sources, int max_cycles, const int64_t* h_receivers,
+                     int n_rcv, int64_t path_cap, void* h_tauR, void* h_tauI, int64_t* h_paths,
+                     int64_t* h_path_len, void* d_scratch, size_t scratch_bytes, void* stream);
+
 /* ---- measurement helpers (no counterpart in the paper) ---------------------- */
 
 /* Measured multiply-add rate of this device in flop/s (2 per FMA), for the

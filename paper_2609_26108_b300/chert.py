@@ -84,6 +84,11 @@ def lib():
     L.chert_raypath.argtypes = [P, I, I64, P, P, I, I64, P, P, P]
     L.chert_parent_ties.argtypes = [P, P, I, I, I, I, I, I, D, P, P, I, P, I, P, P, D, P, P, P, P]
     L.chert_parent_ties.restype = ctypes.c_int
+    L.chert_trace_host_scratch_bytes.argtypes = [I, I, I, I, I, I, I, I, I64, I]
+    L.chert_trace_host_scratch_bytes.restype = SZ
+    L.chert_trace_host.argtypes = [P, I, P, I, ctypes.POINTER(chert_cache_params), I, I, D, P, P, I, P, I, I, P, I,
+                                   I64, P, P, P, P, P, SZ, P]
+    L.chert_trace_host.restype = ctypes.c_int
     L.chert_fma_rate.argtypes = [I, I, ctypes.POINTER(ctypes.c_double), P]
     L.chert_fma_rate.restype = ctypes.c_int
     L.chert_cache_eval_counter.argtypes = [I, P]
@@ -462,6 +467,39 @@ def parent_ties(cache, nx, nz, dx, d_cls, offsets, sources, tauR, tauI, rel_tol,
                                    _dev_ptr(tauI), float(rel_tol), _dev_ptr(tieR), _dev_ptr(tieI),
                                    _dev_ptr(counts), _stream_ptr(stream)))
     return tieR, tieI, counts
+
+
+def _host_ptr(t):
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("host tensor must be contiguous CPU memory")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def trace_host_scratch_bytes(n_classes, n_modes, M, nx, nz, n_off, n_sources, n_rcv, path_cap, precision):
+    return int(lib().chert_trace_host_scratch_bytes(n_classes, n_modes, M, nx, nz, n_off, n_sources, n_rcv,
+                                                    path_cap, precision))
+
+
+def trace_host(h_classes, n_classes, modes, M, nx, nz, dx, h_cls, offsets, h_sources, h_receivers, h_tauR, h_tauI,
+               h_paths, h_lens, d_scratch, scratch_step=0.001 * math.pi / 180, scan_half=30000, kernel="MEV",
+               precision="mixed", max_cycles=64, stream=None):
+    """chert_trace_host: the whole path on host tensors (inputs and outputs
+    page-locked CPU tensors, d_scratch a device uint8 tensor of
+    trace_host_scratch_bytes)."""
+    prec = PRECISION_IDS[precision] if isinstance(precision, str) else precision
+    mode_ids = [MODE_IDS[m] if isinstance(m, str) else m for m in modes]
+    off, off_p = _offsets_arr(offsets)
+    params = chert_cache_params(M, scratch_step, scan_half, KERNEL_IDS.get(kernel, kernel), prec)
+    modes_arr = (ctypes.c_int * len(mode_ids))(*mode_ids)
+    n_rcv = int(h_receivers.numel())
+    cap = int(h_paths.shape[-1])
+    _check(lib().chert_trace_host(_host_ptr(h_classes), n_classes, modes_arr, len(mode_ids), ctypes.byref(params),
+                                  nx, nz, float(dx), _host_ptr(h_cls), off_p, len(off), _host_ptr(h_sources),
+                                  int(h_sources.numel()), max_cycles, _host_ptr(h_receivers), n_rcv, cap,
+                                  _host_ptr(h_tauR), _host_ptr(h_tauI), _host_ptr(h_paths), _host_ptr(h_lens),
+                                  _dev_ptr(d_scratch), d_scratch.numel(), _stream_ptr(stream)))
 
 
 def fma_rate(precision="fp32", iters=1 << 16, stream=None):

@@ -57,12 +57,19 @@ class Tracer:
 
     @property
     def launches_per_run(self):
-        """Kernels of one run: cache build, lookup, class check, relaxation,
+        """Kernels of one run: the cache build's main pass and, for scans
+        beyond 2,048 grid points per side, its finish pass; lookup, class check,
+        the row-class check (standard stencils with lines of at most 512 nodes,
+        where the relaxation runs one node of a line per thread), relaxation,
         2 x raypaths; the hybrid scheduler adds the block-heap continuation
         (launched always, returning at once for converged fields)."""
-        hybrid = chert.relax_scheduler() == "hybrid" and self.max_cycles > 6 and \
-            int(np.max(np.abs(self.offsets[:, [0, 2]]))) <= 8
-        return 6 + int(hybrid)
+        from .inputs import stencil_2d
+        reach = int(np.max(np.abs(self.offsets[:, [0, 2]])))
+        sched = chert.relax_scheduler()
+        hybrid = sched == "hybrid" and self.max_cycles > 6 and reach <= 8
+        standard = len(self.offsets) == len(stencil_2d(reach))
+        rows = sched != "block_heap" and standard and 2 <= reach <= 5 and max(self.nx, self.nz) <= 512
+        return (2 if self.scan_half > 2048 else 1) + 3 + int(rows) + 2 + int(hybrid)
 
     # -- inputs --------------------------------------------------------------
     def set_inputs(self, d_classes, d_cls, sources):
@@ -118,6 +125,49 @@ class Tracer:
 
     def d2h_bytes(self):
         return self.tau[0].numel() * self.tau[0].element_size() * 2
+
+
+class HostTracer:
+    """The whole path as one library call on host buffers (chert_trace_host):
+    holds the device scratch and the page-locked host outputs of one problem
+    size.  ``run`` takes page-locked host inputs (packed classes uint8, class
+    map int32, sources int64) and returns (tauR, tauI, paths, lengths) host
+    tensors."""
+
+    def __init__(self, n_classes, modes, M, nx, nz, dx, offsets, n_sources, receivers, kernel="MEV",
+                 precision="mixed", scan_step=0.001 * math.pi / 180, scan_half=30000, max_cycles=64, path_cap=1024,
+                 device="cuda"):
+        import torch
+        self.n_classes, self.modes, self.M = n_classes, list(modes), M
+        self.nx, self.nz, self.dx = nx, nz, dx
+        self.offsets = np.ascontiguousarray(np.asarray(offsets, np.int32).reshape(-1, 3))
+        self.kernel, self.precision, self.scan_step, self.scan_half = kernel, precision, scan_step, scan_half
+        self.max_cycles = max_cycles
+        prec = chert.PRECISION_IDS[precision]
+        nm, n = len(self.modes), nx * nz
+        nf = n_sources * nm
+        self.h_rcv = torch.as_tensor(np.asarray(receivers, np.int64)).pin_memory()
+        fd = torch.float64 if prec == chert.FP64 else torch.float32
+        self.h_tau = (torch.empty((n_sources, nm, n), dtype=fd).pin_memory(),
+                      torch.empty((n_sources, nm, n), dtype=fd).pin_memory())
+        self.h_paths = torch.empty((2, nf, len(self.h_rcv), path_cap), dtype=torch.int64).pin_memory()
+        self.h_lens = torch.empty((2, nf, len(self.h_rcv)), dtype=torch.int64).pin_memory()
+        nb = chert.trace_host_scratch_bytes(n_classes, nm, M, nx, nz, len(self.offsets), n_sources,
+                                            len(self.h_rcv), path_cap, prec)
+        self.scratch = torch.empty(nb, dtype=torch.uint8, device=device)
+
+    def run(self, h_classes, h_cls, h_sources, stream=None):
+        chert.trace_host(h_classes, self.n_classes, self.modes, self.M, self.nx, self.nz, self.dx, h_cls,
+                         self.offsets, h_sources, self.h_rcv, self.h_tau[0], self.h_tau[1], self.h_paths,
+                         self.h_lens, self.scratch, self.scan_step, self.scan_half, self.kernel, self.precision,
+                         self.max_cycles, stream)
+        return self.h_tau[0], self.h_tau[1], self.h_paths, self.h_lens
+
+    def h2d_bytes(self, h_classes, h_cls, h_sources):
+        return sum(t.numel() * t.element_size() for t in (h_classes, h_cls, h_sources, self.h_rcv))
+
+    def d2h_bytes(self):
+        return sum(t.numel() * t.element_size() for t in (*self.h_tau, self.h_paths, self.h_lens))
 
 
 class Problem:

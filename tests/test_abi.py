@@ -120,15 +120,24 @@ def test_tracer_counts_the_hybrid_continuation(lib):
     tr = Tracer.__new__(Tracer)                     # host state only, no device buffers
     tr.offsets = np.asarray(inputs.stencil_2d(5), np.int32).reshape(-1, 3)
     tr.max_cycles = 64
+    tr.nx = tr.nz = 401
+    tr.scan_half = 30000
+    # main and finish pass of the cache build, lookup, class check, row-class
+    # check, relaxation, 2 raypaths (+ the hybrid's continuation)
     try:
         chert.set_relax_scheduler("hybrid")
-        assert tr.launches_per_run == 7
+        assert tr.launches_per_run == 9
         tr.max_cycles = 6
-        assert tr.launches_per_run == 6
+        assert tr.launches_per_run == 8
         tr.max_cycles = 64
         chert.set_relax_scheduler("sweeps")
-        assert tr.launches_per_run == 6
-        chert.set_relax_scheduler("block_heap")
+        assert tr.launches_per_run == 8
+        chert.set_relax_scheduler("block_heap")                # no sweeps: no row-class check
+        assert tr.launches_per_run == 7
+        chert.set_relax_scheduler("sweeps")
+        tr.scan_half = 2000                          # no finish pass
+        assert tr.launches_per_run == 7
+        tr.nx = 1701                                 # lines too long for the row-class check
         assert tr.launches_per_run == 6
     finally:
         chert.set_relax_scheduler("hybrid")
