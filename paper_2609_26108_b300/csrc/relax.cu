@@ -1335,7 +1335,7 @@ static int try_fast_R(fast::Args& a, const Offsets& off, int smem_max, int block
         a.wrow = a.wcol = nullptr;
     }
     a.rowk = nullptr;
-    if (!pn && ppt == 1 && rowk_area && a.nz <= kRowkMax) {        // row-class path, if every row is one class
+    if (!pn && rowk_area && a.nz <= kRowkMax) {        // row-class path, if every row is one class
         row_classes_kernel<<<a.nz, 128, 0, s>>>(a.cls, a.nx, a.nz, rowk_area);
         const int rc0 = launch_check("relaxation: row classes");
         if (rc0) return rc0;

@@ -401,8 +401,11 @@ __device__ __forceinline__ int row_class(const int* rowk, int z, int nz, int fal
     return (z >= 0 && z < nz) ? rowk[z] : fallback;
 }
 
+// One node of a line per thread (lines of at most 512 nodes): the row-class
+// sweep and verification written for that case, which the compiler
+// schedules better than the general forms below at PPT = 1.
 template <typename T, int R, int AXIS, int DIR>
-__device__ void sweep_rows(const Ctx<T>& c, T* __restrict__ tau, int pass, int since) {
+__device__ void sweep_rows1(const Ctx<T>& c, T* __restrict__ tau, int pass, int since) {
     constexpr int N = Stencil<R>::N;
     const int n_lines = AXIS == 0 ? c.nz : c.nx;
     const int len = AXIS == 0 ? c.nx : c.nz;
@@ -479,11 +482,8 @@ __device__ void sweep_rows(const Ctx<T>& c, T* __restrict__ tau, int pass, int s
     }
 }
 
-// Verification pass of the row-class path: rows, a 16-row ring of tau; the
-// weights of the row's in-neighbours are read from the class-pair table at
-// addresses that are the same for every thread (one broadcast per load).
 template <typename T, int R>
-__device__ bool verify_rows(const Ctx<T>& c, T* __restrict__ tau, int64_t src, int32_t* __restrict__ par,
+__device__ bool verify_rows1(const Ctx<T>& c, T* __restrict__ tau, int64_t src, int32_t* __restrict__ par,
                             int pass, int since) {
     constexpr int N = Stencil<R>::N;
     const int nx = c.nx, nz = c.nz, nk = c.nk;
@@ -540,6 +540,185 @@ __device__ bool verify_rows(const Ctx<T>& c, T* __restrict__ tau, int64_t src, i
                 else if (isinf(cur) || bq < 0) pj = -1;
                 else pj = (int32_t)((long long)j - ((long long)c.sz[bq] * nx + c.sx[bq]));
                 par[j] = pj;
+            }
+        }
+    }
+    return __syncthreads_or(changed);
+}
+
+// Any number of nodes of a line per thread (strided by the block size).
+template <typename T, int R, int PPT, int AXIS, int DIR>
+__device__ void sweep_rows(const Ctx<T>& c, T* __restrict__ tau, int pass, int since) {
+    constexpr int N = Stencil<R>::N;
+    const int n_lines = AXIS == 0 ? c.nz : c.nx;
+    const int len = AXIS == 0 ? c.nx : c.nz;
+    const int nx = c.nx, nk = c.nk;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    T* ring = reinterpret_cast<T*>(c.ring);
+    for (int i = tid; i < 8 * c.LS; i += bd) ring[i] = T(INFINITY);
+    __syncthreads();
+    // wo[p][oz + R]: offset in W of the class pair (row of i = j - o, row of j)
+    // for the entries with z component oz.  Column sweeps: fixed per node for
+    // the whole sweep (depth z = u); row sweeps: fixed per line, the same for
+    // every node of the line (kept in wo[0]).
+    constexpr int NW = AXIS == 1 ? PPT : 1;
+    int wo[NW][2 * R + 1];
+    auto set_wo = [&](int slot, int zj) {
+        const int kj = row_class(c.rowk, zj, c.nz, 0);
+#pragma unroll
+        for (int d = -R; d <= R; ++d) wo[slot][d + R] = (row_class(c.rowk, zj - d, c.nz, kj) * nk + kj) * N;
+    };
+    if constexpr (AXIS == 1) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) set_wo(p, min(tid + p * bd, len - 1));
+    }
+    auto gidx = [&](int line, int u) {
+        return AXIS == 0 ? (size_t)u + (size_t)nx * line : (size_t)line + (size_t)nx * u;
+    };
+    auto ring_line = [&](int line) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int u = tid + p * bd;
+            if (u < len)
+                ring[(line & 7) * c.LS + R + u] = (line >= 0 && line < n_lines) ? tau[gidx(line, u)] : T(INFINITY);
+        }
+    };
+    auto load = [&](int line, T* t) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int u = tid + p * bd;
+            t[p] = u < len ? tau[gidx(line, u)] : T(INFINITY);
+        }
+    };
+    bool reload = false;
+    T cur[PPT];
+    load(DIR > 0 ? 0 : n_lines - 1, cur);
+    for (int step = 0; step < n_lines; ++step) {
+        const int line = DIR > 0 ? step : n_lines - 1 - step;
+        const bool band_start = DIR > 0 ? (line % kTile == 0) : (line == n_lines - 1 || line % kTile == kTile - 1);
+        if (band_start) {
+            const int b = line / kTile;
+            if (!band_dirty<T, AXIS>(c, b, since)) {
+                const int last = DIR > 0 ? min(n_lines - 1, b * kTile + kTile - 1) : b * kTile;
+                step = DIR > 0 ? last : n_lines - 1 - last;
+                reload = true;
+                continue;
+            }
+            if (reload) {
+                for (int lag = 1; lag <= R; ++lag) ring_line(line - DIR * lag);
+                load(line, cur);
+                __syncthreads();
+                reload = false;
+            }
+        }
+        if constexpr (AXIS == 0) set_wo(0, line);
+        T nxt[PPT];
+        if (step + 1 < n_lines) load(DIR > 0 ? line + 1 : line - 1, nxt);
+        const int own = (line & 7) * c.LS + R;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int u = tid + p * bd;
+            if (u < len) {
+                int po[R + 1];              // ring offsets of the previous lines (32-bit shared indices)
+#pragma unroll
+                for (int lag = 1; lag <= R; ++lag) po[lag] = ((line - DIR * lag) & 7) * c.LS + R + u;
+                const int* w = wo[AXIS == 1 ? p : 0];
+                const int tx = (AXIS == 0 ? u : line) / kTile, tz = (AXIS == 0 ? line : u) / kTile;
+                T best = cur[p];
+                if (dirty(c, tx, tz, since)) {
+                    static_for<N>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        constexpr int oa = AXIS == 0 ? Table<R>::v.z[q] : Table<R>::v.x[q];
+                        constexpr int ol = AXIS == 0 ? Table<R>::v.x[q] : Table<R>::v.z[q];
+                        if constexpr (oa * DIR > 0) {
+                            constexpr int lag = oa * DIR;
+                            constexpr int oz = Table<R>::v.z[q];
+                            best = fmin_(best, ring[po[lag] - ol] + c.W[w[oz + R] + q]);
+                        }
+                    });
+                }
+                ring[own + u] = best;
+                if (best < cur[p]) {
+                    tau[gidx(line, u)] = best;
+                    c.stamp[tz * c.TX + tx] = pass;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) cur[p] = nxt[p];
+    }
+}
+
+// Verification pass of the row-class path: rows, a 16-row ring of tau; the
+// weights of the row's in-neighbours are read from the class-pair table at
+// addresses that are the same for every thread (one broadcast per load).
+template <typename T, int R, int PPT>
+__device__ bool verify_rows(const Ctx<T>& c, T* __restrict__ tau, int64_t src, int32_t* __restrict__ par,
+                            int pass, int since) {
+    constexpr int N = Stencil<R>::N;
+    const int nx = c.nx, nz = c.nz, nk = c.nk;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    T* ring = reinterpret_cast<T*>(c.ring);
+    for (int i = tid; i < 16 * c.LS; i += bd) ring[i] = T(INFINITY);
+    __syncthreads();
+    auto store_row = [&](int row) {
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int x = tid + p * bd;
+            if (x < nx)
+                ring[(row & 15) * c.LS + R + x] = (row >= 0 && row < nz) ? tau[(size_t)x + (size_t)nx * row] : T(INFINITY);
+        }
+    };
+    for (int row = 0; row < R && row < nz; ++row) store_row(row);
+    bool changed = false, reload = false;
+    for (int z = 0; z < nz; ++z) {
+        if (z % kTile == 0) {
+            const int b = z / kTile;
+            if (!band_dirty<T, 0>(c, b, since)) {
+                z = min(nz, z + kTile) - 1;
+                reload = true;
+                continue;
+            }
+            if (reload) {
+                for (int row = z - R; row < z + R; ++row) store_row(row);
+                reload = false;
+            }
+        }
+        store_row(z + R);
+        __syncthreads();
+        int wo[2 * R + 1];                  // weight-table offsets of the rows z - d
+        const int kj = c.rowk[z];
+#pragma unroll
+        for (int d = -R; d <= R; ++d) wo[d + R] = (row_class(c.rowk, z - d, nz, kj) * nk + kj) * N;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int x = tid + p * bd;
+            if (x < nx && dirty(c, x / kTile, z / kTile, since)) {
+                int po[2 * R + 1];          // ring offsets of rows z - d
+#pragma unroll
+                for (int d = -R; d <= R; ++d) po[d + R] = ((z - d) & 15) * c.LS + R + x;
+                const T cur = ring[po[R]];
+                const size_t j = (size_t)x + (size_t)nx * z;
+                T best = T(INFINITY);
+                int bq = -1;
+                static_for<N>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    constexpr int oz = Table<R>::v.z[q], ox = Table<R>::v.x[q];
+                    const T cand = ring[po[oz + R] - ox] + c.W[wo[oz + R] + q];
+                    if (cand < best) { best = cand; bq = q; }
+                });
+                if (best < cur) {
+                    tau[j] = best;
+                    changed = true;
+                    c.stamp[(z / kTile) * c.TX + x / kTile] = pass;
+                } else if (par) {
+                    int32_t pj;
+                    if ((int64_t)j == src) pj = (int32_t)src;
+                    else if (isinf(cur) || bq < 0) pj = -1;
+                    else pj = (int32_t)((long long)j - ((long long)c.sz[bq] * nx + c.sx[bq]));
+                    par[j] = pj;
+                }
             }
         }
     }
@@ -607,9 +786,9 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
     __syncthreads();
 
     // Row-class path: every row one class (checked on the row classes that
-    // row_classes_kernel wrote), one node of a line per thread.
+    // row_classes_kernel wrote).
     bool rows = false;
-    if constexpr (!PN && PPT == 1) {
+    if constexpr (!PN) {
         if (a.rowk) {
             bool ok = true;
             for (int z = threadIdx.x; z < a.nz; z += blockDim.x) {
@@ -625,14 +804,23 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
     int pass = 1;
     int last[5] = {0, 0, 0, 0, 0};
     int used = -1;
-    if constexpr (!PN && PPT == 1) {
+    if constexpr (!PN) {
         if (rows) {
             for (int cycle = 0; cycle < a.max_cycles; ++cycle) {
-                sweep_rows<T, R, 0, +1>(c, tau, pass, last[0]); last[0] = pass++;
-                sweep_rows<T, R, 1, +1>(c, tau, pass, last[1]); last[1] = pass++;
-                sweep_rows<T, R, 1, -1>(c, tau, pass, last[2]); last[2] = pass++;
-                sweep_rows<T, R, 0, -1>(c, tau, pass, last[3]); last[3] = pass++;
-                const bool changed = verify_rows<T, R>(c, tau, src, par, pass, last[4]);
+                bool changed;
+                if constexpr (PPT == 1) {
+                    sweep_rows1<T, R, 0, +1>(c, tau, pass, last[0]); last[0] = pass++;
+                    sweep_rows1<T, R, 1, +1>(c, tau, pass, last[1]); last[1] = pass++;
+                    sweep_rows1<T, R, 1, -1>(c, tau, pass, last[2]); last[2] = pass++;
+                    sweep_rows1<T, R, 0, -1>(c, tau, pass, last[3]); last[3] = pass++;
+                    changed = verify_rows1<T, R>(c, tau, src, par, pass, last[4]);
+                } else {
+                    sweep_rows<T, R, PPT, 0, +1>(c, tau, pass, last[0]); last[0] = pass++;
+                    sweep_rows<T, R, PPT, 1, +1>(c, tau, pass, last[1]); last[1] = pass++;
+                    sweep_rows<T, R, PPT, 1, -1>(c, tau, pass, last[2]); last[2] = pass++;
+                    sweep_rows<T, R, PPT, 0, -1>(c, tau, pass, last[3]); last[3] = pass++;
+                    changed = verify_rows<T, R, PPT>(c, tau, src, par, pass, last[4]);
+                }
                 last[4] = pass++;
                 if (!changed) {
                     used = cycle + 1;

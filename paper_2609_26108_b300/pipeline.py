@@ -59,8 +59,8 @@ class Tracer:
     def launches_per_run(self):
         """Kernels of one run: the cache build's main pass and, for scans
         beyond 2,048 grid points per side, its finish pass; lookup, class check,
-        the row-class check (standard stencils with lines of at most 512 nodes,
-        where the relaxation runs one node of a line per thread), relaxation,
+        the row-class check (standard stencils of radius 2 to 5 on lattices of
+        at most 2,048 rows), relaxation,
         2 x raypaths; the hybrid scheduler adds the block-heap continuation
         (launched always, returning at once for converged fields)."""
         from .inputs import stencil_2d
@@ -68,7 +68,7 @@ class Tracer:
         sched = chert.relax_scheduler()
         hybrid = sched == "hybrid" and self.max_cycles > 6 and reach <= 8
         standard = len(self.offsets) == len(stencil_2d(reach))
-        rows = sched != "block_heap" and standard and 2 <= reach <= 5 and max(self.nx, self.nz) <= 512
+        rows = sched != "block_heap" and standard and 2 <= reach <= 5 and max(self.nx, self.nz) <= 2048
         return (2 if self.scan_half > 2048 else 1) + 3 + int(rows) + 2 + int(hybrid)
 
     # -- inputs --------------------------------------------------------------

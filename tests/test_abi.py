@@ -137,7 +137,7 @@ def test_tracer_counts_the_hybrid_continuation(lib):
         chert.set_relax_scheduler("sweeps")
         tr.scan_half = 2000                          # no finish pass
         assert tr.launches_per_run == 7
-        tr.nx = 1701                                 # lines too long for the row-class check
+        tr.nx = 2049                                 # lines too long for the specialised kernel
         assert tr.launches_per_run == 6
     finally:
         chert.set_relax_scheduler("hybrid")
