@@ -541,6 +541,44 @@ def surrogate_section(n_sources, flush, log=None):
             "tauR_median_rel_error_worst_mode": worst}
 
 
+# --------------------------------------------------------------- no-cache ablation
+def section_no_cache(tracer, model, off, classes, value, source_index=31):
+    """The no-cache (MSPM-style) form of the paper's Algorithm 1 on the main
+    workload: for each field of one source (3 modes), every node's own
+    directional table is solved afresh from its medium (160,801 tables of 91
+    solves; nothing shared between nodes or fields), then looked up and
+    relaxed.  Timed with events around the whole per-field work; its fields
+    and parents must equal the cached path's bit for bit."""
+    import torch
+    from paper_2609_26108_b300 import chert
+    from paper_2609_26108_b300.pipeline import no_cache_traveltime, per_node_classes
+    d_nodes = chert.classes_to_device(per_node_classes(classes, model.class_of_node.astype(np.int32)))
+    s = int(model.sources[source_index])
+    no_cache_traveltime(d_nodes, 41, 1, model.dx, off, [0], ["qP"], M_PER_QUADRANT, SCAN_STEP, SCAN_HALF)   # load
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    got = no_cache_traveltime(d_nodes, model.nx, model.nz, model.dx, off, [s], MODES, M_PER_QUADRANT, SCAN_STEP,
+                              SCAN_HALF)
+    b.record()
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    tracer.set_inputs(tracer.d_classes, tracer.d_cls, [s] * tracer.n_sources)
+    ref = tracer.run()
+    torch.cuda.synchronize()
+    same = all(bool(torch.equal(g[0], r[0])) for g, r in zip(got, ref))
+    tracer.set_inputs(tracer.d_classes, tracer.d_cls, model.sources)
+    nf = len(MODES)
+    return {"workload": "layered_visco_tti_2d_401x401, source %d, 3 modes, per-field tables of all %d nodes"
+                        % (source_index, model.nx * model.nz),
+            "fields": nf, "s": t, "s_per_field": t / nf, "fields_per_s": nf / t,
+            "table_solves_per_field": model.nx * model.nz * (M_PER_QUADRANT + 1),
+            "cached_fields_per_s": value, "cache_speedup": value / (nf / t),
+            "identical_to_cached_path": same,
+            "note": "the paper's CPU comparison of the two methods (its MSPM against its CHERT on its layered model, "
+                    "hardware not stated): 329 s against about 5 s"}
+
+
 # --------------------------------------------------------------- 3D
 def section_3d(flush, n_sources=16):
     """3D layered visco-TTI, 201^3 nodes at dx = 10 m, 12 layers (PCG64 seed
@@ -906,6 +944,8 @@ def run_chert(args):
                    "d2h_bytes_per_step": e2e_d2h, "call": "chert_trace_host (one C-ABI call on page-locked host "
                    "buffers: inputs in, cache, traveltimes with parents, raypaths, fields and raypaths out)"},
            "gpu_launches": tr.launches_per_run * args.steps}
+    if world == 1 and args.no_cache:
+        out["no_cache_ablation"] = section_no_cache(tr, model, off, classes, value)
     if world == 1 and args.surrogate_sources > 0:
         out["surrogate"] = surrogate_section(args.surrogate_sources, flush)
     if world == 1 and args.sources_3d > 0:
@@ -967,6 +1007,8 @@ def main():
                     help="sources of the per-cell plain-vs-surrogate comparison (0: leave it out)")
     ap.add_argument("--scheduler-study", type=int, default=0,
                     help="sources of the block-heap vs sweep scheduler comparison on the layered model (0: leave it out)")
+    ap.add_argument("--no-cache", type=int, default=1,
+                    help="1 (default): add the no-cache (MSPM-style) ablation of one source x 3 modes; 0: leave it out")
     ap.add_argument("--cache-only", default=None, choices=["fp32", "mixed", "fp64"],
                     help="profiling aid: build the layered workload's cache twice in this precision and exit")
     args = ap.parse_args()

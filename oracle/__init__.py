@@ -13,6 +13,11 @@ Hamiltonian-Enhanced Ray Tracing in Viscoelastic Anisotropic Media"):
   binary-heap Dijkstra for the relaxation fixed point (Eq. 31), the
   deterministic parent rule and raypath backtracking (Eq. 33-34), plus
   Floyd-Warshall for tiny grids.  Dijkstra is plain C (``graph_oracle.c``).
+* ``nocache_oracle`` -- the no-cache (MSPM-style) traveltime of the paper's
+  Algorithm 1: every node's ray quantities evaluated from its own medium,
+  with no table shared between nodes, then the same lookup and Dijkstra.
+* ``mlp_oracle`` -- the cache surrogate's network, loss, Adam, BF16 rounding
+  and target parametrisation.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 leg may import or execute anything here.  The product path never does; it
@@ -30,4 +35,8 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
   pinned only to the perturbation-theory identity, not to printed values).
 * select_direction, dijkstra, parents, raypath -- pinned by Floyd-Warshall,
   scipy's independent Dijkstra, straight-ray closed forms and reciprocity.
+* in_candidates, parent_ties -- pinned by the Manhattan closed form and by
+  brute force over Floyd-Warshall distances.
+* node_tables, no_cache_fields -- pinned to the cached path (identical
+  tables, fields and parents where nodes share a medium).
 """

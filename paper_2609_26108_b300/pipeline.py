@@ -300,6 +300,49 @@ class GraphBatch:
         return sum(p.n_fields for p in self.problems)
 
 
+def per_node_classes(classes, class_of_node):
+    """Packed chert_class records of every node's medium (host uint8 [n*104]):
+    the input of the no-cache form, where each node carries its own medium."""
+    import ctypes
+    arr = (chert.chert_class * len(classes))(*classes)
+    raw = np.frombuffer(bytes(arr), dtype=np.uint8).reshape(len(classes), ctypes.sizeof(chert.chert_class))
+    return np.ascontiguousarray(raw[np.asarray(class_of_node).reshape(-1)]).reshape(-1)
+
+
+def no_cache_traveltime(d_node_classes, nx, nz, dx, offsets, sources, modes, M, scan_step=0.001 * math.pi / 180,
+                        scan_half=30000, kernel="MEV", precision="mixed", max_cycles=64, stream=None):
+    """The no-cache (MSPM-style) form of the paper's Algorithm 1 with this
+    library's kernels: for every (source, mode) field, every node's own
+    directional table is solved afresh from its medium (chert_build_cache with
+    one class per node; nothing shared between nodes or fields), then looked
+    up and relaxed (chert_traveltime, class map = node index).  Where nodes
+    share a medium the tables equal the class cache's entries, so the fields
+    and parents equal those of the cached path bit for bit; only the cost
+    differs.  d_node_classes: device uint8 [n*104] (per_node_classes).
+    Returns (tauR, tauI, parR, parI) tensors [n_sources, n_modes, nz*nx]."""
+    import torch
+    n = nx * nz
+    dev = d_node_classes.device
+    own = torch.arange(n, dtype=torch.int32, device=dev)
+    prec = chert.PRECISION_IDS[precision]
+    fd = torch.float64 if prec == chert.FP64 else torch.float32
+    src = np.asarray(sources, np.int64).reshape(-1)
+    out = (torch.empty((len(src), len(modes), n), dtype=fd, device=dev),
+           torch.empty((len(src), len(modes), n), dtype=fd, device=dev),
+           torch.empty((len(src), len(modes), n), dtype=torch.int32, device=dev),
+           torch.empty((len(src), len(modes), n), dtype=torch.int32, device=dev))
+    ws = torch.empty(chert.workspace_bytes(1, n, len(np.asarray(offsets).reshape(-1, 3)), prec, 1, nx, nz),
+                     dtype=torch.uint8, device=dev)
+    for si, s in enumerate(src):
+        for mi, mode in enumerate(modes):
+            tables = chert.build_cache(d_node_classes, n, [mode], M, scan_step, scan_half, kernel, precision, stream)
+            f = chert.traveltime(tables, nx, nz, dx, own, offsets, [int(s)], max_cycles, True, stream, workspace=ws)
+            for k in range(4):
+                out[k][si, mi].copy_(f[k][0, 0])
+            del tables, f
+    return out
+
+
 def autotune_points_per_thread(tracer, candidates=(1, 2, 4), repeats=3):
     """Time the relaxation of ``tracer``'s problem (its full run) with each
     launch shape of the specialised 2D kernel and keep the fastest for the

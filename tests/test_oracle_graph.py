@@ -216,3 +216,31 @@ def test_parent_ties_against_brute_force():
                 want[j] = len(c) >= 2 and c[1] - c[0] <= tol * c[0]
             got = go.parent_ties((nx, 1, nz), 10.0, cls, off, sel, comp, tau, src, tol)
             assert np.array_equal(got, want), (trial, tol)
+
+
+def test_no_cache_fields_equal_the_cached_path():
+    """Algorithm 1's per-node evaluation against Algorithm 2's class cache on
+    a small two-layer lattice: each node's own table equals its class's table
+    entry for entry, so the fields and parents are identical (the paper's
+    qP difference below 1e-13 ms between the two methods)."""
+    import math
+    from oracle import cache_oracle as co
+    from oracle import nocache_oracle as nc
+    layers = inputs.seeded_tti_layers(2, seed=4)
+    mods = np.array([co.moduli_from_thomsen(L.vp0, L.vs0, L.eps, L.delta, L.gamma, L.qp, L.qs) for L in layers])
+    tilts = np.array([L.tilt for L in layers])
+    nx, nz = 5, 4
+    cls = inputs.layered_class_map_2d(nx, nz, 2).astype(np.int32)
+    off = inputs.stencil_2d(2)
+    h, K, M = 0.05 * math.pi / 180, 600, 6
+    for mode in ("qP", "qSV"):
+        tables = nc.node_tables(mods, tilts, cls, mode, M, "MEV", h, K)
+        cache = co.build_cache(mods, tilts, [mode], M, "MEV", h, K)
+        for key in ("V", "A", "rx", "rz", "flag"):
+            assert np.array_equal(tables[key][0], cache[key][0][cls], equal_nan=True)
+        _, Vs, As = go.lookup_tables(cache, 0, off)
+        got = nc.no_cache_fields(mods, tilts, cls, (nx, 1, nz), 10.0, off, mode, M, 3, "MEV", h, K)
+        tR, pR = go.dijkstra((nx, 1, nz), 10.0, cls, off, Vs, 0, 3)
+        tI, pI = go.dijkstra((nx, 1, nz), 10.0, cls, off, As, 1, 3)
+        for a, b in zip(got, (tR, pR, tI, pI)):
+            assert np.array_equal(a, b)
