@@ -97,6 +97,11 @@ struct FieldArgs {
     int32_t *parR, *parI;
     const void *Vsel, *Asel;     // [n_modes][n_classes][n_off]
     int* status;                 // [field*2 + component]: cycles used, -1 = cap hit
+    // 3D: CTAs per field component (parts) and their barrier words, kSyncStride
+    // unsigned per field component (barrier count, two change flags), zeroed
+    // before the launch; parts > 1 only under a cooperative launch
+    int parts;
+    unsigned* sync;
 };
 
 template <typename T>
@@ -655,6 +660,56 @@ struct Stage3 {
     int H, SU, SV;      // halo, staged tile extents
 };
 
+// Several CTAs per field component ("parts", one cooperative launch, so all
+// of them are resident): part p takes the tiles t = p, p + parts, ... of every
+// plane, and the parts of a field meet at a barrier after each plane (a plane
+// reads the planes behind it, tiles of the neighbours included).  Traveltimes
+// other parts write are read through L2 (ld.cg), never from a stale L1 line.
+constexpr int kSyncStride = 16;                 // unsigned words per field component (64 bytes)
+constexpr long long kBarrierSpins = 1LL << 24;  // about a second of polling, then give up
+
+struct Part3 {
+    int part, parts;
+    unsigned* word;         // this field component's barrier words, or null for one part
+    unsigned gen;           // barriers passed so far
+    bool failed;            // a barrier wait ran out (status -1, stop)
+};
+
+// Barrier of the parts of one field component; returns false (and marks the
+// part failed) if the others did not all arrive within kBarrierSpins polls.
+__device__ __forceinline__ bool part_barrier(Part3& pt) {
+    if (pt.parts == 1) {
+        __syncthreads();
+        return true;
+    }
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        __threadfence();
+        atomicAdd(pt.word, 1u);
+        const unsigned target = (pt.gen + 1) * (unsigned)pt.parts;
+        long long spins = 0;
+        while (*(volatile unsigned*)pt.word < target) {
+            if (++spins > kBarrierSpins) { s_ok = 0; break; }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    ++pt.gen;
+    if (!s_ok) pt.failed = true;
+    return s_ok != 0;
+}
+
+template <typename TA>
+__device__ __forceinline__ TA ld_tau(const TA* p) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ xf::ff ld_tau<xf::ff>(const xf::ff* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return xf::ff(v.x, v.y);
+}
+
 // In-plane coordinates (u, v) and plane p of a sweep along `axis` (0: x, 1: y,
 // 2: z planes) -> node index.
 __device__ __forceinline__ long long node3(int axis, int u, int v, int p, int nx, int ny) {
@@ -674,7 +729,7 @@ __device__ __forceinline__ void stage_planes(T* st, int* sk, const T* tau, const
         const int u = tu0 - g.H + r % g.SU, v = tv0 - g.H + r / g.SU;
         if (pl >= 0 && pl < np && u >= 0 && u < nu && v >= 0 && v < nv) {
             const long long j = node3(axis, u, v, pl, nx, ny);
-            st[e] = tau[j];
+            st[e] = ld_tau(tau + j);
             sk[e] = clamp_class(cls[j], nk);
         } else {
             st[e] = T(INFINITY);
@@ -689,16 +744,18 @@ template <typename TW, typename TA, int WMODE>
 __device__ bool sweep3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const Offsets& off, const short* qo,
                         const short* qu, const short* qv, const short* ql, int cnt, int axis, int dir, TA* tau,
                         const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk, int comp, TA* st, int* sk,
-                        const Stage3& g) {
+                        const Stage3& g, Part3& part) {
     const int nu = axis == 0 ? ny : nx;
     const int nv = axis == 2 ? ny : nz;
     const int np = axis == 2 ? nz : axis == 1 ? ny : nx;
     const int per = g.SU * g.SV;
+    const int ntu = (nu + kTU - 1) / kTU;
     bool changed = false;
-    for (int step = 0; step < np; ++step) {
+    for (int step = 0; step < np && !part.failed; ++step) {
         const int p = dir > 0 ? step : np - 1 - step;
         for (int tv0 = 0; tv0 < nv; tv0 += kTV) {
             for (int tu0 = 0; tu0 < nu; tu0 += kTU) {
+                if (((tv0 / kTV) * ntu + tu0 / kTU) % part.parts != part.part) continue;
                 // planes p - dir*1 .. p - dir*H at stage slots 0 .. H-1
                 stage_planes(st, sk, tau, cls, nk, axis, nu, nv, np, p - dir, -dir, g.H, tu0, tv0, g, nx, ny);
                 __syncthreads();
@@ -706,7 +763,7 @@ __device__ bool sweep3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const O
                 if (threadIdx.x < kTU * kTV && u < nu && v < nv) {
                     const long long j = node3(axis, u, v, p, nx, ny);
                     const int kj = clamp_class(cls[j], nk);
-                    const TA cur = tau[j];
+                    const TA cur = ld_tau(tau + j);
                     TA best = cur;
                     const int su = u - tu0 + g.H, sv = v - tv0 + g.H;
                     for (int q = 0; q < cnt; ++q) {
@@ -723,6 +780,7 @@ __device__ bool sweep3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const O
                 __syncthreads();
             }
         }
+        part_barrier(part);                     // the plane is complete in every part
     }
     return __syncthreads_or(changed);
 }
@@ -730,12 +788,14 @@ __device__ bool sweep3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const O
 template <typename TW, typename TA, int WMODE>
 __device__ bool verify3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const Offsets& off, TA* tau,
                          const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk, int comp, int64_t src,
-                         int32_t* par, TA* st, int* sk, const Stage3& g) {
+                         int32_t* par, TA* st, int* sk, const Stage3& g, Part3& part) {
     const int per = g.SU * g.SV;
+    const int ntx = (nx + kTU - 1) / kTU;
     bool changed = false;
-    for (int z = 0; z < nz; ++z) {
+    for (int z = 0; z < nz && !part.failed; ++z) {
         for (int ty0 = 0; ty0 < ny; ty0 += kTV) {
             for (int tx0 = 0; tx0 < nx; tx0 += kTU) {
+                if (((ty0 / kTV) * ntx + tx0 / kTU) % part.parts != part.part) continue;
                 // planes z-H .. z+H at stage slots 0 .. 2H
                 stage_planes(st, sk, tau, cls, nk, 2, nx, ny, nz, z - g.H, 1, 2 * g.H + 1, tx0, ty0, g, nx, ny);
                 __syncthreads();
@@ -743,7 +803,7 @@ __device__ bool verify3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const 
                 if (threadIdx.x < kTU * kTV && x < nx && y < ny) {
                     const long long j = node3(2, x, y, z, nx, ny);
                     const int kj = clamp_class(cls[j], nk);
-                    const TA cur = tau[j];
+                    const TA cur = ld_tau(tau + j);
                     TA best = TA(INFINITY);
                     long long bi = -1;
                     const int sx = x - tx0 + g.H, sy = y - ty0 + g.H;
@@ -767,6 +827,7 @@ __device__ bool verify3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const 
                 __syncthreads();
             }
         }
+        part_barrier(part);
     }
     return __syncthreads_or(changed);
 }
@@ -784,8 +845,11 @@ template <typename T, typename TA, int WMODE>
 __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, int H) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = a.n_classes;
-    const int field = blockIdx.x >> 1;
-    const int comp = blockIdx.x & 1;
+    const int fc = blockIdx.x / a.parts;                  // field * 2 + component
+    const int field = fc >> 1;
+    const int comp = fc & 1;
+    Part3 part{(int)(blockIdx.x % a.parts), a.parts, a.parts > 1 ? a.sync + (size_t)fc * kSyncStride : nullptr,
+               0u, false};
     const int mode = field % a.n_modes;
     const int s = field / a.n_modes;
     const size_t n = (size_t)a.nx * a.ny * a.nz;
@@ -845,29 +909,43 @@ __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, 
     int32_t* par = comp == 0 ? a.parR : a.parI;
     if (par) par += static_cast<size_t>(field) * n;
     const int64_t src = a.src[s];
-    for (size_t j = threadIdx.x; j < n; j += blockDim.x) tau[j] = (j == (size_t)src) ? TA(0.0f) : TA(INFINITY);
-    __syncthreads();
+    const size_t stride = (size_t)blockDim.x * part.parts;
+    for (size_t j = threadIdx.x + (size_t)part.part * blockDim.x; j < n; j += stride)
+        tau[j] = (j == (size_t)src) ? TA(0.0f) : TA(INFINITY);
+    part_barrier(part);
 
     int used = -1;
-    for (int cycle = 0; cycle < a.max_cycles; ++cycle) {
+    for (int cycle = 0; cycle < a.max_cycles && !part.failed; ++cycle) {
         for (int l = 0; l < 6; ++l)
             sweep3d<T, TA, WMODE>(sm, sel, off, lists + (4 * l) * off.n, lists + (4 * l + 1) * off.n,
                               lists + (4 * l + 2) * off.n, lists + (4 * l + 3) * off.n, sm.counts[l], ax[l], dr[l],
-                              tau, a.cls, a.nx, a.ny, a.nz, nk, comp, st, sk, g);
-        if (!verify3d<T, TA, WMODE>(sm, sel, off, tau, a.cls, a.nx, a.ny, a.nz, nk, comp, src, par, st, sk, g)) {
+                              tau, a.cls, a.nx, a.ny, a.nz, nk, comp, st, sk, g, part);
+        bool changed = verify3d<T, TA, WMODE>(sm, sel, off, tau, a.cls, a.nx, a.ny, a.nz, nk, comp, src, par, st,
+                                              sk, g, part);
+        if (part.parts > 1) {
+            // OR of the parts' verdicts in flag word 1 + (cycle & 1); the other
+            // flag word, last read a cycle ago, is cleared for the next cycle
+            unsigned* flag = part.word + 1 + (cycle & 1);
+            if (threadIdx.x == 0 && changed) atomicOr(flag, 1u);
+            part_barrier(part);
+            changed = *(volatile unsigned*)flag != 0;
+            if (threadIdx.x == 0 && part.part == 0) part.word[1 + ((cycle + 1) & 1)] = 0u;
+        }
+        if (part.failed) break;
+        if (!changed) {
             used = cycle + 1;
             break;
         }
     }
     if constexpr (std::is_same<TA, xf::ff>::value) {
-        __syncthreads();
+        part_barrier(part);
         double* out = reinterpret_cast<double*>(tau);          // same 8 bytes per node
-        for (size_t j = threadIdx.x; j < n; j += blockDim.x) {
-            const xf::ff v = tau[j];
+        for (size_t j = threadIdx.x + (size_t)part.part * blockDim.x; j < n; j += stride) {
+            const xf::ff v = ld_tau(tau + j);
             out[j] = double(v.hi) + double(v.lo);
         }
     }
-    if (threadIdx.x == 0) a.status[blockIdx.x] = used;
+    if (threadIdx.x == 0 && part.part == 0) a.status[fc] = part.failed ? -1 : used;
 }
 
 // ------------------------------------------------------------ parent ties
@@ -961,7 +1039,7 @@ __global__ void raypath_kernel(const int32_t* __restrict__ par, int n_fields, in
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct WsLayout {
-    size_t sel, idx, src, status, rowk, total;
+    size_t sel, idx, src, status, rowk, sync, total;
 };
 
 constexpr int kRowkMax = 2048;       // rows of a 2D lattice the row-class path handles
@@ -975,7 +1053,8 @@ WsLayout ws_layout(int n_modes, int n_classes, int n_off, int precision, int n_s
     w.src = w.idx + align256(m * 4);
     w.status = w.src + align256(static_cast<size_t>(n_sources) * 8);
     w.rowk = w.status + align256((static_cast<size_t>(n_sources) * n_modes * 2 + 1) * 4);
-    w.total = w.rowk + align256(static_cast<size_t>(kRowkMax) * 4);
+    w.sync = w.rowk + align256(static_cast<size_t>(kRowkMax) * 4);
+    w.total = w.sync + align256(static_cast<size_t>(n_sources) * n_modes * 2 * kSyncStride * 4);
     return w;
 }
 
@@ -1027,12 +1106,41 @@ extern "C" int chert_edge_table(const chert_cache_arrays* cache, int n_modes, in
 }
 
 
+// 3D launch: one CTA per field component, or, when the field components
+// leave SMs idle, `parts` CTAs each (at most 8, every CTA of the grid
+// resident: a cooperative launch), sharing each plane's tiles.  Under stream
+// capture, one CTA per field component.
 template <typename T, int WMODE, typename TA = T>
-static int launch_relax3d(const FieldArgs& a, const Offsets& off, int H, size_t smem, int blocks, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(relax3d_kernel<T, TA, WMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+static int launch_relax3d(FieldArgs a, const Offsets& off, int H, size_t smem, int blocks, cudaStream_t s) {
+    auto kern = relax3d_kernel<T, TA, WMODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
-    relax3d_kernel<T, TA, WMODE><<<blocks, 512, smem, s>>>(a, off, H);
+    int parts = 1;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: capture status");
+    int dev = 0, n_sm = 0, coop = 0, per_sm = 0;
+    if (cap == cudaStreamCaptureStatusNone && a.sync && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem) == cudaSuccess && per_sm > 0) {
+        const long long slots = (long long)per_sm * n_sm;
+        const int tiles = std::min({((a.nx + kTU - 1) / kTU) * ((a.ny + kTV - 1) / kTV),
+                                    ((a.nx + kTU - 1) / kTU) * ((a.nz + kTV - 1) / kTV),
+                                    ((a.ny + kTU - 1) / kTU) * ((a.nz + kTV - 1) / kTV)});
+        parts = (int)std::max(1LL, std::min<long long>({8LL, slots / blocks, (long long)tiles}));
+    }
+    cudaGetLastError();
+    a.parts = parts;
+    if (parts == 1) {
+        kern<<<blocks, 512, smem, s>>>(a, off, H);
+        return launch_check("chert_traveltime: relax3d");
+    }
+    e = cudaMemsetAsync(a.sync, 0, sizeof(unsigned) * (size_t)blocks * kSyncStride, s);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: relax3d barrier words");
+    void* args[] = {&a, const_cast<Offsets*>(&off), &H};
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks * parts), dim3(512), args, smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: relax3d (cooperative)");
     return launch_check("chert_traveltime: relax3d");
 }
 
@@ -1451,6 +1559,8 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     a.src = d_sources ? d_sources : reinterpret_cast<const int64_t*>(w + ws.src);
     a.tauR = d_tauR; a.tauI = d_tauI; a.parR = d_parR; a.parI = d_parI;
     a.Vsel = Vsel; a.Asel = Asel; a.status = reinterpret_cast<int*>(w + ws.status);
+    a.parts = 1;
+    a.sync = reinterpret_cast<unsigned*>(w + ws.sync);
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -219,3 +219,55 @@ def test_relax3d_float_weights_wide_accumulation(torch_dev, n_classes):
             assert gt[s] == 0.0 and gp[s] == s
             assert np.all(gp[~fin] == -1)
             check_parents_fp32(gp, k[si, 0].cpu().numpy(), rt, rp, sel, comp, s, shape, 10.0, cls, off)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_acc64"])
+def test_relax3d_split_across_ctas_equals_one_cta(torch_dev, precision):
+    """A lattice of several tiles per plane with few field components: the
+    eager launch shares each plane's tiles among several CTAs per field
+    component (cooperative launch), the same call captured in a CUDA graph
+    runs one CTA per field component; fields and parents must be identical,
+    bit for bit (the fixed point and its parents do not depend on the order
+    the tiles are relaxed in)."""
+    torch = torch_dev
+    shape = (70, 41, 33)
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    cls = np.minimum((np.arange(n) // (nx * ny)) * 4 // nz, 3).astype(np.int32)
+    cnp, n_az, n_pol = synthetic_cache3d(4, seed=9)
+    nm, nk, _ = cnp["V"].shape
+    cache_prec = chert.FP64 if precision == "fp64" else chert.FP32
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    cache = chert.Cache(cache_to_torch(cnp, dt, "cuda"), list(range(nm)), nk, 0, cache_prec, n_az, n_pol)
+    off = inputs.stencil_3d(2)
+    d_cls = torch.as_tensor(cls, device="cuda")
+    src = torch.as_tensor(np.array([3, n // 2 + 17], np.int64), device="cuda")
+    prec = chert.PRECISION_IDS[precision]
+    ws = torch.empty(chert.workspace_bytes(1, nk, len(off), prec, 2), dtype=torch.uint8, device="cuda")
+    fd = torch.float64
+    outs = []
+    for captured in (False, True):
+        out = (torch.empty((2, 1, n), dtype=fd, device="cuda"), torch.empty((2, 1, n), dtype=fd, device="cuda"),
+               torch.empty((2, 1, n), dtype=torch.int32, device="cuda"),
+               torch.empty((2, 1, n), dtype=torch.int32, device="cuda"))
+        status = torch.zeros(2, dtype=torch.int32, device="cuda")
+        run = lambda: chert.lib().chert_traveltime_enqueue(
+            __import__("ctypes").byref(cache.struct()), 1, nk, cache.n_dir, nx, ny, nz, 10.0,
+            chert._dev_ptr(d_cls), *chert._offsets_arr(off)[1:], len(off), chert._dev_ptr(src), 2, prec, 64,
+            chert._dev_ptr(out[0]), chert._dev_ptr(out[1]), chert._dev_ptr(out[2]), chert._dev_ptr(out[3]),
+            chert._dev_ptr(ws), ws.numel(), chert._dev_ptr(status), chert._stream_ptr(None))
+        if captured:
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(g, stream=s):
+                    assert run() == 0
+            g.replay()
+        else:
+            assert run() == 0
+        torch.cuda.synchronize()
+        assert status.cpu().tolist() == [-1, 0]
+        outs.append(out)
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
