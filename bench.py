@@ -703,9 +703,11 @@ def section_angular(n_sources=8, steps_deg=(0.5, 1.0, 2.0, 5.0, 10.0)):
 
 # --------------------------------------------------------------- scheduler study
 def section_scheduler(n_sources=16, reps=3, percell_sources=2):
-    """Block-heap marching (Eq. 32) and the hybrid scheduler (at most 6
+    """Block-heap marching (Eq. 32), the hybrid scheduler (at most 6
     sweep cycles, then block-heap marching from the source for unconverged
-    fields) against the sweep scheduler.  Layered
+    fields) and frontier label correcting (atomicMin pushes; layered model
+    only, its class-pair table must fit in shared memory) against the sweep
+    scheduler.  Layered
     401x401 model: n_sources surface sources x 3 modes, MIXED cache, FP32
     relaxation with parents, per scheduler the best of `reps` timed
     relaxations (after one untimed).  Per-cell folded and faulted 1701x351
@@ -723,7 +725,7 @@ def section_scheduler(n_sources=16, reps=3, percell_sources=2):
                               "MEV", "mixed")
     res, outs = {}, {}
     try:
-        for name in ("sweeps", "block_heap", "hybrid"):
+        for name in ("sweeps", "block_heap", "hybrid", "frontier"):
             chert.set_relax_scheduler(name)
             run = lambda: chert.traveltime(cache, model.nx, model.nz, model.dx, d_cls, off, model.sources,
                                            max_cycles=128)
@@ -740,9 +742,10 @@ def section_scheduler(n_sources=16, reps=3, percell_sources=2):
             res[name + "_ms"] = best
     finally:
         chert.set_relax_scheduler("hybrid")
-    res["identical"] = all(bool(torch.equal(x, y)) for o in ("block_heap", "hybrid")
+    res["identical"] = all(bool(torch.equal(x, y)) for o in ("block_heap", "hybrid", "frontier")
                            for x, y in zip(outs["sweeps"], outs[o]))
     res["block_heap_over_sweeps"] = res["block_heap_ms"] / res["sweeps_ms"]
+    res["frontier_over_sweeps"] = res["frontier_ms"] / res["sweeps_ms"]
     res["workload"] = "layered_visco_tti_2d_401x401_8layers_%dsrc_3modes_1deg_R5, fp32 relaxation" % n_sources
     if percell_sources <= 0:
         return res

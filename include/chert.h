@@ -253,13 +253,21 @@ int chert_set_relax_points_per_thread(int ppt);
  *     of a changed node re-keyed;
  *   2 (default) hybrid: at most 6 sweep cycles, then block-heap marching, from the
  *     source, for the fields that have not converged (one more launch,
- *     whose CTAs of converged fields return at once).
+ *     whose CTAs of converged fields return at once);
+ *   3 frontier label correcting: one CTA per field component; the nodes
+ *     whose traveltime fell in a round push tau_i + w_ij to their
+ *     out-neighbours with an unsigned atomicMin on the traveltimes' bit
+ *     patterns (non-negative values order like their bits) and mark the
+ *     ones they lowered for the next round; a pull pass then writes the
+ *     parents.  Needs the class-pair table and two frontier bitmaps (one bit
+ *     per node) in shared memory, else CHERT_EINVAL; max_cycles x max(nx, nz)
+ *     rounds at most.
  * All return the same fixed point of Eq. 31 and the same parents; they
  * differ in the work done.  Under scheduler 1, a 2D chert_traveltime whose
  * stencil reaches more than 8 nodes returns CHERT_EINVAL; under 2 it sweeps
  * only, as it does when max_cycles <= 6.  3D lattices always sweep.
  * scheduler < 0 queries without changing.  Returns the previous (or current)
- * setting, or CHERT_EINVAL for scheduler > 2. */
+ * setting, or CHERT_EINVAL for scheduler > 3. */
 int chert_set_relax_scheduler(int scheduler);
 
 /* The same relaxation as chert_traveltime, enqueued on `stream` without any

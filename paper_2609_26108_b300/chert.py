@@ -398,15 +398,17 @@ def traveltime_static(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64,
     return out
 
 
-SCHEDULERS = {"sweeps": 0, "block_heap": 1, "hybrid": 2}
+SCHEDULERS = {"sweeps": 0, "block_heap": 1, "hybrid": 2, "frontier": 3}
 
 
 def set_relax_scheduler(name):
     """Scheduler of every later 2D relaxation in this process: "sweeps"
-    (ordered sweep cycles), "block_heap" (block-heap marching of Eq. 32) or
+    (ordered sweep cycles), "block_heap" (block-heap marching of Eq. 32),
     "hybrid" (the default: at most 6 sweep cycles, then block-heap marching,
-    from the source, for the fields that have not converged).  All return the
-    same fields and parents.  Returns the previous name."""
+    from the source, for the fields that have not converged) or "frontier"
+    (label correcting: pushes from the nodes that changed, atomicMin on the
+    traveltimes' bit patterns).  All return the same fields and parents.
+    Returns the previous name."""
     if name not in SCHEDULERS:
         raise ValueError("scheduler %r: one of %s" % (name, sorted(SCHEDULERS)))
     prev = lib().chert_set_relax_scheduler(SCHEDULERS[name])

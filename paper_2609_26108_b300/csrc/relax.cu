@@ -28,6 +28,7 @@
 #include "common.cuh"
 #include "ff.cuh"
 #include "relax_fast.cuh"
+#include "relax_frontier.cuh"
 
 namespace chert {
 namespace {
@@ -289,6 +290,98 @@ __global__ void __launch_bounds__(512) relax_kernel(FieldArgs a, Offsets off) {
         }
     }
     if (threadIdx.x == 0) a.status[blockIdx.x] = used;
+}
+
+// ------------------------------------------------------------ frontier label correcting
+// (scheduler 3; see relax_frontier.cuh).  Shared memory: the class-pair weight
+// table [n_off][nk][nk], then the two frontier bitmaps.
+template <typename T>
+__global__ void __launch_bounds__(1024) relax_frontier_kernel(frontier::Args a, Offsets off) {
+    using B = frontier::Bits<T>;
+    using U = typename B::U;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nk = a.n_classes;
+    const int nx = a.nx, nz = a.nz;
+    const int n = nx * nz;
+    const int fc = blockIdx.x, field = fc >> 1, comp = fc & 1;
+    const int mode = field % a.n_modes, s = field / a.n_modes;
+    const int nwords = (n + 31) >> 5;
+    T* W = reinterpret_cast<T*>(smem_raw);
+    unsigned* bm0 = reinterpret_cast<unsigned*>(smem_raw + (((size_t)off.n * nk * nk * sizeof(T) + 15) & ~size_t(15)));
+    unsigned* bm1 = bm0 + nwords;
+    const T* sel = static_cast<const T*>(comp == 0 ? a.Vsel : a.Asel) + (size_t)mode * nk * off.n;
+    for (int t = threadIdx.x; t < off.n * nk * nk; t += blockDim.x) {
+        const int kj = t % nk, ki = (t / nk) % nk, o = t / (nk * nk);
+        const double ox = off.x[o], oz = off.z[o];
+        const T L = T(a.dx * sqrt(ox * ox + oz * oz));
+        W[t] = edge_w<T>(comp, L, sel[ki * off.n + o], sel[kj * off.n + o]);
+    }
+    U* tau = reinterpret_cast<U*>(static_cast<T*>(comp == 0 ? a.tauR : a.tauI) + (size_t)field * n);
+    int32_t* par = comp == 0 ? a.parR : a.parI;
+    if (par) par += (size_t)field * n;
+    const int64_t src = a.src[s];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) tau[j] = B::enc(j == src ? T(0) : T(INFINITY));
+    for (int w = threadIdx.x; w < nwords; w += blockDim.x) bm0[w] = (w == (int)(src >> 5)) ? (1u << (src & 31)) : 0u;
+    __syncthreads();
+    unsigned *cur = bm0, *nxt = bm1;
+    int used = -1;
+    for (int round = 0; round < a.max_rounds; ++round) {
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) nxt[w] = 0u;
+        __syncthreads();
+        // every node of the frontier pushes to all its out-neighbours: a warp
+        // takes one bitmap word at a time, and for each node in it the lanes
+        // share the stencil's offsets
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        for (int w = warp; w < nwords; w += nwarps) {
+            unsigned bits = cur[w];
+            while (bits) {
+                const int i = (w << 5) + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const T ti = B::dec(__ldcg(tau + i));
+                const int xi = i % nx, zi = i / nx;
+                const int ki = clamp_class(__ldg(a.cls + i), nk);
+                for (int o = lane; o < off.n; o += 32) {
+                    const int xj = xi + off.x[o], zj = zi + off.z[o];
+                    if (xj < 0 || xj >= nx || zj < 0 || zj >= nz) continue;
+                    const int j = xj + nx * zj;
+                    const int kj = clamp_class(__ldg(a.cls + j), nk);
+                    const U cand = B::enc(ti + W[(o * nk + ki) * nk + kj]);
+                    if (cand < atomicMin(tau + j, cand)) atomicOr(nxt + (j >> 5), 1u << (j & 31));
+                }
+            }
+        }
+        bool any = false;
+        __syncthreads();
+        for (int w = threadIdx.x; w < nwords; w += blockDim.x) any = any || nxt[w] != 0u;
+        if (!__syncthreads_or(any)) {
+            used = round + 1;
+            break;
+        }
+        unsigned* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    // parents, and a check that no in-neighbour improves any node
+    bool bad = false;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int xj = j % nx, zj = j / nx;
+        const int kj = clamp_class(__ldg(a.cls + j), nk);
+        const T tj = B::dec(__ldcg(tau + j));
+        T best = T(INFINITY);
+        int bi = -1;
+        for (int o = 0; o < off.n; ++o) {
+            const int xi = xj - off.x[o], zi = zj - off.z[o];
+            if (xi < 0 || xi >= nx || zi < 0 || zi >= nz) continue;
+            const int i = xi + nx * zi;
+            const int ki = clamp_class(__ldg(a.cls + i), nk);
+            const T c = B::dec(__ldcg(tau + i)) + W[(o * nk + ki) * nk + kj];
+            if (c < best || (c == best && i < bi)) { best = c; bi = i; }
+        }
+        if (best < tj) bad = true;
+        if (par) par[j] = (j == src) ? (int32_t)src : (isinf(tj) ? -1 : bi);
+    }
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) a.status[fc] = bad ? -1 : used;
 }
 
 // ------------------------------------------------------------ block-heap marching
@@ -1599,6 +1692,34 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     const int sched = g_relax_sched.load();
     CHERT_REQUIRE(sched != 1 || R <= kBH, "%s: the block scheduler takes stencils of reach <= %d (got %d)", who,
                   kBH, R);
+    if (sched == 3) {                                  // frontier label correcting
+        const size_t wb = ((size_t)n_off * n_classes * n_classes * es + 15) & ~size_t(15);
+        const size_t smf = wb + 2 * 4 * (((size_t)nx * nz + 31) / 32);
+        CHERT_REQUIRE(smf <= (size_t)smem_max,
+                      "%s: the frontier scheduler needs the class-pair table and two bitmaps in shared memory "
+                      "(%zu > %d bytes)", who, smf, smem_max);
+        frontier::Args fa;
+        fa.nx = nx; fa.nz = nz; fa.n_classes = n_classes; fa.n_modes = n_modes;
+        fa.max_rounds = max_cycles * std::max(nx, nz);
+        fa.dx = dx; fa.cls = a.cls; fa.src = a.src;
+        fa.tauR = d_tauR; fa.tauI = d_tauI; fa.parR = d_parR; fa.parI = d_parI;
+        fa.Vsel = Vsel; fa.Asel = Asel; fa.status = a.status;
+        const bool dbl = precision == CHERT_FP64;
+        cudaError_t e2 = dbl ? cudaFuncSetAttribute(relax_frontier_kernel<double>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf)
+                             : cudaFuncSetAttribute(relax_frontier_kernel<float>,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "chert_traveltime: smem attribute");
+        if (dbl)
+            relax_frontier_kernel<double><<<blocks, 1024, smf, s>>>(fa, off);
+        else
+            relax_frontier_kernel<float><<<blocks, 1024, smf, s>>>(fa, off);
+        rc = launch_check("chert_traveltime: frontier");
+        if (rc) return rc;
+        *blocks_out = blocks;
+        *status_out = a.status;
+        return CHERT_OK;
+    }
     const bool hybrid = sched == 2 && R <= kBH && max_cycles > kHybridSweeps;
     const void* swept_wrow = nullptr;                  // per-node weights the sweeps computed, if any
     auto block_heap = [&](int swept) -> int {
@@ -1893,6 +2014,6 @@ extern "C" int chert_set_relax_points_per_thread(int ppt) {
 
 extern "C" int chert_set_relax_scheduler(int scheduler) {
     if (scheduler < 0) return g_relax_sched.load();
-    CHERT_REQUIRE(scheduler <= 2, "chert_set_relax_scheduler: scheduler=%d (0, 1 or 2)", scheduler);
+    CHERT_REQUIRE(scheduler <= 3, "chert_set_relax_scheduler: scheduler=%d (0, 1, 2 or 3)", scheduler);
     return g_relax_sched.exchange(scheduler);
 }

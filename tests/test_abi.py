@@ -91,12 +91,14 @@ def test_relax_scheduler_switch_host_only(lib):
     change returns the previous setting."""
     assert lib.chert_set_relax_scheduler(-1) == 2
     assert chert.relax_scheduler() == "hybrid"
-    assert lib.chert_set_relax_scheduler(3) == chert.EINVAL
+    assert lib.chert_set_relax_scheduler(4) == chert.EINVAL
     assert lib.chert_set_relax_scheduler(-1) == 2                # unchanged by the refusal
     try:
         assert chert.set_relax_scheduler("block_heap") == "hybrid"
         assert lib.chert_set_relax_scheduler(0) == 1
         assert chert.relax_scheduler() == "sweeps"
+        assert chert.set_relax_scheduler("frontier") == "sweeps"
+        assert lib.chert_set_relax_scheduler(-1) == 3
         with pytest.raises(ValueError):
             chert.set_relax_scheduler("dijkstra")
     finally:

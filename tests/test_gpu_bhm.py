@@ -131,7 +131,7 @@ def test_unreachable_nodes_keep_infinity(torch_dev):
 def test_scheduler_switch_rejects_unknown(torch_dev):
     with pytest.raises(ValueError):
         chert.set_relax_scheduler("heap")
-    assert chert.lib().chert_set_relax_scheduler(3) == chert.EINVAL
+    assert chert.lib().chert_set_relax_scheduler(4) == chert.EINVAL
     assert chert.relax_scheduler() == "hybrid"                 # the default
     assert chert.set_relax_scheduler("sweeps") == "hybrid"
     assert chert.relax_scheduler() == "sweeps"
@@ -221,3 +221,42 @@ def test_hybrid_continuation_on_per_node_weights(torch_dev):
         g = [t.cpu().numpy() for t in chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=7)]
         for a, b in zip(ref, g):
             assert np.array_equal(a, b)
+
+
+def frontier_equals_sweeps(torch, cache, nx, nz, cls, off, src, max_cycles=256):
+    out = {}
+    prev = chert.relax_scheduler()
+    try:
+        for name in ("sweeps", "frontier"):
+            chert.set_relax_scheduler(name)
+            out[name] = run_gpu(torch, cache, nx, nz, 10.0, cls, off, src, max_cycles)
+    finally:
+        chert.set_relax_scheduler(prev)
+    for a, b in zip(out["sweeps"], out["frontier"]):
+        assert np.array_equal(a, b)
+    return out["frontier"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_frontier_label_correcting_equals_sweeps(torch_dev, precision):
+    """The frontier label-correcting scheduler (atomicMin pushes on the
+    traveltimes' bit patterns) against the sweeps, bit for bit: a layered
+    lattice with ragged edges (FP64 also against the oracle), a 12-bend
+    serpentine whose paths turn many times, and degenerate shapes."""
+    nx, nz = 151, 97
+    cls = inputs.layered_class_map_2d(nx, nz, 5).astype(np.int32)
+    off = inputs.stencil_2d(5)
+    cache = as_cache(torch_dev, small_oracle_cache(), precision)
+    src = [0, 77 + nx * 40, nx * nz - 1]
+    g = frontier_equals_sweeps(torch_dev, cache, nx, nz, cls, off, src)
+    if precision == "fp64":
+        ref = oracle_fields(small_oracle_cache(), precision, (nx, 1, nz), 10.0, cls, off, src)
+        _check_fields(g, ref, src, 2, precision, (nx, 1, nz), 10.0, cls, off, small_oracle_cache())
+    nx, nz = 280, 120
+    frontier_equals_sweeps(torch_dev, as_cache(torch_dev, _synthetic_cache([150.0, 6000.0], [1e-3, 1e-5]), precision),
+                           nx, nz, _serpentine(nx, nz, 12), inputs.stencil_2d(3), [2 + nx * 1])
+    for nx, nz in ((1, 1), (1, 40), (40, 1), (33, 2)):
+        frontier_equals_sweeps(torch_dev, as_cache(torch_dev, _synthetic_cache([2000.0, 3000.0], [1e-4, 2e-4]),
+                                                   precision),
+                               nx, nz, (np.arange(nx * nz) % 2).astype(np.int32), inputs.stencil_2d(2),
+                               [0, nx * nz - 1])
