@@ -408,7 +408,7 @@ SURR_BATCH = 4096
 SURR_MAX_CYCLES = 512              # attenuation paths through the folds turn often
 
 
-def surrogate_section(n_sources, flush, log=None):
+def surrogate_section(n_sources, flush, log=None, qsv_angles_deg=(1.0,)):
     """Plain vs surrogate form on the per-cell folded and faulted model.
 
     1701 x 351 nodes (597,051 cells, each its own medium), 10 folded layers and
@@ -496,36 +496,56 @@ def surrogate_section(n_sources, flush, log=None):
         torch.cuda.synchronize()
         return r, a.elapsed_time(b) / 1e3
 
-    res = {}
-    for form, prm, buf, tau in (("plain", None, bufs[0], taus[0]), ("surrogate", params, bufs[1], taus[1])):
+    def run_form(prm, buf, tau):
         cache, t_cache = timed(lambda: surrogate.per_cell_cache(d_cells, n, MODES, M, prm, out=buf))
-        if log:
-            log("%s cache %.3f s" % (form, t_cache))
         _, t_relax = timed(lambda: chert.traveltime(cache, model.nx, model.nz, model.dx, d_cls, off, src,
                                                     max_cycles=SURR_MAX_CYCLES, out=tau, workspace=ws))
-        if log:
-            log("%s relax %.3f s" % (form, t_relax))
         nf = len(src) * len(MODES)
-        res[form] = {"cache_s": t_cache, "relax_s": t_relax,
-                     "cache_entries_per_s": n * len(MODES) * 4 * M / t_cache,
-                     "fields_per_s": nf / (t_cache + t_relax)}
-        if form == "surrogate":
-            res[form]["solves_recomputed_exactly"] = int(cache.n_fallback)
-            res[form]["solves_total"] = n * len(MODES) * (M + 1)
-    errs = {}
-    worst = 0.0
-    for comp, name in ((0, "tauR"), (1, "tauI")):
-        for mi, m in enumerate(MODES):
-            r = taus[0][comp][:, mi].double()
-            g = taus[1][comp][:, mi].double()
-            ok = torch.isfinite(r) & (r > 0)
-            rel = ((g - r).abs() / r)[ok]
-            q = torch.quantile(rel[torch.randperm(rel.numel(), device="cuda")[:1 << 24]],
-                               torch.tensor([0.5, 0.99], dtype=torch.float64, device="cuda"))
-            errs["%s_%s" % (name, m)] = {"median": float(q[0]), "p99": float(q[1]), "max": float(rel.max()),
-                                         "frac_le_1e-4": float((rel <= 1e-4).double().mean())}
-            if comp == 0:
-                worst = max(worst, float(q[0]))
+        r = {"cache_s": t_cache, "relax_s": t_relax, "cache_entries_per_s": n * len(MODES) * 4 * M / t_cache,
+             "fields_per_s": nf / (t_cache + t_relax)}
+        if prm is not None:
+            r["solves_recomputed_exactly"] = int(cache.n_fallback)
+            r["solves_total"] = n * len(MODES) * (M + 1)
+        return r
+
+    def errors():
+        errs = {}
+        for comp, name in ((0, "tauR"), (1, "tauI")):
+            for mi, m in enumerate(MODES):
+                r = taus[0][comp][:, mi].double()
+                g = taus[1][comp][:, mi].double()
+                ok = torch.isfinite(r) & (r > 0)
+                rel = ((g - r).abs() / r)[ok]
+                q = torch.quantile(rel[torch.randperm(rel.numel(), device="cuda")[:1 << 24]],
+                                   torch.tensor([0.5, 0.99], dtype=torch.float64, device="cuda"))
+                errs["%s_%s" % (name, m)] = {"median": float(q[0]), "p99": float(q[1]), "max": float(rel.max()),
+                                             "frac_le_1e-4": float((rel <= 1e-4).double().mean())}
+        return errs
+
+    res = {"plain": run_form(None, bufs[0], taus[0])}
+    if log:
+        log("plain %s" % res["plain"])
+    points = []
+    prev_angle = chert.set_surrogate_qsv_angle(math.radians(qsv_angles_deg[0]))
+    try:
+        for deg in qsv_angles_deg:
+            chert.set_surrogate_qsv_angle(math.radians(deg))
+            r = run_form(params, bufs[1], taus[1])
+            r["qsv_fallback_angle_deg"] = deg
+            r["traveltime_rel_error_vs_plain"] = errors()
+            r["p99_worst"] = max(v["p99"] for v in r["traveltime_rel_error_vs_plain"].values())
+            r["speedup_fields_per_s"] = r["fields_per_s"] / res["plain"]["fields_per_s"]
+            points.append(r)
+            if log:
+                log("surrogate at %.2f deg: %s" % (deg, r))
+    finally:
+        chert.set_surrogate_qsv_angle(prev_angle)
+    # the form reported: the first angle (in the order given) whose worst p99
+    # error over modes and components is within 1e-4, else the last one
+    meet = [p for p in points if p["p99_worst"] <= 1e-4]
+    res["surrogate"] = meet[0] if meet else points[-1]
+    errs = res["surrogate"]["traveltime_rel_error_vs_plain"]
+    worst = max(v["median"] for k, v in errs.items() if k.startswith("tauR"))
     return {"workload": "folded_faulted_visco_tti_2d_1701x351_per_cell_%dsrc_3modes_1deg_R5" % len(src),
             "cells": n, "fields": len(src) * len(MODES),
             "training": {"exact_entries": SURR_TRAIN_CLASSES * (SURR_TRAIN_M + 1) * len(MODES),
@@ -538,6 +558,10 @@ def surrogate_section(n_sources, flush, log=None):
             "speedup_fields_per_s": res["surrogate"]["fields_per_s"] / res["plain"]["fields_per_s"],
             "speedup_cache": res["plain"]["cache_s"] / res["surrogate"]["cache_s"],
             "traveltime_rel_error_vs_plain": errs,
+            "meets_1e-4_at_p99": res["surrogate"]["p99_worst"] <= 1e-4,
+            "operating_points": [{k: p[k] for k in ("qsv_fallback_angle_deg", "fields_per_s", "speedup_fields_per_s",
+                                                    "p99_worst", "solves_recomputed_exactly", "cache_s")}
+                                 for p in points],
             "tauR_median_rel_error_worst_mode": worst}
 
 
@@ -950,7 +974,8 @@ def run_chert(args):
     if world == 1 and args.no_cache:
         out["no_cache_ablation"] = section_no_cache(tr, model, off, classes, value)
     if world == 1 and args.surrogate_sources > 0:
-        out["surrogate"] = surrogate_section(args.surrogate_sources, flush)
+        out["surrogate"] = surrogate_section(args.surrogate_sources, flush,
+                                             qsv_angles_deg=[float(v) for v in args.surrogate_qsv_angles.split(",")])
     if world == 1 and args.sources_3d > 0:
         out["lattice_3d"] = section_3d(flush, args.sources_3d)
     if world == 1 and args.angular_study:
@@ -1008,6 +1033,9 @@ def main():
                     help="sources of the 201^3 3D section (0: leave it out)")
     ap.add_argument("--surrogate-sources", type=int, default=16,
                     help="sources of the per-cell plain-vs-surrogate comparison (0: leave it out)")
+    ap.add_argument("--surrogate-qsv-angles", default="1.0,0",
+                    help="qSV fallback angles (deg, comma-separated) of the surrogate form, tried in order; the "
+                         "first whose worst p99 traveltime error is within 1e-4 is reported (else the last)")
     ap.add_argument("--scheduler-study", type=int, default=0,
                     help="sources of the block-heap vs sweep scheduler comparison on the layered model (0: leave it out)")
     ap.add_argument("--no-cache", type=int, default=1,

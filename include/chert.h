@@ -302,7 +302,9 @@ int chert_traveltime_enqueue(const chert_cache_arrays* cache, int n_modes, int n
  *           out_std[3] = 1), with Vg, psi_el the elastic group velocity and ray
  *           angle of the real moduli and A0 the attenuation Im(1/c) of the
  *           homogeneous plane wave (complex phase velocity c of the complex
- *           Christoffel block along theta) projected on the elastic ray.
+ *           Christoffel block along theta) projected on the elastic ray.  For
+ *           qSH, whose homogeneous plane wave is the exact solution, the cache
+ *           takes A0 itself and ignores output 1.
  * Parameter vector (float, chert_mlp_param_count() values): W0 [256 x 7], b0,
  * W1..W3 [256 x 256], b1..b3, W4 [5 x 256], b4, out_mean [5], out_std [5]
  * (W as [out][in]). */
@@ -350,9 +352,17 @@ int chert_surrogate_dataset(const chert_class* d_classes, int n_classes, int M, 
  * flag = 0 valid, 1 no acceptable root (network), 2 needs the exact solver:
  * the medium lies outside the training range, the network is unsure whether
  * a decaying root exists (0.1 < p < 0.9), or, for qSV, the predicted
- * imaginary angle exceeds 1 deg (cusp / triplication region).  The caller
- * recomputes those solves with chert_build_cache_items. */
+ * imaginary angle exceeds the fallback angle (chert_set_surrogate_qsv_angle,
+ * 1 deg by default: the cusp / triplication region).  The caller recomputes
+ * those solves with chert_build_cache_items. */
 size_t chert_surrogate_cache_workspace_bytes(int n_classes, int M);
+
+/* The qSV fallback angle of chert_surrogate_cache, process-wide: qSV entries
+ * the network calls valid whose predicted imaginary angle exceeds `rad` get
+ * flag 2 (exact solver); the default is 1 deg, 0 hands every such entry to
+ * the exact solver.  rad < 0 queries.  Returns the previous (or current)
+ * angle. */
+double chert_set_surrogate_qsv_angle(double rad);
 int chert_surrogate_cache(const float* const* d_params_per_mode, const chert_class* d_classes,
                           int n_classes, const int* modes, int n_modes, int M, int precision,
                           const chert_cache_arrays* out, void* d_ws, size_t ws_bytes,

@@ -89,6 +89,8 @@ def lib():
     L.chert_trace_host.argtypes = [P, I, P, I, ctypes.POINTER(chert_cache_params), I, I, D, P, P, I, P, I, I, P, I,
                                    I64, P, P, P, P, P, SZ, P]
     L.chert_trace_host.restype = ctypes.c_int
+    L.chert_set_surrogate_qsv_angle.argtypes = [D]
+    L.chert_set_surrogate_qsv_angle.restype = D
     L.chert_fma_rate.argtypes = [I, I, ctypes.POINTER(ctypes.c_double), P]
     L.chert_fma_rate.restype = ctypes.c_int
     L.chert_cache_eval_counter.argtypes = [I, P]
@@ -576,6 +578,12 @@ def surrogate_dataset(d_classes, n_classes, M, mode, mode_slot, exact_cache, str
                                          exact_cache.precision, _dev_ptr(x), _dev_ptr(t), _dev_ptr(scratch),
                                          scratch.numel(), _stream_ptr(stream)))
     return x, t
+
+
+def set_surrogate_qsv_angle(rad):
+    """qSV fallback angle of surrogate_cache (radians; process-wide); returns
+    the previous one."""
+    return float(lib().chert_set_surrogate_qsv_angle(float(rad)))
 
 
 def surrogate_cache(params_per_mode, d_classes, n_classes, modes, M, precision="fp32", stream=None, out=None):

@@ -17,6 +17,7 @@
 // (closed form, derivative by hand) and A0 the attenuation of the homogeneous
 // plane wave along the slowness direction, projected on the elastic ray.
 #include <cuda_bf16.h>
+#include <atomic>
 #include <math.h>
 #include <stdint.h>
 
@@ -174,8 +175,12 @@ constexpr float kSureLogit = 2.2f;
 // region, where the exact solution moves far from the homogeneous wave) go to
 // the exact solver; the training set leaves out their ray quantities beyond
 // twice that angle (NaN targets), which the network then never has to fit.
-constexpr float kQsvBranchAngle = 0.0174533f;
+constexpr float kQsvBranchAngle = 0.0174533f;         // 1 deg: the default fallback angle
 constexpr float kQsvTrainAngle = 2.0f * kQsvBranchAngle;
+// qSV entries whose predicted imaginary angle exceeds this go to the exact
+// solver (chert_set_surrogate_qsv_angle; process-wide; 0 sends every qSV
+// entry the network calls valid to the exact solver).
+std::atomic<float> g_qsv_branch_angle{kQsvBranchAngle};
 
 // Training targets from an exact cache (float or double arrays): entry d = j
 // of the first quadrant (d = M for j = M, mirrored in z), rotated back into
@@ -330,7 +335,7 @@ __global__ void decode_kernel(const chert_class* __restrict__ classes, int n_tot
                               int M, int mi, int mode, const float* __restrict__ y, const float* __restrict__ mean,
                               const float* __restrict__ std, const float* __restrict__ Vg,
                               const float* __restrict__ psi_el, const float* __restrict__ A0,
-                              const uint8_t* __restrict__ outside, chert_cache_arrays out) {
+                              const uint8_t* __restrict__ outside, float qsv_angle, chert_cache_arrays out) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long n = (long long)n_chunk * (M + 1);
     if (i >= n) return;
@@ -343,10 +348,13 @@ __global__ void decode_kernel(const chert_class* __restrict__ classes, int n_tot
     for (int q = 0; q < kOut; ++q) t[q] = y[i * kOut + q] * std[q] + mean[q];
     const float logit = y[i * kOut + 3];
     const bool unsure = fabsf(logit) < kSureLogit ||
-                        (mode == CHERT_QSV && logit > 0.0f && fabsf(t[4]) > kQsvBranchAngle);
+                        (mode == CHERT_QSV && logit > 0.0f && !(fabsf(t[4]) <= qsv_angle));
     const uint8_t fl = (outside[i] || unsure) ? 2 : (logit > 0.0f ? 0 : 1);
     const double V = double(Vg[i]) * vp0 * (1.0 + t[0]);
-    const double A = double(A0[i]) * exp(double(t[1])) / vp0;
+    // qSH: the homogeneous plane wave's attenuation A0 is the exact one (its
+    // energy velocity is homogeneous at vartheta = 0 in a VTI medium), so the
+    // network's correction is not applied
+    const double A = (mode == CHERT_QSH ? double(A0[i]) : double(A0[i]) * exp(double(t[1]))) / vp0;
     const double psi = double(psi_el[i]) + t[2];
     const double vr = 1.0, vi = -A * V;                  // v_I / v_R = -A V
     const double Q = vi == 0.0 ? INFINITY : -(vr * vr - vi * vi) / (2.0 * vr * vi);
@@ -465,6 +473,11 @@ using namespace chert;
 using namespace chert::mlp;
 
 extern "C" size_t chert_mlp_param_count(void) { return layout().total; }
+
+extern "C" double chert_set_surrogate_qsv_angle(double rad) {
+    if (rad < 0) return g_qsv_branch_angle.load();
+    return g_qsv_branch_angle.exchange((float)rad);
+}
 
 extern "C" int chert_mlp_set_tensor_cores(int enable) {
     const int before = gemm::tc::tensor_cores_enabled() ? 1 : 0;
@@ -633,6 +646,7 @@ extern "C" int chert_surrogate_cache(const float* const* d_params_per_mode, cons
     const size_t rest = ws_bytes - (size_t)(p - (unsigned char*)d_ws);
     const Layout L = layout();
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float qsv_angle = g_qsv_branch_angle.load();
     for (int mi = 0; mi < n_modes; ++mi) {
         CHERT_REQUIRE(d_params_per_mode[mi], "chert_surrogate_cache: NULL parameters");
         const float* prm = d_params_per_mode[mi];
@@ -647,12 +661,12 @@ extern "C" int chert_surrogate_cache(const float* const* d_params_per_mode, cons
                 decode_kernel<double><<<grid_for(n, 256), 256, 0, s>>>(d_classes, n_classes, k0, nc, M, mi,
                                                                       modes[mi], y,
                                                                       prm + L.mean, prm + L.std, Vg, psi,
-                                                                      A0, outside, *out);
+                                                                      A0, outside, qsv_angle, *out);
             else
                 decode_kernel<float><<<grid_for(n, 256), 256, 0, s>>>(d_classes, n_classes, k0, nc, M, mi,
                                                                      modes[mi], y,
                                                                      prm + L.mean, prm + L.std, Vg, psi,
-                                                                     A0, outside, *out);
+                                                                     A0, outside, qsv_angle, *out);
         }
     }
     return launch_check("chert_surrogate_cache");

@@ -158,9 +158,16 @@ def test_training_pairs_match_oracle(torch_dev, mode):
 
 def test_trained_surrogate_beats_elastic_baseline(torch_dev):
     """Trained on exact entries of 512 seeded media, evaluated on 48 others:
-    the surrogate's ray velocity and attenuation errors against the exact
-    cache, and the same errors of the elastic baseline alone (the network
-    predicting no correction)."""
+    errors against the exact cache of the surrogate and of the elastic
+    baseline alone (elastic group velocity and ray angle of the real moduli,
+    homogeneous-wave attenuation A0: the network predicting no correction,
+    computed by the oracle).  The network must cut the median ray-velocity
+    error at least 3-fold in every mode and the median qP attenuation error.
+    For qSH the decode uses A0 itself (exact for that mode), so its
+    attenuation equals the baseline's; for qSV, where A0 is already within
+    about 1e-5 of the exact value at the median, the network's attenuation
+    is held to 2e-4 at the median."""
+    from oracle import mlp_oracle as mo
     modes = ["qP", "qSV", "qSH"]
     M = 30
     train_sets = surrogate.exact_training_set(inputs.random_tti_classes(512, seed=21), modes, M)
@@ -174,16 +181,28 @@ def test_trained_surrogate_beats_elastic_baseline(torch_dev):
         params.append(p)
     surr = chert.surrogate_cache(params, d_test, 48, modes, M)
     torch_dev.cuda.synchronize()
-    ex = {k: v.cpu().numpy() for k, v in exact.arrays.items()}
-    su = {k: v.cpu().numpy() for k, v in surr.arrays.items()}
+    ex = {k: v.cpu().numpy()[:, :, :M + 1] for k, v in exact.arrays.items()}
+    su = {k: v.cpu().numpy()[:, :, :M + 1] for k, v in surr.arrays.items()}
     decided = su["flag"] != 2                 # 2: handed to the exact solver
-    both = (ex["flag"] == 0) & (su["flag"] == 0)
     agree = np.mean(((ex["flag"] == 0) == (su["flag"] == 0))[decided])
     assert agree > 0.99
     assert np.mean(decided[0]) > 0.9 and np.mean(decided[2]) > 0.9        # qP, qSH mostly decided
+    mods, _ = oracle_moduli(test_cls)
+    th = (math.pi / 2) * np.arange(M + 1) / M
     for mi, m in enumerate(modes):
-        ok = both[mi]
-        dv = np.abs(su["V"][mi][ok] / ex["V"][mi][ok] - 1)
-        da = np.abs(su["A"][mi][ok] - ex["A"][mi][ok]) / np.abs(ex["A"][mi][ok])
-        assert np.median(dv) < 2e-3, (m, np.median(dv))
-        assert np.median(da) < 5e-2, (m, np.median(da))
+        bV, bA = np.zeros((48, M + 1)), np.zeros((48, M + 1))
+        for k in range(48):
+            Vg, psi = mo.elastic_baseline(mods[k].real, th, m)
+            bV[k], bA[k] = Vg, mo.attenuation_baseline(mods[k], th, m, psi)
+        ok = (ex["flag"][mi] == 0) & (su["flag"][mi] == 0)
+
+        def rel(a, key):
+            return np.median(np.abs(a[ok] / ex[key][mi][ok] - 1))
+
+        assert rel(su["V"][mi], "V") < rel(bV, "V") / 3, (m, rel(su["V"][mi], "V"), rel(bV, "V"))
+        if m == "qP":
+            assert rel(su["A"][mi], "A") < rel(bA, "A"), (m, rel(su["A"][mi], "A"), rel(bA, "A"))
+        elif m == "qSH":
+            assert np.allclose(su["A"][mi][ok], bA[ok], rtol=1e-6)
+        else:
+            assert rel(su["A"][mi], "A") < 2e-4, (m, rel(su["A"][mi], "A"))
