@@ -453,3 +453,37 @@ def test_launch_shapes_give_identical_fields(torch_dev):
         for a, b in zip(outs[1], outs[ppt]):
             assert np.array_equal(a, b)
     assert lib.chert_set_relax_points_per_thread(3) == chert.EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_row_class_path_equals_class_pair_path(torch_dev, precision):
+    """The row-class path (every row of the class map one class: weights read
+    at offsets fixed per line) against the class-pair path (a class load per
+    node and neighbour), bit for bit, at every points-per-thread choice.  The
+    cache gets a sixth class equal to class 2 entry for entry; a class map
+    with one node of a class-2 row relabelled 5 fails the row check, so its
+    fields run on the class-pair path with the same weights as the flat map
+    on the row-class path.  A whole row relabelled 5 keeps the row path."""
+    nx, nz = 151, 97
+    flat = inputs.layered_class_map_2d(nx, nz, 5).astype(np.int32)
+    cnp = small_oracle_cache()
+    dup = {k: np.concatenate([v, v[:, 2:3]], axis=1) for k, v in cnp.items()}
+    cache = as_cache(torch_dev, dup, precision)
+    row2 = int(np.nonzero(flat.reshape(nz, nx)[:, 0] == 2)[0][3])
+    one_node = flat.copy()
+    one_node[row2 * nx + 60] = 5
+    whole_row = flat.copy()
+    whole_row[row2 * nx:(row2 + 1) * nx] = 5
+    off = inputs.stencil_2d(5)
+    src = [0, 77 + nx * 40, nx * nz - 1]
+    lib = chert.lib()
+    try:
+        for ppt in (1, 2, 4):
+            lib.chert_set_relax_points_per_thread(ppt)
+            ref = run_gpu(torch_dev, cache, nx, nz, 10.0, flat, off, src)
+            for cls in (one_node, whole_row):
+                got = run_gpu(torch_dev, cache, nx, nz, 10.0, cls, off, src)
+                for a, b in zip(ref, got):
+                    assert np.array_equal(a, b), ppt
+    finally:
+        lib.chert_set_relax_points_per_thread(0)
