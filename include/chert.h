@@ -75,6 +75,15 @@ int chert_thomsen_to_class(double vp0, double vs0, double eps, double delta,
                            double gamma, double qp, double qs, double rho,
                            double tilt, double azim, chert_class* out);
 
+/* Eq. 2 for a medium given as real moduli aR = (a11, a13, a33, a44, a66) and
+ * one quality factor per component q[5] (the paper's Table 2 lists both):
+ * aI[i] = aR[i] / q[i], and 0 where q[i] is +inf (elastic).  Host arrays of
+ * 5 doubles.  Host only.
+ * Errors: CHERT_EINVAL if a pointer is NULL, a q[i] is not positive, or
+ * a33 or a44 is not positive. */
+int chert_moduli_to_class(const double* aR, const double* q, double rho,
+                          double tilt, double azim, chert_class* out);
+
 /* chert_thomsen_to_class for n classes (host arrays of length n; out holds
  * n records).  Stops at the first invalid class (CHERT_EINVAL, index in the
  * message). */
@@ -317,8 +326,27 @@ size_t chert_mlp_workspace_bytes(int64_t n, int training);
  * used to compare the two).  Returns the previous setting. */
 int chert_mlp_set_tensor_cores(int enable);
 
+/* Every mbarrier wait of the tensor-core GEMM is bounded.  A wait that runs
+ * out sets a device status word; the kernel then waits for its TMA loads in
+ * flight and its tensor-core work, frees its tensor memory and returns without
+ * writing its output tile.  chert_mlp_forward and chert_mlp_train_step read
+ * the word after their work (synchronising the stream) and return
+ * CHERT_ETIMEOUT if it was set, clearing it.
+ *
+ * chert_mlp_check reads and clears the word on its own (synchronises
+ * `stream`): for callers that enqueue the surrogate under stream capture,
+ * where nothing reads it.  Returns CHERT_OK or CHERT_ETIMEOUT.
+ *
+ * chert_mlp_set_wait_limit sets the poll limit of the GEMM's main-loop waits
+ * (default 2^22; polls < 0 queries) and returns the previous one.  It exists
+ * so that a test can make a wait run out (polls = 0) and check the status
+ * and the fallback; process-wide, synchronous. */
+int chert_mlp_check(void* stream);
+long long chert_mlp_set_wait_limit(long long polls);
+
 /* y [n][5] (standardised outputs) for x [n][8]; all device.  Errors:
- * CHERT_EINVAL, CHERT_ENOMEM (workspace), CHERT_ECUDA. */
+ * CHERT_EINVAL, CHERT_ENOMEM (workspace), CHERT_ETIMEOUT (a tensor-core
+ * wait ran out), CHERT_ECUDA. */
 int chert_mlp_forward(const float* d_params, const float* d_x, int64_t n, float* d_y,
                       void* d_ws, size_t ws_bytes, void* stream);
 
@@ -353,8 +381,12 @@ int chert_surrogate_dataset(const chert_class* d_classes, int n_classes, int M, 
  * the medium lies outside the training range, the network is unsure whether
  * a decaying root exists (0.1 < p < 0.9), or, for qSV, the predicted
  * imaginary angle exceeds the fallback angle (chert_set_surrogate_qsv_angle,
- * 1 deg by default: the cusp / triplication region).  The caller recomputes
- * those solves with chert_build_cache_items. */
+ * 1 deg by default: the cusp / triplication region), and every solve if a
+ * tensor-core GEMM wait ran out.  The caller recomputes those solves with
+ * chert_build_cache_items, or calls chert_cache_surrogate, which does both.
+ * Outside stream capture it reads the tensor-core status at the end (one
+ * synchronisation; CHERT_ETIMEOUT if a wait ran out); under capture it does
+ * not (chert_mlp_check). */
 size_t chert_surrogate_cache_workspace_bytes(int n_classes, int M);
 
 /* The qSV fallback angle of chert_surrogate_cache, process-wide: qSV entries
@@ -367,6 +399,26 @@ int chert_surrogate_cache(const float* const* d_params_per_mode, const chert_cla
                           int n_classes, const int* modes, int n_modes, int M, int precision,
                           const chert_cache_arrays* out, void* d_ws, size_t ws_bytes,
                           void* stream);
+
+/* The surrogate cache with its exact fallback in one enqueued sequence, no
+ * host synchronisation (capturable into a CUDA graph): chert_surrogate_cache
+ * (network precision CHERT_FP64 for an FP64 params->precision, else
+ * CHERT_FP32), then the solves it marks with flag 2 are compacted on the
+ * device into a list whose length stays on the device, and recomputed by the
+ * exact solver (chert_build_cache_items' arithmetic at params: scan grid,
+ * kernel, precision).  Every entry then has flag 0 or 1.  The tensor-core
+ * status is not read here: if a GEMM wait ran out, every solve is marked for
+ * and recomputed by the exact solver (a correct, slower cache), and
+ * chert_mlp_check reports it.
+ *   d_ws: device workspace of chert_cache_surrogate_workspace_bytes bytes.
+ *   d_n_fallback: optional device int64, receives the number of solves
+ *   recomputed exactly.
+ * Errors: CHERT_EINVAL (counts, NULL), CHERT_ENOMEM (workspace), CHERT_ECUDA. */
+size_t chert_cache_surrogate_workspace_bytes(int n_classes, int n_modes, int M);
+int chert_cache_surrogate(const float* const* d_params_per_mode, const chert_class* d_classes,
+                          int n_classes, const int* modes, int n_modes,
+                          const chert_cache_params* params, const chert_cache_arrays* out,
+                          void* d_ws, size_t ws_bytes, int64_t* d_n_fallback, void* stream);
 
 /* The paper has no counterpart to this entry point; it exists for callers of
  * this library that cannot allocate device memory: code embedded in a host

@@ -64,6 +64,8 @@ def lib():
     P, I, D, I64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_size_t
     L.chert_last_error.restype = ctypes.c_char_p
     L.chert_thomsen_to_class.argtypes = [D] * 10 + [ctypes.POINTER(chert_class)]
+    L.chert_moduli_to_class.argtypes = [P, P, D, D, D, ctypes.POINTER(chert_class)]
+    L.chert_moduli_to_class.restype = ctypes.c_int
     L.chert_thomsen_to_classes.argtypes = [I64] + [P] * 11
     L.chert_thomsen_to_classes.restype = ctypes.c_int
     L.chert_build_cache.argtypes = [P, I, P, I, ctypes.POINTER(chert_cache_params),
@@ -119,6 +121,15 @@ def lib():
     L.chert_surrogate_cache_workspace_bytes.restype = SZ
     L.chert_surrogate_cache_workspace_bytes.argtypes = [I, I]
     L.chert_surrogate_cache.argtypes = [P, P, I, P, I, I, I, ctypes.POINTER(chert_cache_arrays), P, SZ, P]
+    L.chert_mlp_check.argtypes = [P]
+    L.chert_mlp_check.restype = ctypes.c_int
+    L.chert_mlp_set_wait_limit.argtypes = [ctypes.c_longlong]
+    L.chert_mlp_set_wait_limit.restype = ctypes.c_longlong
+    L.chert_cache_surrogate_workspace_bytes.restype = SZ
+    L.chert_cache_surrogate_workspace_bytes.argtypes = [I, I, I]
+    L.chert_cache_surrogate.argtypes = [P, P, I, P, I, ctypes.POINTER(chert_cache_params),
+                                        ctypes.POINTER(chert_cache_arrays), P, SZ, P, P]
+    L.chert_cache_surrogate.restype = ctypes.c_int
     for name in ("chert_thomsen_to_class", "chert_build_cache", "chert_edge_table",
                  "chert_traveltime", "chert_raypath", "chert_traveltime_static", "chert_mlp_forward",
                  "chert_mlp_train_step", "chert_surrogate_dataset", "chert_surrogate_cache"):
@@ -169,10 +180,9 @@ def thomsen_to_class(vp0, vs0, eps, delta, gamma, qp, qs, rho=2200.0, tilt=0.0, 
 def table_class(aR, q, rho=2200.0, tilt=0.0, azim=0.0):
     """A class from real moduli and per-component Q (Eq. 2: aI = aR/Q)."""
     c = chert_class()
-    for i in range(5):
-        c.aR[i] = float(aR[i])
-        c.aI[i] = 0.0 if math.isinf(q[i]) else float(aR[i]) / float(q[i])
-    c.rho, c.tilt, c.azim = rho, tilt, azim
+    a = (ctypes.c_double * 5)(*[float(v) for v in aR])
+    qq = (ctypes.c_double * 5)(*[float(v) for v in q])
+    _check(lib().chert_moduli_to_class(a, qq, float(rho), float(tilt), float(azim), ctypes.byref(c)))
     return c
 
 
@@ -219,6 +229,14 @@ class Cache:
     def __init__(self, arrays, modes, n_classes, M, precision, n_az=0, n_pol=0):
         self.arrays, self.modes, self.n_classes, self.M, self.precision = arrays, modes, n_classes, M, precision
         self.n_az, self.n_pol = n_az, n_pol
+
+    n_fallback_dev = None     # set by cache_surrogate: device int64 [1]
+
+    @property
+    def n_fallback(self):
+        """Solves that a surrogate cache recomputed exactly (0 for an exact
+        cache); reading it copies one integer from the device."""
+        return 0 if self.n_fallback_dev is None else int(self.n_fallback_dev.item())
 
     @property
     def n_dir(self):
@@ -584,6 +602,50 @@ def set_surrogate_qsv_angle(rad):
     """qSV fallback angle of surrogate_cache (radians; process-wide); returns
     the previous one."""
     return float(lib().chert_set_surrogate_qsv_angle(float(rad)))
+
+
+def cache_surrogate(params_per_mode, d_classes, n_classes, modes, M, scan_step=0.001 * math.pi / 180,
+                    scan_half=30000, kernel="MEV", precision="mixed", stream=None, out=None):
+    """chert_cache_surrogate: the networks' cache with every solve they hand
+    back recomputed by the exact solver, enqueued without a host read.
+    Returns the Cache; cache.n_fallback_dev is a device int64 tensor [1] with
+    the number of solves recomputed exactly."""
+    torch = _torch()
+    prec = PRECISION_IDS[precision] if isinstance(precision, str) else precision
+    mode_ids = [MODE_IDS[m] if isinstance(m, str) else m for m in modes]
+    dev = d_classes.device
+    shape = (len(mode_ids), n_classes, 4 * M)
+    if out is None:
+        fd = _fdtype(prec)
+        out = {k: torch.empty(shape, dtype=fd, device=dev)
+               for k in ("V", "A", "Q", "rx", "rz", "theta", "vartheta")}
+        out["flag"] = torch.empty(shape, dtype=torch.uint8, device=dev)
+    cache = Cache(out, mode_ids, n_classes, M, prec)
+    wsb = int(lib().chert_cache_surrogate_workspace_bytes(n_classes, len(mode_ids), M))
+    if wsb == 0:
+        raise ChertError(EINVAL, "cache_surrogate: bad sizes")
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    cache.n_fallback_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    p = chert_cache_params(M, scan_step, scan_half, KERNEL_IDS.get(kernel, kernel), prec)
+    ptrs = (ctypes.c_void_p * len(mode_ids))(*[q.data_ptr() for q in params_per_mode])
+    modes_arr = (ctypes.c_int * len(mode_ids))(*mode_ids)
+    st = cache.struct()
+    _check(lib().chert_cache_surrogate(ptrs, _dev_ptr(d_classes), n_classes, modes_arr, len(mode_ids),
+                                       ctypes.byref(p), ctypes.byref(st), _dev_ptr(ws), ws.numel(),
+                                       _dev_ptr(cache.n_fallback_dev), _stream_ptr(stream)))
+    cache.workspace = ws
+    return cache
+
+
+def mlp_check(stream=None):
+    """chert_mlp_check: raises ChertError(ETIMEOUT) if a tensor-core GEMM wait
+    ran out since the last check (and clears the status)."""
+    _check(lib().chert_mlp_check(_stream_ptr(stream)))
+
+
+def mlp_set_wait_limit(polls):
+    """chert_mlp_set_wait_limit; returns the previous limit (polls < 0 queries)."""
+    return int(lib().chert_mlp_set_wait_limit(int(polls)))
 
 
 def surrogate_cache(params_per_mode, d_classes, n_classes, modes, M, precision="fp32", stream=None, out=None):

@@ -43,6 +43,24 @@ extern "C" int chert_thomsen_to_class(double vp0, double vs0, double eps, double
     return CHERT_OK;
 }
 
+// Eq. 2 for media given as real moduli and a quality factor per component
+// (the form of the paper's Table 2): aI = aR / Q, an infinite Q elastic.
+extern "C" int chert_moduli_to_class(const double* aR, const double* q, double rho, double tilt, double azim,
+                                     chert_class* out) {
+    CHERT_REQUIRE(aR && q && out, "chert_moduli_to_class: NULL argument");
+    for (int i = 0; i < 5; i++)
+        CHERT_REQUIRE(q[i] > 0, "chert_moduli_to_class: Q of component %d is %g (must be positive)", i, q[i]);
+    CHERT_REQUIRE(aR[2] > 0 && aR[3] > 0, "chert_moduli_to_class: a33 and a44 must be positive");
+    for (int i = 0; i < 5; i++) {
+        out->aR[i] = aR[i];
+        out->aI[i] = isinf(q[i]) ? 0.0 : aR[i] / q[i];
+    }
+    out->rho = rho;
+    out->tilt = tilt;
+    out->azim = azim;
+    return CHERT_OK;
+}
+
 // Batched form of chert_thomsen_to_class for per-cell media (host arrays).
 extern "C" int chert_thomsen_to_classes(int64_t n, const double* vp0, const double* vs0, const double* eps,
                                         const double* delta, const double* gamma, const double* qp,

@@ -753,17 +753,14 @@ __device__ void write_entries(const Outs& out, const Solve<TS, TP>& v, int n_cla
 // With a solve list (items != NULL) warp w takes solve items[w]; a solve is
 // numbered mode_slot*n_classes*P + class*P + j with P = M+1 (2D) or
 // n_az*n_pol (3D, j the entry d).
+// With a device-side count (n_dev != NULL: the list length is known only on
+// the device, e.g. inside a CUDA graph) the grid is sized for the machine and
+// each warp strides over the list.
 template <typename TS, typename TP, typename TO>
-__global__ void __launch_bounds__(256, 2) cache_build_kernel(const chert_class* __restrict__ classes,
-                                                          int n_classes, ModeList modes, Geo g,
-                                                          double h, int K, int kernel, Outs out,
-                                                          const int64_t* __restrict__ items,
-                                                          long long n_items) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const long long total = items ? n_items : static_cast<long long>(modes.n) * n_classes * g.per_class();
-    if (warp >= total) return;
-    const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, g, items ? items[warp] : warp);
+__device__ __forceinline__ void build_solve(const chert_class* __restrict__ classes, int n_classes,
+                                            const ModeList& modes, const Geo& g, double h, int K, int kernel,
+                                            const Outs& out, long long idx, int lane) {
+    const Solve<TS, TP> v = make_solve<TS, TP>(classes, n_classes, modes, g, idx);
     bool found = false;
     TP root = TP(0);
     RayQ<TP> fq{};
@@ -779,6 +776,28 @@ __global__ void __launch_bounds__(256, 2) cache_build_kernel(const chert_class* 
         return;
     }
     write_entries<TS, TP, TO>(out, v, n_classes, g, found, root, fq, lane);
+}
+
+// DEV: the list length is *n_dev (a separate instantiation, so that the
+// common form keeps its register allocation).
+template <typename TS, typename TP, typename TO, bool DEV>
+__global__ void __launch_bounds__(256, 2) cache_build_kernel(const chert_class* __restrict__ classes,
+                                                          int n_classes, ModeList modes, Geo g,
+                                                          double h, int K, int kernel, Outs out,
+                                                          const int64_t* __restrict__ items,
+                                                          long long n_items, const long long* __restrict__ n_dev) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if constexpr (DEV) {
+        const long long total = *n_dev;
+        const long long stride = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+        for (long long w = warp; w < total; w += stride)
+            build_solve<TS, TP, TO>(classes, n_classes, modes, g, h, K, kernel, out, items[w], lane);
+    } else {
+        const long long total = items ? n_items : static_cast<long long>(modes.n) * n_classes * g.per_class();
+        if (warp >= total) return;
+        build_solve<TS, TP, TO>(classes, n_classes, modes, g, h, K, kernel, out, items ? items[warp] : warp, lane);
+    }
 }
 
 // Second launch: one 1024-thread CTA per chunk of `chunk` (<= kFinishChunk)
@@ -831,37 +850,60 @@ __device__ void finish_one(const chert_class* __restrict__ classes, int n_classe
 }
 
 template <typename TS, typename TP, typename TO>
-__global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* __restrict__ classes,
-                                                            int n_classes, ModeList modes, Geo g,
-                                                            double h, int K, int kernel, Outs out,
-                                                            const int64_t* __restrict__ items,
-                                                            long long n_total, int chunk) {
-    __shared__ long long s_list[kFinishChunk];
-    __shared__ int s_count;
+__device__ __forceinline__ void finish_chunk(const chert_class* __restrict__ classes, int n_classes,
+                                             const ModeList& modes, const Geo& g, double h, int K, int kernel,
+                                             const Outs& out, const int64_t* __restrict__ items, long long n_total,
+                                             int chunk, long long base, long long* s_list, int* s_count) {
     const int per = g.per_class();
-    if (threadIdx.x == 0) s_count = 0;
+    if (threadIdx.x == 0) *s_count = 0;
     __syncthreads();
-    const long long t = (long long)blockIdx.x * chunk + threadIdx.x;
+    const long long t = base + threadIdx.x;
     if ((int)threadIdx.x < chunk && t < n_total) {
         const long long idx = items ? items[t] : t;
         const int j = static_cast<int>(idx % per);
         const int k = static_cast<int>((idx / per) % n_classes);
         const int mi = static_cast<int>(idx / (static_cast<long long>(per) * n_classes));
-        if (out.flag[entry_index(mi, k, n_classes, g, j)] == kPending) s_list[atomicAdd(&s_count, 1)] = idx;
+        if (out.flag[entry_index(mi, k, n_classes, g, j)] == kPending) s_list[atomicAdd(s_count, 1)] = idx;
     }
     __syncthreads();
-    const int cnt = s_count;
+    const int cnt = *s_count;
     for (int q = 0; q < cnt; ++q)
         finish_one<TS, TP, TO>(classes, n_classes, modes, g, h, K, kernel, out, s_list[q]);
+}
+
+// DEV: the list length is *n_dev and the CTAs stride over the chunks.
+template <typename TS, typename TP, typename TO, bool DEV>
+__global__ void __launch_bounds__(1024) cache_finish_kernel(const chert_class* __restrict__ classes,
+                                                            int n_classes, ModeList modes, Geo g,
+                                                            double h, int K, int kernel, Outs out,
+                                                            const int64_t* __restrict__ items,
+                                                            long long n_total, int chunk,
+                                                            const long long* __restrict__ n_dev) {
+    __shared__ long long s_list[kFinishChunk];
+    __shared__ int s_count;
+    if constexpr (DEV) {
+        const long long n = *n_dev;
+        for (long long base = (long long)blockIdx.x * chunk; base < n; base += (long long)gridDim.x * chunk) {
+            finish_chunk<TS, TP, TO>(classes, n_classes, modes, g, h, K, kernel, out, items, n, chunk, base,
+                                     s_list, &s_count);
+            __syncthreads();
+        }
+    } else {
+        finish_chunk<TS, TP, TO>(classes, n_classes, modes, g, h, K, kernel, out, items, n_total, chunk,
+                                 (long long)blockIdx.x * chunk, s_list, &s_count);
+    }
 }
 
 }  // namespace
 }  // namespace chert
 
+// d_n_items != NULL: the solve list d_items holds *d_n_items entries (a count
+// on the device, at most n_items); the launches are sized for the machine and
+// stride over the list, so no host read of the count is needed.
 static int launch_build(const chert_class* d_classes, int n_classes, const int* modes, int n_modes,
                         const chert_cache_params* params, const chert_cache_arrays* out,
                         const int64_t* d_items, long long n_items, void* stream, const char* who,
-                        int n_az = 0, int n_pol = 0) {
+                        int n_az = 0, int n_pol = 0, const long long* d_n_items = nullptr) {
     using namespace chert;
     CHERT_REQUIRE(d_classes && modes && params && out, "%s: NULL argument", who);
     CHERT_REQUIRE(n_classes >= 1, "%s: n_classes=%d", who, n_classes);
@@ -899,14 +941,21 @@ static int launch_build(const chert_class* d_classes, int n_classes, const int* 
     }
     const long long per_cta = (warps + 8LL * n_sm - 1) / (8LL * n_sm);        // ~8 CTAs per SM
     const int chunk = (int)std::max(1LL, std::min<long long>(kFinishChunk, per_cta));
-    const unsigned finish_blocks = (unsigned)((warps + chunk - 1) / chunk);
+    unsigned finish_blocks = (unsigned)((warps + chunk - 1) / chunk);
+    unsigned build_blocks = (unsigned)blocks;
+    if (d_n_items) {          // strided launches: 2 CTAs per SM of each kernel (its occupancy)
+        build_blocks = (unsigned)std::min<long long>(blocks, 2LL * n_sm);
+        finish_blocks = (unsigned)std::min<long long>(finish_blocks, 2LL * n_sm);
+    }
     const int kern = params->kernel;
-#define CHERT_LAUNCH_BUILD(TS, TP, TO)                                                                  \
-    cache_build_kernel<TS, TP, TO><<<(unsigned)blocks, threads, 0, s>>>(d_classes, n_classes, ml, geo, h, K, \
-                                                                       kern, o, d_items, n_items);       \
+#define CHERT_LAUNCH_BUILD_DEV(TS, TP, TO, DEV)                                                         \
+    cache_build_kernel<TS, TP, TO, DEV><<<build_blocks, threads, 0, s>>>(d_classes, n_classes, ml, geo, h, K, \
+                                                                        kern, o, d_items, n_items, d_n_items); \
     if (K > kPhase1Reach)                                                                               \
-        cache_finish_kernel<TS, TP, TO><<<finish_blocks, 1024, 0, s>>>(d_classes, n_classes, ml, geo, h, K, kern, \
-                                                                        o, d_items, warps, chunk);
+        cache_finish_kernel<TS, TP, TO, DEV><<<finish_blocks, 1024, 0, s>>>(d_classes, n_classes, ml, geo, h, K, \
+                                                                             kern, o, d_items, warps, chunk, d_n_items);
+#define CHERT_LAUNCH_BUILD(TS, TP, TO)                                                                  \
+    if (d_n_items) { CHERT_LAUNCH_BUILD_DEV(TS, TP, TO, true) } else { CHERT_LAUNCH_BUILD_DEV(TS, TP, TO, false) }
     switch (params->precision) {
         case CHERT_FP64: CHERT_LAUNCH_BUILD(double, double, double) break;
         case CHERT_FP32: CHERT_LAUNCH_BUILD(float, float, float) break;
@@ -914,6 +963,7 @@ static int launch_build(const chert_class* d_classes, int n_classes, const int* 
         default: CHERT_REQUIRE(false, "%s: precision=%d", who, params->precision);
     }
 #undef CHERT_LAUNCH_BUILD
+#undef CHERT_LAUNCH_BUILD_DEV
     return launch_check(who);
 }
 
@@ -931,6 +981,81 @@ extern "C" int chert_build_cache_items(const chert_class* d_classes, int n_class
     CHERT_REQUIRE(d_items && n_items >= 0, "chert_build_cache_items: bad item list");
     return launch_build(d_classes, n_classes, modes, n_modes, params, out, d_items, n_items, stream,
                         "chert_build_cache_items");
+}
+
+namespace chert {
+int surrogate_cache(const float* const* d_params_per_mode, const chert_class* d_classes, int n_classes,
+                    const int* modes, int n_modes, int M, int precision, const chert_cache_arrays* out,
+                    void* d_ws, size_t ws_bytes, void* stream, bool check);
+}
+
+// The solves a surrogate cache hands to the exact solver (flag 2 on the
+// solve's own entry, d = j): compacted into a list with a device-side count.
+__global__ void collect_fallback_kernel(const uint8_t* __restrict__ flag, int n_modes, int n_classes, int M,
+                                        int64_t* __restrict__ items, unsigned long long* __restrict__ count) {
+    const long long per = M + 1;
+    const long long n = (long long)n_modes * n_classes * per;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool take = false;
+    if (t < n) {
+        const long long j = t % per, mk = t / per;             // mk = mode slot * n_classes + class
+        take = flag[mk * 4 * M + j] == 2;
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, take);
+    unsigned long long base = 0;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0 && ballot) base = atomicAdd(count, (unsigned long long)__popc(ballot));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take) items[base + __popc(ballot & ((1u << lane) - 1))] = t;
+}
+
+extern "C" size_t chert_cache_surrogate_workspace_bytes(int n_classes, int n_modes, int M) {
+    if (n_classes < 1 || n_modes < 1 || n_modes > 3 || M < 1) return 0;
+    const size_t s = chert_surrogate_cache_workspace_bytes(n_classes, M);
+    if (s == 0) return 0;
+    auto a256 = [](size_t x) { return (x + 255) & ~size_t(255); };
+    return a256(s) + a256(8 * (size_t)n_modes * n_classes * (M + 1)) + 256;
+}
+
+extern "C" int chert_cache_surrogate(const float* const* d_params_per_mode, const chert_class* d_classes,
+                                     int n_classes, const int* modes, int n_modes,
+                                     const chert_cache_params* params, const chert_cache_arrays* out,
+                                     void* d_ws, size_t ws_bytes, int64_t* d_n_fallback, void* stream) {
+    using namespace chert;
+    const char* who = "chert_cache_surrogate";
+    CHERT_REQUIRE(d_params_per_mode && d_classes && modes && params && out && d_ws, "%s: NULL argument", who);
+    const size_t need = chert_cache_surrogate_workspace_bytes(n_classes, n_modes, params->M);
+    CHERT_REQUIRE(need > 0, "%s: n_classes=%d n_modes=%d M=%d", who, n_classes, n_modes, params->M);
+    if (ws_bytes < need) {
+        set_error("%s: workspace %zu < %zu bytes", who, ws_bytes, need);
+        return CHERT_ENOMEM;
+    }
+    auto a256 = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t s_bytes = chert_surrogate_cache_workspace_bytes(n_classes, params->M);
+    unsigned char* w = static_cast<unsigned char*>(d_ws);
+    int64_t* items = reinterpret_cast<int64_t*>(w + a256(s_bytes));
+    unsigned long long* count =
+        reinterpret_cast<unsigned long long*>(w + a256(s_bytes) + a256(8 * (size_t)n_modes * n_classes * (params->M + 1)));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int net_prec = params->precision == CHERT_FP64 ? CHERT_FP64 : CHERT_FP32;
+    int rc = surrogate_cache(d_params_per_mode, d_classes, n_classes, modes, n_modes, params->M, net_prec, out, d_ws,
+                             s_bytes, stream, false);
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(*count), s);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_cache_surrogate: count reset");
+    const long long n = (long long)n_modes * n_classes * (params->M + 1);
+    collect_fallback_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out->flag, n_modes, n_classes, params->M,
+                                                                         items, count);
+    rc = launch_check("chert_cache_surrogate: fallback list");
+    if (rc) return rc;
+    rc = launch_build(d_classes, n_classes, modes, n_modes, params, out, items, n, stream, who, 0, 0,
+                      reinterpret_cast<const long long*>(count));
+    if (rc) return rc;
+    if (d_n_fallback) {
+        e = cudaMemcpyAsync(d_n_fallback, count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "chert_cache_surrogate: count copy");
+    }
+    return CHERT_OK;
 }
 
 extern "C" int chert_build_cache_3d(const chert_class* d_classes, int n_classes, const int* modes, int n_modes,

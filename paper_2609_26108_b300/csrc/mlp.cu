@@ -349,7 +349,10 @@ __global__ void decode_kernel(const chert_class* __restrict__ classes, int n_tot
     const float logit = y[i * kOut + 3];
     const bool unsure = fabsf(logit) < kSureLogit ||
                         (mode == CHERT_QSV && logit > 0.0f && !(fabsf(t[4]) <= qsv_angle));
-    const uint8_t fl = (outside[i] || unsure) ? 2 : (logit > 0.0f ? 0 : 1);
+    // a tensor-core GEMM that gave up left y unwritten: every solve then goes
+    // to the exact solver
+    const bool gemm_failed = *(volatile int*)&gemm::g_tc_error != 0;
+    const uint8_t fl = (outside[i] || unsure || gemm_failed) ? 2 : (logit > 0.0f ? 0 : 1);
     const double V = double(Vg[i]) * vp0 * (1.0 + t[0]);
     // qSH: the homogeneous plane wave's attenuation A0 is the exact one (its
     // energy velocity is homogeneous at vartheta = 0 in a VTI medium), so the
@@ -479,6 +482,20 @@ extern "C" double chert_set_surrogate_qsv_angle(double rad) {
     return g_qsv_branch_angle.exchange((float)rad);
 }
 
+extern "C" long long chert_mlp_set_wait_limit(long long polls) {
+    long long before = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&before, gemm::g_tc_wait_limit, sizeof(before));
+    if (e != cudaSuccess) return cuda_fail(e, "chert_mlp_set_wait_limit");
+    if (polls < 0) return before;
+    e = cudaMemcpyToSymbol(gemm::g_tc_wait_limit, &polls, sizeof(polls));
+    if (e != cudaSuccess) return cuda_fail(e, "chert_mlp_set_wait_limit");
+    return before;
+}
+
+extern "C" int chert_mlp_check(void* stream) {
+    return gemm::tc::check_and_clear(static_cast<cudaStream_t>(stream), "chert_mlp_check");
+}
+
 extern "C" int chert_mlp_set_tensor_cores(int enable) {
     const int before = gemm::tc::tensor_cores_enabled() ? 1 : 0;
     gemm::tc::tensor_cores_enabled() = enable != 0;
@@ -490,21 +507,27 @@ extern "C" size_t chert_mlp_workspace_bytes(int64_t n, int training) {
     return ws_carve(nullptr, n, training != 0).bytes;
 }
 
-extern "C" int chert_mlp_forward(const float* d_params, const float* d_x, int64_t n, float* d_y,
-                                 void* d_ws, size_t ws_bytes, void* stream) {
-    CHERT_REQUIRE(d_params && d_x && d_y && d_ws && n >= 1, "chert_mlp_forward: bad argument");
+// The forward pass enqueued on s, without reading the tensor-core status.
+static int forward_enqueue(const float* d_params, const float* d_x, int64_t n, float* d_y, void* d_ws,
+                           size_t ws_bytes, cudaStream_t s, const char* who) {
+    CHERT_REQUIRE(d_params && d_x && d_y && d_ws && n >= 1, "%s: bad argument", who);
     const Ws w = ws_carve(static_cast<unsigned char*>(d_ws), n, false);
     if (ws_bytes < w.bytes) {
-        set_error("chert_mlp_forward: workspace %zu < %zu bytes", ws_bytes, w.bytes);
+        set_error("%s: workspace %zu < %zu bytes", who, ws_bytes, w.bytes);
         return CHERT_ENOMEM;
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     to_bf16_kernel<<<grid_for(n * kInPad, 256), 256, 0, s>>>(d_x, w.xb, n * kInPad);
     int rc = forward(w, d_params, n, false, s);
     if (rc) return rc;
     cudaError_t e = cudaMemcpyAsync(d_y, w.y, sizeof(float) * n * kOut, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "chert_mlp_forward");
-    rc = launch_check("chert_mlp_forward");
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return launch_check(who);
+}
+
+extern "C" int chert_mlp_forward(const float* d_params, const float* d_x, int64_t n, float* d_y,
+                                 void* d_ws, size_t ws_bytes, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = forward_enqueue(d_params, d_x, n, d_y, d_ws, ws_bytes, s, "chert_mlp_forward");
     return rc ? rc : gemm::tc::check_and_clear(s, "chert_mlp_forward");
 }
 
@@ -622,10 +645,28 @@ extern "C" size_t chert_surrogate_cache_workspace_bytes(int n_classes, int M) {
            ws_carve(nullptr, n, false).bytes;
 }
 
+namespace chert {
+// chert_surrogate_cache; `check` reads the tensor-core status at the end (one
+// synchronisation of the stream).
+int surrogate_cache(const float* const* d_params_per_mode, const chert_class* d_classes, int n_classes,
+                    const int* modes, int n_modes, int M, int precision, const chert_cache_arrays* out,
+                    void* d_ws, size_t ws_bytes, void* stream, bool check);
+}
+
 extern "C" int chert_surrogate_cache(const float* const* d_params_per_mode, const chert_class* d_classes,
                                      int n_classes, const int* modes, int n_modes, int M, int precision,
                                      const chert_cache_arrays* out, void* d_ws, size_t ws_bytes,
                                      void* stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_surrogate_cache: capture status");
+    return chert::surrogate_cache(d_params_per_mode, d_classes, n_classes, modes, n_modes, M, precision, out, d_ws,
+                                  ws_bytes, stream, cs == cudaStreamCaptureStatusNone);
+}
+
+int chert::surrogate_cache(const float* const* d_params_per_mode, const chert_class* d_classes, int n_classes,
+                           const int* modes, int n_modes, int M, int precision, const chert_cache_arrays* out,
+                           void* d_ws, size_t ws_bytes, void* stream, bool check) {
     CHERT_REQUIRE(d_params_per_mode && d_classes && modes && out && d_ws, "chert_surrogate_cache: NULL");
     CHERT_REQUIRE(n_classes >= 1 && M >= 1 && n_modes >= 1 && n_modes <= 3, "chert_surrogate_cache: counts");
     CHERT_REQUIRE(out->V && out->rx && out->rz && out->flag, "chert_surrogate_cache: outputs");
@@ -655,7 +696,7 @@ extern "C" int chert_surrogate_cache(const float* const* d_params_per_mode, cons
             const long long n = (long long)nc * (M + 1);
             features_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_classes + k0, nc, M, modes[mi], x, Vg, psi,
                                                               A0, outside);
-            int rc = chert_mlp_forward(prm, x, n, y, p, rest, stream);
+            int rc = forward_enqueue(prm, x, n, y, p, rest, s, "chert_surrogate_cache");
             if (rc) return rc;
             if (precision == CHERT_FP64)
                 decode_kernel<double><<<grid_for(n, 256), 256, 0, s>>>(d_classes, n_classes, k0, nc, M, mi,
@@ -669,5 +710,6 @@ extern "C" int chert_surrogate_cache(const float* const* d_params_per_mode, cons
                                                                      A0, outside, qsv_angle, *out);
         }
     }
-    return launch_check("chert_surrogate_cache");
+    const int rc = launch_check("chert_surrogate_cache");
+    return rc || !check ? rc : gemm::tc::check_and_clear(s, "chert_surrogate_cache");
 }

@@ -13,8 +13,10 @@
 //     tcgen05.ld.32x32b (warp w: lanes 32*(w%4).., column half w/4) and apply
 //     the epilogue through a shared-memory transpose (coalesced stores).
 // Every mbarrier wait is bounded: on timeout the kernel records an error in
-// g_tc_error, stops issuing work, waits (bounded) for the tensor cores, frees
-// its tensor memory and returns.
+// g_tc_error, stops issuing work, waits (bounded) for its TMA loads in flight
+// and for the tensor cores, frees its tensor memory and returns.  The poll
+// limit of the main loop's waits is g_tc_wait_limit (settable, so that a
+// test can make a wait run out); the draining waits keep the fixed kSpin.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -25,13 +27,19 @@
 namespace chert {
 namespace gemm {
 
-__device__ int g_tc_error;          // 0 = ok; set on a timed-out wait
+__device__ int g_tc_error;          // 0 = ok; 1 = a main-loop wait timed out, 2 = the accumulator wait,
+                                    // 3 = a TMA load still in flight after the drain
 
 namespace tc {
 
 constexpr int kStages = 3;
 constexpr int kKChunk = 64;          // bf16 elements = 128 bytes = one swizzle row
 constexpr long long kSpin = 1 << 22; // bounded waits
+}  // namespace tc
+
+__device__ long long g_tc_wait_limit = tc::kSpin;   // polls of the main loop's waits
+
+namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -46,10 +54,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
-// Bounded wait on an mbarrier phase; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait on an mbarrier phase (at most `limit` polls); returns false on
+// timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kSpin) {
     const uint32_t a = smem_u32(bar);
-    for (long long i = 0; i < kSpin; ++i) {
+    for (long long i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -172,37 +185,53 @@ __global__ void __launch_bounds__(256, 1) nt_tc_kernel(const __grid_constant__ C
     if (tid == 0) {
         s_fail = 0;
         const uint32_t idesc = instr_desc(NT);
+        const long long limit = g_tc_wait_limit;
         bool ok = true;
+        // pending[st]: the K chunk whose TMA load into stage st has not been
+        // waited for yet, or -1
+        int pending[kStages];
+        for (int i = 0; i < kStages; ++i) pending[i] = -1;
         const int pre = nk < kStages ? nk : kStages;
         for (int c = 0; c < pre; ++c) {
             mbar_expect_tx(&s.full[c], kBytes);
             tma_load_2d(s.a[c], &ta, c * kKChunk, m0, &s.full[c]);
             tma_load_2d(s.b[c], &tb, c * kKChunk, n0, &s.full[c]);
+            pending[c] = c;
         }
         int issued = 0;
         for (int c = 0; c < nk && ok; ++c) {
             const int st = c % kStages;
-            ok = mbar_wait(&s.full[st], (c / kStages) & 1);
+            ok = mbar_wait(&s.full[st], (c / kStages) & 1, limit);
             if (!ok) break;
+            pending[st] = -1;
+            ++issued;
             fence_after_sync();
 #pragma unroll
             for (int kk = 0; kk < kKChunk / 16; ++kk)
                 mma_bf16(tmem, smem_desc(s.a[st] + kk * 16), smem_desc(s.b[st] + kk * 16), idesc,
                          (c > 0 || kk > 0) ? 1u : 0u);
             mma_commit(&s.empty[st]);
-            ++issued;
             const int nxt = c + kStages;
             if (nxt < nk) {
-                ok = mbar_wait(&s.empty[st], (c / kStages) & 1);   // tensor cores done with this stage
+                ok = mbar_wait(&s.empty[st], (c / kStages) & 1, limit);   // tensor cores done with this stage
                 if (!ok) break;
                 mbar_expect_tx(&s.full[st], kBytes);
                 tma_load_2d(s.a[st], &ta, nxt * kKChunk, m0, &s.full[st]);
                 tma_load_2d(s.b[st], &tb, nxt * kKChunk, n0, &s.full[st]);
+                pending[st] = nxt;
             }
         }
-        mma_commit(&s.done);
-        if (!ok) { s_fail = 1; atomicExch(&g_tc_error, 1); }
-        (void)issued;
+        int code = ok ? 0 : 1;
+        if (!ok) {
+            // the loads in flight land before the CTA gives up its shared memory
+            for (int i = 0; i < kStages; ++i)
+                if (pending[i] >= 0 && !mbar_wait(&s.full[i], (pending[i] / kStages) & 1)) code = 3;
+        }
+        if (issued)
+            mma_commit(&s.done);            // arrives once the issued MMAs are complete
+        else
+            mbar_arrive(&s.done);           // nothing in the tensor cores
+        if (code) { s_fail = 1; atomicExch(&g_tc_error, code); }
     }
     // all threads: wait for the accumulator (bounded; commits arrive even after a failure)
     const bool done = mbar_wait(&s.done, 0);

@@ -80,21 +80,17 @@ def train(x, t, steps=2000, batch=4096, lr=2e-3, seed=0, log_every=0):
     return params, history
 
 
-def per_cell_cache(d_classes, n_cells, modes, M, params_per_mode=None, precision="mixed", out=None):
+def per_cell_cache(d_classes, n_cells, modes, M, params_per_mode=None, precision="mixed", out=None, stream=None):
     """Cache with one class per cell: exact (params_per_mode None) or from the
     networks, with every solve they hand back (flag 2: outside the training
-    range, unsure validity, qSV branch region) recomputed by the exact solver.
-    out: optional preallocated cache arrays (the layout of build_cache)."""
-    import torch
+    range, unsure validity, qSV branch region) recomputed by the exact solver
+    -- chert_cache_surrogate, which keeps the fallback list on the device, so
+    this enqueues without a host read (and can be captured into a graph).
+    out: optional preallocated cache arrays (the layout of build_cache).
+    The surrogate form's cache.n_fallback reads the number of exact solves
+    (one device-to-host copy)."""
     if params_per_mode is None:
-        return chert.build_cache(d_classes, n_cells, modes, M, kernel="MEV", precision=precision, out=out)
-    cache = chert.surrogate_cache(params_per_mode, d_classes, n_cells, modes, M,
-                                  precision="fp64" if precision == "fp64" else "fp32", out=out)
-    # solve j of (mode slot, class) writes entry d = j (d = M for j = M)
-    first = cache["flag"][:, :, :M + 1]
-    items = torch.nonzero(first.reshape(-1) == 2).flatten()
-    if items.numel():
-        chert.build_cache_items(cache, d_classes, items.to(torch.int64).contiguous(),
-                                precision="fp64" if precision == "fp64" else precision)
-    cache.n_fallback = int(items.numel())
-    return cache
+        return chert.build_cache(d_classes, n_cells, modes, M, kernel="MEV", precision=precision, out=out,
+                                 stream=stream)
+    return chert.cache_surrogate(params_per_mode, d_classes, n_cells, modes, M, kernel="MEV",
+                                 precision=precision, out=out, stream=stream)

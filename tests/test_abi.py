@@ -56,6 +56,22 @@ def test_thomsen_to_class_rejects_bad_input(lib):
     assert "delta" in lib.chert_last_error().decode()
 
 
+def test_moduli_to_class_table2_layer1(lib):
+    """Eq. 2 in the library for the paper's Table 2 layer 1 (moduli in
+    (km/s)^2 and one Q per component): aI = aR / Q, an infinite Q elastic."""
+    aR = [14.40e6, 4.50e6, 9.00e6, 2.25e6, 3.00e6]
+    q = [30.0, 15.0, 20.0, 15.0, 12.0]
+    c = chert.table_class(aR, q, tilt=0.25)
+    assert list(c.aR) == aR
+    assert list(c.aI) == [0.48e6, 0.3e6, 0.45e6, 0.15e6, 0.25e6]
+    assert c.tilt == 0.25 and c.rho == 2200.0
+    c = chert.table_class(aR, [math.inf] * 5)
+    assert list(c.aI) == [0.0] * 5
+    with pytest.raises(chert.ChertError) as e:
+        chert.table_class(aR, [30.0, 15.0, 0.0, 15.0, 12.0])
+    assert e.value.code == chert.EINVAL and "component 2" in lib.chert_last_error().decode()
+
+
 def test_workspace_query(lib):
     a = chert.workspace_bytes(3, 8, 80, chert.FP32, 64)
     b = chert.workspace_bytes(3, 8, 80, chert.FP64, 64)

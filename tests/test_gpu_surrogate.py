@@ -206,3 +206,95 @@ def test_trained_surrogate_beats_elastic_baseline(torch_dev):
             assert np.allclose(su["A"][mi][ok], bA[ok], rtol=1e-6)
         else:
             assert rel(su["A"][mi], "A") < 2e-4, (m, rel(su["A"][mi], "A"))
+
+
+def _decisive_nets(torch):
+    """Untrained networks of the three modes whose validity logit (output 3)
+    is scaled up, so that they call some solves valid, some invalid and leave
+    some to the exact solver."""
+    params = []
+    for i in range(3):
+        layers, mean, std = _net(40 + i)
+        W, b = layers[-1]
+        W = W.copy()
+        W[3] *= 400.0
+        layers = layers[:-1] + [(W, b)]
+        params.append(torch.as_tensor(surrogate.pack_params(layers, mean, std), device="cuda"))
+    return params
+
+
+def test_cache_surrogate_one_call_equals_composed_flow(torch_dev):
+    """chert_cache_surrogate (networks, then the flag-2 solves compacted on the
+    device and recomputed exactly, with no host read) against the same steps
+    composed on the host (chert_surrogate_cache, the list of flag-2 solves,
+    chert_build_cache_items), bit for bit, with the same count of exact
+    solves; no entry is left with flag 2; a CUDA-graph capture of the call
+    replays the same cache."""
+    torch = torch_dev
+    modes, M, n = ["qP", "qSV", "qSH"], 30, 40
+    params = _decisive_nets(torch)
+    d_cls = chert.classes_to_device(chert.classes_from_layers(inputs.random_tti_classes(n, seed=7)))
+    ref = chert.surrogate_cache(params, d_cls, n, modes, M, precision="fp32")
+    items = torch.nonzero(ref["flag"][:, :, :M + 1].reshape(-1) == 2).flatten().to(torch.int64).contiguous()
+    assert 0 < items.numel() < 3 * n * (M + 1)
+    chert.build_cache_items(ref, d_cls, items, precision="mixed")
+    got = chert.cache_surrogate(params, d_cls, n, modes, M, precision="mixed")
+    torch.cuda.synchronize()
+    assert got.n_fallback == items.numel()
+    for k in ref.arrays:
+        assert torch.equal(torch.nan_to_num(ref[k].float(), nan=-7.0), torch.nan_to_num(got[k].float(), nan=-7.0)), k
+    assert not bool((got["flag"] == 2).any())
+    # captured into a graph: the same cache on replay
+    out = {k: torch.full_like(v, 0) for k, v in got.arrays.items()}
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        cap = chert.cache_surrogate(params, d_cls, n, modes, M, precision="mixed", out=out,
+                                    stream=torch.cuda.current_stream())
+    for _ in range(2):
+        for v in out.values():
+            v.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(cap.n_fallback_dev.item()) == items.numel()
+        for k in ref.arrays:
+            assert torch.equal(torch.nan_to_num(out[k].float(), nan=-7.0), torch.nan_to_num(got[k].float(), nan=-7.0)), k
+
+
+def test_tensor_core_wait_that_runs_out_is_reported(torch_dev):
+    """The bounded mbarrier waits of the tcgen05 GEMM: with the main-loop poll
+    limit set to 0 every wait runs out at once (the TMA loads are still in
+    flight), the kernel drains its loads, frees its tensor memory and returns,
+    and chert_mlp_forward reports CHERT_ETIMEOUT.  chert_cache_surrogate then
+    hands every solve to the exact solver, so its cache equals the exact
+    build, and chert_mlp_check reports the time-out once.  With the limit
+    restored the same context gives the same outputs as before."""
+    torch = torch_dev
+    modes, M, n = ["qP", "qSV", "qSH"], 30, 40
+    params = _decisive_nets(torch)
+    x = torch.as_tensor(_x(1000, 4), dtype=torch.float32, device="cuda")
+    y0 = chert.mlp_forward(params[0], x)
+    d_cls = chert.classes_to_device(chert.classes_from_layers(inputs.random_tti_classes(n, seed=7)))
+    exact = chert.build_cache(d_cls, n, modes, M, kernel="MEV", precision="mixed")
+    torch.cuda.synchronize()
+    prev = chert.mlp_set_wait_limit(0)
+    try:
+        assert prev == 1 << 22
+        with pytest.raises(chert.ChertError) as e:
+            chert.mlp_forward(params[0], x)
+        assert e.value.code == chert.ETIMEOUT
+        c = chert.cache_surrogate(params, d_cls, n, modes, M, precision="mixed")
+        torch.cuda.synchronize()
+        assert c.n_fallback == len(modes) * n * (M + 1)
+        with pytest.raises(chert.ChertError) as e:
+            chert.mlp_check()
+        assert e.value.code == chert.ETIMEOUT
+    finally:
+        chert.mlp_set_wait_limit(prev)
+    chert.mlp_check()
+    for k in exact.arrays:
+        assert torch.equal(torch.nan_to_num(exact[k].float(), nan=-7.0), torch.nan_to_num(c[k].float(), nan=-7.0)), k
+    y1 = chert.mlp_forward(params[0], x)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1)
