@@ -506,6 +506,10 @@ def surrogate_section(n_sources, flush, log=None, qsv_angles_deg=(1.0,)):
         if prm is not None:
             r["solves_recomputed_exactly"] = int(cache.n_fallback)
             r["solves_total"] = n * len(MODES) * (M + 1)
+            # nodewise angular coverage; missing angles against the exact (plain) cache
+            r["coverage"] = coverage_summary(cache, off, None, bufs[0]["flag"])
+        else:
+            r["coverage"] = coverage_summary(cache, off)
         return r
 
     def errors():
@@ -668,6 +672,40 @@ def section_3d(flush, n_sources=16):
             "edge_relaxations_per_s": edges * nf * 2 / t_relax, "directed_edges_per_field": edges}
 
 
+# --------------------------------------------------------------- angular coverage
+def coverage_summary(cache, off, class_of_node=None, truth_flag=None):
+    """Per-node angular coverage of a 2D cache (chert_angular_coverage), per
+    mode: over the model's nodes (each node takes its class's counts;
+    class_of_node None: one class per node), the mean and minimum coverage
+    ratio (covered stencil directions / stencil directions), the fraction of
+    nodes with full coverage, the mean branch-mismatch ratio (mismatched /
+    covered directions) and the fraction of nodes with any mismatch, and --
+    with a reference cache's flags -- the mean and maximum missing-angle ratio
+    (entries valid in the reference but flagged here / entries)."""
+    import torch
+    from paper_2609_26108_b300 import chert
+
+    covd, mis, miss = chert.angular_coverage(cache, off, truth_flag=truth_flag)
+    n_off = len(off)
+    out = {}
+    for mi, m in enumerate(MODES[:len(cache.modes)]):
+        c, x, g = covd[mi].double(), mis[mi].double(), miss[mi].double()
+        if class_of_node is not None:
+            idx = class_of_node.long()
+            c, x, g = c[idx], x[idx], g[idx]
+        cr = c / n_off
+        mr = torch.where(c > 0, x / c.clamp_min(1), torch.zeros_like(x))
+        r = {"coverage_ratio_mean": float(cr.mean()), "coverage_ratio_min": float(cr.min()),
+             "nodes_full_coverage": float((c == n_off).double().mean()),
+             "branch_mismatch_ratio_mean": float(mr.mean()), "nodes_with_mismatch": float((x > 0).double().mean())}
+        if truth_flag is not None:
+            gr = g / cache.n_dir
+            r["missing_angle_ratio_mean"] = float(gr.mean())
+            r["missing_angle_ratio_max"] = float(gr.max())
+        out[m] = r
+    return out
+
+
 # --------------------------------------------------------------- angular step
 def section_angular(n_sources=8, steps_deg=(0.5, 1.0, 2.0, 5.0, 10.0)):
     """Cache angular-step study on the layered 401x401 model: caches of
@@ -711,6 +749,10 @@ def section_angular(n_sources=8, steps_deg=(0.5, 1.0, 2.0, 5.0, 10.0)):
         for mi, m in enumerate(MODES):
             a = ang[mi][idx[mi] >= 0]
             row["lookup_angle_deg_%s" % m] = {"mean": float(a.mean()), "max": float(a.max())}
+        # nodewise angular coverage; missing angles against the FP64 cache of the same step
+        truth = chert.build_cache(d_classes, nk, MODES, M, SCAN_STEP, SCAN_HALF, "MEV", "fp64")
+        row["coverage"] = coverage_summary(cache, off, d_cls, truth["flag"])
+        del truth
         if ref is None:
             ref = [f.double().clone() for f in fields[:2]]
         else:
@@ -723,6 +765,70 @@ def section_angular(n_sources=8, steps_deg=(0.5, 1.0, 2.0, 5.0, 10.0)):
         rows.append(row)
     return {"workload": "layered_visco_tti_2d_401x401_8layers_%dsrc_3modes_R5, caches %s deg"
                         % (len(model.sources), list(steps_deg)), "reference": "0.5 deg fields", "rows": rows}
+
+
+def section_angular_cells(n_sources=8, steps_deg=(0.5, 1.0, 2.0, 5.0, 10.0), n_truth=4096):
+    """The angular-step study on the per-cell folded and faulted 1701x351
+    model (597,051 cells, each its own medium): exact MIXED per-cell caches
+    at 0.5 to 10 deg, n_sources surface sources x 3 modes, FP32 relaxation;
+    per step the RMS relative tau misfit against the 0.5 deg fields and the
+    nodewise angular coverage over all nodes.  Missing angles are counted on
+    n_truth seeded cells against their FP64 caches of the same step."""
+    import torch
+    from paper_2609_26108_b300 import chert
+
+    model = inputs.folded_faulted(n_sources=n_sources)
+    n = model.nx * model.nz
+    p = model.params
+    keys = ["vp0", "vs0", "eps", "delta", "gamma", "qp", "qs", "tilt"]
+    d_cells = chert.classes_to_device(chert.classes_from_arrays(**{k: p[k] for k in keys}))
+    d_cls = torch.arange(n, dtype=torch.int32, device="cuda")
+    off = inputs.stencil_2d(RADIUS)
+    src = [int(v) for v in model.sources]
+    pick = np.sort(np.random.default_rng(1007).choice(n, n_truth, replace=False))
+    sub = {k: p[k][pick] for k in keys}
+    d_sub = chert.classes_to_device(chert.classes_from_arrays(**sub))
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b) / 1e3
+
+    rows, ref = [], None
+    for deg in steps_deg:
+        M = int(round(90.0 / deg))
+        cache, t_c = timed(lambda: chert.build_cache(d_cells, n, MODES, M, SCAN_STEP, SCAN_HALF, "MEV", "mixed"))
+        fields, t_r = timed(lambda: chert.traveltime(cache, model.nx, model.nz, model.dx, d_cls, off, src,
+                                                     max_cycles=SURR_MAX_CYCLES))
+        row = {"step_deg": deg, "cache_s": t_c, "relax_s": t_r, "coverage": coverage_summary(cache, off)}
+        del cache
+        mixed = chert.build_cache(d_sub, n_truth, MODES, M, SCAN_STEP, SCAN_HALF, "MEV", "mixed")
+        truth = chert.build_cache(d_sub, n_truth, MODES, M, SCAN_STEP, SCAN_HALF, "MEV", "fp64")
+        sc = coverage_summary(mixed, off, None, truth["flag"])
+        for m in sc:
+            row["coverage"][m]["missing_angle_ratio_mean_sampled"] = sc[m]["missing_angle_ratio_mean"]
+            row["coverage"][m]["missing_angle_ratio_max_sampled"] = sc[m]["missing_angle_ratio_max"]
+        del mixed, truth
+        if ref is None:
+            ref = [f.double().clone() for f in fields[:2]]
+        else:
+            for comp, name in ((0, "tauR"), (1, "tauI")):
+                for mi, m in enumerate(MODES):
+                    r = ref[comp][:, mi]
+                    g = fields[comp][:, mi].double()
+                    ok = torch.isfinite(r) & (r > 0) & torch.isfinite(g)
+                    rel = ((g - r) / r)[ok]
+                    row["rms_rel_misfit_%s_%s" % (name, m)] = float((rel ** 2).mean().sqrt())
+                    row["median_abs_rel_misfit_%s_%s" % (name, m)] = float(rel.abs().median())
+        del fields
+        rows.append(row)
+    return {"workload": "folded_faulted_visco_tti_2d_1701x351_per_cell_%dsrc_3modes_R5, caches %s deg"
+                        % (len(src), list(steps_deg)),
+            "reference": "0.5 deg fields; missing angles on %d seeded cells against FP64" % n_truth, "rows": rows}
 
 
 # --------------------------------------------------------------- scheduler study
@@ -980,6 +1086,8 @@ def run_chert(args):
         out["lattice_3d"] = section_3d(flush, args.sources_3d)
     if world == 1 and args.angular_study:
         out["angular_study"] = section_angular()
+    if world == 1 and args.angular_study_cells:
+        out["angular_study_cells"] = section_angular_cells()
     if world == 1 and args.scheduler_study > 0:
         out["scheduler_study"] = section_scheduler(args.scheduler_study)
     if world == 1 and args.batch_sources > 0:
@@ -1024,6 +1132,8 @@ def main():
                     help="surface sources (64 = the benchmark workload; fewer only for profiling)")
     ap.add_argument("--angular-study", action="store_true",
                     help="add the cache angular-step study (0.5-10 deg) on the layered model")
+    ap.add_argument("--angular-study-cells", action="store_true",
+                    help="add the cache angular-step study (0.5-10 deg) on the per-cell folded model")
     ap.add_argument("--batch-sources", type=int, default=0,
                     help="sources of the per-cell 2D problem in the CUDA-graph batch (0, the default: leave it "
                          "out; the measured batch is --batch-sources 64 --batch-sources-3d 16)")

@@ -192,6 +192,32 @@ int chert_edge_table(const chert_cache_arrays* cache, int n_modes, int n_classes
                      int n_dir, int precision, const int32_t* offsets, int n_off,
                      int32_t* d_idx, void* d_Vsel, void* d_Asel, void* stream);
 
+/* Nodewise angular coverage of a 2D cache (the paper's angular-coverage
+ * validation; it names coverage ratio, missing-angle ratio and branch
+ * mismatch without formulas -- this is one reading).  For every (mode, class)
+ * k and stencil direction d = o/|o|:
+ *   covered     two cyclically adjacent valid entries e, e+1 whose ray
+ *               directions are less than 90 deg apart hold d on the closed
+ *               short arc between them (a bracket);
+ *   mismatched  d is covered, and the entry of chert_edge_table's lookup is
+ *               neither end of the first-arrival bracket: the bracket with the
+ *               largest ray velocity interpolated at d, V_e + t (V_e+1 - V_e)
+ *               with t = cross(r_e, d) / cross(r_e, r_e+1), ties to the lower
+ *               e (at a qSV fold, the path search would take a slower branch).
+ * and, with a reference cache's flags (d_truth_flag, same layout; may be
+ * NULL), missing = entries valid in the reference but flagged here.
+ * Bracket arithmetic in double, each operation rounded separately; the
+ * lookup in the cache's precision as chert_edge_table.  cache: rx, rz, V,
+ * flag of [n_modes][n_classes][n_dir] (n_dir = 4M).  offsets: host int32
+ * [n_off][3], oy = 0, 1 <= n_off <= 512.  Outputs: device int32
+ * [n_modes][n_classes] each (covered and mismatched count directions, out of
+ * n_off; missing counts entries, out of n_dir).
+ * Errors: CHERT_EINVAL (NULL, counts, 3D offsets), CHERT_ECUDA. */
+int chert_angular_coverage(const chert_cache_arrays* cache, int n_modes, int n_classes, int n_dir,
+                           int precision, const int32_t* offsets, int n_off,
+                           const uint8_t* d_truth_flag, int32_t* d_covered, int32_t* d_mismatched,
+                           int32_t* d_missing, void* stream);
+
 /* ---- traveltime relaxation (Eq. 22, 27-33) ------------------------------ */
 
 /* Scratch bytes chert_traveltime needs for this problem size (the class

@@ -18,6 +18,9 @@ Hamiltonian-Enhanced Ray Tracing in Viscoelastic Anisotropic Media"):
   with no table shared between nodes, then the same lookup and Dijkstra.
 * ``mlp_oracle`` -- the cache surrogate's network, loss, Adam, BF16 rounding
   and target parametrisation.
+* ``coverage_oracle`` -- the nodewise angular-coverage counts (covered stencil
+  directions, branch mismatches at folds, missing angles) of one reading of
+  the paper's angular-coverage validation.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 leg may import or execute anything here.  The product path never does; it
@@ -39,4 +42,7 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
   brute force over Floyd-Warshall distances.
 * node_tables, no_cache_fields -- pinned to the cached path (identical
   tables, fields and parents where nodes share a medium).
+* coverage_counts, brackets -- pinned by the isotropic closed form,
+  hand-built holes, a hand-built fold with known branch velocities, planted
+  missing entries, and the convex qP/qSH caches of the layered model.
 """

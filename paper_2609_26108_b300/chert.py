@@ -121,6 +121,8 @@ def lib():
     L.chert_surrogate_cache_workspace_bytes.restype = SZ
     L.chert_surrogate_cache_workspace_bytes.argtypes = [I, I]
     L.chert_surrogate_cache.argtypes = [P, P, I, P, I, I, I, ctypes.POINTER(chert_cache_arrays), P, SZ, P]
+    L.chert_angular_coverage.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, P, I, P, P, P, P, P]
+    L.chert_angular_coverage.restype = ctypes.c_int
     L.chert_mlp_check.argtypes = [P]
     L.chert_mlp_check.restype = ctypes.c_int
     L.chert_mlp_set_wait_limit.argtypes = [ctypes.c_longlong]
@@ -635,6 +637,21 @@ def cache_surrogate(params_per_mode, d_classes, n_classes, modes, M, scan_step=0
                                        _dev_ptr(cache.n_fallback_dev), _stream_ptr(stream)))
     cache.workspace = ws
     return cache
+
+
+def angular_coverage(cache, offsets, truth_flag=None, stream=None):
+    """chert_angular_coverage for a 2D Cache: (covered, mismatched, missing)
+    device int32 tensors [n_modes, n_classes]."""
+    torch = _torch()
+    off, off_p = _offsets_arr(offsets)
+    nm, nk = len(cache.modes), cache.n_classes
+    dev = cache["V"].device
+    outs = [torch.empty((nm, nk), dtype=torch.int32, device=dev) for _ in range(3)]
+    st = cache.struct()
+    _check(lib().chert_angular_coverage(ctypes.byref(st), nm, nk, cache.n_dir, cache.precision, off_p, len(off),
+                                        None if truth_flag is None else _dev_ptr(truth_flag),
+                                        *[_dev_ptr(t) for t in outs], _stream_ptr(stream)))
+    return tuple(outs)
 
 
 def mlp_check(stream=None):
