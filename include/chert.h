@@ -322,6 +322,45 @@ int chert_traveltime_enqueue(const chert_cache_arrays* cache, int n_modes, int n
                              int32_t* d_parI, void* d_workspace, size_t workspace_bytes, int32_t* d_status,
                              void* stream);
 
+/* 3D tile shape of the plane sweeps, process-wide: 0 (default) 32 x 16 nodes
+ * per tile, 1 64 x 8 (longer contiguous rows along x, more halo).  For an
+ * autotuner; the fields and parents do not depend on it.  Returns the
+ * previous setting, or CHERT_EINVAL. */
+int chert_set_relax3d_tile(int tile);
+
+/* One 3D lattice of chert_traveltime_batch: chert_traveltime_enqueue's
+ * arguments for it (its own cache, classes, class map, device sources,
+ * outputs, workspace of chert_traveltime_workspace_bytes and device status
+ * int32[2]); ny > 1. */
+typedef struct {
+    const chert_cache_arrays* cache;
+    int n_classes, n_dir;
+    int nx, ny, nz;
+    double dx;
+    const int32_t* d_class_of_node;
+    const int64_t* d_sources;
+    int n_sources;
+    void* d_tauR;
+    void* d_tauI;
+    int32_t* d_parR;
+    int32_t* d_parI;
+    void* d_workspace;
+    size_t workspace_bytes;
+    int32_t* d_status;
+} chert_lattice;
+
+/* Several 3D lattices of uneven size (up to 48; same modes, precision,
+ * stencil and cycle cap) relaxed in ONE persistent launch: every lattice's
+ * field components are work items, numbered largest lattice first; a grid of
+ * one wave of resident CTAs claims them from the device counter d_counter
+ * (device uint64, zeroed here on `stream`) until none is left, each item
+ * relaxed as chert_traveltime relaxes it (same fields, parents and status,
+ * bit for bit).  Edge tables and class checks run per lattice before it.  No
+ * host synchronisation: capturable.  Errors: as chert_traveltime_enqueue. */
+int chert_traveltime_batch(const chert_lattice* lattices, int n_lattices, int n_modes, int precision,
+                           const int32_t* offsets, int n_off, int max_cycles,
+                           unsigned long long* d_counter, void* stream);
+
 /* ---- cache surrogate (a learned stand-in for the cache build; no counterpart in the paper)
  * One MLP per wave mode, 7 -> 256 -> 256 -> 256 -> 256 -> 5 with SiLU hidden
  * activations, BF16 operands, FP32 accumulation and FP32 master weights.  It

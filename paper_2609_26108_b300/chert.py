@@ -45,6 +45,15 @@ class chert_cache_arrays(ctypes.Structure):
                 ("phi", ctypes.c_void_p)]
 
 
+class chert_lattice(ctypes.Structure):
+    _fields_ = [("cache", ctypes.c_void_p), ("n_classes", ctypes.c_int), ("n_dir", ctypes.c_int),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("dx", ctypes.c_double),
+                ("d_class_of_node", ctypes.c_void_p), ("d_sources", ctypes.c_void_p), ("n_sources", ctypes.c_int),
+                ("d_tauR", ctypes.c_void_p), ("d_tauI", ctypes.c_void_p), ("d_parR", ctypes.c_void_p),
+                ("d_parI", ctypes.c_void_p), ("d_workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("d_status", ctypes.c_void_p)]
+
+
 class chert_cache_params(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("scan_step", ctypes.c_double), ("scan_half", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("precision", ctypes.c_int)]
@@ -100,6 +109,10 @@ def lib():
     L.chert_traveltime_enqueue.argtypes = [ctypes.POINTER(chert_cache_arrays), I, I, I, I, I, I, D, P, P, I,
                                            P, I, I, I, P, P, P, P, P, SZ, P, P]
     L.chert_traveltime_enqueue.restype = ctypes.c_int
+    L.chert_traveltime_batch.argtypes = [P, I, I, I, P, I, I, P, P]
+    L.chert_traveltime_batch.restype = ctypes.c_int
+    L.chert_set_relax3d_tile.argtypes = [I]
+    L.chert_set_relax3d_tile.restype = ctypes.c_int
     L.chert_set_relax_points_per_thread.argtypes = [I]
     L.chert_set_relax_points_per_thread.restype = ctypes.c_int
     L.chert_set_relax_scheduler.argtypes = [I]
@@ -392,6 +405,42 @@ def traveltime_enqueue(cache, nx, nz, dx, d_cls, offsets, d_sources, out, worksp
                                           _dev_ptr(out[2]), _dev_ptr(out[3]), _dev_ptr(workspace),
                                           workspace.numel(), _dev_ptr(d_status), _stream_ptr(stream)))
     return out
+
+
+def traveltime_batch(items, offsets, d_counter, max_cycles=64, stream=None, precision=None):
+    """chert_traveltime_batch: several 3D lattices in one persistent launch.
+    items: list of dicts with cache (Cache), nx, ny, nz, dx, d_cls, d_sources,
+    out (tauR, tauI, parR, parI), workspace and d_status (as for
+    traveltime_enqueue); all caches share modes and precision (precision:
+    the caches' by default, or "fp32_acc64").  d_counter: device int64 [1]
+    (the work counter)."""
+    off, off_p = _offsets_arr(offsets)
+    keep = []
+    arr = (chert_lattice * len(items))()
+    for i, it in enumerate(items):
+        c = it["cache"]
+        st = c.struct()
+        keep.append(st)
+        o = it["out"]
+        arr[i] = chert_lattice(ctypes.addressof(st), c.n_classes, c.n_dir, it["nx"], it["ny"], it["nz"],
+                               float(it["dx"]), it["d_cls"].data_ptr(), it["d_sources"].data_ptr(),
+                               int(it["d_sources"].numel()), o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(),
+                               o[3].data_ptr(), it["workspace"].data_ptr(), it["workspace"].numel(),
+                               it["d_status"].data_ptr())
+    c0 = items[0]["cache"]
+    prec = c0.precision if precision is None else (PRECISION_IDS[precision] if isinstance(precision, str)
+                                                   else precision)
+    _check(lib().chert_traveltime_batch(arr, len(items), len(c0.modes), prec, off_p, len(off), max_cycles,
+                                        _dev_ptr(d_counter), _stream_ptr(stream)))
+
+
+def set_relax3d_tile(tile):
+    """3D tile shape of every later 3D relaxation: 0 (32 x 16, default) or 1
+    (64 x 8); returns the previous one."""
+    rc = int(lib().chert_set_relax3d_tile(int(tile)))
+    if rc < 0:
+        _check(rc)
+    return rc
 
 
 def traveltime_static(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64, parents=True,

@@ -24,6 +24,7 @@
 #include <atomic>
 #include <type_traits>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "ff.cuh"
@@ -747,6 +748,8 @@ __global__ void __launch_bounds__(1024) relax_bhm_std_kernel(FieldArgs a, Offset
 // best is skipped without reading its class or weight (weights are >= 0, so
 // it cannot improve).  The verification pass stages planes z-H..z+H and
 // applies the 2D parent rule.
+// 3D tile shapes (in-plane u x v nodes, one thread per node of a 512-thread
+// CTA): 0 = 32 x 16 (the default), 1 = 64 x 8 (longer rows along x).
 constexpr int kTU = 32, kTV = 16;
 
 struct Stage3 {
@@ -833,7 +836,7 @@ __device__ __forceinline__ void stage_planes(T* st, int* sk, const T* tau, const
 
 // TW: weight type; TA: traveltime accumulation and storage type (double,
 // float, or float-float pairs for float weights with ~48-bit accumulation).
-template <typename TW, typename TA, int WMODE>
+template <typename TW, typename TA, int WMODE, int TU, int TV>
 __device__ bool sweep3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const Offsets& off, const short* qo,
                         const short* qu, const short* qv, const short* ql, int cnt, int axis, int dir, TA* tau,
                         const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk, int comp, TA* st, int* sk,
@@ -842,18 +845,18 @@ __device__ bool sweep3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const O
     const int nv = axis == 2 ? ny : nz;
     const int np = axis == 2 ? nz : axis == 1 ? ny : nx;
     const int per = g.SU * g.SV;
-    const int ntu = (nu + kTU - 1) / kTU;
+    const int ntu = (nu + TU - 1) / TU;
     bool changed = false;
     for (int step = 0; step < np && !part.failed; ++step) {
         const int p = dir > 0 ? step : np - 1 - step;
-        for (int tv0 = 0; tv0 < nv; tv0 += kTV) {
-            for (int tu0 = 0; tu0 < nu; tu0 += kTU) {
-                if (((tv0 / kTV) * ntu + tu0 / kTU) % part.parts != part.part) continue;
+        for (int tv0 = 0; tv0 < nv; tv0 += TV) {
+            for (int tu0 = 0; tu0 < nu; tu0 += TU) {
+                if (((tv0 / TV) * ntu + tu0 / TU) % part.parts != part.part) continue;
                 // planes p - dir*1 .. p - dir*H at stage slots 0 .. H-1
                 stage_planes(st, sk, tau, cls, nk, axis, nu, nv, np, p - dir, -dir, g.H, tu0, tv0, g, nx, ny);
                 __syncthreads();
-                const int u = tu0 + (int)(threadIdx.x % kTU), v = tv0 + (int)(threadIdx.x / kTU);
-                if (threadIdx.x < kTU * kTV && u < nu && v < nv) {
+                const int u = tu0 + (int)(threadIdx.x % TU), v = tv0 + (int)(threadIdx.x / TU);
+                if (threadIdx.x < TU * TV && u < nu && v < nv) {
                     const long long j = node3(axis, u, v, p, nx, ny);
                     const int kj = clamp_class(cls[j], nk);
                     const TA cur = ld_tau(tau + j);
@@ -878,22 +881,22 @@ __device__ bool sweep3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const O
     return __syncthreads_or(changed);
 }
 
-template <typename TW, typename TA, int WMODE>
+template <typename TW, typename TA, int WMODE, int TU, int TV>
 __device__ bool verify3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const Offsets& off, TA* tau,
                          const int32_t* __restrict__ cls, int nx, int ny, int nz, int nk, int comp, int64_t src,
                          int32_t* par, TA* st, int* sk, const Stage3& g, Part3& part) {
     const int per = g.SU * g.SV;
-    const int ntx = (nx + kTU - 1) / kTU;
+    const int ntx = (nx + TU - 1) / TU;
     bool changed = false;
     for (int z = 0; z < nz && !part.failed; ++z) {
-        for (int ty0 = 0; ty0 < ny; ty0 += kTV) {
-            for (int tx0 = 0; tx0 < nx; tx0 += kTU) {
-                if (((ty0 / kTV) * ntx + tx0 / kTU) % part.parts != part.part) continue;
+        for (int ty0 = 0; ty0 < ny; ty0 += TV) {
+            for (int tx0 = 0; tx0 < nx; tx0 += TU) {
+                if (((ty0 / TV) * ntx + tx0 / TU) % part.parts != part.part) continue;
                 // planes z-H .. z+H at stage slots 0 .. 2H
                 stage_planes(st, sk, tau, cls, nk, 2, nx, ny, nz, z - g.H, 1, 2 * g.H + 1, tx0, ty0, g, nx, ny);
                 __syncthreads();
-                const int x = tx0 + (int)(threadIdx.x % kTU), y = ty0 + (int)(threadIdx.x / kTU);
-                if (threadIdx.x < kTU * kTV && x < nx && y < ny) {
+                const int x = tx0 + (int)(threadIdx.x % TU), y = ty0 + (int)(threadIdx.x / TU);
+                if (threadIdx.x < TU * TV && x < nx && y < ny) {
                     const long long j = node3(2, x, y, z, nx, ny);
                     const int kj = clamp_class(cls[j], nk);
                     const TA cur = ld_tau(tau + j);
@@ -928,21 +931,21 @@ __device__ bool verify3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const 
 // Shared memory of relax3d_kernel after the weight table: L [n_off], six
 // per-sweep lists of (offset, in-plane u, in-plane v, lag) as shorts, counts,
 // then the stage (tau, then class) for 2H+1 planes.
-__host__ __device__ inline size_t stage3_elems(int H) {
-    return (size_t)(2 * H + 1) * (kTU + 2 * H) * (kTV + 2 * H);
+__host__ __device__ inline size_t stage3_elems(int H, int TU = kTU, int TV = kTV) {
+    return (size_t)(2 * H + 1) * (TU + 2 * H) * (TV + 2 * H);
 }
 
 // TA = xf::ff: float weights, traveltimes accumulated as float-float pairs in
 // the (double) output arrays, converted to double in place at the end.
-template <typename T, typename TA, int WMODE>
-__global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, int H) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// One field component fc (= field * 2 + component) of one lattice, by the
+// CTA (or, parts > 1, by part `part_idx` of a cooperative group of CTAs).
+template <typename T, typename TA, int WMODE, int TU, int TV>
+__device__ void relax3d_field(const FieldArgs& a, const Offsets& off, int H, int fc, int part_idx,
+                              unsigned char* smem_raw) {
     const int nk = a.n_classes;
-    const int fc = blockIdx.x / a.parts;                  // field * 2 + component
     const int field = fc >> 1;
     const int comp = fc & 1;
-    Part3 part{(int)(blockIdx.x % a.parts), a.parts, a.parts > 1 ? a.sync + (size_t)fc * kSyncStride : nullptr,
-               0u, false};
+    Part3 part{part_idx, a.parts, a.parts > 1 ? a.sync + (size_t)fc * kSyncStride : nullptr, 0u, false};
     const int mode = field % a.n_modes;
     const int s = field / a.n_modes;
     const size_t n = (size_t)a.nx * a.ny * a.nz;
@@ -953,9 +956,9 @@ __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, 
                           : WMODE == 0 ? static_cast<size_t>(nk) * off.n : 0;
     sm.W = reinterpret_cast<T*>(p); p += wcount * sizeof(T);
     sm.L = reinterpret_cast<T*>(p); p += off.n * sizeof(T);
-    Stage3 g{H, kTU + 2 * H, kTV + 2 * H};
-    TA* st = reinterpret_cast<TA*>(p); p += stage3_elems(H) * sizeof(TA);
-    int* sk = reinterpret_cast<int*>(p); p += stage3_elems(H) * sizeof(int);
+    Stage3 g{H, TU + 2 * H, TV + 2 * H};
+    TA* st = reinterpret_cast<TA*>(p); p += stage3_elems(H, TU, TV) * sizeof(TA);
+    int* sk = reinterpret_cast<int*>(p); p += stage3_elems(H, TU, TV) * sizeof(int);
     sm.ring = nullptr;
     sm.cring = nullptr;
     short* lists = reinterpret_cast<short*>(p); p += 4 * 6 * off.n * sizeof(short);
@@ -1010,10 +1013,10 @@ __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, 
     int used = -1;
     for (int cycle = 0; cycle < a.max_cycles && !part.failed; ++cycle) {
         for (int l = 0; l < 6; ++l)
-            sweep3d<T, TA, WMODE>(sm, sel, off, lists + (4 * l) * off.n, lists + (4 * l + 1) * off.n,
+            sweep3d<T, TA, WMODE, TU, TV>(sm, sel, off, lists + (4 * l) * off.n, lists + (4 * l + 1) * off.n,
                               lists + (4 * l + 2) * off.n, lists + (4 * l + 3) * off.n, sm.counts[l], ax[l], dr[l],
                               tau, a.cls, a.nx, a.ny, a.nz, nk, comp, st, sk, g, part);
-        bool changed = verify3d<T, TA, WMODE>(sm, sel, off, tau, a.cls, a.nx, a.ny, a.nz, nk, comp, src, par, st,
+        bool changed = verify3d<T, TA, WMODE, TU, TV>(sm, sel, off, tau, a.cls, a.nx, a.ny, a.nz, nk, comp, src, par, st,
                                               sk, g, part);
         if (part.parts > 1) {
             // OR of the parts' verdicts in flag word 1 + (cycle & 1); the other
@@ -1039,6 +1042,47 @@ __global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, 
         }
     }
     if (threadIdx.x == 0 && part.part == 0) a.status[fc] = part.failed ? -1 : used;
+}
+
+template <typename T, typename TA, int WMODE, int TU, int TV>
+__global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, int H) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    relax3d_field<T, TA, WMODE, TU, TV>(a, off, H, (int)(blockIdx.x / a.parts), (int)(blockIdx.x % a.parts),
+                                        smem_raw);
+}
+
+// Several 3D lattices in one persistent launch: the work items are the field
+// components of every lattice, numbered lattice by lattice (start[l] .. 
+// start[l + 1] - 1; the host orders the lattices largest first, so that the
+// longest items start first).  Each CTA claims the next item from a device
+// counter (zeroed before the launch) until none is left, and relaxes it with
+// the lattice's own arguments from the table (a kernel parameter, read in
+// place).  One CTA per item: parts = 1 in every entry.
+constexpr int kMaxLattices = 48;
+
+struct LatticeTable {
+    int n;
+    long long start[kMaxLattices + 1];
+    FieldArgs a[kMaxLattices];
+};
+
+template <typename T, typename TA, int WMODE, int TU, int TV>
+__global__ void __launch_bounds__(512, 2) relax3d_multi_kernel(const __grid_constant__ LatticeTable t,
+                                                            const __grid_constant__ Offsets off, int H,
+                                                            unsigned long long* counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long s_item;
+    const long long total = t.start[t.n];
+    for (;;) {
+        __syncthreads();                      // the previous item's shared memory is no longer read
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        int l = 0;
+        while (l + 1 < t.n && t.start[l + 1] <= item) ++l;
+        relax3d_field<T, TA, WMODE, TU, TV>(t.a[l], off, H, (int)(item - t.start[l]), 0, smem_raw);
+    }
 }
 
 // ------------------------------------------------------------ parent ties
@@ -1203,9 +1247,9 @@ extern "C" int chert_edge_table(const chert_cache_arrays* cache, int n_modes, in
 // leave SMs idle, `parts` CTAs each (at most 8, every CTA of the grid
 // resident: a cooperative launch), sharing each plane's tiles.  Under stream
 // capture, one CTA per field component.
-template <typename T, int WMODE, typename TA = T>
+template <typename T, int WMODE, typename TA, int TU, int TV>
 static int launch_relax3d(FieldArgs a, const Offsets& off, int H, size_t smem, int blocks, cudaStream_t s) {
-    auto kern = relax3d_kernel<T, TA, WMODE>;
+    auto kern = relax3d_kernel<T, TA, WMODE, TU, TV>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime: smem attribute");
     int parts = 1;
@@ -1218,9 +1262,9 @@ static int launch_relax3d(FieldArgs a, const Offsets& off, int H, size_t smem, i
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem) == cudaSuccess && per_sm > 0) {
         const long long slots = (long long)per_sm * n_sm;
-        const int tiles = std::min({((a.nx + kTU - 1) / kTU) * ((a.ny + kTV - 1) / kTV),
-                                    ((a.nx + kTU - 1) / kTU) * ((a.nz + kTV - 1) / kTV),
-                                    ((a.ny + kTU - 1) / kTU) * ((a.nz + kTV - 1) / kTV)});
+        const int tiles = std::min({((a.nx + TU - 1) / TU) * ((a.ny + TV - 1) / TV),
+                                    ((a.nx + TU - 1) / TU) * ((a.nz + TV - 1) / TV),
+                                    ((a.ny + TU - 1) / TU) * ((a.nz + TV - 1) / TV)});
         parts = (int)std::max(1LL, std::min<long long>({8LL, slots / blocks, (long long)tiles}));
     }
     cudaGetLastError();
@@ -1432,6 +1476,38 @@ __global__ void node_weights_kernel(const T* __restrict__ selT, const int32_t* _
 // length; 1, 2 or 4 = forced where the line fits in 512 threads (set by
 // chert_set_relax_points_per_thread, e.g. by an autotuner).
 std::atomic<int> g_relax_ppt{0};
+std::atomic<int> g_relax3d_tile{0};           // 0: 32 x 16, 1: 64 x 8
+
+// Shared memory of the 3D kernels and their weight mode (1: class-pair table,
+// 0: per-class table, 2: tables in global memory) for n_classes classes.
+struct Smem3 {
+    int mode;
+    size_t bytes;
+};
+static Smem3 smem3(int n_classes, int n_off, int H, int precision, int tile, int smem_max) {
+    const size_t es = precision == CHERT_FP64 ? 8 : 4;
+    const size_t tas = precision == CHERT_FP32 || precision == CHERT_MIXED ? 4 : 8;   // accumulation type
+    const size_t st = tile == 1 ? stage3_elems(H, 64, 8) : stage3_elems(H, 32, 16);
+    const size_t base3 = n_off * es + st * (tas + 4) + 4 * 6 * n_off * 2 + 64;
+    const size_t t3 = (size_t)n_off * n_classes * n_classes * es + base3;
+    const size_t r3 = (size_t)n_classes * n_off * es + base3;
+    const int mode = t3 <= (size_t)std::min(smem_max, 160 * 1024) ? 1 : r3 <= (size_t)smem_max ? 0 : 2;
+    return {mode, mode == 1 ? t3 : mode == 0 ? r3 : base3};
+}
+
+// launch_relax3d for the process-wide tile shape and a weight mode
+template <typename T, typename TA>
+static int launch_relax3d_any(const FieldArgs& a, const Offsets& off, int H, const Smem3& m, int blocks,
+                              cudaStream_t s) {
+    const int tile = g_relax3d_tile.load();
+    if (tile == 1)
+        return m.mode == 1 ? launch_relax3d<T, 1, TA, 64, 8>(a, off, H, m.bytes, blocks, s)
+             : m.mode == 0 ? launch_relax3d<T, 0, TA, 64, 8>(a, off, H, m.bytes, blocks, s)
+                           : launch_relax3d<T, 2, TA, 64, 8>(a, off, H, m.bytes, blocks, s);
+    return m.mode == 1 ? launch_relax3d<T, 1, TA, 32, 16>(a, off, H, m.bytes, blocks, s)
+         : m.mode == 0 ? launch_relax3d<T, 0, TA, 32, 16>(a, off, H, m.bytes, blocks, s)
+                       : launch_relax3d<T, 2, TA, 32, 16>(a, off, H, m.bytes, blocks, s);
+}
 // 2D scheduler: 0 = ordered sweeps, 1 = block-heap marching, 2 (default) =
 // sweeps, then block-heap marching for the fields not yet converged.
 std::atomic<int> g_relax_sched{2};
@@ -1584,13 +1660,19 @@ extern "C" size_t chert_traveltime_workspace_bytes_grid(int n_modes, int n_class
 // `s`, using `w` (bytes long) as scratch.  On success *blocks_out is the number
 // of relaxation CTAs and *status_out points at their status words (followed by
 // the class-check flag), which the caller reads back.
+// A 3D lattice prepared (edge tables, class check, status) for a batched launch.
+struct Prep3 {
+    FieldArgs a;
+    int H, blocks;
+};
+
 static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, int n_modes,
                               int n_classes, int n_dir, int nx, int ny, int nz, double dx,
                               const int32_t* d_class_of_node, const int32_t* offsets, int n_off,
                               const int64_t* sources, int n_sources, int precision, int max_cycles,
                               void* d_tauR, void* d_tauI, int32_t* d_parR, int32_t* d_parI,
                               unsigned char* w, size_t bytes, cudaStream_t s, int* blocks_out,
-                              int** status_out, const int64_t* d_sources = nullptr) {
+                              int** status_out, const int64_t* d_sources = nullptr, Prep3* prep = nullptr) {
     CHERT_REQUIRE(nx >= 1 && ny >= 1 && nz >= 1 && (long long)nx * ny * nz < (1LL << 31),
                   "%s: bad lattice %d x %d x %d", who, nx, ny, nz);
     const long long n_nodes = (long long)nx * ny * nz;
@@ -1663,24 +1745,19 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         for (int i = 0; i < n_off; i++)
             H = std::max(H, std::max(abs((int)off.y[i]), std::max(abs((int)off.x[i]), abs((int)off.z[i]))));
         CHERT_REQUIRE(H <= 8, "%s: 3D offsets reach %d nodes (at most 8)", who, H);
-        const size_t tas = precision == CHERT_FP32 || precision == CHERT_MIXED ? 4 : 8;   // accumulation type
-        const size_t base3 = n_off * es + stage3_elems(H) * (tas + 4) + 4 * 6 * n_off * 2 + 64;
-        const size_t t3 = (size_t)n_off * n_classes * n_classes * es + base3;
-        const size_t r3 = (size_t)n_classes * n_off * es + base3;
-        const int mode3 = t3 <= (size_t)std::min(smem_max, 160 * 1024) ? 1 : r3 <= (size_t)smem_max ? 0 : 2;
-        const size_t sm3 = mode3 == 1 ? t3 : mode3 == 0 ? r3 : base3;
+        const Smem3 m3 = smem3(n_classes, n_off, H, precision, g_relax3d_tile.load(), smem_max);
+        if (prep) {                                    // a batched launch runs the relaxation
+            prep->a = a;
+            prep->H = H;
+            prep->blocks = blocks;
+            return CHERT_OK;
+        }
         if (precision == CHERT_FP32_ACC64)
-            rc = mode3 == 1 ? launch_relax3d<float, 1, xf::ff>(a, off, H, sm3, blocks, s)
-               : mode3 == 0 ? launch_relax3d<float, 0, xf::ff>(a, off, H, sm3, blocks, s)
-                            : launch_relax3d<float, 2, xf::ff>(a, off, H, sm3, blocks, s);
+            rc = launch_relax3d_any<float, xf::ff>(a, off, H, m3, blocks, s);
         else if (precision == CHERT_FP64)
-            rc = mode3 == 1 ? launch_relax3d<double, 1>(a, off, H, sm3, blocks, s)
-               : mode3 == 0 ? launch_relax3d<double, 0>(a, off, H, sm3, blocks, s)
-                            : launch_relax3d<double, 2>(a, off, H, sm3, blocks, s);
+            rc = launch_relax3d_any<double, double>(a, off, H, m3, blocks, s);
         else
-            rc = mode3 == 1 ? launch_relax3d<float, 1>(a, off, H, sm3, blocks, s)
-               : mode3 == 0 ? launch_relax3d<float, 0>(a, off, H, sm3, blocks, s)
-                            : launch_relax3d<float, 2>(a, off, H, sm3, blocks, s);
+            rc = launch_relax3d_any<float, float>(a, off, H, m3, blocks, s);
         if (rc) return rc;
         *blocks_out = blocks;
         *status_out = a.status;
@@ -1949,6 +2026,100 @@ extern "C" int chert_traveltime_enqueue(const chert_cache_arrays* cache, int n_m
     if (rc) return rc;
     status_summary_kernel<<<1, 256, 0, s>>>(status, blocks, d_status);
     return launch_check("chert_traveltime_enqueue: status");
+}
+
+template <typename T, typename TA, int TU, int TV>
+static int launch_multi3d(const LatticeTable& t, const Offsets& off, int H, const Smem3& m, long long items,
+                          unsigned long long* counter, cudaStream_t s) {
+    auto k = m.mode == 1 ? relax3d_multi_kernel<T, TA, 1, TU, TV>
+           : m.mode == 0 ? relax3d_multi_kernel<T, TA, 0, TU, TV>
+                         : relax3d_multi_kernel<T, TA, 2, TU, TV>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime_batch: smem attribute");
+    int dev = 0, n_sm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 512, m.bytes) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        n_sm = 148;
+        per_sm = 1;
+    }
+    const long long grid = std::min<long long>(items, (long long)n_sm * per_sm);   // persistent: one wave
+    k<<<(unsigned)grid, 512, m.bytes, s>>>(t, off, H, counter);
+    return launch_check("chert_traveltime_batch: relax3d (persistent)");
+}
+
+extern "C" int chert_traveltime_batch(const chert_lattice* lattices, int n_lattices, int n_modes, int precision,
+                                      const int32_t* offsets, int n_off, int max_cycles,
+                                      unsigned long long* d_counter, void* stream) {
+    const char* who = "chert_traveltime_batch";
+    CHERT_REQUIRE(lattices && offsets && d_counter, "%s: NULL argument", who);
+    CHERT_REQUIRE(n_lattices >= 1 && n_lattices <= kMaxLattices, "%s: n_lattices=%d (1..%d)", who, n_lattices,
+                  kMaxLattices);
+    CHERT_REQUIRE(precision == CHERT_FP64 || precision == CHERT_FP32 || precision == CHERT_MIXED ||
+                      precision == CHERT_FP32_ACC64, "%s: precision=%d", who, precision);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<Prep3> prep(n_lattices);
+    int max_nk = 1;
+    for (int i = 0; i < n_lattices; ++i) {
+        const chert_lattice& L = lattices[i];
+        CHERT_REQUIRE(L.cache && L.d_sources && L.d_status, "%s: lattice %d: NULL cache, sources or status", who, i);
+        CHERT_REQUIRE(L.ny > 1, "%s: lattice %d is 2D (ny = 1); the batch takes 3D lattices", who, i);
+        int blocks = 0;
+        int* st = nullptr;
+        const int rc = enqueue_traveltime(who, L.cache, n_modes, L.n_classes, L.n_dir, L.nx, L.ny, L.nz, L.dx,
+                                          L.d_class_of_node, offsets, n_off, nullptr, L.n_sources, precision,
+                                          max_cycles, L.d_tauR, L.d_tauI, L.d_parR, L.d_parI,
+                                          static_cast<unsigned char*>(L.d_workspace), L.workspace_bytes, s, &blocks,
+                                          &st, L.d_sources, &prep[i]);
+        if (rc) return rc;
+        prep[i].a.parts = 1;
+        max_nk = std::max(max_nk, L.n_classes);
+    }
+    // largest lattices first, so that the longest items start first
+    std::vector<int> order(n_lattices);
+    for (int i = 0; i < n_lattices; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const FieldArgs &a = prep[x].a, &b = prep[y].a;
+        return (long long)a.nx * a.ny * a.nz > (long long)b.nx * b.ny * b.nz;
+    });
+    LatticeTable t;
+    t.n = n_lattices;
+    t.start[0] = 0;
+    for (int i = 0; i < n_lattices; ++i) {
+        t.a[i] = prep[order[i]].a;
+        t.start[i + 1] = t.start[i] + prep[order[i]].blocks;
+    }
+    Offsets off;
+    int rc = fill_offsets(off, offsets, n_off, who);
+    if (rc) return rc;
+    const int H = prep[0].H;
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int tile = g_relax3d_tile.load();
+    const Smem3 m = smem3(max_nk, n_off, H, precision, tile, smem_max);
+    cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime_batch: counter");
+    const long long items = t.start[n_lattices];
+    if (precision == CHERT_FP32_ACC64)
+        rc = tile == 1 ? launch_multi3d<float, xf::ff, 64, 8>(t, off, H, m, items, d_counter, s)
+                       : launch_multi3d<float, xf::ff, 32, 16>(t, off, H, m, items, d_counter, s);
+    else if (precision == CHERT_FP64)
+        rc = tile == 1 ? launch_multi3d<double, double, 64, 8>(t, off, H, m, items, d_counter, s)
+                       : launch_multi3d<double, double, 32, 16>(t, off, H, m, items, d_counter, s);
+    else
+        rc = tile == 1 ? launch_multi3d<float, float, 64, 8>(t, off, H, m, items, d_counter, s)
+                       : launch_multi3d<float, float, 32, 16>(t, off, H, m, items, d_counter, s);
+    if (rc) return rc;
+    for (int i = 0; i < n_lattices; ++i)
+        status_summary_kernel<<<1, 256, 0, s>>>(prep[i].a.status, prep[i].blocks, lattices[i].d_status);
+    return launch_check("chert_traveltime_batch: status");
+}
+
+extern "C" int chert_set_relax3d_tile(int tile) {
+    CHERT_REQUIRE(tile == 0 || tile == 1, "chert_set_relax3d_tile: tile=%d (0: 32 x 16, 1: 64 x 8)", tile);
+    return g_relax3d_tile.exchange(tile);
 }
 
 extern "C" int chert_raypath(const int32_t* d_par, int n_fields, int64_t n_nodes,

@@ -271,3 +271,86 @@ def test_relax3d_split_across_ctas_equals_one_cta(torch_dev, precision):
         outs.append(out)
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+def _lattice_case(torch, shape, n_classes, seed, precision, sources):
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    rng = np.random.default_rng(seed)
+    if n_classes <= 6:
+        cls = np.minimum((np.arange(n) // (nx * ny)) * n_classes // nz, n_classes - 1).astype(np.int32)
+    else:
+        cls = rng.integers(0, n_classes, n).astype(np.int32)
+    cnp, n_az, n_pol = synthetic_cache3d(n_classes, seed=seed)
+    nm, nk, _ = cnp["V"].shape
+    cache_prec = chert.FP64 if precision == "fp64" else chert.FP32
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    cache = chert.Cache(cache_to_torch(cnp, dt, "cuda"), list(range(nm)), nk, 0, cache_prec, n_az, n_pol)
+    fd = torch.float64 if precision in ("fp64", "fp32_acc64") else torch.float32
+    ns = len(sources)
+    out = (torch.full((ns, nm, n), -3.0, dtype=fd, device="cuda"), torch.full((ns, nm, n), -3.0, dtype=fd, device="cuda"),
+           torch.full((ns, nm, n), -7, dtype=torch.int32, device="cuda"),
+           torch.full((ns, nm, n), -7, dtype=torch.int32, device="cuda"))
+    prec = chert.PRECISION_IDS[precision]
+    ws = torch.empty(chert.workspace_bytes(nm, nk, 98, prec, ns), dtype=torch.uint8, device="cuda")
+    return {"cache": cache, "nx": nx, "ny": ny, "nz": nz, "dx": 10.0,
+            "d_cls": torch.as_tensor(cls, device="cuda"),
+            "d_sources": torch.as_tensor(np.asarray(sources, np.int64), device="cuda"), "out": out,
+            "workspace": ws, "d_status": torch.full((2,), 5, dtype=torch.int32, device="cuda")}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_acc64", "fp32"])
+def test_batch_of_uneven_lattices_equals_single_calls(torch_dev, precision):
+    """chert_traveltime_batch (one persistent launch over the field components
+    of several 3D lattices of uneven size and class count) against
+    chert_traveltime on each lattice alone: fields and parents bit for bit,
+    status [-1, 0] for each.  Under both 3D tile shapes, and captured in a
+    CUDA graph (two replays)."""
+    torch = torch_dev
+    off = inputs.stencil_3d(2)
+    cases = [((19, 14, 11), 4, 1, [0, 19 * 14 * 11 - 1, 700]), ((33, 9, 21), 30, 2, [5, 2000]),
+             ((12, 12, 12), 6, 3, [100]), ((41, 17, 8), 400, 4, [3, 4000, 5000])]
+    prev = chert.set_relax3d_tile(0)
+    try:
+        for tile in (0, 1):
+            chert.set_relax3d_tile(tile)
+            items = [_lattice_case(torch, sh, nk, sd, precision, src) for sh, nk, sd, src in cases]
+            counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+            chert.traveltime_batch(items, off, counter, precision=precision)
+            torch.cuda.synchronize()
+            for it in items:
+                assert it["d_status"].cpu().tolist() == [-1, 0]
+                ref = chert.traveltime(it["cache"], it["nx"], it["nz"], 10.0, it["d_cls"], off,
+                                       it["d_sources"].cpu().numpy(), ny=it["ny"], precision=precision)
+                torch.cuda.synchronize()
+                for a, b in zip(ref, it["out"]):
+                    assert torch.equal(a, b), tile
+            # the same batch recorded in a graph
+            for it in items:
+                for o in it["out"]:
+                    o.fill_(-1)
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                chert.traveltime_batch(items, off, counter, precision=precision, stream=s)
+            for _ in range(2):
+                g.replay()
+                torch.cuda.synchronize()
+                for it in items:
+                    ref = chert.traveltime(it["cache"], it["nx"], it["nz"], 10.0, it["d_cls"], off,
+                                           it["d_sources"].cpu().numpy(), ny=it["ny"], precision=precision)
+                    torch.cuda.synchronize()
+                    for a, b in zip(ref, it["out"]):
+                        assert torch.equal(a, b)
+    finally:
+        chert.set_relax3d_tile(prev)
+
+
+def test_batch_rejects_2d_lattices(torch_dev):
+    torch = torch_dev
+    it = _lattice_case(torch, (19, 14, 11), 4, 1, "fp64", [0])
+    it["ny"], it["nz"] = 1, 14 * 11
+    with pytest.raises(chert.ChertError) as e:
+        chert.traveltime_batch([it], inputs.stencil_3d(2), torch.zeros(1, dtype=torch.int64, device="cuda"))
+    assert e.value.code == chert.EINVAL
