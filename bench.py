@@ -962,6 +962,83 @@ def section_batch(n2d, n3d):
                     "and raypaths"}
 
 
+def section_c5(n2d=512, n_blocks=8, n3d_per_block=16, block=101):
+    """Many sources and modes of uneven grid size as one batched job: the
+    per-cell folded and faulted 1701x351 model (597,051 cells) with n2d
+    surface sources x 3 modes, and n_blocks blocks of block^3 nodes cut at
+    seeded corners of the 201^3 layered 3D model with n3d_per_block sources
+    x qP/qSV each.  One CUDA graph per form: the 2D per-cell cache (exact, or
+    the surrogate with its exact fallback on the device), the 3D blocks' one
+    shared MIXED cache (1 x 1 deg), the 2D relaxation with parents, the 3D
+    blocks' relaxations in ONE persistent launch (float weights, float-float
+    accumulation), raypaths to receiver lines.  Launch shapes (3D tile, 2D
+    points per thread) come from the batch's autotuner on the first eager
+    pass.  Timed: one graph replay per form (the surrogate's training is
+    one-off, before)."""
+    import torch
+    from paper_2609_26108_b300 import chert, surrogate
+    from paper_2609_26108_b300.pipeline import GraphBatch, Problem
+
+    fm = inputs.folded_faulted(n_sources=n2d)
+    n = fm.nx * fm.nz
+    keys = ["vp0", "vs0", "eps", "delta", "gamma", "qp", "qs", "tilt"]
+    d_cells = chert.classes_to_device(chert.classes_from_arrays(**{k: fm.params[k] for k in keys}))
+    d_own = torch.arange(n, dtype=torch.int32, device="cuda")
+    big = inputs.layered_tti_3d()
+    d3 = chert.classes_to_device(chert.classes_from_layers(big.layers))
+    blocks = [inputs.subvolume_3d(big, block, seed=1005 + b, n_sources=n3d_per_block) for b in range(n_blocks)]
+    train = surrogate.exact_training_set(inputs.random_tti_classes(SURR_TRAIN_CLASSES, seed=2003), MODES,
+                                         SURR_TRAIN_M)
+    params = [surrogate.train(*train[m], steps=SURR_TRAIN_STEPS, batch=SURR_BATCH, lr=2e-3, seed=1)[0]
+              for m in MODES]
+    del train
+    prev_angle = chert.set_surrogate_qsv_angle(0.0)      # the operating point within 1e-4 (qSV exact)
+    out = {"workload": "c5: folded_faulted 1701x351 per-cell %dsrc x 3 modes + %d blocks %d^3 of layered_tti_3d "
+                       "x %dsrc x qP/qSV, one CUDA graph, 3D relaxations in one persistent launch"
+                       % (len(fm.sources), n_blocks, block, n3d_per_block),
+           "fields_2d": len(fm.sources) * 3, "fields_3d": n_blocks * n3d_per_block * 2}
+    try:
+        for form, prm in (("exact", None), ("surrogate", params)):
+            probs = [Problem(d_cells, n, MODES, fm.nx, fm.nz, fm.dx, d_own, inputs.stencil_2d(RADIUS), fm.sources,
+                             receivers=np.arange(0, fm.nx, 40), M=M_PER_QUADRANT, max_cycles=SURR_MAX_CYCLES,
+                             surrogate_params=prm, path_cap=2048)]
+            for b in blocks:
+                probs.append(Problem(d3, len(big.layers), ["qP", "qSV"], b.nx, b.nz, b.dx,
+                                     torch.as_tensor(b.class_of_node, device="cuda"), inputs.stencil_3d(2),
+                                     b.sources, receivers=np.arange(0, b.nx * b.ny, 997), n_az=360, n_pol=180,
+                                     ny=b.ny, cache_precision="mixed", relax_precision="fp32_acc64"))
+            batch = GraphBatch(probs, persistent_3d=True)
+            t0 = time.perf_counter()
+            batch.run_eager()
+            torch.cuda.synchronize()
+            t_eager = time.perf_counter() - t0
+            batch.check()
+            tuned = batch.autotune()
+            batch.capture(warm=False)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            batch.replay()
+            b.record()
+            torch.cuda.synchronize()
+            t_graph = a.elapsed_time(b) / 1e3
+            batch.check()
+            nf = batch.n_fields
+            r = {"graph_s": t_graph, "fields_per_s": nf / t_graph, "first_eager_pass_s": t_eager,
+                 "autotune_ms": tuned}
+            if prm is not None:
+                r["solves_recomputed_exactly"] = int(batch.state[0]["cache"].n_fallback)
+                r["solves_total"] = n * 3 * (M_PER_QUADRANT + 1)
+            out[form] = r
+            del batch, probs
+            torch.cuda.empty_cache()
+    finally:
+        chert.set_surrogate_qsv_angle(prev_angle)
+    out["fields"] = out["fields_2d"] + out["fields_3d"]
+    out["surrogate_speedup"] = out["surrogate"]["fields_per_s"] / out["exact"]["fields_per_s"]
+    return out
+
+
 # --------------------------------------------------------------- GPU arm
 def run_chert(args):
     import torch
@@ -1092,6 +1169,8 @@ def run_chert(args):
         out["scheduler_study"] = section_scheduler(args.scheduler_study)
     if world == 1 and args.batch_sources > 0:
         out["batch"] = section_batch(args.batch_sources, args.batch_sources_3d)
+    if world == 1 and args.c5:
+        out["c5"] = section_c5()
     if world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(model, off)
         out["cpu_baseline"] = {"value": cb["fields_per_s"], "unit": "fields/s", "cores": cb["cores"],
@@ -1132,6 +1211,9 @@ def main():
                     help="surface sources (64 = the benchmark workload; fewer only for profiling)")
     ap.add_argument("--angular-study", action="store_true",
                     help="add the cache angular-step study (0.5-10 deg) on the layered model")
+    ap.add_argument("--c5", action="store_true",
+                    help="add the batched job: 512 sources x 3 modes on the per-cell model + 8 x 101^3 3D blocks "
+                         "x 16 sources x 2 modes, one CUDA graph per form (exact, surrogate)")
     ap.add_argument("--angular-study-cells", action="store_true",
                     help="add the cache angular-step study (0.5-10 deg) on the per-cell folded model")
     ap.add_argument("--batch-sources", type=int, default=0,

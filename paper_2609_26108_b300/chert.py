@@ -391,7 +391,7 @@ def traveltime(cache, nx, nz, dx, d_cls, offsets, sources, max_cycles=64, parent
 
 
 def traveltime_enqueue(cache, nx, nz, dx, d_cls, offsets, d_sources, out, workspace, d_status, max_cycles=64,
-                       ny=1, stream=None):
+                       ny=1, stream=None, precision=None):
     """chert_traveltime_enqueue: no host synchronisation or copy (capturable
     in a CUDA graph).  d_sources: device int64 [n_sources]; out: (tauR, tauI,
     parR, parI) preallocated; d_status: device int32[2] (first field*2+comp that
@@ -401,8 +401,9 @@ def traveltime_enqueue(cache, nx, nz, dx, d_cls, offsets, d_sources, out, worksp
     st = cache.struct()
     _check(lib().chert_traveltime_enqueue(ctypes.byref(st), nm, cache.n_classes, cache.n_dir, nx, ny, nz,
                                           float(dx), _dev_ptr(d_cls), off_p, len(off), _dev_ptr(d_sources), ns,
-                                          cache.precision, max_cycles, _dev_ptr(out[0]), _dev_ptr(out[1]),
-                                          _dev_ptr(out[2]), _dev_ptr(out[3]), _dev_ptr(workspace),
+                                          cache.precision if precision is None else precision, max_cycles,
+                                          _dev_ptr(out[0]), _dev_ptr(out[1]), _dev_ptr(out[2]), _dev_ptr(out[3]),
+                                          _dev_ptr(workspace),
                                           workspace.numel(), _dev_ptr(d_status), _stream_ptr(stream)))
     return out
 

@@ -177,7 +177,14 @@ class Problem:
 
     def __init__(self, d_classes, n_classes, modes, nx, nz, dx, d_cls, offsets, sources, receivers=None,
                  M=90, n_az=0, n_pol=0, ny=1, cache_precision="mixed", scan_step=0.001 * math.pi / 180,
-                 scan_half=30000, kernel="MEV", max_cycles=64, path_cap=1024):
+                 scan_half=30000, kernel="MEV", max_cycles=64, path_cap=1024, surrogate_params=None,
+                 relax_precision=None):
+        """surrogate_params: one network parameter vector per mode (2D only):
+        the cache comes from chert_cache_surrogate (networks, exact fallback
+        on the device) instead of the exact build.  relax_precision: the
+        relaxation's precision if not the cache's (e.g. "fp32_acc64" in 3D)."""
+        self.surrogate_params = surrogate_params
+        self.relax_precision = relax_precision
         self.d_classes, self.n_classes, self.modes = d_classes, n_classes, list(modes)
         self.nx, self.ny, self.nz, self.dx = nx, ny, nz, dx
         self.d_cls = d_cls
@@ -198,35 +205,63 @@ class GraphBatch:
     once into one CUDA graph and replayed as one launch.  Each problem is
     captured on its own stream (forked from and joined to the capture
     stream), so the graph's branches run concurrently and fill the SMs that
-    one problem's fields leave idle.  Every step is libchert's: cache build,
-    lookup + relaxation + parents (``chert_traveltime_enqueue``: device
-    sources, device status, no host synchronisation), raypaths."""
+    one problem's fields leave idle.  Every step is libchert's: cache build
+    (exact, or the surrogate with its exact fallback), lookup + relaxation +
+    parents (``chert_traveltime_enqueue``: device sources, device status, no
+    host synchronisation), raypaths.
 
-    def __init__(self, problems, device="cuda"):
+    persistent_3d: the 3D problems' relaxations run as ONE persistent launch
+    (``chert_traveltime_batch``) once all their caches are built; they must
+    share modes, stencil, precision and cycle cap.  Problems with the same
+    classes tensor and cache settings share one cache build."""
+
+    def __init__(self, problems, device="cuda", persistent_3d=False):
         import torch
         self.torch = torch
         self.problems = list(problems)
-        self.state = [self._allocate(p, device) for p in self.problems]
+        self.persistent_3d = persistent_3d
+        self.cache_owner = []                # index of the problem whose cache each problem reads
+        keys = {}
+        for i, p in enumerate(self.problems):
+            k = (id(p.d_classes), p.n_classes, tuple(p.modes), p.M, p.n_az, p.n_pol, p.cache_precision,
+                 p.scan_step, p.scan_half, p.kernel, id(p.surrogate_params))
+            self.cache_owner.append(keys.setdefault(k, i))
+        self.state = [self._allocate(p, device, self.cache_owner[i] == i) for i, p in enumerate(self.problems)]
+        three = [i for i, p in enumerate(self.problems) if p.ny > 1]
+        if persistent_3d and three:
+            q = [self.problems[i] for i in three]
+            same = all(p.modes == q[0].modes and np.array_equal(p.offsets, q[0].offsets) and
+                       p.cache_precision == q[0].cache_precision and p.relax_precision == q[0].relax_precision and
+                       p.max_cycles == q[0].max_cycles for p in q)
+            if not same:
+                raise ValueError("persistent_3d: the 3D problems must share modes, stencil, precision and cycle cap")
+        self.three = three if persistent_3d else []
+        self.counter = torch.zeros(1, dtype=torch.int64, device=device)
+        self.stream3 = torch.cuda.Stream(device=device)
         self.graph = None
 
-    def _allocate(self, p, device):
+    def _allocate(self, p, device, owns_cache):
         torch = self.torch
         prec = chert.PRECISION_IDS[p.cache_precision]
+        rprec = prec if p.relax_precision is None else chert.PRECISION_IDS[p.relax_precision]
         fd = torch.float64 if prec == chert.FP64 else torch.float32
+        td = torch.float64 if rprec in (chert.FP64, chert.FP32_ACC64) else torch.float32
         nd = p.n_az * p.n_pol if p.n_az else 4 * p.M
         shape = (len(p.modes), p.n_classes, nd)
         keys = ("V", "A", "Q", "rx", "rz", "theta", "vartheta") + (("ry", "phi") if p.n_az else ())
-        cache_out = {k: torch.empty(shape, dtype=fd, device=device) for k in keys}
-        cache_out["flag"] = torch.empty(shape, dtype=torch.uint8, device=device)
+        cache_out = None
+        if owns_cache:
+            cache_out = {k: torch.empty(shape, dtype=fd, device=device) for k in keys}
+            cache_out["flag"] = torch.empty(shape, dtype=torch.uint8, device=device)
         n = p.nx * p.ny * p.nz
         fshape = (len(p.sources), len(p.modes), n)
-        tau = (torch.empty(fshape, dtype=fd, device=device), torch.empty(fshape, dtype=fd, device=device),
+        tau = (torch.empty(fshape, dtype=td, device=device), torch.empty(fshape, dtype=td, device=device),
                torch.empty(fshape, dtype=torch.int32, device=device),
                torch.empty(fshape, dtype=torch.int32, device=device))
         if p.ny == 1:
-            wsb = chert.workspace_bytes(len(p.modes), p.n_classes, len(p.offsets), prec, len(p.sources), p.nx, p.nz)
+            wsb = chert.workspace_bytes(len(p.modes), p.n_classes, len(p.offsets), rprec, len(p.sources), p.nx, p.nz)
         else:
-            wsb = chert.workspace_bytes(len(p.modes), p.n_classes, len(p.offsets), prec, len(p.sources))
+            wsb = chert.workspace_bytes(len(p.modes), p.n_classes, len(p.offsets), rprec, len(p.sources))
         st = {"cache_out": cache_out, "tau": tau,
               "ws": torch.empty(wsb, dtype=torch.uint8, device=device),
               "d_src": torch.as_tensor(p.sources, device=device),
@@ -240,39 +275,137 @@ class GraphBatch:
                            torch.empty((2, nf, len(p.receivers)), dtype=torch.int64, device=device))
         return st
 
-    def _enqueue(self, p, st, stream):
-        if p.n_az:
+    def _build_cache(self, p, st, stream):
+        if p.surrogate_params is not None:
+            if p.n_az:
+                raise ValueError("the surrogate cache is 2D")
+            cache = chert.cache_surrogate(p.surrogate_params, p.d_classes, p.n_classes, p.modes, p.M, p.scan_step,
+                                          p.scan_half, p.kernel, p.cache_precision, stream, out=st["cache_out"])
+        elif p.n_az:
             cache = chert.build_cache_3d(p.d_classes, p.n_classes, p.modes, p.n_az, p.n_pol, p.scan_step,
                                          p.scan_half, p.kernel, p.cache_precision, stream, out=st["cache_out"])
         else:
             cache = chert.build_cache(p.d_classes, p.n_classes, p.modes, p.M, p.scan_step, p.scan_half,
                                       p.kernel, p.cache_precision, stream, out=st["cache_out"])
         st["cache"] = cache
-        chert.traveltime_enqueue(cache, p.nx, p.nz, p.dx, p.d_cls, p.offsets, st["d_src"], st["tau"], st["ws"],
-                                 st["status"], p.max_cycles, p.ny, stream)
+
+    def _raypaths(self, p, st, stream):
         if p.receivers is not None:
             nf = p.n_fields
             for comp in (0, 1):
                 chert.raypath(st["tau"][2 + comp].reshape(nf, -1), st["d_fsrc"], st["d_rcv"], p.path_cap, stream,
                               out=(st["paths"][0][comp], st["paths"][1][comp]))
 
+    def _relax(self, i, stream):
+        p, st = self.problems[i], self.state[i]
+        cache = self.state[self.cache_owner[i]]["cache"]
+        prec = None if p.relax_precision is None else chert.PRECISION_IDS[p.relax_precision]
+        chert.traveltime_enqueue(cache, p.nx, p.nz, p.dx, p.d_cls, p.offsets, st["d_src"], st["tau"], st["ws"],
+                                 st["status"], p.max_cycles, p.ny, stream, precision=prec)
+        self._raypaths(p, st, stream)
+
+    def _relax_3d_batch(self, stream):
+        items = []
+        for i in self.three:
+            p, st = self.problems[i], self.state[i]
+            items.append({"cache": self.state[self.cache_owner[i]]["cache"], "nx": p.nx, "ny": p.ny, "nz": p.nz,
+                          "dx": p.dx, "d_cls": p.d_cls, "d_sources": st["d_src"], "out": st["tau"],
+                          "workspace": st["ws"], "d_status": st["status"]})
+        p0 = self.problems[self.three[0]]
+        chert.traveltime_batch(items, p0.offsets, self.counter, p0.max_cycles, stream,
+                               precision=p0.relax_precision)
+        for i in self.three:
+            self._raypaths(self.problems[i], self.state[i], stream)
+
     def run_eager(self):
         """One pass without the graph (also loads every kernel before capture)."""
-        for p, st in zip(self.problems, self.state):
-            self._enqueue(p, st, None)
+        for i, (p, st) in enumerate(zip(self.problems, self.state)):
+            if self.cache_owner[i] == i:
+                self._build_cache(p, st, None)
+        for i in range(len(self.problems)):
+            if i not in self.three:
+                self._relax(i, None)
+        if self.three:
+            self._relax_3d_batch(None)
 
-    def capture(self):
+    def _timed(self, fn, repeats):
         torch = self.torch
-        self.run_eager()
+        best = float("inf")
+        for _ in range(repeats):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    def autotune(self, repeats=1):
+        """Launch shapes for this batch, chosen by timing its relaxations on
+        the caches of one eager pass (run it first): the 3D tile shape
+        (chert_set_relax3d_tile: 32 x 16 or 64 x 8) on the 3D problems, and
+        the points per thread of the 2D kernel (1, 2 or 4) on the 2D ones.
+        The fastest of each is kept for the process, so a later capture
+        records it; results do not depend on either.  Returns
+        {"tile3d": {tile: ms}, "ppt2d": {ppt: ms}, "chosen": {...}}."""
+        out = {"tile3d": {}, "ppt2d": {}, "chosen": {}}
+        three = [i for i, p in enumerate(self.problems) if p.ny > 1]
+        two = [i for i, p in enumerate(self.problems) if p.ny == 1]
+        if three:
+            run3 = (lambda: self._relax_3d_batch(None)) if self.three else \
+                (lambda: [self._relax(i, None) for i in three])
+            for tile in (0, 1):
+                chert.set_relax3d_tile(tile)
+                out["tile3d"][tile] = self._timed(run3, repeats)
+            best = min(out["tile3d"], key=out["tile3d"].get)
+            chert.set_relax3d_tile(best)
+            out["chosen"]["tile3d"] = best
+        if two:
+            line = max(max(self.problems[i].nx, self.problems[i].nz) for i in two)
+            for ppt in (1, 2, 4):
+                if (line + ppt - 1) // ppt > 512:
+                    continue
+                chert.lib().chert_set_relax_points_per_thread(ppt)
+                out["ppt2d"][ppt] = self._timed(lambda: [self._relax(i, None) for i in two], repeats)
+            best = min(out["ppt2d"], key=out["ppt2d"].get)
+            chert.lib().chert_set_relax_points_per_thread(best)
+            out["chosen"]["ppt2d"] = best
+        return out
+
+    def capture(self, warm=True):
+        """Record the batch into one CUDA graph (warm: one eager pass first, to
+        load every kernel; skip it when a pass has already run)."""
+        torch = self.torch
+        if warm:
+            self.run_eager()
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             main = torch.cuda.current_stream()
-            for p, st in zip(self.problems, self.state):
+            # caches, each on its problem's stream
+            for i, (p, st) in enumerate(zip(self.problems, self.state)):
+                st["stream"].wait_stream(main)
+                if self.cache_owner[i] == i:
+                    with torch.cuda.stream(st["stream"]):
+                        self._build_cache(p, st, st["stream"])
+            # relaxations: each problem after its cache's build; the 3D batch
+            # after every 3D problem's cache
+            for i, st in enumerate(self.state):
+                if i in self.three:
+                    continue
                 s = st["stream"]
-                s.wait_stream(main)
+                s.wait_stream(self.state[self.cache_owner[i]]["stream"])
                 with torch.cuda.stream(s):
-                    self._enqueue(p, st, s)
+                    self._relax(i, s)
+            if self.three:
+                s3 = self.stream3
+                s3.wait_stream(main)
+                for i in self.three:
+                    s3.wait_stream(self.state[self.cache_owner[i]]["stream"])
+                with torch.cuda.stream(s3):
+                    self._relax_3d_batch(s3)
+                main.wait_stream(s3)
             for st in self.state:
                 main.wait_stream(st["stream"])
         self.graph = g

@@ -92,3 +92,71 @@ def test_graph_batch_replays_eager_results(torch_dev):
                 for a, b in zip(eager_paths[i], batch.state[i]["paths"]):
                     assert torch_dev.equal(a, b)
     assert batch.n_fields == 4 * 3 + 3 * 2 + 4 * 2
+
+
+def test_persistent_batch_with_surrogate_and_autotuner(torch_dev):
+    """The batched form of many problems: a per-cell 2D problem whose cache
+    comes from the surrogate with its exact fallback (chert_cache_surrogate),
+    and three 3D blocks of uneven size cut from one model (one shared cache
+    build) relaxed in one persistent launch (chert_traveltime_batch); launch
+    shapes chosen by the batch's autotuner, then the whole batch captured in
+    one CUDA graph.  Replays equal the eager pass bit for bit, and every
+    problem's fields equal chert_traveltime on its own cache."""
+    torch = torch_dev
+    from test_gpu_surrogate import _decisive_nets
+    params = _decisive_nets(torch)
+    fm = inputs.folded_faulted(nx=71, nz=33, n_layers=4, n_sources=3, seed=7)
+    n = fm.nx * fm.nz
+    keys = ["vp0", "vs0", "eps", "delta", "gamma", "qp", "qs", "tilt"]
+    d_cells = chert.classes_to_device(chert.classes_from_arrays(**{k: fm.params[k] for k in keys}))
+    d_own = torch.as_tensor(np.arange(n, dtype=np.int32), device="cuda")
+    probs = [Problem(d_cells, n, ["qP", "qSV", "qSH"], fm.nx, fm.nz, fm.dx, d_own, inputs.stencil_2d(5),
+                     fm.sources, receivers=[0, 500, n - 1], M=30, scan_step=0.02 * DEG, scan_half=1500,
+                     surrogate_params=params)]
+    big = inputs.layered_tti_3d(n=41, n_layers=3, n_sources=4)
+    d3 = chert.classes_to_device(chert.classes_from_layers(big.layers))
+    for size, seed in ((21, 1), (15, 2), (27, 3)):
+        sub = inputs.subvolume_3d(big, size, seed=seed, n_sources=4)
+        probs.append(Problem(d3, len(big.layers), ["qP", "qSV"], sub.nx, sub.nz, sub.dx,
+                             torch.as_tensor(sub.class_of_node, device="cuda"), inputs.stencil_3d(2), sub.sources,
+                             receivers=[0, size ** 3 - 1], n_az=24, n_pol=12, ny=sub.ny, cache_precision="mixed",
+                             relax_precision="fp32_acc64", scan_step=0.02 * DEG, scan_half=1500))
+    batch = GraphBatch(probs, persistent_3d=True)
+    assert batch.cache_owner == [0, 1, 1, 1]
+    prev_tile = chert.set_relax3d_tile(0)
+    prev_ppt = chert.lib().chert_set_relax_points_per_thread(0)
+    try:
+        batch.run_eager()
+        torch.cuda.synchronize()
+        batch.check()
+        tuned = batch.autotune()
+        assert set(tuned["tile3d"]) == {0, 1} and tuned["chosen"]["ppt2d"] in (1, 2, 4)
+        batch.run_eager()
+        torch.cuda.synchronize()
+        eager = [[t.clone() for t in batch.fields(i)] for i in range(len(probs))]
+        eager_paths = [[t.clone() for t in st["paths"]] for st in batch.state]
+        # each problem alone, on the batch's caches
+        for i, p in enumerate(probs):
+            cache = batch.state[batch.cache_owner[i]]["cache"]
+            ref = chert.traveltime(cache, p.nx, p.nz, p.dx, p.d_cls, p.offsets, p.sources, max_cycles=p.max_cycles,
+                                   ny=p.ny, precision=p.relax_precision)
+            torch.cuda.synchronize()
+            for a, b in zip(ref, eager[i]):
+                assert torch.equal(a, b), i
+        assert int(batch.state[0]["cache"].n_fallback_dev.item()) > 0
+        batch.capture(warm=False)
+        for _ in range(2):
+            for st in batch.state:
+                for t in st["tau"]:
+                    t.fill_(0)
+            batch.replay()
+            torch.cuda.synchronize()
+            batch.check()
+            for i in range(len(probs)):
+                for a, b in zip(eager[i], batch.fields(i)):
+                    assert torch.equal(a, b)
+                for a, b in zip(eager_paths[i], batch.state[i]["paths"]):
+                    assert torch.equal(a, b)
+    finally:
+        chert.set_relax3d_tile(prev_tile)
+        chert.lib().chert_set_relax_points_per_thread(prev_ppt)
