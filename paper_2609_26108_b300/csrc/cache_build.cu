@@ -684,9 +684,9 @@ __device__ void write_entries(const Outs& out, const Solve<TS, TP>& v, int n_cla
             sincos(v.phl, &sp, &cp);
             const double rs = double(q.rx);
             const double rl[3] = {rs * cp, rs * sp, v.sz * double(q.rz)};
-            const double r[3] = {E[0][0] * rl[0] + E[1][0] * rl[1] + E[2][0] * rl[2],
-                                 E[0][1] * rl[0] + E[1][1] * rl[1] + E[2][1] * rl[2],
-                                 E[0][2] * rl[0] + E[1][2] * rl[1] + E[2][2] * rl[2]};
+            double r[3];
+            for (int c = 0; c < 3; ++c)
+                r[c] = __fma_rn(E[2][c], rl[2], __fma_rn(E[1][c], rl[1], __dmul_rn(E[0][c], rl[0])));
             put<TO>(out.rx, e, r[0]);
             put<TO>(out.ry, e, r[1]);
             put<TO>(out.rz, e, r[2]);
@@ -727,9 +727,11 @@ __device__ void write_entries(const Outs& out, const Solve<TS, TP>& v, int n_cla
     sincos(v.cls.tilt, &st, &ct);
     put<TO>(out.theta, e, (M_PI / 2 * d) / M + v.cls.tilt);
     if (found) {
+        // the tilt rotation with its roundings spelled out, so that every
+        // kernel that writes entries rounds it alike
         const double lx = sx * double(q.rx), lz = sz * double(q.rz);
-        put<TO>(out.rx, e, lx * ct + lz * st);
-        put<TO>(out.rz, e, -lx * st + lz * ct);
+        put<TO>(out.rx, e, __fma_rn(lx, ct, __dmul_rn(lz, st)));
+        put<TO>(out.rz, e, __fma_rn(lz, ct, -__dmul_rn(lx, st)));
         put<TO>(out.V, e, double(q.V));
         put<TO>(out.A, e, double(q.A));
         put<TO>(out.Q, e, double(q.Q));
