@@ -161,6 +161,14 @@ int chert_build_cache_items(const chert_class* d_classes, int n_classes,
                             const int64_t* d_items, int64_t n_items,
                             const chert_cache_arrays* out, void* stream);
 
+/* Threads per CTA of the cache build's finish pass (the solves with no
+ * decaying root within 2,048 grid points per side), process-wide: 0 (default)
+ * 1024 for builds of at most 65,536 solves and 256 above; or 256, 512, 1024.
+ * The cache is the same for every choice (the nearest 64-point slice with a
+ * root wins); this is for measurement and tuning.  Returns the previous
+ * setting, or CHERT_EINVAL. */
+int chert_set_cache_finish_threads(int threads);
+
 /* 3D cache (Eq. 35, the 3D TTI extension of the paper's experiments): entry
  * d = i*n_az + j of class k is the global slowness direction of polar angle
  * (i + 1/2)*pi/n_pol and azimuth j*2*pi/n_az (arrays [n_modes][n_classes]

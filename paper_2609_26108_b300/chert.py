@@ -111,6 +111,8 @@ def lib():
     L.chert_traveltime_enqueue.restype = ctypes.c_int
     L.chert_traveltime_batch.argtypes = [P, I, I, I, P, I, I, P, P]
     L.chert_traveltime_batch.restype = ctypes.c_int
+    L.chert_set_cache_finish_threads.argtypes = [I]
+    L.chert_set_cache_finish_threads.restype = ctypes.c_int
     L.chert_set_relax3d_tile.argtypes = [I]
     L.chert_set_relax3d_tile.restype = ctypes.c_int
     L.chert_set_relax_points_per_thread.argtypes = [I]

@@ -145,3 +145,34 @@ def test_cache_rejects_bad_arguments(torch_dev):
         chert.build_cache(d_cls, 5, ["qP"], 0)
     with pytest.raises(chert.ChertError):
         chert.build_cache(d_cls, 5, ["qP"], 4, scan_step=-1.0)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_finish_pass_thread_counts_give_the_same_cache(torch_dev, precision):
+    """The finish pass with 1024, 512 and 256 threads a CTA (rounds of 2,048,
+    1,024 and 512 grid points per side; the nearest 64-point slice with a
+    decaying root wins in each) gives the same cache bit for bit -- the
+    layered model's 8 classes x 3 modes at the full 0.001 deg x 30,000 grid,
+    whose pending qSV solves include ones with no decaying root."""
+    torch = torch_dev
+    model = inputs.layered_tti()
+    d_classes = chert.classes_to_device(chert.classes_from_layers(model.layers))
+    lib = chert.lib()
+    prev = lib.chert_set_cache_finish_threads(0)
+    try:
+        out = {}
+        for nt in (1024, 512, 256):
+            lib.chert_set_cache_finish_threads(nt)
+            c = chert.build_cache(d_classes, 8, MODES, 90, 0.001 * DEG, 30000, "MEV", precision)
+            torch.cuda.synchronize()
+            out[nt] = {k: v.clone() for k, v in c.arrays.items()}
+        assert int((out[1024]["flag"] == 1).sum()) > 0
+        for nt in (512, 256):
+            for k in out[nt]:
+                a, b = out[1024][k], out[nt][k]
+                if a.dtype != torch.uint8:
+                    a, b = torch.nan_to_num(a, nan=-7.0), torch.nan_to_num(b, nan=-7.0)
+                assert torch.equal(a, b), (nt, k)
+        assert lib.chert_set_cache_finish_threads(128) == chert.EINVAL
+    finally:
+        lib.chert_set_cache_finish_threads(prev)
