@@ -1372,7 +1372,7 @@ static size_t fast_smem(int nk, int nx, int nz, size_t es, bool pn) {
     const size_t LS = ((line_max + 2 * R) + 3) & ~3;
     const size_t tiles = (size_t)((nx + fast::kTile - 1) / fast::kTile) * ((nz + fast::kTile - 1) / fast::kTile);
     return (pn ? 0 : (size_t)nk * nk * fast::Stencil<R>::N * es) + 16 * LS * (2 * es) + 4 * tiles +
-           4 * fast::Stencil<R>::N + 4 * (size_t)nz + 64;
+           4 * fast::Stencil<R>::N + 4 * (2 * (size_t)nz + 2 * R) + 64;
 }
 
 // Row classes of a 2D class map: rowk[z] = the class of every node of row z,

@@ -118,6 +118,8 @@ constexpr int kTile = 32;
 template <typename T>
 struct Ctx {
     const int* rowk; // [nz] class of each row (row-class path), shared memory
+    const int* rowoff; // rowoff[z] = rowk[z] * nk * N for z in [0, nz), 0 for the R rows
+                       // either side (their traveltimes are +inf in the ring)
     T* W;            // [nk][nk][N]: W[(ki*nk + kj)*N + q] (class-pair mode)
     Cell<T>* ring;   // [16][LS]
     short* sx;       // stencil offsets (for decoding the winning parent)
@@ -135,6 +137,7 @@ __device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b);
 // Whether the tiles around tile (tx, tz) changed in or after pass `since`.
 template <typename T>
 __device__ __forceinline__ bool dirty(const Ctx<T>& c, int tx, int tz, int since) {
+    if (since <= 0) return true;       // every stamp is >= 0: the first pass of a sweep relaxes everything
     int m = 0;
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz) {
@@ -155,6 +158,7 @@ __device__ __forceinline__ bool dirty(const Ctx<T>& c, int tx, int tz, int since
 // tile column b).  Block-wide (every thread must call it).
 template <typename T, int AXIS>
 __device__ __forceinline__ bool band_dirty(const Ctx<T>& c, int b, int since) {
+    if (since <= 0) return true;                // uniform over the block, as the barrier below
     const int nb = AXIS == 0 ? c.TZ : c.TX;     // bands
     const int per = AXIS == 0 ? c.TX : c.TZ;    // tiles per band
     bool d = false;
@@ -421,7 +425,7 @@ __device__ void sweep_rows1(const Ctx<T>& c, T* __restrict__ tau, int pass, int 
     auto set_wo = [&](int zj) {
         const int kj = row_class(c.rowk, zj, c.nz, 0);
 #pragma unroll
-        for (int d = -R; d <= R; ++d) wo[d + R] = (row_class(c.rowk, zj - d, c.nz, kj) * nk + kj) * N;
+        for (int d = -R; d <= R; ++d) wo[d + R] = c.rowoff[zj - d] + kj * N;
     };
     if constexpr (AXIS == 1) set_wo(u < len ? u : 0);
     auto gidx = [&](int line) {
@@ -517,7 +521,7 @@ __device__ bool verify_rows1(const Ctx<T>& c, T* __restrict__ tau, int64_t src, 
 #pragma unroll
         for (int d = -R; d <= R; ++d) {
             po[d + R] = ((z - d) & 15) * c.LS + R + x;
-            wo[d + R] = (row_class(c.rowk, z - d, nz, kj) * nk + kj) * N;
+            wo[d + R] = c.rowoff[z - d] + kj * N;
         }
         if (x < nx && dirty(c, x / kTile, z / kTile, since)) {
             const T cur = ring[po[R]];
@@ -566,7 +570,7 @@ __device__ void sweep_rows(const Ctx<T>& c, T* __restrict__ tau, int pass, int s
     auto set_wo = [&](int slot, int zj) {
         const int kj = row_class(c.rowk, zj, c.nz, 0);
 #pragma unroll
-        for (int d = -R; d <= R; ++d) wo[slot][d + R] = (row_class(c.rowk, zj - d, c.nz, kj) * nk + kj) * N;
+        for (int d = -R; d <= R; ++d) wo[slot][d + R] = c.rowoff[zj - d] + kj * N;
     };
     if constexpr (AXIS == 1) {
 #pragma unroll
@@ -690,7 +694,7 @@ __device__ bool verify_rows(const Ctx<T>& c, T* __restrict__ tau, int64_t src, i
         int wo[2 * R + 1];                  // weight-table offsets of the rows z - d
         const int kj = c.rowk[z];
 #pragma unroll
-        for (int d = -R; d <= R; ++d) wo[d + R] = (row_class(c.rowk, z - d, nz, kj) * nk + kj) * N;
+        for (int d = -R; d <= R; ++d) wo[d + R] = c.rowoff[z - d] + kj * N;
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
             const int x = tid + p * bd;
@@ -752,6 +756,8 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
     c.sz = reinterpret_cast<short*>(p); p += N * sizeof(short);
     int* rowk_s = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(p) + 3) & ~uintptr_t(3));
     c.rowk = rowk_s;
+    int* rowoff_s = rowk_s + a.nz;              // [nz + 2R], entry z + R for row z
+    c.rowoff = rowoff_s + R;
     c.wr = PN ? static_cast<const T*>(a.wrow) + (size_t)(mode * 2 + comp) * N * c.n : nullptr;
     c.wc = PN ? static_cast<const T*>(a.wcol) + (size_t)(mode * 2 + comp) * N * c.n : nullptr;
 
@@ -797,6 +803,11 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
                 ok = ok && k >= 0 && k < nk;
             }
             rows = __syncthreads_and(ok);
+            if (rows) {
+                for (int z = (int)threadIdx.x - R; z < a.nz + R; z += blockDim.x)
+                    rowoff_s[z + R] = (z >= 0 && z < a.nz) ? rowk_s[z] * nk * N : 0;
+                __syncthreads();
+            }
         }
     }
 
