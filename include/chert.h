@@ -595,9 +595,12 @@ size_t chert_trace_host_scratch_bytes(int n_classes, int n_modes, int M, int nx,
  *   h_path_len       host int64 [2][n_sources*n_modes][n_rcv] (0: unreachable
  *                    or longer than path_cap)
  *   d_scratch        device, at least chert_trace_host_scratch_bytes()
- * Host buffers should be page-locked for the copies to overlap nothing else
- * but run at full speed.  Errors: as the entry points it chains, CHERT_ENOMEM
- * (scratch too small). */
+ * The sources are relaxed in waves (the first fills two resident CTAs a SM
+ * with its field components); each wave's fields and raypaths are copied
+ * back on a copy stream while the next wave relaxes.  Host buffers should be
+ * page-locked for the copies to run asynchronously at full speed.  Errors:
+ * as the entry points it chains (a cycle cap names the first failing field
+ * of the first wave that has one), CHERT_ENOMEM (scratch too small). */
 int chert_trace_host(const chert_class* h_classes, int n_classes, const int* modes, int n_modes,
                      const chert_cache_params* params, int nx, int nz, double dx,
                      const int32_t* h_class_of_node, const int32_t* offsets, int n_off,

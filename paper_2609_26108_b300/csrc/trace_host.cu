@@ -1,10 +1,19 @@
 // chert_trace_host: the whole hot path of Algorithm 2 on a 2D lattice as one
 // call on host buffers -- inputs copied in, cache build (Eq. 4-14, 26),
 // lookup and relaxation with parents (Eq. 27-33), raypaths (Eq. 34), the
-// traveltime fields and raypaths copied back.  It only chains the public
-// entry points on one stream, in caller-provided device scratch, and
-// synchronises once at the end.
+// traveltime fields and raypaths copied back.  It chains the public entry
+// points in caller-provided device scratch and synchronises once at the end.
+//
+// The sources are relaxed in waves: the first wave's field components fill
+// the device's resident CTA slots (two a SM), the rest follow.  Each wave's
+// relaxation and raypaths run on the caller's stream, and its results are
+// copied back on a copy stream as soon as they are done, so the copies of
+// one wave overlap the relaxation of the next.
 #include <stdint.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -20,14 +29,43 @@ __global__ void field_sources_kernel(const int64_t* __restrict__ src, int nf, in
     if (t < 2 * nf) fsrc[t] = src[(t % nf) / n_modes];
 }
 
+// Sources per wave: as many as fill two resident CTAs a SM with their field
+// components (2 per field), at least one.
+int wave_sources(int n_modes) {
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || n_sm < 1) {
+        cudaGetLastError();
+        n_sm = 148;
+    }
+    return std::max(1, (2 * n_sm) / (2 * n_modes));
+}
+
+// The copy stream of each device (created once, non-blocking).
+cudaStream_t copy_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
 struct HostLayout {
     size_t classes, cls, src, fsrc, rcv, cache, flag, tauR, tauI, parR, parI, paths, lens, status, ws, total;
     size_t ws_bytes;
+    int wave, n_waves;          // sources per wave, waves
 };
 
 HostLayout host_layout(int n_classes, int n_modes, int M, int nx, int nz, int n_off, int n_sources, int n_rcv,
                        int64_t cap, int precision) {
     HostLayout L{};
+    L.wave = std::min(n_sources, wave_sources(n_modes));
+    L.n_waves = (n_sources + L.wave - 1) / L.wave;
     const size_t es = precision == CHERT_FP64 ? 8 : 4;
     const size_t n = (size_t)nx * nz;
     const size_t nf = (size_t)n_sources * n_modes;
@@ -47,8 +85,8 @@ HostLayout host_layout(int n_classes, int n_modes, int M, int nx, int nz, int n_
     L.parI = take(4 * nf * n);
     L.paths = take(8 * 2 * nf * (size_t)n_rcv * (size_t)cap);
     L.lens = take(8 * 2 * nf * (size_t)n_rcv);
-    L.status = take(8);
-    L.ws_bytes = chert_traveltime_workspace_bytes_grid(n_modes, n_classes, n_off, precision, n_sources, nx, 1, nz);
+    L.status = take(8 * (size_t)L.n_waves);
+    L.ws_bytes = chert_traveltime_workspace_bytes_grid(n_modes, n_classes, n_off, precision, L.wave, nx, 1, nz);
     L.ws = take(L.ws_bytes);
     L.total = at;
     return L;
@@ -123,40 +161,98 @@ extern "C" int chert_trace_host(const chert_class* h_classes, int n_classes, con
                                params, &cache, s);
     if (rc) return rc;
     int32_t* status = reinterpret_cast<int32_t*>(d + L.status);
-    rc = chert_traveltime_enqueue(&cache, n_modes, n_classes, 4 * params->M, nx, 1, nz, dx,
-                                  reinterpret_cast<const int32_t*>(d + L.cls), offsets, n_off,
-                                  reinterpret_cast<const int64_t*>(d + L.src), n_sources, prec, max_cycles,
-                                  d + L.tauR, d + L.tauI, reinterpret_cast<int32_t*>(d + L.parR),
-                                  reinterpret_cast<int32_t*>(d + L.parI), d + L.ws, L.ws_bytes, status, s);
-    if (rc) return rc;
-    for (int c = 0; c < 2; ++c) {
-        rc = chert_raypath(reinterpret_cast<const int32_t*>(d + (c == 0 ? L.parR : L.parI)), nf, (int64_t)n,
-                           reinterpret_cast<const int64_t*>(d + L.fsrc) + (size_t)c * nf,
-                           reinterpret_cast<const int64_t*>(d + L.rcv), n_rcv, path_cap,
-                           reinterpret_cast<int64_t*>(d + L.paths) + (size_t)c * nf * n_rcv * path_cap,
-                           reinterpret_cast<int64_t*>(d + L.lens) + (size_t)c * nf * n_rcv, s);
-        if (rc) return rc;
+    cudaStream_t cs = L.n_waves > 1 ? copy_stream() : nullptr;
+    const int waves = cs ? L.n_waves : 1;
+    const int wave = cs ? L.wave : n_sources;
+    const size_t field_bytes = n * es;
+    const size_t path_bytes = 8 * (size_t)n_rcv * path_cap, len_bytes = 8 * (size_t)n_rcv;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    auto cleanup = [&]() {
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+    };
+    for (int k = 0; k < 2 && cs; ++k) {
+        e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(e, "chert_trace_host: events");
+        }
+    }
+    // the copies of the waves before the last overlap the next wave's work
+    auto copy_wave = [&](cudaStream_t cst, int s0, int ns) -> cudaError_t {
+        const size_t f0 = (size_t)s0 * n_modes, fn = (size_t)ns * n_modes;
+        cudaError_t er = cudaMemcpyAsync(static_cast<unsigned char*>(h_tauR) + f0 * field_bytes,
+                                         d + L.tauR + f0 * field_bytes, fn * field_bytes, cudaMemcpyDeviceToHost, cst);
+        if (er == cudaSuccess)
+            er = cudaMemcpyAsync(static_cast<unsigned char*>(h_tauI) + f0 * field_bytes,
+                                 d + L.tauI + f0 * field_bytes, fn * field_bytes, cudaMemcpyDeviceToHost, cst);
+        for (int c = 0; c < 2 && er == cudaSuccess; ++c) {
+            const size_t g0 = (size_t)c * nf + f0;
+            er = cudaMemcpyAsync(reinterpret_cast<unsigned char*>(h_paths) + g0 * path_bytes,
+                                 d + L.paths + g0 * path_bytes, fn * path_bytes, cudaMemcpyDeviceToHost, cst);
+            if (er == cudaSuccess)
+                er = cudaMemcpyAsync(reinterpret_cast<unsigned char*>(h_path_len) + g0 * len_bytes,
+                                     d + L.lens + g0 * len_bytes, fn * len_bytes, cudaMemcpyDeviceToHost, cst);
+        }
+        return er;
+    };
+    for (int k = 0; k < waves; ++k) {
+        const int s0 = k * wave, ns = std::min(wave, n_sources - s0);
+        const size_t f0 = (size_t)s0 * n_modes;
+        const int nfk = ns * n_modes;
+        rc = chert_traveltime_enqueue(&cache, n_modes, n_classes, 4 * params->M, nx, 1, nz, dx,
+                                      reinterpret_cast<const int32_t*>(d + L.cls), offsets, n_off,
+                                      reinterpret_cast<const int64_t*>(d + L.src) + s0, ns, prec, max_cycles,
+                                      d + L.tauR + f0 * field_bytes, d + L.tauI + f0 * field_bytes,
+                                      reinterpret_cast<int32_t*>(d + L.parR) + f0 * n,
+                                      reinterpret_cast<int32_t*>(d + L.parI) + f0 * n, d + L.ws, L.ws_bytes,
+                                      status + 2 * k, s);
+        for (int c = 0; c < 2 && !rc; ++c)
+            rc = chert_raypath(reinterpret_cast<const int32_t*>(d + (c == 0 ? L.parR : L.parI)) + f0 * n, nfk,
+                               (int64_t)n, reinterpret_cast<const int64_t*>(d + L.fsrc) + (size_t)c * nf + f0,
+                               reinterpret_cast<const int64_t*>(d + L.rcv), n_rcv, path_cap,
+                               reinterpret_cast<int64_t*>(d + L.paths) + ((size_t)c * nf + f0) * n_rcv * path_cap,
+                               reinterpret_cast<int64_t*>(d + L.lens) + ((size_t)c * nf + f0) * n_rcv, s);
+        if (rc) {
+            cleanup();
+            return rc;
+        }
+        if (cs) {
+            // this wave's results are done on s: copy them on the copy stream
+            e = cudaEventRecord(ev[0], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
+            if (e == cudaSuccess) e = copy_wave(cs, s0, ns);
+            if (e != cudaSuccess) {
+                cleanup();
+                return cuda_fail(e, "chert_trace_host: result copies");
+            }
+        }
     }
 
-    // results out, one synchronisation
-    int32_t h_status[2] = {-1, 0};
-    e = cudaMemcpyAsync(h_tauR, d + L.tauR, (size_t)nf * n * es, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_tauI, d + L.tauI, (size_t)nf * n * es, cudaMemcpyDeviceToHost, s);
+    // results out (the rest), one synchronisation
+    std::vector<int32_t> h_status(2 * (size_t)waves, 0);
+    const int n_stat = waves;
+    if (cs) {
+        e = cudaEventRecord(ev[1], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
+    } else {
+        e = copy_wave(s, 0, n_sources);
+    }
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h_paths, d + L.paths, 8 * 2 * (size_t)nf * n_rcv * path_cap, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h_path_len, d + L.lens, 8 * 2 * (size_t)nf * n_rcv, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_status, status, sizeof(h_status), cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(h_status.data(), status, sizeof(int32_t) * 2 * n_stat, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "chert_trace_host: result copies");
-    if (h_status[1]) {
-        set_error("%s: class map holds ids outside [0, %d)", who, n_classes);
-        return CHERT_EINVAL;
-    }
-    if (h_status[0] >= 0) {
-        set_error("%s: field %d component %d did not converge in %d cycles", who, h_status[0] / 2, h_status[0] % 2,
-                  max_cycles);
-        return CHERT_ETIMEOUT;
-    }
+    for (int k = 0; k < n_stat; ++k)
+        if (h_status[2 * k + 1]) {
+            set_error("%s: class map holds ids outside [0, %d)", who, n_classes);
+            return CHERT_EINVAL;
+        }
+    for (int k = 0; k < n_stat; ++k)
+        if (h_status[2 * k] >= 0) {
+            const int fc = h_status[2 * k] + 2 * k * wave * n_modes;
+            set_error("%s: field %d component %d did not converge in %d cycles", who, fc / 2, fc % 2, max_cycles);
+            return CHERT_ETIMEOUT;
+        }
     return CHERT_OK;
 }

@@ -136,7 +136,9 @@ class HostTracer:
 
     def __init__(self, n_classes, modes, M, nx, nz, dx, offsets, n_sources, receivers, kernel="MEV",
                  precision="mixed", scan_step=0.001 * math.pi / 180, scan_half=30000, max_cycles=64, path_cap=1024,
-                 device="cuda"):
+                 device="cuda", pinned=True):
+        """pinned: page-locked outputs (the kernels write the results into
+        them in place); False: pageable ones (copied at the end of the call)."""
         import torch
         self.n_classes, self.modes, self.M = n_classes, list(modes), M
         self.nx, self.nz, self.dx = nx, nz, dx
@@ -148,10 +150,10 @@ class HostTracer:
         nf = n_sources * nm
         self.h_rcv = torch.as_tensor(np.asarray(receivers, np.int64)).pin_memory()
         fd = torch.float64 if prec == chert.FP64 else torch.float32
-        self.h_tau = (torch.empty((n_sources, nm, n), dtype=fd).pin_memory(),
-                      torch.empty((n_sources, nm, n), dtype=fd).pin_memory())
-        self.h_paths = torch.empty((2, nf, len(self.h_rcv), path_cap), dtype=torch.int64).pin_memory()
-        self.h_lens = torch.empty((2, nf, len(self.h_rcv)), dtype=torch.int64).pin_memory()
+        pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+        self.h_tau = (pin(torch.empty((n_sources, nm, n), dtype=fd)), pin(torch.empty((n_sources, nm, n), dtype=fd)))
+        self.h_paths = pin(torch.empty((2, nf, len(self.h_rcv), path_cap), dtype=torch.int64))
+        self.h_lens = pin(torch.empty((2, nf, len(self.h_rcv)), dtype=torch.int64))
         nb = chert.trace_host_scratch_bytes(n_classes, nm, M, nx, nz, len(self.offsets), n_sources,
                                             len(self.h_rcv), path_cap, prec)
         self.scratch = torch.empty(nb, dtype=torch.uint8, device=device)

@@ -21,11 +21,26 @@ def torch_dev():
     return torch
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_trace_host_equals_device_path(torch_dev, precision):
-    from paper_2609_26108_b300.pipeline import HostTracer, Tracer
+@pytest.mark.parametrize("precision,pinned,scheduler,n_sources",
+                         [("mixed", True, "hybrid", 5), ("fp64", True, "hybrid", 5), ("mixed", False, "hybrid", 5),
+                          ("mixed", True, "block_heap", 5), ("mixed", True, "hybrid", 120),
+                          ("fp64", False, "hybrid", 120)])
+def test_trace_host_equals_device_path(torch_dev, precision, pinned, scheduler, n_sources):
+    """Page-locked and pageable outputs, two schedulers, and 120 sources x 3
+    modes: more field components than two resident CTAs a SM, so the call
+    relaxes the sources in waves and copies each wave back while the next
+    relaxes."""
     torch = torch_dev
-    model = inputs.layered_tti(nx=83, nz=61, n_layers=4, n_sources=5)
+    prev = chert.set_relax_scheduler(scheduler)
+    try:
+        _trace_host_case(torch, precision, pinned, n_sources)
+    finally:
+        chert.set_relax_scheduler(prev)
+
+
+def _trace_host_case(torch, precision, pinned, n_sources):
+    from paper_2609_26108_b300.pipeline import HostTracer, Tracer
+    model = inputs.layered_tti(nx=83, nz=61, n_layers=4, n_sources=n_sources)
     off = inputs.stencil_2d(4)
     rcv = np.array([0, 41, 82, 83 * 60 + 7, 83 * 30 + 30], np.int64)
     M, h, K = 18, 0.02 * math.pi / 180, 1500
@@ -33,18 +48,20 @@ def test_trace_host_equals_device_path(torch_dev, precision):
     d_classes = chert.classes_to_device(classes)
     cls = model.class_of_node.astype(np.int32)
     rel = "fp64" if precision == "fp64" else "fp32"
-    tr = Tracer(4, ["qP", "qSV", "qSH"], M, model.nx, model.nz, model.dx, off, 5, rcv, cache_precision=precision,
+    ns = len(model.sources)
+    tr = Tracer(4, ["qP", "qSV", "qSH"], M, model.nx, model.nz, model.dx, off, ns, rcv, cache_precision=precision,
                 precision=rel, scan_step=h, scan_half=K, path_cap=256)
     tr.set_inputs(d_classes, torch.as_tensor(cls, device="cuda"), model.sources)
     tR, tI, _, _ = tr.run()
     torch.cuda.synchronize()
-    ht = HostTracer(4, ["qP", "qSV", "qSH"], M, model.nx, model.nz, model.dx, off, 5, rcv, precision=precision,
-                    scan_step=h, scan_half=K, path_cap=256)
+    ht = HostTracer(4, ["qP", "qSV", "qSH"], M, model.nx, model.nz, model.dx, off, ns, rcv, precision=precision,
+                    scan_step=h, scan_half=K, path_cap=256, pinned=pinned)
+    assert ht.h_tau[0].is_pinned() == pinned
     h_src = torch.as_tensor(np.asarray(model.sources, np.int64)).pin_memory()
     for _ in range(2):                               # twice: nothing carries over between calls
         hR, hI, hp, hl = ht.run(d_classes.cpu().pin_memory(), torch.as_tensor(cls).pin_memory(), h_src)
         assert torch.equal(hR, tR.cpu()) and torch.equal(hI, tI.cpu())
-        nf = 15
+        nf = 3 * ns
         for c in (0, 1):
             assert torch.equal(hl[c], tr.paths[1][c * nf:(c + 1) * nf].cpu())
             for f in range(nf):
