@@ -159,3 +159,32 @@ def test_tracer_counts_the_hybrid_continuation(lib):
         assert tr.launches_per_run == 6
     finally:
         chert.set_relax_scheduler("hybrid")
+
+
+def test_new_switches_and_sizes_host_only(lib):
+    """Process-wide launch-shape switches refuse values they do not know and
+    return the previous setting; workspace queries refuse bad sizes; argument
+    checks run before any device work."""
+    import ctypes
+    assert lib.chert_set_relax3d_tile(2) == chert.EINVAL
+    prev = lib.chert_set_relax3d_tile(1)
+    assert lib.chert_set_relax3d_tile(prev) == 1
+    assert lib.chert_set_cache_finish_threads(128) == chert.EINVAL
+    prev = lib.chert_set_cache_finish_threads(512)
+    assert lib.chert_set_cache_finish_threads(prev) == 512
+    # the surrogate cache with its device-side fallback list: the network's
+    # scratch plus one int64 per solve and the counter
+    s1 = lib.chert_surrogate_cache_workspace_bytes(10, 30)
+    s2 = lib.chert_cache_surrogate_workspace_bytes(10, 3, 30)
+    assert s1 > 0 and s2 >= s1 + 8 * 3 * 10 * 31 + 8
+    assert lib.chert_cache_surrogate_workspace_bytes(10, 4, 30) == 0
+    assert lib.chert_cache_surrogate_workspace_bytes(0, 3, 30) == 0
+    # argument checks before any launch
+    assert lib.chert_traveltime_batch(None, 1, 1, chert.FP64, None, 0, 8, None, None) == chert.EINVAL
+    arr = (chert.chert_lattice * 49)()
+    off = (ctypes.c_int32 * 3)(1, 0, 0)
+    ctr = ctypes.c_void_p(8)                                   # never dereferenced: the count is refused first
+    assert lib.chert_traveltime_batch(arr, 49, 1, chert.FP64, off, 1, 8, ctr, None) == chert.EINVAL
+    assert "n_lattices" in lib.chert_last_error().decode()
+    assert lib.chert_angular_coverage(None, 1, 1, 8, chert.FP32, None, 0, None, None, None, None, None) == chert.EINVAL
+    assert lib.chert_mlp_set_wait_limit(-1) in (1 << 22, chert.ECUDA)
