@@ -260,3 +260,24 @@ def test_frontier_label_correcting_equals_sweeps(torch_dev, precision):
                                                    precision),
                                nx, nz, (np.arange(nx * nz) % 2).astype(np.int32), inputs.stencil_2d(2),
                                [0, nx * nz - 1])
+
+
+def test_frontier_round_cap_reports_timeout(torch_dev):
+    """The frontier scheduler runs at most max_cycles x max(nx, nz) rounds: on
+    the 12-bend serpentine, whose shortest paths take far more than 280 hops,
+    max_cycles = 1 stops it and the call reports CHERT_ETIMEOUT; the same
+    context then relaxes the field to the sweeps' fixed point."""
+    nx, nz = 280, 120
+    cls = _serpentine(nx, nz, 12)
+    cache = as_cache(torch_dev, _synthetic_cache([150.0, 6000.0], [1e-3, 1e-5]), "fp32")
+    off = inputs.stencil_2d(3)
+    src = [2 + nx * 1]
+    d_cls = torch_dev.as_tensor(cls, device="cuda")
+    prev = chert.set_relax_scheduler("frontier")
+    try:
+        with pytest.raises(chert.ChertError) as e:
+            chert.traveltime(cache, nx, nz, 10.0, d_cls, off, src, max_cycles=1)
+        assert e.value.code == chert.ETIMEOUT
+    finally:
+        chert.set_relax_scheduler(prev)
+    frontier_equals_sweeps(torch_dev, cache, nx, nz, cls, off, src)
