@@ -550,21 +550,29 @@ __device__ bool verify_rows1(const Ctx<T>& c, T* __restrict__ tau, int64_t src, 
     return __syncthreads_or(changed);
 }
 
-// Any number of nodes of a line per thread (strided by the block size).
+// Several adjacent nodes of a line per thread: thread t takes nodes
+// PPT*t .. PPT*t + PPT-1.  The pulls of a thread's nodes from one previous
+// line read overlapping windows of that line in the ring (offsets -R..R of
+// each node), and in row sweeps and the verification the same weight serves
+// all of them, so the unrolled loop loads each ring cell and each weight once
+// for the PPT nodes: about (2R + PPT) + 2R + 1 shared loads per PPT (2R + 1)
+// pulls, against two per pull with one node a thread.  Same pulls, in the same
+// order per node, same rounding: fields and parents are bit-identical.
 template <typename T, int R, int PPT, int AXIS, int DIR>
 __device__ void sweep_rows(const Ctx<T>& c, T* __restrict__ tau, int pass, int since) {
     constexpr int N = Stencil<R>::N;
     const int n_lines = AXIS == 0 ? c.nz : c.nx;
     const int len = AXIS == 0 ? c.nx : c.nz;
-    const int nx = c.nx, nk = c.nk;
+    const int nx = c.nx;
     const int tid = threadIdx.x, bd = blockDim.x;
+    const int u0 = PPT * tid;                       // the thread's first node
     T* ring = reinterpret_cast<T*>(c.ring);
     for (int i = tid; i < 8 * c.LS; i += bd) ring[i] = T(INFINITY);
     __syncthreads();
     // wo[p][oz + R]: offset in W of the class pair (row of i = j - o, row of j)
     // for the entries with z component oz.  Column sweeps: fixed per node for
-    // the whole sweep (depth z = u); row sweeps: fixed per line, the same for
-    // every node of the line (kept in wo[0]).
+    // the whole sweep (depth z = u0 + p); row sweeps: fixed per line, the same
+    // for every node of the line (kept in wo[0]).
     constexpr int NW = AXIS == 1 ? PPT : 1;
     int wo[NW][2 * R + 1];
     auto set_wo = [&](int slot, int zj) {
@@ -574,7 +582,7 @@ __device__ void sweep_rows(const Ctx<T>& c, T* __restrict__ tau, int pass, int s
     };
     if constexpr (AXIS == 1) {
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) set_wo(p, min(tid + p * bd, len - 1));
+        for (int p = 0; p < PPT; ++p) set_wo(p, min(u0 + p, len - 1));
     }
     auto gidx = [&](int line, int u) {
         return AXIS == 0 ? (size_t)u + (size_t)nx * line : (size_t)line + (size_t)nx * u;
@@ -582,7 +590,7 @@ __device__ void sweep_rows(const Ctx<T>& c, T* __restrict__ tau, int pass, int s
     auto ring_line = [&](int line) {
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            const int u = tid + p * bd;
+            const int u = u0 + p;
             if (u < len)
                 ring[(line & 7) * c.LS + R + u] = (line >= 0 && line < n_lines) ? tau[gidx(line, u)] : T(INFINITY);
         }
@@ -590,7 +598,7 @@ __device__ void sweep_rows(const Ctx<T>& c, T* __restrict__ tau, int pass, int s
     auto load = [&](int line, T* t) {
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            const int u = tid + p * bd;
+            const int u = u0 + p;
             t[p] = u < len ? tau[gidx(line, u)] : T(INFINITY);
         }
     };
@@ -619,34 +627,48 @@ __device__ void sweep_rows(const Ctx<T>& c, T* __restrict__ tau, int pass, int s
         T nxt[PPT];
         if (step + 1 < n_lines) load(DIR > 0 ? line + 1 : line - 1, nxt);
         const int own = (line & 7) * c.LS + R;
+        if (u0 < len) {
+            int po[R + 1];                  // ring offsets of the thread's first node in the previous lines
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) {
-            const int u = tid + p * bd;
-            if (u < len) {
-                int po[R + 1];              // ring offsets of the previous lines (32-bit shared indices)
+            for (int lag = 1; lag <= R; ++lag) po[lag] = ((line - DIR * lag) & 7) * c.LS + R + u0;
+            // the thread's nodes share their tile (PPT divides the tile width)
+            const int tx = (AXIS == 0 ? u0 : line) / kTile, tz = (AXIS == 0 ? line : u0) / kTile;
+            T best[PPT];
 #pragma unroll
-                for (int lag = 1; lag <= R; ++lag) po[lag] = ((line - DIR * lag) & 7) * c.LS + R + u;
-                const int* w = wo[AXIS == 1 ? p : 0];
-                const int tx = (AXIS == 0 ? u : line) / kTile, tz = (AXIS == 0 ? line : u) / kTile;
-                T best = cur[p];
-                if (dirty(c, tx, tz, since)) {
-                    static_for<N>([&](auto qc) {
-                        constexpr int q = decltype(qc)::value;
-                        constexpr int oa = AXIS == 0 ? Table<R>::v.z[q] : Table<R>::v.x[q];
-                        constexpr int ol = AXIS == 0 ? Table<R>::v.x[q] : Table<R>::v.z[q];
-                        if constexpr (oa * DIR > 0) {
-                            constexpr int lag = oa * DIR;
-                            constexpr int oz = Table<R>::v.z[q];
-                            best = fmin_(best, ring[po[lag] - ol] + c.W[w[oz + R] + q]);
+            for (int p = 0; p < PPT; ++p) best[p] = cur[p];
+            if (dirty(c, tx, tz, since)) {
+                static_for<N>([&](auto qc) {
+                    constexpr int q = decltype(qc)::value;
+                    constexpr int oa = AXIS == 0 ? Table<R>::v.z[q] : Table<R>::v.x[q];
+                    constexpr int ol = AXIS == 0 ? Table<R>::v.x[q] : Table<R>::v.z[q];
+                    if constexpr (oa * DIR > 0) {
+                        constexpr int lag = oa * DIR;
+                        constexpr int oz = Table<R>::v.z[q];
+                        if constexpr (AXIS == 0) {
+                            const T w = c.W[wo[0][oz + R] + q];
+#pragma unroll
+                            for (int p = 0; p < PPT; ++p) best[p] = fmin_(best[p], ring[po[lag] + p - ol] + w);
+                        } else {
+#pragma unroll
+                            for (int p = 0; p < PPT; ++p)
+                                best[p] = fmin_(best[p], ring[po[lag] + p - ol] + c.W[wo[p][oz + R] + q]);
                         }
-                    });
-                }
-                ring[own + u] = best;
-                if (best < cur[p]) {
-                    tau[gidx(line, u)] = best;
-                    c.stamp[tz * c.TX + tx] = pass;
+                    }
+                });
+            }
+            bool touched = false;
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) {
+                const int u = u0 + p;
+                if (u < len) {
+                    ring[own + u] = best[p];
+                    if (best[p] < cur[p]) {
+                        tau[gidx(line, u)] = best[p];
+                        touched = true;
+                    }
                 }
             }
+            if (touched) c.stamp[tz * c.TX + tx] = pass;
         }
         __syncthreads();
 #pragma unroll
@@ -656,20 +678,22 @@ __device__ void sweep_rows(const Ctx<T>& c, T* __restrict__ tau, int pass, int s
 
 // Verification pass of the row-class path: rows, a 16-row ring of tau; the
 // weights of the row's in-neighbours are read from the class-pair table at
-// addresses that are the same for every thread (one broadcast per load).
+// addresses that are the same for every thread (one broadcast per load) and
+// serve the thread's PPT adjacent nodes.
 template <typename T, int R, int PPT>
 __device__ bool verify_rows(const Ctx<T>& c, T* __restrict__ tau, int64_t src, int32_t* __restrict__ par,
                             int pass, int since) {
     constexpr int N = Stencil<R>::N;
-    const int nx = c.nx, nz = c.nz, nk = c.nk;
+    const int nx = c.nx, nz = c.nz;
     const int tid = threadIdx.x, bd = blockDim.x;
+    const int x0 = PPT * tid;
     T* ring = reinterpret_cast<T*>(c.ring);
     for (int i = tid; i < 16 * c.LS; i += bd) ring[i] = T(INFINITY);
     __syncthreads();
     auto store_row = [&](int row) {
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
-            const int x = tid + p * bd;
+            const int x = x0 + p;
             if (x < nx)
                 ring[(row & 15) * c.LS + R + x] = (row >= 0 && row < nz) ? tau[(size_t)x + (size_t)nx * row] : T(INFINITY);
         }
@@ -691,38 +715,52 @@ __device__ bool verify_rows(const Ctx<T>& c, T* __restrict__ tau, int64_t src, i
         }
         store_row(z + R);
         __syncthreads();
-        int wo[2 * R + 1];                  // weight-table offsets of the rows z - d
-        const int kj = c.rowk[z];
+        if (x0 < nx && dirty(c, x0 / kTile, z / kTile, since)) {
+            int wo[2 * R + 1], po[2 * R + 1];   // weight-table offsets and ring offsets of the rows z - d
+            const int kj = c.rowk[z];
 #pragma unroll
-        for (int d = -R; d <= R; ++d) wo[d + R] = c.rowoff[z - d] + kj * N;
+            for (int d = -R; d <= R; ++d) {
+                wo[d + R] = c.rowoff[z - d] + kj * N;
+                po[d + R] = ((z - d) & 15) * c.LS + R + x0;
+            }
+            T best[PPT];
+            int bq[PPT];
 #pragma unroll
-        for (int p = 0; p < PPT; ++p) {
-            const int x = tid + p * bd;
-            if (x < nx && dirty(c, x / kTile, z / kTile, since)) {
-                int po[2 * R + 1];          // ring offsets of rows z - d
+            for (int p = 0; p < PPT; ++p) {
+                best[p] = T(INFINITY);
+                bq[p] = -1;
+            }
+            static_for<N>([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                constexpr int oz = Table<R>::v.z[q], ox = Table<R>::v.x[q];
+                const T w = c.W[wo[oz + R] + q];
 #pragma unroll
-                for (int d = -R; d <= R; ++d) po[d + R] = ((z - d) & 15) * c.LS + R + x;
-                const T cur = ring[po[R]];
+                for (int p = 0; p < PPT; ++p) {
+                    const T cand = ring[po[oz + R] + p - ox] + w;
+                    if (cand < best[p]) { best[p] = cand; bq[p] = q; }
+                }
+            });
+            bool touched = false;
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) {
+                const int x = x0 + p;
+                if (x >= nx) continue;
+                const T cur = ring[po[R] + p];
                 const size_t j = (size_t)x + (size_t)nx * z;
-                T best = T(INFINITY);
-                int bq = -1;
-                static_for<N>([&](auto qc) {
-                    constexpr int q = decltype(qc)::value;
-                    constexpr int oz = Table<R>::v.z[q], ox = Table<R>::v.x[q];
-                    const T cand = ring[po[oz + R] - ox] + c.W[wo[oz + R] + q];
-                    if (cand < best) { best = cand; bq = q; }
-                });
-                if (best < cur) {
-                    tau[j] = best;
-                    changed = true;
-                    c.stamp[(z / kTile) * c.TX + x / kTile] = pass;
+                if (best[p] < cur) {
+                    tau[j] = best[p];
+                    touched = true;
                 } else if (par) {
                     int32_t pj;
                     if ((int64_t)j == src) pj = (int32_t)src;
-                    else if (isinf(cur) || bq < 0) pj = -1;
-                    else pj = (int32_t)((long long)j - ((long long)c.sz[bq] * nx + c.sx[bq]));
+                    else if (isinf(cur) || bq[p] < 0) pj = -1;
+                    else pj = (int32_t)((long long)j - ((long long)c.sz[bq[p]] * nx + c.sx[bq[p]]));
                     par[j] = pj;
                 }
+            }
+            if (touched) {
+                changed = true;
+                c.stamp[(z / kTile) * c.TX + x0 / kTile] = pass;
             }
         }
     }
