@@ -188,3 +188,13 @@ def test_new_switches_and_sizes_host_only(lib):
     assert "n_lattices" in lib.chert_last_error().decode()
     assert lib.chert_angular_coverage(None, 1, 1, 8, chert.FP32, None, 0, None, None, None, None, None) == chert.EINVAL
     assert lib.chert_mlp_set_wait_limit(-1) in (1 << 22, chert.ECUDA)
+
+
+def test_autotuner_keeps_the_first_shape_on_a_tie():
+    """The launch-shape choice of the autotuners: the smallest candidate unless
+    another is faster by more than 3%, so timing noise does not flip it."""
+    from paper_2609_26108_b300.pipeline import _pick
+    assert _pick({1: 7.27, 2: 7.27, 4: 7.88}) == 1
+    assert _pick({1: 7.27, 2: 7.10, 4: 7.88}) == 1            # 2.3% faster: a tie
+    assert _pick({1: 8.00, 2: 7.50, 4: 7.90}) == 2
+    assert _pick({0: 1490.0, 1: 1450.0}) == 1
