@@ -197,4 +197,4 @@ def test_autotuner_keeps_the_first_shape_on_a_tie():
     assert _pick({1: 7.27, 2: 7.27, 4: 7.88}) == 1
     assert _pick({1: 7.27, 2: 7.10, 4: 7.88}) == 1            # 2.3% faster: a tie
     assert _pick({1: 8.00, 2: 7.50, 4: 7.90}) == 2
-    assert _pick({0: 1490.0, 1: 1450.0}) == 1
+    assert _pick({0: 1490.0, 1: 1440.0}) == 1                  # 3.4% faster
