@@ -14,6 +14,11 @@ step h = 0.001 deg, K = 30000 (the [-30, 30] deg bracket):
   model (seed 1003) drawn (PCG64 seed 4242) from a 241 x 101 slice of it
   (x 730..970, z 120..220, across the fault), with their Thomsen parameters,
   in qP, qSV and qSH: 13,104 solves.
+* ``homogeneous_vti_cache_M90.txt``: the one class of the small homogeneous
+  visco-VTI case (inputs.homogeneous_vti(): Vp0 3000, Vs0 1500, eps 0.2,
+  delta 0.1, gamma 0.1, Qp 60, Qs 30) in qP, qSV and qSH: 273 solves.
+
+``--which homogeneous`` writes that one only.
 
 Each solve line: mode class j flag vartheta V A Q r_x r_z, with r the ray
 direction in the class's symmetry-axis frame (before the tilt rotation);
@@ -84,9 +89,25 @@ def write(path, header, rows, tasks_meta):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--procs", type=int, default=os.cpu_count() or 1)
+    ap.add_argument("--which", default="all", choices=["all", "homogeneous"])
     args = ap.parse_args()
     from oracle import cache_oracle as co
     from paper_2609_26108_b300 import inputs
+
+    common = ["written by tests/golden/make_cache_golden.py from oracle/cache_oracle.py alone",
+              "kernel MEV, M = %d, scan step 0.001 deg, K = %d" % (M, K),
+              "columns: mode class j flag vartheta V A Q r_x r_z (r in the symmetry-axis frame)"]
+    if True:                                   # the homogeneous case (every run)
+        L = inputs.homogeneous_vti().layers[0]
+        a5 = co.moduli_from_thomsen(L.vp0, L.vs0, L.eps, L.delta, L.gamma, L.qp, L.qs)
+        meta = [(m, 0) for m in MODES]
+        with mp.get_context("spawn").Pool(min(args.procs, len(meta))) as pool:
+            rows = pool.map(_solve, [(m, a5) for m, _ in meta], chunksize=1)
+        write(os.path.join(HERE, "homogeneous_vti_cache_M90.txt"),
+              ["homogeneous visco-VTI: inputs.homogeneous_vti(), 1 class"] + common + ["tilts: " + _fmt(L.tilt)],
+              rows, meta)
+        if args.which == "homogeneous":
+            return
 
     layered = inputs.layered_tti().layers
     lay_mods = [co.moduli_from_thomsen(L.vp0, L.vs0, L.eps, L.delta, L.gamma, L.qp, L.qs) for L in layered]
@@ -102,9 +123,6 @@ def main():
         rows = pool.map(_solve, tasks, chunksize=1)
     print("%d solves in %.0f s on %d processes" % ((M + 1) * len(tasks), time.time() - t0, args.procs))
 
-    common = ["written by tests/golden/make_cache_golden.py from oracle/cache_oracle.py alone",
-              "kernel MEV, M = %d, scan step 0.001 deg, K = %d" % (M, K),
-              "columns: mode class j flag vartheta V A Q r_x r_z (r in the symmetry-axis frame)"]
     write(os.path.join(HERE, "layered_tti_cache_M90.txt"),
           ["layered 401x401 model: inputs.layered_tti(), 8 classes, PCG64 seed 1002"] + common +
           ["tilts: " + " ".join(_fmt(L.tilt) for L in layered)],

@@ -49,3 +49,31 @@ def test_cell_golden_is_the_oracle():
             for _, p in g["cells"]]
     rng = np.random.default_rng(12)
     _resolve(g, mods, [("qSV", int(rng.integers(48)), int(rng.integers(91))) for _ in range(2)])
+
+
+def test_homogeneous_golden_axes_closed_form_and_oracle():
+    """The small case's golden (tests/golden/homogeneous_vti_cache_M90.txt):
+    along the symmetry axis (j = 0) and across it (j = 90) of a VTI medium
+    the qP, qSV and qSH waves are homogeneous plane waves with ray along the
+    slowness, so vartheta = 0 and, with c^2 the modulus of the direction
+    (qP: a33 / a11; qSV: a44 both ways; qSH: a44 / a66), V = 1/Re(1/c),
+    A = Im(1/c), Q = -Re(c^2)/Im(c^2) (Eq. 10-11).  The C1 moduli (a11 =
+    1.26e7, a13 = 5.3468744e6, a33 = 9.0e6, a44 = 2.25e6, a66 = 2.7e6) are
+    checked on the way; two sampled solves are the oracle's again."""
+    g = load_cache_golden("homogeneous_vti_cache_M90.txt")
+    L = inputs.homogeneous_vti().layers[0]
+    a = co.moduli_from_thomsen(L.vp0, L.vs0, L.eps, L.delta, L.gamma, L.qp, L.qs)
+    assert np.allclose(np.real(a), [1.26e7, 5.3468744e6, 9.0e6, 2.25e6, 2.7e6], rtol=1e-8)
+    assert len(g["folded"]) == 3 and all(len(v) == 91 for v in g["folded"].values())
+    a11, a13, a33, a44, a66 = a
+    for mode, along, across in (("qP", a33, a11), ("qSV", a44, a44), ("qSH", a44, a66)):
+        for j, c2 in ((0, along), (90, across)):
+            s = g["folded"][(mode, 0)][j]
+            c = np.sqrt(complex(c2))
+            assert s["flag"] == 0 and abs(s["vartheta"]) < 1e-13
+            assert math.isclose(s["V"], 1 / (1 / c).real, rel_tol=1e-12)
+            assert math.isclose(s["A"], (1 / c).imag, rel_tol=1e-12)
+            assert math.isclose(s["Q"], -complex(c2).real / complex(c2).imag, rel_tol=1e-12)
+            r = s["r"][[0, 2]]
+            assert np.allclose(r, [0.0, 1.0] if j == 0 else [1.0, 0.0], atol=1e-12)
+    _resolve(g, [a], [("qP", 0, 37), ("qSV", 0, 52)])
