@@ -336,10 +336,11 @@ int chert_traveltime_enqueue(const chert_cache_arrays* cache, int n_modes, int n
  * previous setting, or CHERT_EINVAL. */
 int chert_set_relax3d_tile(int tile);
 
-/* One 3D lattice of chert_traveltime_batch: chert_traveltime_enqueue's
+/* One lattice of chert_traveltime_batch: chert_traveltime_enqueue's
  * arguments for it (its own cache, classes, class map, device sources,
- * outputs, workspace of chert_traveltime_workspace_bytes and device status
- * int32[2]); ny > 1. */
+ * outputs, workspace and device status int32[2]).  3D: ny > 1, workspace of
+ * chert_traveltime_workspace_bytes.  2D: ny = 1, workspace of
+ * chert_traveltime_workspace_bytes_grid (room for per-node weights). */
 typedef struct {
     const chert_cache_arrays* cache;
     int n_classes, n_dir;
@@ -357,14 +358,24 @@ typedef struct {
     int32_t* d_status;
 } chert_lattice;
 
-/* Several 3D lattices of uneven size (up to 48; same modes, precision,
- * stencil and cycle cap) relaxed in ONE persistent launch: every lattice's
- * field components are work items, numbered largest lattice first; a grid of
- * one wave of resident CTAs claims them from the device counter d_counter
- * (device uint64, zeroed here on `stream`) until none is left, each item
- * relaxed as chert_traveltime relaxes it (same fields, parents and status,
- * bit for bit).  Edge tables and class checks run per lattice before it.  No
- * host synchronisation: capturable.  Errors: as chert_traveltime_enqueue. */
+/* Several lattices of uneven size (up to 48; all 3D or all 2D; same modes,
+ * precision, stencil and cycle cap) relaxed in persistent launches: every
+ * lattice's field components are work items, numbered largest lattice first;
+ * a grid of one wave of resident CTAs claims them from the device counter
+ * d_counter (device uint64, zeroed here on `stream`) until none is left.
+ *   3D: ONE launch of the plane-sweep kernel; each item relaxed as
+ *       chert_traveltime relaxes it (same fields, parents and status, bit for
+ *       bit).
+ *   2D: the lattices the specialised sweep kernel takes with the radius-5
+ *       stencil, grouped by launch shape (nodes a thread, class-pair table or
+ *       per-node weights), each group one launch of up to 24 lattices,
+ *       attenuation components first; each item relaxed as chert_traveltime
+ *       relaxes it under the sweeps scheduler (scheduler 0: no block-heap
+ *       continuation).  Other 2D lattices are relaxed on their own, as
+ *       chert_traveltime_enqueue relaxes them.
+ * Edge tables and class checks run per lattice before the launches.  No host
+ * synchronisation: capturable.  Errors: as chert_traveltime_enqueue;
+ * CHERT_EINVAL for a mix of 2D and 3D lattices. */
 int chert_traveltime_batch(const chert_lattice* lattices, int n_lattices, int n_modes, int precision,
                            const int32_t* offsets, int n_off, int max_cycles,
                            unsigned long long* d_counter, void* stream);

@@ -1569,12 +1569,24 @@ static PnLayout pn_layout(int n_modes, int n_classes, int n_off, int precision, 
     return L;
 }
 
-// Returns 1 if the specialised kernel was launched, 0 if the caller must use
-// the generic one, or a negative status.  pn_area (pn_bytes long) is the
+// A 2D lattice prepared for a batched launch of the specialised kernel: its
+// arguments (per-node weights and row classes already enqueued) and launch
+// shape.
+struct FastPrep {
+    fast::Args a;
+    int R, ppt, threads, blocks;
+    bool pn, dbl;
+    size_t smem;
+};
+
+// Returns 1 if the specialised kernel was launched (or, with prep, set up for
+// a batched launch and described in *prep), 0 if the caller must use the
+// generic one, or a negative status.  pn_area (pn_bytes long) is the
 // workspace's per-node area, or null.
 template <typename T, int R>
 static int try_fast_R(fast::Args& a, const Offsets& off, int smem_max, int blocks, const void* Vsel,
-                      unsigned char* pn_area, size_t pn_bytes, int n_modes, int* rowk_area, cudaStream_t s) {
+                      unsigned char* pn_area, size_t pn_bytes, int n_modes, int* rowk_area, cudaStream_t s,
+                      FastPrep* prep = nullptr) {
     if (!standard_map<R>(off, a.map)) return 0;
     const int line_max = std::max(a.nx, a.nz);
     if (line_max > 2048) return 0;
@@ -1618,6 +1630,17 @@ static int try_fast_R(fast::Args& a, const Offsets& off, int smem_max, int block
         if (rc0) return rc0;
         a.rowk = rowk_area;
     }
+    if (prep) {
+        prep->a = a;
+        prep->R = R;
+        prep->ppt = ppt;
+        prep->threads = threads;
+        prep->blocks = blocks;
+        prep->pn = pn;
+        prep->dbl = sizeof(T) == 8;
+        prep->smem = smem;
+        return 1;
+    }
     int rc;
     if (pn)
         rc = ppt == 1 ? launch_fast_ppt<T, R, 1, true>(a, smem, blocks, threads, s)
@@ -1632,12 +1655,13 @@ static int try_fast_R(fast::Args& a, const Offsets& off, int smem_max, int block
 
 template <typename T>
 static int try_fast(fast::Args& a, const Offsets& off, int R, int smem_max, int blocks, const void* Vsel,
-                    unsigned char* pn_area, size_t pn_bytes, int n_modes, int* rowk_area, cudaStream_t s) {
+                    unsigned char* pn_area, size_t pn_bytes, int n_modes, int* rowk_area, cudaStream_t s,
+                    FastPrep* prep = nullptr) {
     switch (R) {
-        case 2: return try_fast_R<T, 2>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s);
-        case 3: return try_fast_R<T, 3>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s);
-        case 4: return try_fast_R<T, 4>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s);
-        case 5: return try_fast_R<T, 5>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s);
+        case 2: return try_fast_R<T, 2>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s, prep);
+        case 3: return try_fast_R<T, 3>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s, prep);
+        case 4: return try_fast_R<T, 4>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s, prep);
+        case 5: return try_fast_R<T, 5>(a, off, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes, rowk_area, s, prep);
         default: return 0;
     }
 }
@@ -1660,10 +1684,14 @@ extern "C" size_t chert_traveltime_workspace_bytes_grid(int n_modes, int n_class
 // `s`, using `w` (bytes long) as scratch.  On success *blocks_out is the number
 // of relaxation CTAs and *status_out points at their status words (followed by
 // the class-check flag), which the caller reads back.
-// A 3D lattice prepared (edge tables, class check, status) for a batched launch.
+// A lattice prepared (edge tables, class check, status) for a batched launch:
+// 3D (FieldArgs, halo H) or 2D (fast2d set, fast2d_ok = 1 when the
+// specialised kernel takes it; 0: the caller relaxes it on its own).
 struct Prep3 {
     FieldArgs a;
     int H, blocks;
+    FastPrep fast2d;
+    int fast2d_ok;
 };
 
 static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, int n_modes,
@@ -1761,6 +1789,30 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         if (rc) return rc;
         *blocks_out = blocks;
         *status_out = a.status;
+        return CHERT_OK;
+    }
+    if (prep) {
+        // a batched launch (chert_traveltime_batch): the sweeps of the
+        // specialised kernel, set up here and launched with the batch
+        fast::Args fa;
+        fa.nx = nx; fa.nz = nz; fa.n_classes = n_classes; fa.n_modes = n_modes;
+        fa.max_cycles = max_cycles; fa.dx = dx; fa.cls = a.cls; fa.src = a.src;
+        fa.tauR = d_tauR; fa.tauI = d_tauI; fa.parR = d_parR; fa.parI = d_parI;
+        fa.Vsel = Vsel; fa.Asel = Asel; fa.n_off = n_off; fa.status = a.status;
+        fa.wrow = fa.wcol = nullptr;
+        unsigned char* pn_area = bytes > ws.total ? w + ws.total : nullptr;
+        const size_t pn_bytes = bytes > ws.total ? bytes - ws.total : 0;
+        int* rowk_area = reinterpret_cast<int*>(w + ws.rowk);
+        const int fr = precision == CHERT_FP64
+                           ? try_fast<double>(fa, off, R, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes,
+                                              rowk_area, s, &prep->fast2d)
+                           : try_fast<float>(fa, off, R, smem_max, blocks, Vsel, pn_area, pn_bytes, n_modes,
+                                             rowk_area, s, &prep->fast2d);
+        if (fr < 0) return fr;
+        prep->fast2d_ok = fr;
+        prep->a = a;
+        prep->H = 0;
+        prep->blocks = blocks;
         return CHERT_OK;
     }
     // 2D schedulers: 0 sweeps; 1 block-heap marching; 2 sweeps for at most
@@ -2049,6 +2101,106 @@ static int launch_multi3d(const LatticeTable& t, const Offsets& off, int H, cons
     return launch_check("chert_traveltime_batch: relax3d (persistent)");
 }
 
+// One persistent launch of 2D lattices that share a launch shape (radius-5
+// stencil, nodes a thread, weight form, precision): at most
+// kMaxFastLattices of them.
+template <typename T, int PPT, bool PN>
+static int launch_multi2d(const fast::FastTable& t, int threads, size_t smem, long long items,
+                          unsigned long long* counter, cudaStream_t s) {
+    auto k = fast::relax_fast_multi_kernel<T, 5, PPT, PN>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime_batch: smem attribute");
+    int dev = 0, n_sm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        n_sm = 148;
+        per_sm = 1;
+    }
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "chert_traveltime_batch: counter");
+    const long long grid = std::min<long long>(items, (long long)n_sm * per_sm);   // persistent: one wave
+    k<<<(unsigned)grid, threads, smem, s>>>(t, counter);
+    return launch_check("chert_traveltime_batch: relax_fast (persistent)");
+}
+
+// The 2D lattices of a batch: the ones the specialised kernel takes with the
+// radius-5 stencil are grouped by launch shape, each group one persistent
+// launch (of at most kMaxFastLattices lattices); the others are relaxed on
+// their own, as chert_traveltime_enqueue relaxes them.
+static int batch_2d(const chert_lattice* lattices, int n_lattices, int n_modes, int precision,
+                    const int32_t* offsets, int n_off, int max_cycles, std::vector<Prep3>& prep,
+                    unsigned long long* d_counter, cudaStream_t s) {
+    std::vector<int> alone, grouped;
+    for (int i = 0; i < n_lattices; ++i)
+        (prep[i].fast2d_ok == 1 && prep[i].fast2d.R == 5 ? grouped : alone).push_back(i);
+    for (int i : alone) {
+        const chert_lattice& L = lattices[i];
+        const int rc = chert_traveltime_enqueue(L.cache, n_modes, L.n_classes, L.n_dir, L.nx, 1, L.nz, L.dx,
+                                                L.d_class_of_node, offsets, n_off, L.d_sources, L.n_sources,
+                                                precision, max_cycles, L.d_tauR, L.d_tauI, L.d_parR, L.d_parI,
+                                                L.d_workspace, L.workspace_bytes, L.d_status, s);
+        if (rc) return rc;
+    }
+    // largest lattices first
+    std::stable_sort(grouped.begin(), grouped.end(), [&](int x, int y) {
+        const fast::Args &a = prep[x].fast2d.a, &b = prep[y].fast2d.a;
+        return (long long)a.nx * a.nz > (long long)b.nx * b.nz;
+    });
+    std::vector<char> done(n_lattices, 0);
+    for (size_t g0 = 0; g0 < grouped.size(); ++g0) {
+        const int lead = grouped[g0];
+        if (done[lead]) continue;
+        const FastPrep& P = prep[lead].fast2d;
+        std::vector<int> members;
+        for (size_t g = g0; g < grouped.size() && (int)members.size() < fast::kMaxFastLattices; ++g) {
+            const FastPrep& Q = prep[grouped[g]].fast2d;
+            if (!done[grouped[g]] && Q.ppt == P.ppt && Q.pn == P.pn && Q.dbl == P.dbl) {
+                members.push_back(grouped[g]);
+                done[grouped[g]] = 1;
+            }
+        }
+        fast::FastTable t;
+        t.n = (int)members.size();
+        long long at = 0;
+        int threads = 32;
+        size_t smem = 0;
+        for (int m = 0; m < t.n; ++m) {            // attenuation components of every lattice
+            const FastPrep& Q = prep[members[m]].fast2d;
+            t.a[m] = Q.a;
+            t.start[m] = at;
+            at += Q.blocks / 2;
+            threads = std::max(threads, Q.threads);
+            smem = std::max(smem, Q.smem);
+        }
+        for (int m = 0; m < t.n; ++m) {            // then the propagation components
+            t.start[t.n + m] = at;
+            at += prep[members[m]].fast2d.blocks / 2;
+        }
+        t.start[2 * t.n] = at;
+        int rc;
+        if (P.dbl)
+            rc = P.pn ? (P.ppt == 1 ? launch_multi2d<double, 1, true>(t, threads, smem, at, d_counter, s)
+                       : P.ppt == 2 ? launch_multi2d<double, 2, true>(t, threads, smem, at, d_counter, s)
+                                    : launch_multi2d<double, 4, true>(t, threads, smem, at, d_counter, s))
+                      : (P.ppt == 1 ? launch_multi2d<double, 1, false>(t, threads, smem, at, d_counter, s)
+                       : P.ppt == 2 ? launch_multi2d<double, 2, false>(t, threads, smem, at, d_counter, s)
+                                    : launch_multi2d<double, 4, false>(t, threads, smem, at, d_counter, s));
+        else
+            rc = P.pn ? (P.ppt == 1 ? launch_multi2d<float, 1, true>(t, threads, smem, at, d_counter, s)
+                       : P.ppt == 2 ? launch_multi2d<float, 2, true>(t, threads, smem, at, d_counter, s)
+                                    : launch_multi2d<float, 4, true>(t, threads, smem, at, d_counter, s))
+                      : (P.ppt == 1 ? launch_multi2d<float, 1, false>(t, threads, smem, at, d_counter, s)
+                       : P.ppt == 2 ? launch_multi2d<float, 2, false>(t, threads, smem, at, d_counter, s)
+                                    : launch_multi2d<float, 4, false>(t, threads, smem, at, d_counter, s));
+        if (rc) return rc;
+    }
+    for (int i : grouped)
+        status_summary_kernel<<<1, 256, 0, s>>>(prep[i].a.status, prep[i].blocks, lattices[i].d_status);
+    return launch_check("chert_traveltime_batch: status");
+}
+
 extern "C" int chert_traveltime_batch(const chert_lattice* lattices, int n_lattices, int n_modes, int precision,
                                       const int32_t* offsets, int n_off, int max_cycles,
                                       unsigned long long* d_counter, void* stream) {
@@ -2061,10 +2213,13 @@ extern "C" int chert_traveltime_batch(const chert_lattice* lattices, int n_latti
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<Prep3> prep(n_lattices);
     int max_nk = 1;
+    const bool two_d = lattices[0].ny == 1;
     for (int i = 0; i < n_lattices; ++i) {
         const chert_lattice& L = lattices[i];
         CHERT_REQUIRE(L.cache && L.d_sources && L.d_status, "%s: lattice %d: NULL cache, sources or status", who, i);
-        CHERT_REQUIRE(L.ny > 1, "%s: lattice %d is 2D (ny = 1); the batch takes 3D lattices", who, i);
+        CHERT_REQUIRE((L.ny == 1) == two_d, "%s: lattice %d: a batch is all 2D (ny = 1) or all 3D", who, i);
+        CHERT_REQUIRE(L.ny >= 1, "%s: lattice %d: ny=%d", who, i, L.ny);
+        prep[i].fast2d_ok = 0;
         int blocks = 0;
         int* st = nullptr;
         const int rc = enqueue_traveltime(who, L.cache, n_modes, L.n_classes, L.n_dir, L.nx, L.ny, L.nz, L.dx,
@@ -2076,6 +2231,8 @@ extern "C" int chert_traveltime_batch(const chert_lattice* lattices, int n_latti
         prep[i].a.parts = 1;
         max_nk = std::max(max_nk, L.n_classes);
     }
+    if (two_d)
+        return batch_2d(lattices, n_lattices, n_modes, precision, offsets, n_off, max_cycles, prep, d_counter, s);
     // largest lattices first, so that the longest items start first
     std::vector<int> order(n_lattices);
     for (int i = 0; i < n_lattices; ++i) order[i] = i;

@@ -767,16 +767,12 @@ __device__ bool verify_rows(const Ctx<T>& c, T* __restrict__ tau, int64_t src, i
     return __syncthreads_or(changed);
 }
 
+// One field component (field, comp) of one lattice, by the CTA.
 template <typename T, int R, int PPT, bool PN>
-__global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
+__device__ __forceinline__ void relax_fast_field(const Args& a, int field, int comp) {
     constexpr int N = Stencil<R>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nk = a.n_classes;
-    // Attenuation fields (several sweep cycles) launch first and propagation
-    // fields (mostly one cycle) fill the tail of the grid.
-    const int n_fields = gridDim.x >> 1;
-    const int comp = (int)blockIdx.x < n_fields ? 1 : 0;
-    const int field = comp ? (int)blockIdx.x : (int)blockIdx.x - n_fields;
     const int mode = field % a.n_modes;
     const int s = field / a.n_modes;
     const int line_max = max(a.nx, a.nz);
@@ -893,6 +889,53 @@ __global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
         }
     }
     if (threadIdx.x == 0) a.status[field * 2 + comp] = used;
+}
+
+template <typename T, int R, int PPT, bool PN>
+__global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
+    // Attenuation fields (several sweep cycles) launch first and propagation
+    // fields (mostly one cycle) fill the tail of the grid.
+    const int n_fields = gridDim.x >> 1;
+    const int comp = (int)blockIdx.x < n_fields ? 1 : 0;
+    const int field = comp ? (int)blockIdx.x : (int)blockIdx.x - n_fields;
+    relax_fast_field<T, R, PPT, PN>(a, field, comp);
+}
+
+// Several 2D lattices of one launch shape (stencil, nodes a thread, weight
+// form) in one persistent launch.  The work items are the field components
+// of every lattice: first the attenuation components of all lattices, then
+// the propagation ones (each lattice's in turn, largest lattice first; the
+// host orders the table).  Each CTA claims the next item from a device counter
+// (zeroed before the launch) until none is left, and relaxes it with its
+// lattice's arguments, read in place from the table (a kernel parameter).
+// The block is sized for the longest line of the batch and the shared memory
+// for its largest lattice.  With one node a thread the kernel is held to 64
+// registers, two CTAs an SM, as the single-lattice kernel chooses by itself
+// (a few bytes of spills); with 2 or 4 it keeps 128, no spills.
+constexpr int kMaxFastLattices = 24;
+
+struct FastTable {
+    int n;
+    long long start[2 * kMaxFastLattices + 1];   // item ranges: attenuation of lattice l at start[l], propagation at start[n + l]
+    Args a[kMaxFastLattices];
+};
+
+template <typename T, int R, int PPT, bool PN>
+__global__ void __launch_bounds__(512, PPT == 1 ? 2 : 1) relax_fast_multi_kernel(const __grid_constant__ FastTable t,
+                                                               unsigned long long* counter) {
+    __shared__ long long s_item;
+    const long long total = t.start[2 * t.n];
+    for (;;) {
+        __syncthreads();                      // the previous item's shared memory is no longer read
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= total) break;
+        int r = 0;
+        while (r + 1 < 2 * t.n && t.start[r + 1] <= item) ++r;
+        const int l = r < t.n ? r : r - t.n;
+        relax_fast_field<T, R, PPT, PN>(t.a[l], (int)(item - t.start[r]), r < t.n ? 1 : 0);
+    }
 }
 
 }  // namespace fast

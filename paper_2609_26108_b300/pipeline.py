@@ -214,10 +214,12 @@ class GraphBatch:
 
     persistent_3d: the 3D problems' relaxations run as ONE persistent launch
     (``chert_traveltime_batch``) once all their caches are built; they must
-    share modes, stencil, precision and cycle cap.  Problems with the same
-    classes tensor and cache settings share one cache build."""
+    share modes, stencil, precision and cycle cap.  persistent_2d: the same
+    for the 2D problems (one persistent launch per launch shape of the
+    specialised kernel, sweeps scheduler).  Problems with the same classes
+    tensor and cache settings share one cache build."""
 
-    def __init__(self, problems, device="cuda", persistent_3d=False):
+    def __init__(self, problems, device="cuda", persistent_3d=False, persistent_2d=False):
         import torch
         self.torch = torch
         self.problems = list(problems)
@@ -229,17 +231,22 @@ class GraphBatch:
                  p.scan_step, p.scan_half, p.kernel, id(p.surrogate_params))
             self.cache_owner.append(keys.setdefault(k, i))
         self.state = [self._allocate(p, device, self.cache_owner[i] == i) for i, p in enumerate(self.problems)]
-        three = [i for i, p in enumerate(self.problems) if p.ny > 1]
-        if persistent_3d and three:
-            q = [self.problems[i] for i in three]
+        # batched groups: the 3D problems and the 2D problems, each relaxed by
+        # one chert_traveltime_batch call on a stream and counter of its own
+        self.groups = []
+        for want, dims in ((persistent_3d, lambda p: p.ny > 1), (persistent_2d, lambda p: p.ny == 1)):
+            members = [i for i, p in enumerate(self.problems) if dims(p)]
+            if not want or not members:
+                continue
+            q = [self.problems[i] for i in members]
             same = all(p.modes == q[0].modes and np.array_equal(p.offsets, q[0].offsets) and
                        p.cache_precision == q[0].cache_precision and p.relax_precision == q[0].relax_precision and
                        p.max_cycles == q[0].max_cycles for p in q)
             if not same:
-                raise ValueError("persistent_3d: the 3D problems must share modes, stencil, precision and cycle cap")
-        self.three = three if persistent_3d else []
-        self.counter = torch.zeros(1, dtype=torch.int64, device=device)
-        self.stream3 = torch.cuda.Stream(device=device)
+                raise ValueError("a persistent group's problems must share modes, stencil, precision and cycle cap")
+            self.groups.append({"members": members, "counter": torch.zeros(1, dtype=torch.int64, device=device),
+                                "stream": torch.cuda.Stream(device=device)})
+        self.batched = {i for g in self.groups for i in g["members"]}
         self.graph = None
 
     def _allocate(self, p, device, owns_cache):
@@ -306,17 +313,17 @@ class GraphBatch:
                                  st["status"], p.max_cycles, p.ny, stream, precision=prec)
         self._raypaths(p, st, stream)
 
-    def _relax_3d_batch(self, stream):
+    def _relax_group(self, g, stream):
         items = []
-        for i in self.three:
+        for i in g["members"]:
             p, st = self.problems[i], self.state[i]
             items.append({"cache": self.state[self.cache_owner[i]]["cache"], "nx": p.nx, "ny": p.ny, "nz": p.nz,
                           "dx": p.dx, "d_cls": p.d_cls, "d_sources": st["d_src"], "out": st["tau"],
                           "workspace": st["ws"], "d_status": st["status"]})
-        p0 = self.problems[self.three[0]]
-        chert.traveltime_batch(items, p0.offsets, self.counter, p0.max_cycles, stream,
+        p0 = self.problems[g["members"][0]]
+        chert.traveltime_batch(items, p0.offsets, g["counter"], p0.max_cycles, stream,
                                precision=p0.relax_precision)
-        for i in self.three:
+        for i in g["members"]:
             self._raypaths(self.problems[i], self.state[i], stream)
 
     def run_eager(self):
@@ -325,10 +332,10 @@ class GraphBatch:
             if self.cache_owner[i] == i:
                 self._build_cache(p, st, None)
         for i in range(len(self.problems)):
-            if i not in self.three:
+            if i not in self.batched:
                 self._relax(i, None)
-        if self.three:
-            self._relax_3d_batch(None)
+        for g in self.groups:
+            self._relax_group(g, None)
 
     def _timed(self, fn, repeats):
         torch = self.torch
@@ -354,8 +361,10 @@ class GraphBatch:
         out = {"tile3d": {}, "ppt2d": {}, "chosen": {}}
         three = [i for i, p in enumerate(self.problems) if p.ny > 1]
         two = [i for i, p in enumerate(self.problems) if p.ny == 1]
+        g3 = [g for g in self.groups if self.problems[g["members"][0]].ny > 1]
+        g2 = [g for g in self.groups if self.problems[g["members"][0]].ny == 1]
         if three:
-            run3 = (lambda: self._relax_3d_batch(None)) if self.three else \
+            run3 = (lambda: self._relax_group(g3[0], None)) if g3 else \
                 (lambda: [self._relax(i, None) for i in three])
             for tile in (0, 1):
                 chert.set_relax3d_tile(tile)
@@ -369,7 +378,9 @@ class GraphBatch:
                 if (line + ppt - 1) // ppt > 512:
                     continue
                 chert.lib().chert_set_relax_points_per_thread(ppt)
-                out["ppt2d"][ppt] = self._timed(lambda: [self._relax(i, None) for i in two], repeats)
+                run2 = (lambda: self._relax_group(g2[0], None)) if g2 else \
+                    (lambda: [self._relax(i, None) for i in two])
+                out["ppt2d"][ppt] = self._timed(run2, repeats)
             best = _pick(out["ppt2d"])
             chert.lib().chert_set_relax_points_per_thread(best)
             out["chosen"]["ppt2d"] = best
@@ -391,23 +402,23 @@ class GraphBatch:
                 if self.cache_owner[i] == i:
                     with torch.cuda.stream(st["stream"]):
                         self._build_cache(p, st, st["stream"])
-            # relaxations: each problem after its cache's build; the 3D batch
-            # after every 3D problem's cache
+            # relaxations: each problem after its cache's build; a batched
+            # group after every one of its problems' caches
             for i, st in enumerate(self.state):
-                if i in self.three:
+                if i in self.batched:
                     continue
                 s = st["stream"]
                 s.wait_stream(self.state[self.cache_owner[i]]["stream"])
                 with torch.cuda.stream(s):
                     self._relax(i, s)
-            if self.three:
-                s3 = self.stream3
-                s3.wait_stream(main)
-                for i in self.three:
-                    s3.wait_stream(self.state[self.cache_owner[i]]["stream"])
-                with torch.cuda.stream(s3):
-                    self._relax_3d_batch(s3)
-                main.wait_stream(s3)
+            for grp in self.groups:
+                sg = grp["stream"]
+                sg.wait_stream(main)
+                for i in grp["members"]:
+                    sg.wait_stream(self.state[self.cache_owner[i]]["stream"])
+                with torch.cuda.stream(sg):
+                    self._relax_group(grp, sg)
+                main.wait_stream(sg)
             for st in self.state:
                 main.wait_stream(st["stream"])
         self.graph = g

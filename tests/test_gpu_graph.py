@@ -96,11 +96,12 @@ def test_graph_batch_replays_eager_results(torch_dev):
 
 def test_persistent_batch_with_surrogate_and_autotuner(torch_dev):
     """The batched form of many problems: a per-cell 2D problem whose cache
-    comes from the surrogate with its exact fallback (chert_cache_surrogate),
-    and three 3D blocks of uneven size cut from one model (one shared cache
-    build) relaxed in one persistent launch (chert_traveltime_batch); launch
-    shapes chosen by the batch's autotuner, then the whole batch captured in
-    one CUDA graph.  Replays equal the eager pass bit for bit, and every
+    comes from the surrogate with its exact fallback (chert_cache_surrogate)
+    and a layered 2D problem, relaxed together by one batch call (persistent
+    launches of the specialised kernel), and three 3D blocks of uneven size
+    cut from one model (one shared cache build) relaxed in one persistent
+    launch; launch shapes chosen by the batch's autotuner, then the whole
+    batch captured in one CUDA graph.  Replays equal the eager pass bit for bit, and every
     problem's fields equal chert_traveltime on its own cache."""
     torch = torch_dev
     from test_gpu_surrogate import _decisive_nets
@@ -121,8 +122,14 @@ def test_persistent_batch_with_surrogate_and_autotuner(torch_dev):
                              torch.as_tensor(sub.class_of_node, device="cuda"), inputs.stencil_3d(2), sub.sources,
                              receivers=[0, size ** 3 - 1], n_az=24, n_pol=12, ny=sub.ny, cache_precision="mixed",
                              relax_precision="fp32_acc64", scan_step=0.02 * DEG, scan_half=1500))
-    batch = GraphBatch(probs, persistent_3d=True)
-    assert batch.cache_owner == [0, 1, 1, 1]
+    m = inputs.layered_tti(nx=61, nz=47, n_layers=4, n_sources=3)
+    probs.append(Problem(chert.classes_to_device(chert.classes_from_layers(m.layers)), len(m.layers),
+                         ["qP", "qSV", "qSH"], m.nx, m.nz, m.dx,
+                         torch.as_tensor(m.class_of_node.astype(np.int32), device="cuda"), inputs.stencil_2d(5),
+                         m.sources, receivers=[0, 30, m.nx * m.nz - 1], M=30, scan_step=0.02 * DEG, scan_half=1500))
+    batch = GraphBatch(probs, persistent_3d=True, persistent_2d=True)
+    assert batch.cache_owner == [0, 1, 1, 1, 4]
+    assert [sorted(g["members"]) for g in batch.groups] == [[1, 2, 3], [0, 4]]
     prev_tile = chert.set_relax3d_tile(0)
     prev_ppt = chert.lib().chert_set_relax_points_per_thread(0)
     try:
