@@ -969,10 +969,10 @@ def section_c5(n2d=512, n_blocks=8, n3d_per_block=16, block=101):
     seeded corners of the 201^3 layered 3D model with n3d_per_block sources
     x qP/qSV each.  One CUDA graph per form: the 2D per-cell cache (exact, or
     the surrogate with its exact fallback on the device), the 3D blocks' one
-    shared MIXED cache (1 x 1 deg), the 2D relaxation with parents (a
-    persistent launch of the specialised kernel), the 3D blocks' relaxations
-    in ONE persistent launch (float weights, float-float accumulation),
-    raypaths to receiver lines.  Launch shapes (3D tile, 2D
+    shared MIXED cache (1 x 1 deg), the 2D relaxation with parents (hybrid
+    scheduler: its per-cell qSV attenuation fields need block-heap marching),
+    the 3D blocks' relaxations in ONE persistent launch (float weights,
+    float-float accumulation), raypaths to receiver lines.  Launch shapes (3D tile, 2D
     points per thread) come from the batch's autotuner on the first eager
     pass.  Timed: one graph replay per form (the surrogate's training is
     one-off, before)."""
@@ -1008,7 +1008,7 @@ def section_c5(n2d=512, n_blocks=8, n3d_per_block=16, block=101):
                                      torch.as_tensor(b.class_of_node, device="cuda"), inputs.stencil_3d(2),
                                      b.sources, receivers=np.arange(0, b.nx * b.ny, 997), n_az=360, n_pol=180,
                                      ny=b.ny, cache_precision="mixed", relax_precision="fp32_acc64"))
-            batch = GraphBatch(probs, persistent_3d=True, persistent_2d=True)
+            batch = GraphBatch(probs, persistent_3d=True)
             t0 = time.perf_counter()
             batch.run_eager()
             torch.cuda.synchronize()

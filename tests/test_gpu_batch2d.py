@@ -1,6 +1,7 @@
 """chert_traveltime_batch on 2D lattices: lattices of uneven size and launch
-shape (the row-class path, the class-pair table, per-node weights, one and
-two nodes a thread) grouped into persistent launches, against
+shape (the row-class path, the class-pair table, per-node weights, one, two
+and four nodes a thread) grouped into persistent launches (a group of more
+than 24 lattices of one shape split over launches), against
 chert_traveltime on each lattice alone under the sweeps scheduler: fields and
 parents bit for bit, status [-1, 0] for each; also captured in a CUDA graph.
 A stencil other than radius 5 is relaxed lattice by lattice, with the same
@@ -60,6 +61,8 @@ def _cases(torch, precision, off):
         _item(torch, precision, 70, 50, rng.integers(0, 400, 70 * 50), [10, 3000], 400, off),  # per-node weights
         _item(torch, precision, 600, 40, inputs.layered_class_map_2d(600, 40, 5), [3, 599], 5, off),  # 2 nodes a thread
         _item(torch, precision, 64, 33, inputs.layered_class_map_2d(64, 33, 5), [0], 5, off),
+        _item(torch, precision, 1100, 24, inputs.layered_class_map_2d(1100, 24, 5), [7, 1100 * 12 + 1099], 5,
+              off),                                                         # 4 nodes a thread
     ]
 
 
@@ -98,6 +101,19 @@ def test_batch_of_uneven_2d_lattices_equals_single_calls(torch_dev, precision):
         g.replay()
         torch.cuda.synchronize()
         _check(torch, items, off)
+
+
+def test_batch_2d_more_lattices_than_one_launch_takes(torch_dev):
+    """26 lattices of one launch shape (one launch takes 24): two launches on
+    the one counter, each lattice as chert_traveltime relaxes it alone."""
+    torch = torch_dev
+    off = inputs.stencil_2d(5)
+    items = [_item(torch, "fp32", 40 + 3 * i, 21 + i % 5, inputs.layered_class_map_2d(40 + 3 * i, 21 + i % 5, 5),
+                   [i, 20 + 3 * i], 5, off) for i in range(26)]
+    counter = torch.zeros(1, dtype=torch.int64, device="cuda")
+    chert.traveltime_batch(items, off, counter)
+    torch.cuda.synchronize()
+    _check(torch, items, off)
 
 
 def test_batch_2d_other_stencil_and_mix_refused(torch_dev):
