@@ -104,6 +104,8 @@ struct FieldArgs {
     // before the launch; parts > 1 only under a cooperative launch
     int parts;
     unsigned* sync;
+    // 3D: the offsets are the standard reach-2 table (Stencil3) in its order
+    int std3;
 };
 
 template <typename T>
@@ -928,6 +930,163 @@ __device__ bool verify3d(const Smem<TW>& sm, const TW* __restrict__ gsel, const 
     return __syncthreads_or(changed);
 }
 
+// ---- the standard 3D stencil of reach 2, unrolled
+// The 98 lattice directions (ox, oy, oz) with max(|ox|, |oy|, |oz|) <= 2 and
+// gcd(|ox|, |oy|, |oz|) = 1 (the 26 neighbours and 72 secondary nodes), in
+// the order of the callers' offset arrays: oz, then oy, then ox ascending.
+// When a launch's offsets are exactly this table and the class-pair weight
+// table is in shared memory, the sweeps and the verification unroll the
+// stencil at compile time: a pull's stage index is the thread's base plus a
+// constant and its weight index a constant plus the class pair, where the
+// general form loads four list entries and recomputes both per pull.  Same
+// pulls, same comparisons: the fields and parents are those of the general
+// form, bit for bit.
+struct Stencil3 {
+    static constexpr int N = 98;
+    int x[N], y[N], z[N];
+    constexpr Stencil3() : x(), y(), z() {
+        int n = 0;
+        for (int zz = -2; zz <= 2; ++zz)
+            for (int yy = -2; yy <= 2; ++yy)
+                for (int xx = -2; xx <= 2; ++xx)
+                    if ((xx || yy || zz) &&
+                        fast::cgcd(fast::cgcd(fast::cabs(xx), fast::cabs(yy)), fast::cabs(zz)) == 1 && n < N) {
+                        x[n] = xx; y[n] = yy; z[n] = zz; ++n;
+                    }
+    }
+};
+constexpr int stencil3_count() {
+    int n = 0;
+    for (int zz = -2; zz <= 2; ++zz)
+        for (int yy = -2; yy <= 2; ++yy)
+            for (int xx = -2; xx <= 2; ++xx)
+                n += (xx || yy || zz) && fast::cgcd(fast::cgcd(fast::cabs(xx), fast::cabs(yy)), fast::cabs(zz)) == 1;
+    return n;
+}
+static_assert(stencil3_count() == Stencil3::N, "the reach-2 3D stencil has 98 directions");
+template <int D>
+struct Table3 {
+    static constexpr Stencil3 v{};
+};
+// Pulls between compiler fences in the unrolled loops (register pressure:
+// without fences every stage load of a sweep is hoisted ahead of the first
+// pull, and the kernel needs 128 registers, one CTA per SM).
+constexpr int kFence3 = 6;
+
+// sweep3d over the unrolled stencil: sweep along AXIS (0: x, 1: y, 2: z
+// planes) in direction DIR; halo H = 2; weights from the class-pair table
+// W[o][k_i][k_j].
+template <typename TW, typename TA, int TU, int TV, int AXIS, int DIR>
+__device__ bool sweep3d_std(const Smem<TW>& sm, TA* tau, const int32_t* __restrict__ cls, int nx, int ny, int nz,
+                            int nk, TA* st, int* sk, Part3& part) {
+    constexpr int H = 2, SU = TU + 2 * H, SV = TV + 2 * H, per = SU * SV;
+    const Stage3 g{H, SU, SV};
+    const int nu = AXIS == 0 ? ny : nx;
+    const int nv = AXIS == 2 ? ny : nz;
+    const int np = AXIS == 2 ? nz : AXIS == 1 ? ny : nx;
+    const int ntu = (nu + TU - 1) / TU;
+    const int nk2 = nk * nk;
+    bool changed = false;
+    for (int step = 0; step < np && !part.failed; ++step) {
+        const int p = DIR > 0 ? step : np - 1 - step;
+        for (int tv0 = 0; tv0 < nv; tv0 += TV) {
+            for (int tu0 = 0; tu0 < nu; tu0 += TU) {
+                if (((tv0 / TV) * ntu + tu0 / TU) % part.parts != part.part) continue;
+                // planes p - DIR*1 .. p - DIR*H at stage slots 0 .. H-1
+                stage_planes(st, sk, tau, cls, nk, AXIS, nu, nv, np, p - DIR, -DIR, H, tu0, tv0, g, nx, ny);
+                __syncthreads();
+                const int u = tu0 + (int)(threadIdx.x % TU), v = tv0 + (int)(threadIdx.x / TU);
+                if (threadIdx.x < TU * TV && u < nu && v < nv) {
+                    const long long j = node3(AXIS, u, v, p, nx, ny);
+                    const int kj = clamp_class(cls[j], nk);
+                    const TA cur = ld_tau(tau + j);
+                    TA best = cur;
+                    const int base = (v - tv0 + H) * SU + (u - tu0 + H);
+                    const TW* Wj = sm.W + kj;
+                    fast::static_for<Stencil3::N>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        constexpr int ox = Table3<0>::v.x[q], oy = Table3<0>::v.y[q], oz = Table3<0>::v.z[q];
+                        constexpr int oa = AXIS == 2 ? oz : AXIS == 1 ? oy : ox;
+                        if constexpr (oa * DIR > 0) {
+                            constexpr int ou = AXIS == 0 ? oy : ox;
+                            constexpr int ov = AXIS == 2 ? oy : oz;
+                            constexpr int d = (oa * DIR - 1) * per - ov * SU - ou;
+                            const TA ti = st[base + d];
+                            if (ti < best) best = fmin(best, ti + Wj[q * nk2 + sk[base + d] * nk]);
+                            // a compiler fence every kFence3 entries keeps the
+                            // loads of a few pulls in flight, not of all of them
+                            if constexpr (q % kFence3 == kFence3 - 1) asm volatile("" ::: "memory");
+                        }
+                    });
+                    if (best < cur) {
+                        tau[j] = best;
+                        changed = true;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        part_barrier(part);                     // the plane is complete in every part
+    }
+    return __syncthreads_or(changed);
+}
+
+// verify3d over the unrolled stencil (in-neighbours in offset order, the
+// parent rule's tie break on the smaller node index as in verify3d).
+template <typename TW, typename TA, int TU, int TV>
+__device__ bool verify3d_std(const Smem<TW>& sm, TA* tau, const int32_t* __restrict__ cls, int nx, int ny, int nz,
+                             int nk, int64_t src, int32_t* par, TA* st, int* sk, Part3& part) {
+    constexpr int H = 2, SU = TU + 2 * H, SV = TV + 2 * H, per = SU * SV;
+    const Stage3 g{H, SU, SV};
+    const int ntx = (nx + TU - 1) / TU;
+    const int nk2 = nk * nk;
+    bool changed = false;
+    for (int z = 0; z < nz && !part.failed; ++z) {
+        for (int ty0 = 0; ty0 < ny; ty0 += TV) {
+            for (int tx0 = 0; tx0 < nx; tx0 += TU) {
+                if (((ty0 / TV) * ntx + tx0 / TU) % part.parts != part.part) continue;
+                // planes z-H .. z+H at stage slots 0 .. 2H
+                stage_planes(st, sk, tau, cls, nk, 2, nx, ny, nz, z - H, 1, 2 * H + 1, tx0, ty0, g, nx, ny);
+                __syncthreads();
+                const int x = tx0 + (int)(threadIdx.x % TU), y = ty0 + (int)(threadIdx.x / TU);
+                if (threadIdx.x < TU * TV && x < nx && y < ny) {
+                    const long long j = node3(2, x, y, z, nx, ny);
+                    const int kj = clamp_class(cls[j], nk);
+                    const TA cur = ld_tau(tau + j);
+                    TA best = TA(INFINITY);
+                    long long bi = -1;
+                    const int base = H * per + (y - ty0 + H) * SU + (x - tx0 + H);
+                    const TW* Wj = sm.W + kj;
+                    fast::static_for<Stencil3::N>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        constexpr int ox = Table3<0>::v.x[q], oy = Table3<0>::v.y[q], oz = Table3<0>::v.z[q];
+                        constexpr int d = -oz * per - oy * SU - ox;
+                        const int xi = x - ox, yi = y - oy, zi = z - oz;
+                        if (xi >= 0 && xi < nx && yi >= 0 && yi < ny && zi >= 0 && zi < nz) {
+                            const TA ti = st[base + d];
+                            if (!(ti > best)) {
+                                const TA c = ti + Wj[q * nk2 + sk[base + d] * nk];
+                                const long long i = node3(2, xi, yi, zi, nx, ny);
+                                if (c < best || (c == best && i < bi)) { best = c; bi = i; }
+                            }
+                        }
+                        if constexpr (q % kFence3 == kFence3 - 1) asm volatile("" ::: "memory");
+                    });
+                    if (best < cur) {
+                        tau[j] = best;
+                        changed = true;
+                    } else if (par) {
+                        par[j] = (j == src) ? static_cast<int32_t>(src) : (!(cur < TA(INFINITY)) ? -1 : (int32_t)bi);
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        part_barrier(part);
+    }
+    return __syncthreads_or(changed);
+}
+
 // Shared memory of relax3d_kernel after the weight table: L [n_off], six
 // per-sweep lists of (offset, in-plane u, in-plane v, lag) as shorts, counts,
 // then the stage (tau, then class) for 2H+1 planes.
@@ -1011,13 +1170,26 @@ __device__ void relax3d_field(const FieldArgs& a, const Offsets& off, int H, int
     part_barrier(part);
 
     int used = -1;
+    const bool unrolled = WMODE == 1 && a.std3 && H == 2;
     for (int cycle = 0; cycle < a.max_cycles && !part.failed; ++cycle) {
-        for (int l = 0; l < 6; ++l)
-            sweep3d<T, TA, WMODE, TU, TV>(sm, sel, off, lists + (4 * l) * off.n, lists + (4 * l + 1) * off.n,
-                              lists + (4 * l + 2) * off.n, lists + (4 * l + 3) * off.n, sm.counts[l], ax[l], dr[l],
-                              tau, a.cls, a.nx, a.ny, a.nz, nk, comp, st, sk, g, part);
-        bool changed = verify3d<T, TA, WMODE, TU, TV>(sm, sel, off, tau, a.cls, a.nx, a.ny, a.nz, nk, comp, src, par, st,
-                                              sk, g, part);
+        bool changed;
+        if (WMODE == 1 && unrolled) {
+            // the six sweeps in the general form's order: (z,+) (y,+) (x,+) (x,-) (y,-) (z,-)
+            sweep3d_std<T, TA, TU, TV, 2, 1>(sm, tau, a.cls, a.nx, a.ny, a.nz, nk, st, sk, part);
+            sweep3d_std<T, TA, TU, TV, 1, 1>(sm, tau, a.cls, a.nx, a.ny, a.nz, nk, st, sk, part);
+            sweep3d_std<T, TA, TU, TV, 0, 1>(sm, tau, a.cls, a.nx, a.ny, a.nz, nk, st, sk, part);
+            sweep3d_std<T, TA, TU, TV, 0, -1>(sm, tau, a.cls, a.nx, a.ny, a.nz, nk, st, sk, part);
+            sweep3d_std<T, TA, TU, TV, 1, -1>(sm, tau, a.cls, a.nx, a.ny, a.nz, nk, st, sk, part);
+            sweep3d_std<T, TA, TU, TV, 2, -1>(sm, tau, a.cls, a.nx, a.ny, a.nz, nk, st, sk, part);
+            changed = verify3d_std<T, TA, TU, TV>(sm, tau, a.cls, a.nx, a.ny, a.nz, nk, src, par, st, sk, part);
+        } else {
+            for (int l = 0; l < 6; ++l)
+                sweep3d<T, TA, WMODE, TU, TV>(sm, sel, off, lists + (4 * l) * off.n, lists + (4 * l + 1) * off.n,
+                                  lists + (4 * l + 2) * off.n, lists + (4 * l + 3) * off.n, sm.counts[l], ax[l],
+                                  dr[l], tau, a.cls, a.nx, a.ny, a.nz, nk, comp, st, sk, g, part);
+            changed = verify3d<T, TA, WMODE, TU, TV>(sm, sel, off, tau, a.cls, a.nx, a.ny, a.nz, nk, comp, src, par,
+                                                     st, sk, g, part);
+        }
         if (part.parts > 1) {
             // OR of the parts' verdicts in flag word 1 + (cycle & 1); the other
             // flag word, last read a cycle ago, is cleared for the next cycle
@@ -1045,7 +1217,7 @@ __device__ void relax3d_field(const FieldArgs& a, const Offsets& off, int H, int
 }
 
 template <typename T, typename TA, int WMODE, int TU, int TV>
-__global__ void __launch_bounds__(512) relax3d_kernel(FieldArgs a, Offsets off, int H) {
+__global__ void __launch_bounds__(512, 2) relax3d_kernel(FieldArgs a, Offsets off, int H) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     relax3d_field<T, TA, WMODE, TU, TV>(a, off, H, (int)(blockIdx.x / a.parts), (int)(blockIdx.x % a.parts),
                                         smem_raw);
@@ -1495,6 +1667,15 @@ static Smem3 smem3(int n_classes, int n_off, int H, int precision, int tile, int
     return {mode, mode == 1 ? t3 : mode == 0 ? r3 : base3};
 }
 
+// Whether the offsets are the reach-2 3D table of the unrolled sweeps, in its order.
+static bool is_standard3(const Offsets& off) {
+    constexpr Stencil3 t{};
+    if (off.n != Stencil3::N) return false;
+    for (int i = 0; i < Stencil3::N; ++i)
+        if (off.x[i] != t.x[i] || off.y[i] != t.y[i] || off.z[i] != t.z[i]) return false;
+    return true;
+}
+
 // launch_relax3d for the process-wide tile shape and a weight mode
 template <typename T, typename TA>
 static int launch_relax3d_any(const FieldArgs& a, const Offsets& off, int H, const Smem3& m, int blocks,
@@ -1764,6 +1945,7 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
     a.Vsel = Vsel; a.Asel = Asel; a.status = reinterpret_cast<int*>(w + ws.status);
     a.parts = 1;
     a.sync = reinterpret_cast<unsigned*>(w + ws.sync);
+    a.std3 = 0;
     int dev = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -1773,6 +1955,7 @@ static int enqueue_traveltime(const char* who, const chert_cache_arrays* cache, 
         for (int i = 0; i < n_off; i++)
             H = std::max(H, std::max(abs((int)off.y[i]), std::max(abs((int)off.x[i]), abs((int)off.z[i]))));
         CHERT_REQUIRE(H <= 8, "%s: 3D offsets reach %d nodes (at most 8)", who, H);
+        a.std3 = H == 2 && is_standard3(off) ? 1 : 0;
         const Smem3 m3 = smem3(n_classes, n_off, H, precision, g_relax3d_tile.load(), smem_max);
         if (prep) {                                    // a batched launch runs the relaxation
             prep->a = a;

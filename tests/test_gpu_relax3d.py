@@ -354,3 +354,34 @@ def test_batch_rejects_2d_lattices(torch_dev):
     with pytest.raises(chert.ChertError) as e:
         chert.traveltime_batch([it], inputs.stencil_3d(2), torch.zeros(1, dtype=torch.int64, device="cuda"))
     assert e.value.code == chert.EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_acc64"])
+def test_unrolled_stencil_equals_general_form(torch_dev, precision):
+    """The reach-2 stencil in its standard order runs the unrolled sweeps
+    (class-pair table); the same 98 offsets in reverse order run the general
+    form.  The fixed point and the parent rule (smallest node index among
+    equal candidates) do not depend on the order of the offsets, so fields
+    and parents must be identical, bit for bit, on a ragged lattice of
+    several tiles per plane."""
+    torch = torch_dev
+    shape = (45, 23, 19)
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    cls = np.minimum((np.arange(n) // (nx * ny)) * 5 // nz, 4).astype(np.int32)
+    cnp, n_az, n_pol = synthetic_cache3d(5, seed=4)
+    nm, nk, _ = cnp["V"].shape
+    cache_prec = chert.FP64 if precision == "fp64" else chert.FP32
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    cache = chert.Cache(cache_to_torch(cnp, dt, "cuda"), list(range(nm)), nk, 0, cache_prec, n_az, n_pol)
+    d_cls = torch.as_tensor(cls, device="cuda")
+    sources = [0, 21 + nx * (11 + ny * 9), n - 1]
+    off = inputs.stencil_3d(2)
+    res = []
+    for o in (off, np.ascontiguousarray(off[::-1])):
+        r = chert.traveltime(cache, nx, nz, 10.0, d_cls, o, sources, max_cycles=64, ny=ny, precision=precision)
+        torch.cuda.synchronize()
+        res.append(r)
+    for a, b in zip(*res):
+        assert torch.equal(a, b)
+    assert np.all(np.isfinite(res[0][0].cpu().numpy()))
