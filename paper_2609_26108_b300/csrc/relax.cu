@@ -973,6 +973,15 @@ struct Table3 {
 // pull, and the kernel needs 128 registers, one CTA per SM).
 constexpr int kFence3 = 6;
 
+// Float-float traveltimes (float weights): a candidate ti + w whose float sum
+// fl(ti.hi + w) is above best.hi * (1 + 2^-21) exceeds best exactly (the
+// dropped ti.lo and the two roundings move it by under 3 * 2^-24 relative;
+// ti, w >= 0), so the float-float addition and comparison are skipped for it.
+// The skipped candidates would lose anyway, ties included (at best = 0 the
+// test is fl(ti.hi + w) > 0, which no tie at 0 passes): same results, fewer
+// instructions.
+__device__ __forceinline__ float ff_skip_above(const xf::ff& best) { return best.hi * (1.0f + 0x1p-21f); }
+
 // sweep3d over the unrolled stencil: sweep along AXIS (0: x, 1: y, 2: z
 // planes) in direction DIR; halo H = 2; weights from the class-pair table
 // W[o][k_i][k_j].
@@ -980,6 +989,7 @@ template <typename TW, typename TA, int TU, int TV, int AXIS, int DIR>
 __device__ bool sweep3d_std(const Smem<TW>& sm, TA* tau, const int32_t* __restrict__ cls, int nx, int ny, int nz,
                             int nk, TA* st, int* sk, Part3& part) {
     constexpr int H = 2, SU = TU + 2 * H, SV = TV + 2 * H, per = SU * SV;
+    constexpr bool kFF = std::is_same<TA, xf::ff>::value;
     const Stage3 g{H, SU, SV};
     const int nu = AXIS == 0 ? ny : nx;
     const int nv = AXIS == 2 ? ny : nz;
@@ -1003,6 +1013,8 @@ __device__ bool sweep3d_std(const Smem<TW>& sm, TA* tau, const int32_t* __restri
                     TA best = cur;
                     const int base = (v - tv0 + H) * SU + (u - tu0 + H);
                     const TW* Wj = sm.W + kj;
+                    [[maybe_unused]] float skip = 0.0f;
+                    if constexpr (kFF) skip = ff_skip_above(best);
                     fast::static_for<Stencil3::N>([&](auto qc) {
                         constexpr int q = decltype(qc)::value;
                         constexpr int ox = Table3<0>::v.x[q], oy = Table3<0>::v.y[q], oz = Table3<0>::v.z[q];
@@ -1012,7 +1024,17 @@ __device__ bool sweep3d_std(const Smem<TW>& sm, TA* tau, const int32_t* __restri
                             constexpr int ov = AXIS == 2 ? oy : oz;
                             constexpr int d = (oa * DIR - 1) * per - ov * SU - ou;
                             const TA ti = st[base + d];
-                            if (ti < best) best = fmin(best, ti + Wj[q * nk2 + sk[base + d] * nk]);
+                            if (ti < best) {
+                                const TW w = Wj[q * nk2 + sk[base + d] * nk];
+                                if constexpr (kFF) {
+                                    if (ti.hi + w <= skip) {
+                                        best = fmin(best, ti + w);
+                                        skip = ff_skip_above(best);
+                                    }
+                                } else {
+                                    best = fmin(best, ti + w);
+                                }
+                            }
                             // a compiler fence every kFence3 entries keeps the
                             // loads of a few pulls in flight, not of all of them
                             if constexpr (q % kFence3 == kFence3 - 1) asm volatile("" ::: "memory");
@@ -1037,6 +1059,7 @@ template <typename TW, typename TA, int TU, int TV>
 __device__ bool verify3d_std(const Smem<TW>& sm, TA* tau, const int32_t* __restrict__ cls, int nx, int ny, int nz,
                              int nk, int64_t src, int32_t* par, TA* st, int* sk, Part3& part) {
     constexpr int H = 2, SU = TU + 2 * H, SV = TV + 2 * H, per = SU * SV;
+    constexpr bool kFF = std::is_same<TA, xf::ff>::value;
     const Stage3 g{H, SU, SV};
     const int ntx = (nx + TU - 1) / TU;
     const int nk2 = nk * nk;
@@ -1057,6 +1080,7 @@ __device__ bool verify3d_std(const Smem<TW>& sm, TA* tau, const int32_t* __restr
                     long long bi = -1;
                     const int base = H * per + (y - ty0 + H) * SU + (x - tx0 + H);
                     const TW* Wj = sm.W + kj;
+                    [[maybe_unused]] float skip = INFINITY;
                     fast::static_for<Stencil3::N>([&](auto qc) {
                         constexpr int q = decltype(qc)::value;
                         constexpr int ox = Table3<0>::v.x[q], oy = Table3<0>::v.y[q], oz = Table3<0>::v.z[q];
@@ -1065,9 +1089,18 @@ __device__ bool verify3d_std(const Smem<TW>& sm, TA* tau, const int32_t* __restr
                         if (xi >= 0 && xi < nx && yi >= 0 && yi < ny && zi >= 0 && zi < nz) {
                             const TA ti = st[base + d];
                             if (!(ti > best)) {
-                                const TA c = ti + Wj[q * nk2 + sk[base + d] * nk];
-                                const long long i = node3(2, xi, yi, zi, nx, ny);
-                                if (c < best || (c == best && i < bi)) { best = c; bi = i; }
+                                const TW w = Wj[q * nk2 + sk[base + d] * nk];
+                                bool take = true;
+                                if constexpr (kFF) take = ti.hi + w <= skip;
+                                if (take) {
+                                    const TA c = ti + w;
+                                    const long long i = node3(2, xi, yi, zi, nx, ny);
+                                    if (c < best || (c == best && i < bi)) {
+                                        best = c;
+                                        bi = i;
+                                        if constexpr (kFF) skip = ff_skip_above(best);
+                                    }
+                                }
                             }
                         }
                         if constexpr (q % kFence3 == kFence3 - 1) asm volatile("" ::: "memory");

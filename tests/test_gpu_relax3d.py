@@ -356,20 +356,24 @@ def test_batch_rejects_2d_lattices(torch_dev):
     assert e.value.code == chert.EINVAL
 
 
+@pytest.mark.parametrize("elastic", [False, True])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_acc64"])
-def test_unrolled_stencil_equals_general_form(torch_dev, precision):
+def test_unrolled_stencil_equals_general_form(torch_dev, precision, elastic):
     """The reach-2 stencil in its standard order runs the unrolled sweeps
     (class-pair table); the same 98 offsets in reverse order run the general
     form.  The fixed point and the parent rule (smallest node index among
     equal candidates) do not depend on the order of the offsets, so fields
     and parents must be identical, bit for bit, on a ragged lattice of
-    several tiles per plane."""
+    several tiles per plane.  elastic: A = 0 everywhere, so the attenuation
+    field is 0 and every parent is decided by the tie rule alone."""
     torch = torch_dev
     shape = (45, 23, 19)
     nx, ny, nz = shape
     n = nx * ny * nz
     cls = np.minimum((np.arange(n) // (nx * ny)) * 5 // nz, 4).astype(np.int32)
     cnp, n_az, n_pol = synthetic_cache3d(5, seed=4)
+    if elastic:
+        cnp["A"] = np.zeros_like(cnp["A"])
     nm, nk, _ = cnp["V"].shape
     cache_prec = chert.FP64 if precision == "fp64" else chert.FP32
     dt = torch.float64 if precision == "fp64" else torch.float32
@@ -385,3 +389,5 @@ def test_unrolled_stencil_equals_general_form(torch_dev, precision):
     for a, b in zip(*res):
         assert torch.equal(a, b)
     assert np.all(np.isfinite(res[0][0].cpu().numpy()))
+    if elastic:
+        assert not res[0][1].any()
