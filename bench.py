@@ -127,6 +127,33 @@ def issue_roofline(alg_pulls, launch_s, sm_max_mhz):
             "peak_source": "derived: 148 SMs x 4 schedulers x max SM clock x 32 lanes / instructions per pull"}
 
 
+def host_link(nbytes, reps=3):
+    """Device-to-host copy rate of this machine's host link: one copy of nbytes
+    from device memory into page-locked host memory, timed with CUDA events
+    on its stream (median of reps), and the time the step's device-to-host
+    bytes take at that rate: the floor of an end-to-end step whose copies
+    overlap its kernels completely."""
+    import torch
+    n = max(int(nbytes), 1)
+    src = torch.empty(n, dtype=torch.uint8, device="cuda")
+    src.fill_(1)
+    dst = torch.empty(n, dtype=torch.uint8).pin_memory()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    ms = []
+    for _ in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            e0.record(s)
+            dst.copy_(src, non_blocking=True)
+            e1.record(s)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms[1:])
+    return {"d2h_gbs": n / t / 1e6, "d2h_bytes": n, "d2h_ms_at_link_rate": t,
+            "note": "one page-locked copy of the step's device-to-host bytes, CUDA events"}
+
+
 def relax_sources_sha():
     """Digest of the 2D relaxation's sources, to tie a DRAM capture to the
     kernel version it measured."""
@@ -1112,6 +1139,9 @@ def run_chert(args):
     e2e_value, _ = replicas.job_throughput(sum(e2e_times), nf * args.steps, device="cuda")
     e2e_h2d, e2e_d2h = ht.h2d_bytes(h_classes, h_cls, h_src), ht.d2h_bytes()
     del ht
+    e2e_link = host_link(e2e_d2h)
+    e2e_link["e2e_ms_per_step"] = 1e3 * sum(e2e_times) / args.steps
+    e2e_link["device_ms_per_step"] = total_ms / args.steps
 
     # roofline of the dominant kernel (relaxation): algorithmic work = one
     # relaxation (add + min: 2 FP32 ops) per directed edge per field component
@@ -1153,7 +1183,8 @@ def run_chert(args):
            "roofline": roofline, "roofline_cache_build": roof_cache, "clocks": clocks,
            "e2e": {"value": e2e_value, "unit": "fields/s", "h2d_bytes_per_step": e2e_h2d,
                    "d2h_bytes_per_step": e2e_d2h, "call": "chert_trace_host (one C-ABI call on page-locked host "
-                   "buffers: inputs in, cache, traveltimes with parents, raypaths, fields and raypaths out)"},
+                   "buffers: inputs in, cache, traveltimes with parents, raypaths, fields and raypaths out)",
+                   "link": e2e_link},
            "gpu_launches": tr.launches_per_run * args.steps}
     if world == 1 and args.no_cache:
         out["no_cache_ablation"] = section_no_cache(tr, model, off, classes, value)
