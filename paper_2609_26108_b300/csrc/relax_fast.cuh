@@ -428,6 +428,17 @@ __device__ void sweep_rows1(const Ctx<T>& c, T* __restrict__ tau, int pass, int 
         for (int d = -R; d <= R; ++d) wo[d + R] = c.rowoff[zj - d] + kj * N;
     };
     if constexpr (AXIS == 1) set_wo(u < len ? u : 0);
+    // Column sweeps: the thread's depth, and so each of its pulls' weights,
+    // is fixed for the whole sweep; they are read once into registers (the
+    // entries of the other sweep direction are never read).
+    [[maybe_unused]] T wreg[N];
+    if constexpr (AXIS == 1) {
+        static_for<N>([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            constexpr int ox = Table<R>::v.x[q], oz = Table<R>::v.z[q];
+            if constexpr (ox * DIR > 0) wreg[q] = c.W[wo[oz + R] + q];
+        });
+    }
     auto gidx = [&](int line) {
         return AXIS == 0 ? (size_t)u + (size_t)nx * line : (size_t)line + (size_t)nx * u;
     };
@@ -471,7 +482,10 @@ __device__ void sweep_rows1(const Ctx<T>& c, T* __restrict__ tau, int pass, int 
                     if constexpr (oa * DIR > 0) {
                         constexpr int lag = oa * DIR;
                         constexpr int oz = Table<R>::v.z[q];
-                        best = fmin_(best, ring[po[lag] - ol] + c.W[wo[oz + R] + q]);
+                        if constexpr (AXIS == 1)
+                            best = fmin_(best, ring[po[lag] - ol] + wreg[q]);
+                        else
+                            best = fmin_(best, ring[po[lag] - ol] + c.W[wo[oz + R] + q]);
                     }
                 });
             }
@@ -892,7 +906,7 @@ __device__ __forceinline__ void relax_fast_field(const Args& a, int field, int c
 }
 
 template <typename T, int R, int PPT, bool PN>
-__global__ void __launch_bounds__(512) relax_fast_kernel(Args a) {
+__global__ void __launch_bounds__(512, PPT == 1 && sizeof(T) == 4 ? 2 : 1) relax_fast_kernel(Args a) {
     // Attenuation fields (several sweep cycles) launch first and propagation
     // fields (mostly one cycle) fill the tail of the grid.
     const int n_fields = gridDim.x >> 1;
